@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the two-scale micro-solve hot path on GB300.
+
+Workload (default): 64x64 macro Q1 mesh -> 4225 micro problems, each a 32x32
+Q1 mesh on the reference cell (1089 DoFs, 4.60M micro DoFs in total), bump
+deformation a ~ U[0, 0.2] (seeded), D = I, kappa = 1, u0 = 1, v0 = 0,
+dt = 0.005, relative tolerance 1e-8 (micro solves, FP64 residual),
+coupling tolerance 1e-10.  One benchmark step = one implicit Euler step of
+the coupled system: every coupling iteration solves all micro problems
+(FP32 CG + FP64 refinement) and the macro problem.
+
+Metric: micro DOF-CG-iterations per second (sum over micro problems of
+DoFs x inner CG iterations, divided by the time of the timed steps), with the
+two-scale steps/s beside it.  Under torchrun every rank advances its own
+independent replica of the workload (weak scaling, no collective on the data
+path); the value is the sum over ranks divided by the slowest rank's time.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# algorithmic bytes of the micro solve (streaming accounting, stencil stored):
+# an FP32 PCG iteration moves 11 vector words + 5 stencil words per DoF,
+# an FP64 iteration the same in 8-byte words; an FP64 refinement residual
+# reads v, b and 5 stencil words and writes r (8 words of 8 bytes).
+BYTES_PER_DOF_ITER = {"mixed": 64, "fp64": 128}
+BYTES_PER_DOF_SWEEP = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, e2e, cpu baseline")
+    return ap.parse_args()
+
+
+def workload(name, seed=0):
+    import workloads as W
+    return W.c2(seed=seed) if name == "c2" else W.c3(seed=seed)
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def make_problem(T, w, precision, stream, **opts):
+    prec = T.TSF_MIXED if precision == "mixed" else T.TSF_FP64
+    P = T.TwoScale(w.Nm, w.NM, bc=w.bc, precision=prec, stream=stream, cg_tol=w.tol, coupling_tol=w.coupling_tol,
+                   **opts)
+    P.set_physics(w.D, w.kappa, w.Du)
+    P.set_deformation(w.family, w.params)
+    P.set_state(w.u0, None)
+    return P
+
+
+def timed_steps(torch, P, w, steps, barrier):
+    """device time (ms) of `steps` graph-launched steps on the current stream"""
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    P.step(w.dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2103_17040_gb300 as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    T.load_library()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allmax(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def allsum(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # the library enqueues on this (non-default) torch stream, so torch's CUDA
+    # events on it bracket exactly the library's work
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    w = workload(args.workload, seed=rank)
+    nm, nM = w.nm, w.nM
+    K, Wm = args.steps, args.warmup
+
+    # ---- main timed region (graph-launched steps, inputs resident) ----
+    P = make_problem(T, w, args.precision, stream)
+    P.step(w.dt, Wm)
+    P.synchronize()
+    P.reset_stats()
+    clk = Clocks(local)
+    clk.start()
+    ms = timed_steps(torch, P, w, K, barrier)
+    clocks = clk.stop()
+    P.synchronize()
+    st = P.stats()
+    ms_max = allmax(ms)
+    dof_iters = allsum(float(st["dof_cg_iters"]))
+    value = dof_iters / (ms_max / 1e3)
+    steps_per_s = world * K / (ms_max / 1e3)
+    launches = 2 * K + 2 * st["coupling_iters_total"]
+
+    line = {
+        "metric": "micro DOF-CG-iters/s",
+        "value": value,
+        "unit": "DOF-iter/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": ms_max / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: macro {w.NM}x{w.NM} Q1 ({nM} micro problems), micro "
+                               f"{w.Nm}x{w.Nm} Q1 ({nm} DoFs each, {nM * nm} micro DoFs), "
+                               f"dt={w.dt}, tol={w.tol}, {args.precision}",
+                   "macro_mesh": w.NM, "micro_mesh": w.Nm, "micro_dofs": nM * nm, "dt": w.dt, "tol": w.tol,
+                   "coupling_tol": w.coupling_tol, "precision": args.precision, "replicas": world,
+                   "l2": "working set > L2 (stencils + vectors ~0.6 GB), no flush"},
+        "steps_per_s": steps_per_s,
+        "coupling_iters_per_step": st["coupling_iters_total"] / K,
+        "inner_iters_per_solve": st["inner_iters"] / max(st["micro_solves"], 1),
+        "refine_sweeps_per_solve": st["refine_sweeps"] / max(st["micro_solves"], 1),
+        "macro_iters_per_solve": st["macro_iters"] / max(st["coupling_iters_total"], 1),
+        "tiling_nodes_per_thread": st["tiling"],
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+    # ---- per-kernel timing of the micro solve (plain launches, CUDA events) ----
+    opts = T.tsf_default_options()
+    opts.precision = T.TSF_MIXED if args.precision == "mixed" else T.TSF_FP64
+    opts.cg_tol, opts.coupling_tol = w.tol, w.coupling_tol
+    opts.use_graph, opts.profile = 0, 1
+    opts.tiling = {1: 0, 2: 1, 4: 2, 8: 3}[st["tiling"]]
+    opts.cuda_stream = stream.cuda_stream
+    T.tsf_set_options(P.ctx, opts)
+    P.reset_stats()
+    P.step(w.dt, min(K, 10))
+    P.synchronize()
+    sp = P.stats()
+    micro_ms = sp["micro_kernel_ms"] / max(sp["micro_launches"], 1)
+    bytes_launch = (BYTES_PER_DOF_ITER[args.precision] * sp["dof_cg_iters"] +
+                    (BYTES_PER_DOF_SWEEP * sp["refine_sweeps"] * nm if args.precision == "mixed" else 0)) \
+        / max(sp["micro_launches"], 1)
+    achieved = bytes_launch / (micro_ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    line["roofline"] = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": None, "kernel": "k_micro_solve", "bytes_per_launch": bytes_launch,
+        "avg_launch_ms": micro_ms, "launches_timed": sp["micro_launches"],
+        "macro_kernel_share": sp["macro_kernel_ms"] / max(sp["macro_kernel_ms"] + sp["micro_kernel_ms"], 1e-30),
+        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
+    }
+    P.close()
+
+    if not args.no_extras and rank == 0:
+        # ---- FP64 path at equal tolerance (comparison) ----
+        if args.precision == "mixed":
+            Q = make_problem(T, w, "fp64", stream)
+            Q.step(w.dt, 2)
+            Q.synchronize()
+            Q.reset_stats()
+            k64 = max(2, min(K, 10))
+            ms64 = timed_steps(torch, Q, w, k64, lambda: None)
+            s64 = Q.stats()
+            line["fp64_path"] = {"value": s64["dof_cg_iters"] / (ms64 / 1e3), "unit": "DOF-iter/s",
+                                 "ms_per_step": ms64 / k64, "steps": k64,
+                                 "speedup_mixed_vs_fp64_per_step": (ms64 / k64) / (ms_max / K)}
+            Q.close()
+        # ---- end to end through the public API with host buffers ----
+        line["e2e"] = run_e2e(torch, T, w, args, stream)
+        # ---- CPU baseline: the oracle on this host's cores + error of the GPU path ----
+        if world == 1:
+            line["cpu_baseline"], line["error_vs_oracle"] = run_cpu_baseline(T, w, args, stream)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(torch, T, w, args, stream):
+    """Each step: pinned host -> device state upload, one step, macro field and
+    micro averages back to pinned host memory."""
+    P = make_problem(T, w, args.precision, stream)
+    P.step(w.dt, 2)
+    P.synchronize()
+    u_h = torch.empty(w.nM, dtype=torch.float64).pin_memory()
+    v_h = torch.empty(w.nM * w.nm, dtype=torch.float64).pin_memory()
+    vbar_h = np.empty(w.nM)
+    u_out = np.empty(w.nM)
+    u_h.copy_(torch.from_numpy(P.u()))
+    v_h.copy_(torch.from_numpy(P.v().ravel()))
+    u_np, v_np = u_h.numpy(), v_h.numpy()
+    P.reset_stats()
+    k = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        P.set_state(u_np, v_np)
+        P.step(w.dt, 1)
+        P.u(u_out)
+        P.vbar(vbar_h)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    st = P.stats()
+    P.close()
+    return {"value": st["dof_cg_iters"] / dt, "unit": "DOF-iter/s", "steps": k, "ms_per_step": 1e3 * dt / k,
+            "h2d_bytes_per_step": 8 * (w.nM + w.nM * w.nm), "d2h_bytes_per_step": 8 * 2 * w.nM}
+
+
+def run_cpu_baseline(T, w, args, stream):
+    """The FP64 oracle on the host cores for a bounded sample of the same
+    workload: full-size steps from the initial state until the time budget is
+    spent; the GPU path is advanced by the same steps and compared."""
+    import oracle
+    R = oracle.Problem(w.Nm, w.NM, w.bc, w.family, w.params, D=w.D, kappa=w.kappa, Du=w.Du)
+    R.set_state(w.u0, None)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        R.step(w.dt, 1, cg_tol=w.tol, coupling_tol=w.coupling_tol, macro_tol=1e-12)
+        n += 1
+        if time.perf_counter() - t0 > args.cpu_seconds or n >= 50:
+            break
+    el = time.perf_counter() - t0
+    rs = R.stats()
+    cpu = {"value": rs["inner_iters"] * w.nm / el, "unit": "DOF-iter/s", "cores": oracle.num_threads(),
+           "kind": "oracle", "sample": f"{n} full-size steps of the workload from u0=1, v0=0 (FP64, CSR Jacobi-PCG, "
+                                       f"OpenMP over micro problems), {el:.1f} s",
+           "steps_per_s": n / el}
+    P = make_problem(T, w, args.precision, stream)
+    P.step(w.dt, n)
+    P.synchronize()
+    u, v = P.u(), P.v()
+    P.close()
+    err = {"steps": n, "rel_l2_u": float(np.linalg.norm(u - R.u) / np.linalg.norm(R.u)),
+           "rel_l2_v": float(np.linalg.norm(v - R.v) / np.linalg.norm(R.v)),
+           "note": "both sides at the benchmark tolerances (relative residual 1e-8, coupling 1e-10)"}
+    return cpu, err
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step one full-size
+    implicit Euler step of a 16x16-macro sample of the workload (same micro
+    problems, fewer of them)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    full = workload(args.workload)
+    w = W.c2(NM=16, Nm=full.Nm) if args.workload == "c2" else W.c3(NM=16, Nm=full.Nm)
+    R = oracle.Problem(w.Nm, w.NM, w.bc, w.family, w.params, D=w.D, kappa=w.kappa, Du=w.Du)
+    R.set_state(w.u0, None)
+    R.step(w.dt, args.warmup, cg_tol=w.tol, coupling_tol=w.coupling_tol, macro_tol=1e-12)
+    R.reset_stats()
+    t0 = time.perf_counter()
+    R.step(w.dt, args.steps, cg_tol=w.tol, coupling_tol=w.coupling_tol, macro_tol=1e-12)
+    el = time.perf_counter() - t0
+    rs = R.stats()
+    value = rs["inner_iters"] * w.nm / el
+    sample = (f"{args.steps} steps of a {w.NM}x{w.NM}-macro sample ({w.nM} micro problems of {w.nm} DoFs) "
+              f"of the {args.workload} workload")
+    line = {"metric": "micro DOF-CG-iters/s", "value": value, "unit": "DOF-iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{args.workload} (sample: macro {w.NM}x{w.NM}, micro {w.Nm}x{w.Nm})",
+                       "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "DOF-iter/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "DOF-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * tsfem.h -- C ABI of the GB300 two-scale finite element library.
+ *
+ * The library advances, one implicit Euler step at a time, the coupled
+ * macro/micro system of Lakkis, Muntean, Richardson and Venkataraman
+ * ("Parallel two-scale finite element implementation of a system with varying
+ * microstructure"): a macroscopic field u on Omega = [0,1]^2 and one
+ * microscopic field v_i per macroscopic node x_i (Sec. 3.3: one micro system
+ * per macro degree of freedom, located at its support point).  Every micro
+ * problem lives on the shared reference cell Z = [0,1]^2 and sees the
+ * geometry of its own cell Y_{x_i} = chi(x_i, Z) only through pulled-back
+ * coefficients (Sec. 3.1, Eqs. (13)-(16)):
+ *
+ *   J = det F,  C = J F^{-1} D F^{-T},  s = |cof(F) nu|,   F = D_yhat chi.
+ *
+ * One step solves (u-v part of the model system Eq. (5), with a time
+ * derivative added to both equations; discrete form Eq. (17)):
+ *
+ *   (M_i/dt + A_i + kappa R_i) v_i - kappa r_i u_i = M_i (v_i^n/dt + fv_i) + R_i g_i
+ *   (M_H/dt + Du K_H + kappa L Gam) u - kappa L rho(v) = M_H (u^n/dt + fu) - L G
+ *
+ * with Q1 elements on uniform square meshes, 2x2 Gauss quadrature, the Robin
+ * (inflow) edge yhat_1 = 1 of Z, homogeneous Neumann data on the other micro
+ * edges, r_i = R_i 1, |Gam_i| = 1^T r_i, L = diag(row sums of M_H),
+ * rho(v)_i = r_i^T v_i and G_i = r_i^T g_i.  The coupled step is solved by
+ * the partitioned fixed-point iteration of Sec. 3.3 (all micro problems with
+ * the current u, then the macro problem with the new micro fluxes) until the
+ * relative change of u is below a tolerance.
+ *
+ * Node numbering (both meshes): node (p, q) of an N x N cell mesh has index
+ * p + (N+1) q and sits at (p, q)/N.  Micro fields are stored instance-major:
+ * v[i * nm + j], nm = (Nm+1)^2.
+ *
+ * Conventions for every entry point:
+ *  - Pointers flagged "on_device" are CUDA device pointers of the current
+ *    device, otherwise host pointers.  The library copies what it reads and
+ *    never keeps a caller pointer after the call returns (except a workspace
+ *    bound with tsf_bind_workspace, which the caller keeps alive).
+ *  - All work is enqueued on the stream given in tsf_options.cuda_stream
+ *    (NULL = a stream the library creates).  Setters and tsf_step return
+ *    once the work is enqueued; getters synchronise that stream.
+ *  - Every function returns a tsf_status and never aborts the process; on an
+ *    error tsf_last_error() describes it.  Device-side outcomes of tsf_step
+ *    (a solve that did not converge, a NaN) are reported by
+ *    tsf_synchronize() and tsf_get_stats().
+ */
+#ifndef TSFEM_H
+#define TSFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsf_ctx tsf_ctx;
+
+typedef enum tsf_status {
+    TSF_OK = 0,
+    TSF_E_ARG = 1,           /* invalid argument (sizes, family, NULL pointer, ...) */
+    TSF_E_STATE = 2,         /* call out of order (e.g. step before meshes were set) */
+    TSF_E_BAD_JACOBIAN = 3,  /* det F <= 0 at a quadrature point (Eq. (3) requires det F > 0) */
+    TSF_E_NOT_CONVERGED = 4, /* a CG solve or the coupling iteration hit its iteration cap */
+    TSF_E_NAN = 5,           /* a non-finite value appeared in a solve */
+    TSF_E_CUDA = 6,          /* a CUDA runtime call failed */
+    TSF_E_OOM = 7,           /* device memory allocation failed or workspace too small */
+    TSF_E_BREAKDOWN = 8      /* p^T A p <= 0 in a CG solve (operator not SPD) */
+} tsf_status;
+
+/* arithmetic of the micro solves */
+enum {
+    TSF_FP64 = 0,  /* Jacobi-PCG in FP64 */
+    TSF_MIXED = 1  /* FP32 Jacobi-PCG inner solves, FP64 residual and iterative refinement */
+};
+
+/* deformation families chi(x_i, .) : Z -> Y_{x_i} (Sec. 2, Eqs. (2)-(3)) and their
+ * per-node parameters */
+enum {
+    TSF_FAMILY_IDENTITY = 0,    /* chi = yhat;                                     0 params */
+    TSF_FAMILY_BUMP = 1,        /* chi = yhat + a (sin pi y1 sin pi y2, 0);        1: a */
+    TSF_FAMILY_SHEAR_BUMP = 2,  /* chi = (y1 + s y2 + b sin pi y1 sin pi y2, y2);  2: s, b */
+    TSF_FAMILY_AFFINE = 3,      /* chi = A yhat + c;   6: A11, A12, A21, A22, c1, c2 */
+    TSF_FAMILY_AFFINE_BUMP = 4  /* chi = A yhat + b (sin pi y1 sin pi y2, 0); 5: A11, A12, A21, A22, b */
+};
+
+/* macroscopic boundary condition */
+enum { TSF_BC_NEUMANN = 0, TSF_BC_DIRICHLET = 1 };
+
+typedef struct tsf_options {
+    int precision;           /* TSF_FP64 or TSF_MIXED */
+    double cg_tol;           /* micro solves: stop when ||b - A v||_2 <= cg_tol ||b||_2 (FP64 residual) */
+    double inner_tol;        /* TSF_MIXED: relative tolerance of each FP32 inner solve */
+    double macro_tol;        /* macro solve: relative residual tolerance */
+    double coupling_tol;     /* stop the coupling iteration when ||u_new - u||_2 <= coupling_tol ||u_new||_2 */
+    int cg_maxit;            /* cap on CG iterations per micro solve (inner iterations summed over sweeps) */
+    int max_sweeps;          /* TSF_MIXED: cap on refinement sweeps per micro solve */
+    int macro_maxit;         /* cap on macro CG iterations */
+    int coupling_maxit;      /* cap on coupling iterations per step */
+    int tiling;              /* -1: library choice; >= 0 fixed micro-kernel variant (see tsf_stats.tiling) */
+    int use_graph;           /* 1: each step is one CUDA graph launch with a device-controlled
+                                coupling loop; 0: kernels launched one by one */
+    void *cuda_stream;       /* cudaStream_t to enqueue on, NULL = library-owned stream */
+    int profile;             /* 1 (with use_graph = 0): time every micro and macro kernel launch
+                                with CUDA events on the stream; totals in tsf_stats */
+} tsf_options;
+
+typedef struct tsf_stats {
+    int64_t inner_iters;        /* CG iterations summed over micro instances, solves and steps */
+    int64_t dof_cg_iters;       /* inner_iters * nm: micro DOF-CG-iterations */
+    int64_t refine_sweeps;      /* FP64 residual evaluations of the micro problems (summed over instances) */
+    int64_t micro_solves;       /* micro solves (instances x coupling iterations) */
+    int64_t macro_iters;        /* macro CG iterations */
+    int coupling_iters_last;    /* coupling iterations of the last step */
+    int coupling_iters_total;
+    int max_inner_iters;        /* largest inner-iteration count of a single micro solve */
+    int steps;                  /* steps taken since the last tsf_reset_stats */
+    int status;                 /* first device-side error (tsf_status), TSF_OK if none */
+    int tiling;                 /* micro-kernel variant in use */
+    double coupling_change;     /* final ||du|| / ||u|| of the last step */
+    int64_t micro_launches;     /* profiled micro-solve kernel launches */
+    int64_t macro_launches;     /* profiled macro-solve kernel launches */
+    double micro_kernel_ms;     /* summed CUDA-event time of the profiled micro-solve launches */
+    double macro_kernel_ms;     /* summed CUDA-event time of the profiled macro-solve launches */
+} tsf_stats;
+
+/* Fill *opt with defaults: TSF_MIXED, cg_tol 1e-8, inner_tol 1e-5, macro_tol 1e-12,
+ * coupling_tol 1e-10, cg_maxit 5000, max_sweeps 20, macro_maxit 500, coupling_maxit 50,
+ * tiling -1, use_graph 1, cuda_stream NULL, profile 0. */
+void tsf_default_options(tsf_options *opt);
+
+/* Create a context.  opt may be NULL (defaults).  *out receives the handle.
+ * Errors: TSF_E_ARG (out NULL, bad option), TSF_E_CUDA (no device / stream). */
+tsf_status tsf_create(tsf_ctx **out, const tsf_options *opt);
+
+/* Replace the options of an existing context (stream excluded). */
+tsf_status tsf_set_options(tsf_ctx *ctx, const tsf_options *opt);
+
+/* Reference micro mesh on Z = [0,1]^2 (Sec. 3.1: one mesh of the reference
+ * domain, shared by all micro problems).  nx = ny = Nm cells per side,
+ * 1 <= Nm <= 89 (each micro problem must fit one thread block).  robin_edge
+ * must be 0 (the edge yhat_1 = 1).  Errors: TSF_E_ARG. */
+tsf_status tsf_set_micro_mesh(tsf_ctx *ctx, int nx, int ny, int robin_edge);
+
+/* Macro mesh on Omega = [0,1]^2 with nx = ny = NM cells per side
+ * (1 <= NM <= 1023), hence nM = (NM+1)^2 micro problems.  bc: TSF_BC_NEUMANN
+ * (homogeneous, whole boundary) or TSF_BC_DIRICHLET (whole boundary);
+ * dirichlet_vals: host array of nM values read on boundary nodes, NULL keeps
+ * the current state there.  Errors: TSF_E_ARG. */
+tsf_status tsf_set_macro_mesh(tsf_ctx *ctx, int nx, int ny, int bc, const double *dirichlet_vals);
+
+/* Micro diffusion D = [[D11, D12], [D12, D22]] (symmetric positive definite),
+ * Robin transfer coefficient kappa >= 0 (kappa_1 = kappa_2 = kappa in Eq. (5)),
+ * macro diffusion macro_diff > 0.  Errors: TSF_E_ARG. */
+tsf_status tsf_set_physics(tsf_ctx *ctx, const double D[3], double kappa, double macro_diff);
+
+/* Per-node deformation parameters params[i * nparam + k], i < nM, for the
+ * given family (nparam must match it).  Computes the pulled-back Q1 operators
+ * of every micro problem on the device and validates det F > 0 at every
+ * quadrature point (TSF_E_BAD_JACOBIAN otherwise).  Requires both meshes. */
+tsf_status tsf_set_deformation(tsf_ctx *ctx, int family, int nparam, const double *params, int params_on_device);
+
+/* State: u[nM] and v[nM * nm] (NULL = zero micro field). */
+tsf_status tsf_set_state(tsf_ctx *ctx, const double *u, const double *v, int on_device);
+
+/* Nodal source data used by the following steps (each may be NULL = zero):
+ *   fv[nM * nm]        micro volume source at the micro nodes,
+ *   g[nM * (Nm+1)]     Robin data at the Robin-edge nodes yhat = (1, q/Nm),
+ *   fu[nM]             macro volume source,
+ *   ud[nM]             Dirichlet values (read on boundary nodes when bc = Dirichlet).
+ * Load vectors are mass (resp. boundary-mass) matrices times nodal values. */
+tsf_status tsf_set_sources(tsf_ctx *ctx, const double *fv, const double *g, const double *fu, const double *ud,
+                           int on_device);
+
+/* Advance nsteps implicit Euler steps of size dt > 0.  Enqueued on the stream;
+ * returns TSF_OK once enqueued.  Requires meshes, deformation and state. */
+tsf_status tsf_step(tsf_ctx *ctx, double dt, int nsteps);
+
+/* Wait for the stream; returns the first device-side error of the steps
+ * since the last tsf_reset_stats (TSF_OK if none). */
+tsf_status tsf_synchronize(tsf_ctx *ctx);
+
+/* Getters (synchronise the stream): macro field u[nM]; micro averages
+ * vbar_i = int_{Y_x_i} v / |Y_x_i| = 1^T M_i v_i / vol_i; micro fields
+ * v[nM * nm]; boundary fluxes F_i = kappa (|Gam_i| u_i - r_i^T v_i) + G_i;
+ * geometry |Gam_i| and |Y_x_i|. */
+tsf_status tsf_get_macro(tsf_ctx *ctx, double *u_out, int on_device);
+tsf_status tsf_get_micro_averages(tsf_ctx *ctx, double *vbar_out, int on_device);
+tsf_status tsf_get_micro_field(tsf_ctx *ctx, double *v_out, int on_device);
+tsf_status tsf_get_flux(tsf_ctx *ctx, double *flux_out, int on_device);
+tsf_status tsf_get_geometry(tsf_ctx *ctx, double *gamma_out, double *vol_out, int on_device);
+
+tsf_status tsf_get_stats(tsf_ctx *ctx, tsf_stats *out);
+tsf_status tsf_reset_stats(tsf_ctx *ctx);
+
+/* Device memory: bytes of the workspace the current meshes need, and binding
+ * of a caller-owned device buffer of at least that size (256-byte aligned)
+ * that the library then uses for all its arrays (e.g. memory from PyTorch's
+ * caching allocator).  Without a bound workspace the library allocates its
+ * own on first use.  Rebinding or changing a mesh invalidates the state. */
+tsf_status tsf_workspace_bytes(tsf_ctx *ctx, size_t *bytes);
+tsf_status tsf_bind_workspace(tsf_ctx *ctx, void *device_ptr, size_t bytes);
+
+/* Text of the last error of this context ("" if none); never NULL. */
+const char *tsf_last_error(const tsf_ctx *ctx);
+
+/* Release everything the context owns (not a bound workspace).  NULL is a no-op. */
+void tsf_destroy(tsf_ctx *ctx);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int tsf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSFEM_H */

@@ -1,0 +1,361 @@
+"""ctypes binding of ``libtsfem`` (include/tsfem.h), argument marshalling only.
+
+Every C entry point has a Python function of the same name.  Array arguments
+may be NumPy arrays (host memory) or CUDA ``torch.Tensor`` s (device memory,
+passed by ``data_ptr()``); the ``on_device`` flag is derived from the array.
+A non-OK status raises :class:`TsfError` with the library's error text.
+All arithmetic runs in the CUDA library: if ``libtsfem.so`` is missing this
+module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtsfem.so")
+
+TSF_OK, TSF_E_ARG, TSF_E_STATE, TSF_E_BAD_JACOBIAN, TSF_E_NOT_CONVERGED = 0, 1, 2, 3, 4
+TSF_E_NAN, TSF_E_CUDA, TSF_E_OOM, TSF_E_BREAKDOWN = 5, 6, 7, 8
+TSF_FP64, TSF_MIXED = 0, 1
+TSF_FAMILY_IDENTITY, TSF_FAMILY_BUMP, TSF_FAMILY_SHEAR_BUMP, TSF_FAMILY_AFFINE, TSF_FAMILY_AFFINE_BUMP = 0, 1, 2, 3, 4
+TSF_BC_NEUMANN, TSF_BC_DIRICHLET = 0, 1
+STATUS_NAMES = {0: "TSF_OK", 1: "TSF_E_ARG", 2: "TSF_E_STATE", 3: "TSF_E_BAD_JACOBIAN", 4: "TSF_E_NOT_CONVERGED",
+                5: "TSF_E_NAN", 6: "TSF_E_CUDA", 7: "TSF_E_OOM", 8: "TSF_E_BREAKDOWN"}
+
+# every symbol include/tsfem.h declares
+EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micro_mesh", "tsf_set_macro_mesh",
+           "tsf_set_physics", "tsf_set_deformation", "tsf_set_state", "tsf_set_sources", "tsf_step",
+           "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux",
+           "tsf_get_geometry", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
+           "tsf_last_error", "tsf_destroy", "tsf_version"]
+
+
+class tsf_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("cg_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("macro_tol", ctypes.c_double), ("coupling_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int), ("macro_maxit", ctypes.c_int), ("coupling_maxit", ctypes.c_int),
+                ("tiling", ctypes.c_int), ("use_graph", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("profile", ctypes.c_int)]
+
+
+class tsf_stats(ctypes.Structure):
+    _fields_ = [("inner_iters", ctypes.c_int64), ("dof_cg_iters", ctypes.c_int64), ("refine_sweeps", ctypes.c_int64),
+                ("micro_solves", ctypes.c_int64), ("macro_iters", ctypes.c_int64),
+                ("coupling_iters_last", ctypes.c_int), ("coupling_iters_total", ctypes.c_int),
+                ("max_inner_iters", ctypes.c_int), ("steps", ctypes.c_int), ("status", ctypes.c_int),
+                ("tiling", ctypes.c_int), ("coupling_change", ctypes.c_double),
+                ("micro_launches", ctypes.c_int64), ("macro_launches", ctypes.c_int64),
+                ("micro_kernel_ms", ctypes.c_double), ("macro_kernel_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TsfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtsfem.so (built by ``paper_2103_17040_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build the CUDA library first "
+                           "(python -m paper_2103_17040_gb300.build or __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.tsf_default_options.argtypes = [ctypes.POINTER(tsf_options)]
+    L.tsf_default_options.restype = None
+    L.tsf_create.argtypes = [pp, ctypes.POINTER(tsf_options)]
+    L.tsf_set_options.argtypes = [vp, ctypes.POINTER(tsf_options)]
+    L.tsf_set_micro_mesh.argtypes = [vp, i, i, i]
+    L.tsf_set_macro_mesh.argtypes = [vp, i, i, i, vp]
+    L.tsf_set_physics.argtypes = [vp, vp, d, d]
+    L.tsf_set_deformation.argtypes = [vp, i, i, vp, i]
+    L.tsf_set_state.argtypes = [vp, vp, vp, i]
+    L.tsf_set_sources.argtypes = [vp, vp, vp, vp, vp, i]
+    L.tsf_step.argtypes = [vp, d, i]
+    L.tsf_synchronize.argtypes = [vp]
+    for f in ("tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux"):
+        getattr(L, f).argtypes = [vp, vp, i]
+    L.tsf_get_geometry.argtypes = [vp, vp, vp, i]
+    L.tsf_get_stats.argtypes = [vp, ctypes.POINTER(tsf_stats)]
+    L.tsf_reset_stats.argtypes = [vp]
+    L.tsf_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.tsf_bind_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    L.tsf_last_error.argtypes = [vp]
+    L.tsf_last_error.restype = ctypes.c_char_p
+    L.tsf_destroy.argtypes = [vp]
+    L.tsf_destroy.restype = None
+    L.tsf_version.argtypes = []
+    for f in EXPORTS:
+        fn = getattr(L, f)
+        if f not in ("tsf_default_options", "tsf_last_error", "tsf_destroy"):
+            fn.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(ctx, status):
+    if status != TSF_OK:
+        msg = _lib.tsf_last_error(ctx).decode() if ctx else ""
+        raise TsfError(status, msg)
+
+
+def _is_cuda_tensor(a):
+    return hasattr(a, "is_cuda") and hasattr(a, "data_ptr") and a.is_cuda
+
+
+def _ptr_in(a, n=None, dtype=np.float64):
+    """(pointer, on_device, keepalive) for an input array; None -> NULL."""
+    if a is None:
+        return None, 0, None
+    if _is_cuda_tensor(a):
+        import torch
+        t = a.contiguous()
+        if t.dtype != torch.float64:
+            t = t.to(torch.float64)
+        if n is not None and t.numel() != n:
+            raise ValueError(f"expected {n} values, got {t.numel()}")
+        return t.data_ptr(), 1, t
+    h = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    if n is not None and h.size != n:
+        raise ValueError(f"expected {n} values, got {h.size}")
+    return h.ctypes.data, 0, h
+
+
+def _out(out, n):
+    """(pointer, on_device, array) for an output; None -> new host array."""
+    if out is None:
+        out = np.empty(n, dtype=np.float64)
+    if _is_cuda_tensor(out):
+        if out.numel() != n or not out.is_contiguous():
+            raise ValueError("output tensor must be contiguous with the right size")
+        return out.data_ptr(), 1, out
+    if out.dtype != np.float64 or out.size != n or not out.flags.c_contiguous:
+        raise ValueError("output array must be contiguous float64 with the right size")
+    return out.ctypes.data, 0, out
+
+
+# ---------------------------------------------------------------------------
+# functions with the C names
+# ---------------------------------------------------------------------------
+def tsf_version() -> int:
+    return load_library().tsf_version()
+
+
+def tsf_default_options() -> tsf_options:
+    o = tsf_options()
+    load_library().tsf_default_options(ctypes.byref(o))
+    return o
+
+
+def tsf_create(opt: tsf_options | None = None) -> int:
+    L = load_library()
+    h = ctypes.c_void_p()
+    st = L.tsf_create(ctypes.byref(h), ctypes.byref(opt) if opt is not None else None)
+    if st != TSF_OK:
+        raise TsfError(st, "tsf_create failed (no CUDA device?)")
+    return h.value
+
+
+def tsf_set_options(ctx, opt: tsf_options):
+    _check(ctx, _lib.tsf_set_options(ctx, ctypes.byref(opt)))
+
+
+def tsf_set_micro_mesh(ctx, nx, ny, robin_edge=0):
+    _check(ctx, _lib.tsf_set_micro_mesh(ctx, int(nx), int(ny), int(robin_edge)))
+
+
+def tsf_set_macro_mesh(ctx, nx, ny, bc=TSF_BC_NEUMANN, dirichlet_vals=None):
+    h = None if dirichlet_vals is None else np.ascontiguousarray(np.asarray(dirichlet_vals, np.float64))
+    _check(ctx, _lib.tsf_set_macro_mesh(ctx, int(nx), int(ny), int(bc), None if h is None else h.ctypes.data))
+
+
+def tsf_set_physics(ctx, D=(1.0, 0.0, 1.0), kappa=1.0, macro_diff=1.0):
+    Da = np.ascontiguousarray(np.asarray(D, np.float64))
+    _check(ctx, _lib.tsf_set_physics(ctx, Da.ctypes.data, float(kappa), float(macro_diff)))
+
+
+def tsf_set_deformation(ctx, family, nparam, params):
+    p, dev, keep = _ptr_in(params) if nparam else (None, 0, None)
+    _check(ctx, _lib.tsf_set_deformation(ctx, int(family), int(nparam), p, dev))
+
+
+def tsf_set_state(ctx, u, v=None):
+    pu, du, ku = _ptr_in(u)
+    pv, dv, kv = _ptr_in(v)
+    if v is not None and du != dv:
+        raise ValueError("u and v must both be host arrays or both device tensors")
+    _check(ctx, _lib.tsf_set_state(ctx, pu, pv, du))
+
+
+def tsf_set_sources(ctx, fv=None, g=None, fu=None, ud=None):
+    args = [_ptr_in(a) for a in (fv, g, fu, ud)]
+    devs = {a[1] for a, x in zip(args, (fv, g, fu, ud)) if x is not None}
+    if len(devs) > 1:
+        raise ValueError("sources must all live on the host or all on the device")
+    _check(ctx, _lib.tsf_set_sources(ctx, *[a[0] for a in args], devs.pop() if devs else 0))
+
+
+def tsf_step(ctx, dt, nsteps=1):
+    _check(ctx, _lib.tsf_step(ctx, float(dt), int(nsteps)))
+
+
+def tsf_synchronize(ctx):
+    _check(ctx, _lib.tsf_synchronize(ctx))
+
+
+def _getter(name, ctx, n, out):
+    p, dev, arr = _out(out, n)
+    _check(ctx, getattr(_lib, name)(ctx, p, dev))
+    return arr
+
+
+def tsf_get_macro(ctx, nM, out=None):
+    return _getter("tsf_get_macro", ctx, nM, out)
+
+
+def tsf_get_micro_averages(ctx, nM, out=None):
+    return _getter("tsf_get_micro_averages", ctx, nM, out)
+
+
+def tsf_get_micro_field(ctx, n, out=None):
+    return _getter("tsf_get_micro_field", ctx, n, out)
+
+
+def tsf_get_flux(ctx, nM, out=None):
+    return _getter("tsf_get_flux", ctx, nM, out)
+
+
+def tsf_get_geometry(ctx, nM):
+    g = np.empty(nM)
+    v = np.empty(nM)
+    _check(ctx, _lib.tsf_get_geometry(ctx, g.ctypes.data, v.ctypes.data, 0))
+    return g, v
+
+
+def tsf_get_stats(ctx) -> dict:
+    s = tsf_stats()
+    _check(ctx, _lib.tsf_get_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def tsf_reset_stats(ctx):
+    _check(ctx, _lib.tsf_reset_stats(ctx))
+
+
+def tsf_workspace_bytes(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, _lib.tsf_workspace_bytes(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def tsf_bind_workspace(ctx, ptr, nbytes):
+    _check(ctx, _lib.tsf_bind_workspace(ctx, ptr, int(nbytes)))
+
+
+def tsf_last_error(ctx) -> str:
+    return _lib.tsf_last_error(ctx).decode()
+
+
+def tsf_destroy(ctx):
+    if ctx and _lib is not None:
+        _lib.tsf_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper (still marshalling only)
+# ---------------------------------------------------------------------------
+class TwoScale:
+    """One two-scale problem on the current CUDA device.
+
+    Meshes: Nm x Nm micro cells on the reference cell, NM x NM macro cells.
+    ``workspace='torch'`` allocates the library's device workspace through
+    PyTorch's caching allocator; ``None`` lets the library allocate it.
+    """
+
+    def __init__(self, Nm, NM, bc=TSF_BC_NEUMANN, precision=TSF_MIXED, stream=None, workspace="torch", **opts):
+        o = tsf_default_options()
+        o.precision = int(precision)
+        for k, v in opts.items():
+            setattr(o, k, v)
+        if stream is not None:
+            o.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+            if not o.cuda_stream:
+                raise ValueError("pass a non-default stream (a NULL stream makes the library create its own)")
+        self.ctx = tsf_create(o)
+        self.Nm, self.NM = int(Nm), int(NM)
+        self.nm, self.nM = (self.Nm + 1) ** 2, (self.NM + 1) ** 2
+        tsf_set_micro_mesh(self.ctx, self.Nm, self.Nm, 0)
+        tsf_set_macro_mesh(self.ctx, self.NM, self.NM, bc, None)
+        self._ws = None
+        if workspace == "torch":
+            import torch
+            nbytes = tsf_workspace_bytes(self.ctx)
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            tsf_bind_workspace(self.ctx, (base + 255) // 256 * 256, nbytes)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            tsf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_physics(self, D=(1.0, 0.0, 1.0), kappa=1.0, macro_diff=1.0):
+        tsf_set_physics(self.ctx, D, kappa, macro_diff)
+
+    def set_deformation(self, family, params):
+        params = np.zeros((self.nM, 0)) if params is None else params
+        nparam = {0: 0, 1: 1, 2: 2, 3: 6, 4: 5}[int(family)]
+        tsf_set_deformation(self.ctx, family, nparam, params)
+
+    def set_state(self, u, v=None):
+        tsf_set_state(self.ctx, u, v)
+
+    def set_sources(self, fv=None, g=None, fu=None, ud=None):
+        tsf_set_sources(self.ctx, fv, g, fu, ud)
+
+    def step(self, dt, nsteps=1):
+        tsf_step(self.ctx, dt, nsteps)
+
+    def synchronize(self):
+        tsf_synchronize(self.ctx)
+
+    def u(self, out=None):
+        return tsf_get_macro(self.ctx, self.nM, out)
+
+    def v(self, out=None):
+        a = tsf_get_micro_field(self.ctx, self.nM * self.nm, out)
+        return a.reshape(self.nM, self.nm) if isinstance(a, np.ndarray) else a
+
+    def vbar(self, out=None):
+        return tsf_get_micro_averages(self.ctx, self.nM, out)
+
+    def flux(self, out=None):
+        return tsf_get_flux(self.ctx, self.nM, out)
+
+    def geometry(self):
+        return tsf_get_geometry(self.ctx, self.nM)
+
+    def stats(self):
+        return tsf_get_stats(self.ctx)
+
+    def reset_stats(self):
+        tsf_reset_stats(self.ctx)

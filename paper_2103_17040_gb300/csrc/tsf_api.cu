@@ -1,0 +1,848 @@
+// tsf_api.cu -- C ABI and host runtime of the GB300 two-scale library.
+//
+// Host responsibilities: validation of the inputs, one device workspace
+// (caller-bound or self-allocated) carved into all arrays, rebuilding the
+// pulled-back operators when the geometry, the physics or dt change, the
+// choice of the micro-kernel tiling (measured on the actual problem), and the
+// time step itself: a CUDA graph per dt whose coupling loop is a
+// device-controlled conditional WHILE node (the macro kernel decides whether
+// the Sec. 3.3 fixed-point iteration goes on), so one step costs one graph
+// launch and no host round trip.
+#include "tsfem.h"
+#include "tsf_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace tsf;
+
+namespace {
+
+constexpr int kMaxNm = 64;     // micro cells per side (one thread block per micro problem)
+constexpr int kMaxNM = 1023;   // macro cells per side
+constexpr size_t kAlign = 256;
+
+struct Arena {
+    size_t total = 0;
+    size_t take(size_t bytes) {
+        size_t o = total;
+        total += (bytes + kAlign - 1) / kAlign * kAlign;
+        return o;
+    }
+};
+
+}  // namespace
+
+struct tsf_ctx {
+    tsf_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int smem_optin = 0;
+    // meshes
+    int Nm = 0, n1 = 0, nm = 0, nmp = 0;
+    int NM = 0, N1 = 0, nM = 0, bc = 0;
+    bool micro_set = false, macro_set = false;
+    std::vector<double> dir_vals;
+    // physics
+    double D[3] = {1.0, 0.0, 1.0};
+    double kappa = 1.0, Du = 1.0;
+    // workspace
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false, ws_valid = false;
+    // device arrays
+    double *prm5 = nullptr, *M64 = nullptr, *S64 = nullptr, *lm = nullptr, *redge = nullptr, *Rd = nullptr,
+           *Ru = nullptr, *gam = nullptr, *vol = nullptr;
+    float* S32 = nullptr;
+    double *v = nullptr, *c = nullptr, *vtmp = nullptr, *fv = nullptr, *g = nullptr, *G = nullptr;
+    double *u = nullptr, *uk = nullptr, *cH = nullptr, *fu = nullptr, *ud = nullptr, *rho = nullptr,
+           *out = nullptr;
+    double *mx = nullptr, *mr = nullptr, *mz = nullptr, *mzo = nullptr, *mp = nullptr, *mq = nullptr;
+    int* inst_iters = nullptr;
+    DevCtl* ctl = nullptr;
+    DevCtl* ctl_host = nullptr;  // pinned
+    // status of the contents
+    bool geom_set = false, state_set = false;
+    int family = 0;
+    double ops_dt = -1.0;
+    bool ops_valid = false;
+    bool has_fv = false, has_g = false, has_fu = false, has_ud = false;
+    int K = 0;                   // micro tiling (nodes per thread), 0 = not chosen
+    int K_prec = -1;             // precision the tiling was chosen for
+    bool use_dct = false;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_valid = false;
+    double graph_dt = -1.0;
+    // per-launch CUDA-event timing of the plain-launch path (options.profile)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t prof_micro_n = 0, prof_macro_n = 0;
+    double prof_micro_ms = 0.0, prof_macro_ms = 0.0;
+    std::string err;
+};
+
+static tsf_status fail(tsf_ctx* ctx, tsf_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+#define CU(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? TSF_E_OOM : TSF_E_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+    } while (0)
+
+static void invalidate_graph(tsf_ctx* ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+    ctx->graph_valid = false;
+}
+
+static bool options_ok(const tsf_options* o) {
+    return o && (o->precision == TSF_FP64 || o->precision == TSF_MIXED) && o->cg_tol >= 0 && o->inner_tol > 0 &&
+           o->inner_tol < 1 && o->macro_tol >= 0 && o->coupling_tol >= 0 && o->cg_maxit > 0 && o->max_sweeps > 0 &&
+           o->macro_maxit > 0 && o->coupling_maxit > 0 &&
+           (o->tiling == -1 || (o->tiling >= 0 && o->tiling <= 3));
+}
+
+extern "C" {
+
+int tsf_version(void) { return 100; }
+
+void tsf_default_options(tsf_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof *opt);
+    opt->precision = TSF_MIXED;
+    opt->cg_tol = 1e-8;
+    opt->inner_tol = 1e-5;
+    opt->macro_tol = 1e-12;
+    opt->coupling_tol = 1e-10;
+    opt->cg_maxit = 5000;
+    opt->max_sweeps = 20;
+    opt->macro_maxit = 500;
+    opt->coupling_maxit = 50;
+    opt->tiling = -1;
+    opt->use_graph = 1;
+    opt->cuda_stream = nullptr;
+}
+
+const char* tsf_last_error(const tsf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+tsf_status tsf_create(tsf_ctx** out, const tsf_options* opt) {
+    if (!out) return TSF_E_ARG;
+    *out = nullptr;
+    tsf_options o;
+    tsf_default_options(&o);
+    if (opt) o = *opt;
+    if (!options_ok(&o)) return TSF_E_ARG;
+    tsf_ctx* ctx = new (std::nothrow) tsf_ctx();
+    if (!ctx) return TSF_E_OOM;
+    ctx->opt = o;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if (e == cudaSuccess) {
+        if (o.cuda_stream) {
+            ctx->stream = (cudaStream_t)o.cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = configure_micro_kernels(ctx->smem_optin);
+    if (e == cudaSuccess) e = configure_macro_kernels(ctx->smem_optin);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->ctl_host, sizeof(DevCtl));
+    if (e != cudaSuccess) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return TSF_E_CUDA;
+    }
+    memset(ctx->ctl_host, 0, sizeof(DevCtl));
+    *out = ctx;
+    return TSF_OK;
+}
+
+tsf_status tsf_set_options(tsf_ctx* ctx, const tsf_options* opt) {
+    if (!ctx) return TSF_E_ARG;
+    if (!options_ok(opt)) return fail(ctx, TSF_E_ARG, "invalid options");
+    void* keep = ctx->opt.cuda_stream;
+    const bool prec_changed = opt->precision != ctx->opt.precision;
+    ctx->opt = *opt;
+    ctx->opt.cuda_stream = keep;
+    if (prec_changed || opt->tiling >= 0) ctx->K = 0;
+    invalidate_graph(ctx);
+    return TSF_OK;
+}
+
+void tsf_destroy(tsf_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    invalidate_graph(ctx);
+    for (int k = 0; k < 4; ++k)
+        if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+    if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+tsf_status tsf_set_micro_mesh(tsf_ctx* ctx, int nx, int ny, int robin_edge) {
+    if (!ctx) return TSF_E_ARG;
+    if (nx != ny || nx < 1 || nx > kMaxNm)
+        return fail(ctx, TSF_E_ARG, "micro mesh must be square with 1..%d cells per side (got %d x %d)", kMaxNm, nx, ny);
+    if (robin_edge != 0) return fail(ctx, TSF_E_ARG, "only robin_edge 0 (yhat_1 = 1) is supported");
+    ctx->Nm = nx;
+    ctx->n1 = nx + 1;
+    ctx->nm = ctx->n1 * ctx->n1;
+    ctx->nmp = (ctx->nm + 31) / 32 * 32;
+    ctx->micro_set = true;
+    ctx->ws_valid = false;
+    ctx->geom_set = ctx->state_set = ctx->ops_valid = false;
+    ctx->K = 0;
+    invalidate_graph(ctx);
+    return TSF_OK;
+}
+
+tsf_status tsf_set_macro_mesh(tsf_ctx* ctx, int nx, int ny, int bc, const double* dirichlet_vals) {
+    if (!ctx) return TSF_E_ARG;
+    if (nx != ny || nx < 1 || nx > kMaxNM)
+        return fail(ctx, TSF_E_ARG, "macro mesh must be square with 1..%d cells per side (got %d x %d)", kMaxNM, nx, ny);
+    if (bc != TSF_BC_NEUMANN && bc != TSF_BC_DIRICHLET) return fail(ctx, TSF_E_ARG, "bc must be 0 or 1");
+    ctx->NM = nx;
+    ctx->N1 = nx + 1;
+    ctx->nM = ctx->N1 * ctx->N1;
+    ctx->bc = bc;
+    ctx->dir_vals.clear();
+    if (dirichlet_vals) ctx->dir_vals.assign(dirichlet_vals, dirichlet_vals + ctx->nM);
+    ctx->macro_set = true;
+    ctx->ws_valid = false;
+    ctx->geom_set = ctx->state_set = ctx->ops_valid = false;
+    invalidate_graph(ctx);
+    return TSF_OK;
+}
+
+tsf_status tsf_set_physics(tsf_ctx* ctx, const double D[3], double kappa, double macro_diff) {
+    if (!ctx || !D) return TSF_E_ARG;
+    if (!(D[0] > 0 && D[2] > 0 && D[0] * D[2] - D[1] * D[1] > 0))
+        return fail(ctx, TSF_E_ARG, "D must be symmetric positive definite");
+    if (!(kappa >= 0) || !(macro_diff > 0) || !std::isfinite(kappa) || !std::isfinite(macro_diff))
+        return fail(ctx, TSF_E_ARG, "need kappa >= 0 and macro_diff > 0");
+    ctx->D[0] = D[0];
+    ctx->D[1] = D[1];
+    ctx->D[2] = D[2];
+    ctx->kappa = kappa;
+    ctx->Du = macro_diff;
+    ctx->ops_valid = false;
+    invalidate_graph(ctx);
+    return TSF_OK;
+}
+
+static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
+    const size_t nM = ctx->nM, pl = ctx->nmp, n1 = ctx->n1;
+    int k = 0;
+    off[k++] = A.take(nM * 5 * sizeof(double));                  // prm5
+    off[k++] = A.take(nM * kPlanes * pl * sizeof(double));       // M64
+    off[k++] = A.take(nM * kPlanes * pl * sizeof(double));       // S64
+    off[k++] = A.take(nM * kPlanes * pl * sizeof(float));        // S32
+    off[k++] = A.take(nM * pl * sizeof(double));                 // lm
+    off[k++] = A.take(nM * n1 * sizeof(double));                 // redge
+    off[k++] = A.take(nM * n1 * sizeof(double));                 // Rd
+    off[k++] = A.take(nM * n1 * sizeof(double));                 // Ru
+    off[k++] = A.take(nM * sizeof(double));                      // gam
+    off[k++] = A.take(nM * sizeof(double));                      // vol
+    off[k++] = A.take(nM * pl * sizeof(double));                 // v
+    off[k++] = A.take(nM * pl * sizeof(double));                 // c
+    off[k++] = A.take(nM * pl * sizeof(double));                 // vtmp
+    off[k++] = A.take(nM * pl * sizeof(double));                 // fv
+    off[k++] = A.take(nM * n1 * sizeof(double));                 // g
+    off[k++] = A.take(nM * sizeof(double));                      // G
+    for (int r = 0; r < 13; ++r) off[k++] = A.take(nM * sizeof(double));  // u uk cH fu ud rho out mx mr mz mzo mp mq
+    off[k++] = A.take(nM * sizeof(int));                         // inst_iters
+    off[k++] = A.take(sizeof(DevCtl));                           // ctl
+}
+
+static void assign(tsf_ctx* ctx, const size_t* off) {
+    unsigned char* b = ctx->ws;
+    int k = 0;
+    ctx->prm5 = (double*)(b + off[k++]);
+    ctx->M64 = (double*)(b + off[k++]);
+    ctx->S64 = (double*)(b + off[k++]);
+    ctx->S32 = (float*)(b + off[k++]);
+    ctx->lm = (double*)(b + off[k++]);
+    ctx->redge = (double*)(b + off[k++]);
+    ctx->Rd = (double*)(b + off[k++]);
+    ctx->Ru = (double*)(b + off[k++]);
+    ctx->gam = (double*)(b + off[k++]);
+    ctx->vol = (double*)(b + off[k++]);
+    ctx->v = (double*)(b + off[k++]);
+    ctx->c = (double*)(b + off[k++]);
+    ctx->vtmp = (double*)(b + off[k++]);
+    ctx->fv = (double*)(b + off[k++]);
+    ctx->g = (double*)(b + off[k++]);
+    ctx->G = (double*)(b + off[k++]);
+    double** r[13] = {&ctx->u, &ctx->uk, &ctx->cH, &ctx->fu, &ctx->ud, &ctx->rho, &ctx->out,
+                      &ctx->mx, &ctx->mr, &ctx->mz, &ctx->mzo, &ctx->mp, &ctx->mq};
+    for (int i = 0; i < 13; ++i) *r[i] = (double*)(b + off[k++]);
+    ctx->inst_iters = (int*)(b + off[k++]);
+    ctx->ctl = (DevCtl*)(b + off[k++]);
+}
+
+static constexpr int kNumBuffers = 16 + 13 + 2;
+
+tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return TSF_E_ARG;
+    if (!ctx->micro_set || !ctx->macro_set) return fail(ctx, TSF_E_STATE, "set both meshes first");
+    Arena A;
+    size_t off[kNumBuffers];
+    layout(ctx, A, off);
+    *bytes = A.total;
+    return TSF_OK;
+}
+
+static tsf_status init_workspace(tsf_ctx* ctx) {
+    Arena A;
+    size_t off[kNumBuffers];
+    layout(ctx, A, off);
+    assign(ctx, off);
+    CU(cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), ctx->stream));
+    CU(cudaMemsetAsync(ctx->u, 0, (size_t)ctx->nM * sizeof(double), ctx->stream));
+    CU(cudaMemsetAsync(ctx->v, 0, (size_t)ctx->nM * ctx->nmp * sizeof(double), ctx->stream));
+    CU(cudaMemsetAsync(ctx->G, 0, (size_t)ctx->nM * sizeof(double), ctx->stream));
+    if (!ctx->dir_vals.empty())
+        CU(cudaMemcpyAsync(ctx->ud, ctx->dir_vals.data(), ctx->nM * sizeof(double), cudaMemcpyHostToDevice,
+                           ctx->stream));
+    ctx->has_ud = !ctx->dir_vals.empty();
+    ctx->has_fv = ctx->has_g = ctx->has_fu = false;
+    ctx->geom_set = ctx->state_set = ctx->ops_valid = false;
+    ctx->ws_valid = true;
+    invalidate_graph(ctx);
+    return TSF_OK;
+}
+
+tsf_status tsf_bind_workspace(tsf_ctx* ctx, void* device_ptr, size_t bytes) {
+    if (!ctx || !device_ptr) return TSF_E_ARG;
+    size_t need = 0;
+    tsf_status st = tsf_workspace_bytes(ctx, &need);
+    if (st) return st;
+    if (bytes < need) return fail(ctx, TSF_E_OOM, "workspace of %zu bytes < %zu needed", bytes, need);
+    if (((uintptr_t)device_ptr) % kAlign) return fail(ctx, TSF_E_ARG, "workspace must be 256-byte aligned");
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = (unsigned char*)device_ptr;
+    ctx->ws_bytes = bytes;
+    ctx->own_ws = false;
+    return init_workspace(ctx);
+}
+
+static tsf_status ensure_workspace(tsf_ctx* ctx) {
+    if (!ctx->micro_set || !ctx->macro_set) return fail(ctx, TSF_E_STATE, "set both meshes first");
+    if (ctx->ws_valid) return TSF_OK;
+    size_t need = 0;
+    tsf_workspace_bytes(ctx, &need);
+    if (!ctx->ws || ctx->ws_bytes < need || !ctx->own_ws) {
+        if (ctx->own_ws && ctx->ws) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->ws);
+        }
+        ctx->ws = nullptr;
+        ctx->own_ws = false;
+        cudaError_t e = cudaMalloc((void**)&ctx->ws, need);
+        if (e != cudaSuccess) {
+            ctx->ws = nullptr;
+            cudaGetLastError();
+            return fail(ctx, TSF_E_OOM, "cudaMalloc of %zu bytes failed: %s", need, cudaGetErrorString(e));
+        }
+        ctx->ws_bytes = need;
+        ctx->own_ws = true;
+    }
+    return init_workspace(ctx);
+}
+
+static tsf_status copy_in(tsf_ctx* ctx, double* dst, const double* src, size_t n, int on_device) {
+    CU(cudaMemcpyAsync(dst, src, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return TSF_OK;
+}
+
+// rows of nm values (caller, contiguous) <-> rows of nmp values (device, padded)
+static tsf_status copy_field_in(tsf_ctx* ctx, double* dst, const double* src, int on_device) {
+    CU(cudaMemcpy2DAsync(dst, ctx->nmp * sizeof(double), src, ctx->nm * sizeof(double), ctx->nm * sizeof(double),
+                         ctx->nM, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    return TSF_OK;
+}
+
+static tsf_status build_operators(tsf_ctx* ctx, double dt) {
+    GeomArgs a{};
+    a.Nm = ctx->Nm;
+    a.n1 = ctx->n1;
+    a.nm = ctx->nm;
+    a.nmp = ctx->nmp;
+    a.nM = ctx->nM;
+    a.prm5 = ctx->prm5;
+    a.D11 = ctx->D[0];
+    a.D12 = ctx->D[1];
+    a.D22 = ctx->D[2];
+    a.kappa = ctx->kappa;
+    a.dt = dt;
+    a.M64 = ctx->M64;
+    a.S64 = ctx->S64;
+    a.S32 = ctx->S32;
+    a.lm = ctx->lm;
+    a.redge = ctx->redge;
+    a.Rd = ctx->Rd;
+    a.Ru = ctx->Ru;
+    a.ctl = ctx->ctl;
+    CU(launch_geometry(a, ctx->stream));
+    CU(launch_instance_sums(ctx->n1, ctx->nm, ctx->nmp, ctx->nM, ctx->lm, ctx->redge, ctx->gam, ctx->vol,
+                            ctx->stream));
+    ctx->ops_dt = dt;
+    ctx->ops_valid = true;
+    return TSF_OK;
+}
+
+tsf_status tsf_set_deformation(tsf_ctx* ctx, int family, int nparam, const double* params, int params_on_device) {
+    if (!ctx) return TSF_E_ARG;
+    static const int np_of[5] = {0, 1, 2, 6, 5};
+    if (family < 0 || family > 4) return fail(ctx, TSF_E_ARG, "unknown deformation family %d", family);
+    if (nparam != np_of[family])
+        return fail(ctx, TSF_E_ARG, "family %d takes %d parameters per node (got %d)", family, np_of[family], nparam);
+    if (nparam > 0 && !params) return fail(ctx, TSF_E_ARG, "params is NULL");
+    tsf_status st = ensure_workspace(ctx);
+    if (st) return st;
+    if (nparam > 0) {
+        // stage the raw parameters in the scratch field, then expand on the device
+        st = copy_in(ctx, ctx->vtmp, params, (size_t)ctx->nM * nparam, params_on_device);
+        if (st) return st;
+    }
+    CU(launch_expand_params(family, nparam, ctx->vtmp, ctx->prm5, ctx->nM, ctx->stream));
+    CU(cudaMemsetAsync(&ctx->ctl->geom_error, 0, sizeof(int), ctx->stream));
+    st = build_operators(ctx, 1.0);
+    if (st) return st;
+    int gerr = 0;
+    CU(cudaMemcpyAsync(&gerr, &ctx->ctl->geom_error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->family = family;
+    invalidate_graph(ctx);
+    if (gerr) {
+        ctx->geom_set = false;
+        ctx->ops_valid = false;
+        return fail(ctx, TSF_E_BAD_JACOBIAN, "det F <= 0 at a quadrature point of some micro problem");
+    }
+    ctx->geom_set = true;
+    return TSF_OK;
+}
+
+tsf_status tsf_set_state(tsf_ctx* ctx, const double* u, const double* v, int on_device) {
+    if (!ctx || !u) return TSF_E_ARG;
+    tsf_status st = ensure_workspace(ctx);
+    if (st) return st;
+    st = copy_in(ctx, ctx->u, u, ctx->nM, on_device);
+    if (st) return st;
+    if (v) {
+        st = copy_field_in(ctx, ctx->v, v, on_device);
+        if (st) return st;
+    } else {
+        CU(cudaMemsetAsync(ctx->v, 0, (size_t)ctx->nM * ctx->nmp * sizeof(double), ctx->stream));
+    }
+    ctx->state_set = true;
+    return TSF_OK;
+}
+
+tsf_status tsf_set_sources(tsf_ctx* ctx, const double* fv, const double* g, const double* fu, const double* ud,
+                           int on_device) {
+    if (!ctx) return TSF_E_ARG;
+    tsf_status st = ensure_workspace(ctx);
+    if (st) return st;
+    const bool before[4] = {ctx->has_fv, ctx->has_g, ctx->has_fu, ctx->has_ud};
+    if (fv && (st = copy_field_in(ctx, ctx->fv, fv, on_device))) return st;
+    if (g && (st = copy_in(ctx, ctx->g, g, (size_t)ctx->nM * ctx->n1, on_device))) return st;
+    if (fu && (st = copy_in(ctx, ctx->fu, fu, ctx->nM, on_device))) return st;
+    if (ud && (st = copy_in(ctx, ctx->ud, ud, ctx->nM, on_device))) return st;
+    ctx->has_fv = fv != nullptr;
+    ctx->has_g = g != nullptr;
+    ctx->has_fu = fu != nullptr;
+    ctx->has_ud = ud != nullptr;
+    if (!ud && !ctx->dir_vals.empty()) {
+        // no new values: fall back to the ones given with the macro mesh
+        if ((st = copy_in(ctx, ctx->ud, ctx->dir_vals.data(), ctx->nM, 0))) return st;
+        ctx->has_ud = true;
+    }
+    if (before[0] != ctx->has_fv || before[1] != ctx->has_g || before[2] != ctx->has_fu || before[3] != ctx->has_ud)
+        invalidate_graph(ctx);
+    return TSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the step
+// ---------------------------------------------------------------------------
+static MicroArgs micro_args(tsf_ctx* ctx, double* v) {
+    MicroArgs a{};
+    a.n1 = ctx->n1;
+    a.nm = ctx->nm;
+    a.nmp = ctx->nmp;
+    a.W = ctx->n1 + 2;
+    a.nM = ctx->nM;
+    a.S32 = ctx->S32;
+    a.S64 = ctx->S64;
+    a.c = ctx->c;
+    a.v = v;
+    a.u = ctx->uk;
+    a.redge = ctx->redge;
+    a.kappa = ctx->kappa;
+    a.tol = ctx->opt.cg_tol;
+    a.inner_tol = ctx->opt.inner_tol;
+    a.maxit = ctx->opt.cg_maxit;
+    a.max_sweeps = ctx->opt.max_sweeps;
+    a.rho = ctx->rho;
+    a.inst_iters = ctx->inst_iters;
+    a.ctl = ctx->ctl;
+    return a;
+}
+
+static MacroArgs macro_args(tsf_ctx* ctx, double dt, bool set_cond, cudaGraphConditionalHandle cond) {
+    MacroArgs a{};
+    a.NM = ctx->NM;
+    a.N1 = ctx->N1;
+    a.nM = ctx->nM;
+    a.bc = ctx->bc;
+    a.H = 1.0 / ctx->NM;
+    a.dt = dt;
+    a.Du = ctx->Du;
+    a.kappa = ctx->kappa;
+    a.gam = ctx->gam;
+    a.cH = ctx->cH;
+    a.rho = ctx->rho;
+    a.uk = ctx->uk;
+    a.u = ctx->u;
+    a.x = ctx->mx;
+    a.r = ctx->mr;
+    a.z = ctx->mz;
+    a.zo = ctx->mzo;
+    a.p = ctx->mp;
+    a.q = ctx->mq;
+    a.tol = ctx->opt.macro_tol;
+    a.maxit = ctx->opt.macro_maxit;
+    a.coupling_tol = ctx->opt.coupling_tol;
+    a.coupling_maxit = ctx->opt.coupling_maxit;
+    a.use_dct = ctx->use_dct ? 1 : 0;
+    a.set_cond = set_cond ? 1 : 0;
+    a.cond = cond;
+    a.ctl = ctx->ctl;
+    return a;
+}
+
+static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt) {
+    PrologueArgs p{};
+    p.n1 = ctx->n1;
+    p.nm = ctx->nm;
+    p.nmp = ctx->nmp;
+    p.nM = ctx->nM;
+    p.dt = dt;
+    p.M64 = ctx->M64;
+    p.v = ctx->v;
+    p.fv = ctx->has_fv ? ctx->fv : nullptr;
+    p.g = ctx->has_g ? ctx->g : nullptr;
+    p.redge = ctx->redge;
+    p.Rd = ctx->Rd;
+    p.Ru = ctx->Ru;
+    p.c = ctx->c;
+    p.G = ctx->G;
+    CU(launch_micro_prologue(p, ctx->stream));
+    MacroPrologueArgs m{};
+    m.NM = ctx->NM;
+    m.N1 = ctx->N1;
+    m.nM = ctx->nM;
+    m.bc = ctx->bc;
+    m.H = 1.0 / ctx->NM;
+    m.dt = dt;
+    m.u = ctx->u;
+    m.fu = ctx->has_fu ? ctx->fu : nullptr;
+    m.ud = ctx->has_ud ? ctx->ud : nullptr;
+    m.G = ctx->G;
+    m.cH = ctx->cH;
+    m.uk = ctx->uk;
+    m.ctl = ctx->ctl;
+    CU(launch_macro_prologue(m, ctx->stream));
+    return TSF_OK;
+}
+
+static int tiling_K(int t) { return 1 << t; }  // tiling index -> nodes per thread
+
+static bool tiling_ok(tsf_ctx* ctx, int K) {
+    const int T = micro_threads(ctx->nm, K);
+    const int maxT = K <= 2 ? 1024 : (K == 4 ? 512 : 544);
+    return T <= maxT;
+}
+
+// Choose the micro tiling (nodes per thread K) by timing one solve of every
+// admissible variant on the actual problem (right-hand side of the current
+// step, warm start from the current state, written to a scratch copy).
+static tsf_status autotune(tsf_ctx* ctx, double dt) {
+    const int prec = ctx->opt.precision;
+    if (ctx->opt.tiling >= 0) {
+        const int K = tiling_K(ctx->opt.tiling);
+        if (!tiling_ok(ctx, K)) return fail(ctx, TSF_E_ARG, "tiling %d does not fit this micro mesh", ctx->opt.tiling);
+        ctx->K = K;
+        ctx->K_prec = prec;
+        return TSF_OK;
+    }
+    DevCtl saved;
+    CU(cudaMemcpyAsync(&saved, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    tsf_status st = enqueue_prologue(ctx, dt);
+    if (st) return st;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestK = 0;
+    const size_t bytes = (size_t)ctx->nM * ctx->nmp * sizeof(double);
+    for (int t = 0; t < 4; ++t) {
+        const int K = tiling_K(t);
+        if (!tiling_ok(ctx, K)) continue;
+        MicroArgs a = micro_args(ctx, ctx->vtmp);
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CU(cudaMemcpyAsync(ctx->vtmp, ctx->v, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            CU(cudaEventRecord(e0, ctx->stream));
+            CU(launch_micro_solve(a, prec, K, ctx->stream));
+            CU(cudaEventRecord(e1, ctx->stream));
+            CU(cudaEventSynchronize(e1));
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms < best) {
+            best = ms;
+            bestK = K;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CU(cudaMemcpyAsync(ctx->ctl, &saved, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (!bestK) return fail(ctx, TSF_E_ARG, "no micro tiling fits this mesh");
+    ctx->K = bestK;
+    ctx->K_prec = prec;
+    return TSF_OK;
+}
+
+static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
+    invalidate_graph(ctx);
+    CU(cudaGraphCreate(&ctx->graph, 0));
+    cudaGraphConditionalHandle cond;
+    CU(cudaGraphConditionalHandleCreate(&cond, ctx->graph, 1, cudaGraphCondAssignDefault));
+    CU(cudaStreamBeginCaptureToGraph(ctx->stream, ctx->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    tsf_status st = enqueue_prologue(ctx, dt);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t capg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &capg, &deps, nullptr, &ndeps);
+    cudaGraphNode_t cnode = nullptr;
+    cudaGraph_t body = nullptr;
+    if (!st && e == cudaSuccess) {
+        alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+        memset(cpbuf, 0, sizeof cpbuf);
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&cnode, capg, deps, nullptr, ndeps, &cp);
+        if (e == cudaSuccess) {
+            body = cp.conditional.phGraph_out[0];
+            e = cudaStreamUpdateCaptureDependencies(ctx->stream, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        }
+    }
+    cudaGraph_t endg = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &endg);
+    if (st) return st;
+    CU(e);
+    CU(e2);
+    CU(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    MicroArgs ma = micro_args(ctx, ctx->v);
+    e = launch_micro_solve(ma, ctx->opt.precision, ctx->K, ctx->stream);
+    if (e == cudaSuccess) e = launch_macro_solve(macro_args(ctx, dt, true, cond), ctx->stream);
+    e2 = cudaStreamEndCapture(ctx->stream, &body);
+    CU(e);
+    CU(e2);
+    CU(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+    ctx->graph_valid = true;
+    ctx->graph_dt = dt;
+    return TSF_OK;
+}
+
+tsf_status tsf_step(tsf_ctx* ctx, double dt, int nsteps) {
+    if (!ctx) return TSF_E_ARG;
+    if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(ctx, TSF_E_ARG, "need dt > 0 and nsteps >= 0");
+    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
+    if (!ctx->state_set) return fail(ctx, TSF_E_STATE, "set the state first");
+    if (nsteps == 0) return TSF_OK;
+    if (!ctx->ops_valid || ctx->ops_dt != dt) {
+        tsf_status st = build_operators(ctx, dt);
+        if (st) return st;
+        invalidate_graph(ctx);
+    }
+    ctx->use_dct = macro_smem_bytes(ctx->N1, ctx->bc, 1) <= (size_t)ctx->smem_optin;
+    if (micro_smem_bytes(ctx->n1, ctx->opt.precision) > (size_t)ctx->smem_optin)
+        return fail(ctx, TSF_E_ARG, "micro mesh too large for one thread block in this precision");
+    if (ctx->K == 0 || ctx->K_prec != ctx->opt.precision) {
+        tsf_status st = autotune(ctx, dt);
+        if (st) return st;
+        invalidate_graph(ctx);
+    }
+    if (ctx->opt.use_graph) {
+        if (!ctx->graph_valid || ctx->graph_dt != dt) {
+            tsf_status st = capture_graph(ctx, dt);
+            if (st) return st;
+        }
+        for (int s = 0; s < nsteps; ++s) CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
+        return TSF_OK;
+    }
+    // plain launches, host-controlled coupling loop
+    const bool prof = ctx->opt.profile != 0;
+    if (prof && !ctx->ev[0])
+        for (int k = 0; k < 4; ++k) CU(cudaEventCreate(&ctx->ev[k]));
+    for (int s = 0; s < nsteps; ++s) {
+        tsf_status st = enqueue_prologue(ctx, dt);
+        if (st) return st;
+        for (int it = 0; it < ctx->opt.coupling_maxit; ++it) {
+            if (prof) CU(cudaEventRecord(ctx->ev[0], ctx->stream));
+            CU(launch_micro_solve(micro_args(ctx, ctx->v), ctx->opt.precision, ctx->K, ctx->stream));
+            if (prof) CU(cudaEventRecord(ctx->ev[1], ctx->stream));
+            cudaGraphConditionalHandle none{};
+            CU(launch_macro_solve(macro_args(ctx, dt, false, none), ctx->stream));
+            if (prof) CU(cudaEventRecord(ctx->ev[2], ctx->stream));
+            CU(cudaMemcpyAsync(&ctx->ctl_host->cont, &ctx->ctl->cont, sizeof(int), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+            CU(cudaStreamSynchronize(ctx->stream));
+            if (prof) {
+                float a = 0.f, b = 0.f;
+                CU(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
+                CU(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+                ctx->prof_micro_ms += a;
+                ctx->prof_macro_ms += b;
+                ctx->prof_micro_n += 1;
+                ctx->prof_macro_n += 1;
+            }
+            if (!ctx->ctl_host->cont) break;
+        }
+    }
+    return TSF_OK;
+}
+
+tsf_status tsf_synchronize(tsf_ctx* ctx) {
+    if (!ctx) return TSF_E_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->ws_valid) return TSF_OK;
+    int status = 0;
+    CU(cudaMemcpy(&status, &ctx->ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) return fail(ctx, (tsf_status)status, "device reported status %d during the steps", status);
+    return TSF_OK;
+}
+
+static tsf_status copy_out(tsf_ctx* ctx, double* dst, const double* src, size_t n, int on_device) {
+    CU(cudaMemcpyAsync(dst, src, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return TSF_OK;
+}
+
+tsf_status tsf_get_macro(tsf_ctx* ctx, double* u_out, int on_device) {
+    if (!ctx || !u_out) return TSF_E_ARG;
+    if (!ctx->ws_valid) return fail(ctx, TSF_E_STATE, "no state");
+    return copy_out(ctx, u_out, ctx->u, ctx->nM, on_device);
+}
+
+tsf_status tsf_get_micro_field(tsf_ctx* ctx, double* v_out, int on_device) {
+    if (!ctx || !v_out) return TSF_E_ARG;
+    if (!ctx->ws_valid) return fail(ctx, TSF_E_STATE, "no state");
+    CU(cudaMemcpy2DAsync(v_out, ctx->nm * sizeof(double), ctx->v, ctx->nmp * sizeof(double), ctx->nm * sizeof(double),
+                         ctx->nM, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return TSF_OK;
+}
+
+tsf_status tsf_get_micro_averages(tsf_ctx* ctx, double* vbar_out, int on_device) {
+    if (!ctx || !vbar_out) return TSF_E_ARG;
+    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
+    CU(launch_vbar(ctx->nm, ctx->nmp, ctx->nM, ctx->lm, ctx->vol, ctx->v, ctx->out, ctx->stream));
+    return copy_out(ctx, vbar_out, ctx->out, ctx->nM, on_device);
+}
+
+tsf_status tsf_get_flux(tsf_ctx* ctx, double* flux_out, int on_device) {
+    if (!ctx || !flux_out) return TSF_E_ARG;
+    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
+    if (!ctx->ops_valid) {
+        tsf_status st = build_operators(ctx, ctx->ops_dt > 0 ? ctx->ops_dt : 1.0);
+        if (st) return st;
+    }
+    CU(launch_flux(ctx->n1, ctx->nm, ctx->nmp, ctx->nM, ctx->kappa, ctx->gam, ctx->u, ctx->v, ctx->redge,
+                   ctx->has_g ? ctx->g : nullptr, ctx->out, ctx->stream));
+    return copy_out(ctx, flux_out, ctx->out, ctx->nM, on_device);
+}
+
+tsf_status tsf_get_geometry(tsf_ctx* ctx, double* gamma_out, double* vol_out, int on_device) {
+    if (!ctx) return TSF_E_ARG;
+    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
+    tsf_status st = TSF_OK;
+    if (gamma_out && (st = copy_out(ctx, gamma_out, ctx->gam, ctx->nM, on_device))) return st;
+    if (vol_out && (st = copy_out(ctx, vol_out, ctx->vol, ctx->nM, on_device))) return st;
+    return TSF_OK;
+}
+
+tsf_status tsf_get_stats(tsf_ctx* ctx, tsf_stats* out) {
+    if (!ctx || !out) return TSF_E_ARG;
+    memset(out, 0, sizeof *out);
+    out->tiling = ctx->K;
+    out->micro_launches = ctx->prof_micro_n;
+    out->macro_launches = ctx->prof_macro_n;
+    out->micro_kernel_ms = ctx->prof_micro_ms;
+    out->macro_kernel_ms = ctx->prof_macro_ms;
+    if (!ctx->ws_valid) return TSF_OK;
+    CU(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const DevCtl& c = *ctx->ctl_host;
+    out->inner_iters = (int64_t)c.inner_iters;
+    out->dof_cg_iters = (int64_t)c.inner_iters * ctx->nm;
+    out->refine_sweeps = (int64_t)c.sweeps;
+    out->micro_solves = (int64_t)c.micro_solves;
+    out->macro_iters = (int64_t)c.macro_iters;
+    out->coupling_iters_last = c.coupling_iters_last;
+    out->coupling_iters_total = c.coupling_iters_total;
+    out->max_inner_iters = c.max_inner;
+    out->steps = c.steps;
+    out->status = c.status;
+    out->coupling_change = c.change;
+    return TSF_OK;
+}
+
+tsf_status tsf_reset_stats(tsf_ctx* ctx) {
+    if (!ctx) return TSF_E_ARG;
+    ctx->prof_micro_n = ctx->prof_macro_n = 0;
+    ctx->prof_micro_ms = ctx->prof_macro_ms = 0.0;
+    if (!ctx->ws_valid) return TSF_OK;
+    // keep geom_error, coupling_iter, cont; clear the counters and the status
+    CU(cudaMemsetAsync(ctx->ctl, 0, offsetof(DevCtl, coupling_iter), ctx->stream));
+    const int zero4[4] = {0, 0, 0, 0};
+    CU(cudaMemcpyAsync(&ctx->ctl->coupling_iters_total, zero4, 4 * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(&ctx->ctl->steps, zero4, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return TSF_OK;
+}
+
+}  // extern "C"

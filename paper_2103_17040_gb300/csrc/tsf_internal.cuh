@@ -1,0 +1,218 @@
+// tsf_internal.cuh -- device-side structures and helpers shared by the
+// kernels of the GB300 two-scale library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tsf {
+
+// Stencil planes of a Q1 operator on an (n1 x n1) node grid.  The operator is
+// symmetric, so only the couplings of node (p,q) to itself and to its
+// "forward" neighbours are stored:
+//   0: C (p,q)   1: E (p+1,q)   2: N (p,q+1)   3: NE (p+1,q+1)   4: NW (p-1,q+1)
+// The remaining four couplings are read from the neighbour that stores them:
+//   W = E(p-1,q), S = N(p,q-1), SW = NE(p-1,q-1), SE = NW(p+1,q-1).
+// Couplings to nodes outside the mesh are stored as zero.
+constexpr int kPlanes = 5;
+
+// Device status codes (same values as tsf_status).
+enum : int { kOk = 0, kNotConverged = 4, kNaN = 5, kBreakdown = 8, kBadJacobian = 3 };
+
+// Control and statistics block living in device memory.
+struct DevCtl {
+    unsigned long long inner_iters;   // inner CG iterations, summed over instances
+    unsigned long long sweeps;        // FP64 residual evaluations of micro problems
+    unsigned long long micro_solves;
+    unsigned long long macro_iters;
+    int coupling_iter;                // coupling iterations of the current step
+    int coupling_iters_total;
+    int coupling_iters_last;
+    int max_inner;
+    int status;                       // first device-side error, 0 if none
+    int steps;
+    int geom_error;                   // set by the geometry kernel on det F <= 0
+    int cont;                         // 1 while the coupling loop must go on
+    double change;                    // last relative change of u
+    double gamma_bar;                 // preconditioner value of |Gamma| (macro)
+};
+
+__device__ __forceinline__ void set_status(DevCtl* ctl, int code) {
+    atomicCAS(&ctl->status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide all-reduce of NV values.  blockDim.x must be a multiple of 32 and
+// at most 1024.  buf must hold NV*32 elements and must not be reused by the
+// block until every thread has returned from this call and passed one more
+// __syncthreads (callers alternate two buffers).  The summation order is
+// fixed (warp tree, then the warp partials in warp order through a second
+// warp tree), so every thread gets the same, reproducible value.
+// ---------------------------------------------------------------------------
+template <typename T, int NV>
+__device__ __forceinline__ void block_allreduce(T (&v)[NV], T* buf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) buf[i * 32 + warp] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T s = lane < nw ? buf[i * 32 + lane] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        v[i] = s;
+    }
+}
+
+// Error-free transformation a + b = s + e (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+    s = a + b;
+    double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated block sum of one double per thread (sum and running error
+// carried through the warp tree), result broadcast to all threads.
+__device__ __forceinline__ double block_sum_compensated(double x, double* buf /* 64 */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    double s = x, c = 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double so = __shfl_xor_sync(0xffffffffu, s, o);
+        double co = __shfl_xor_sync(0xffffffffu, c, o);
+        double t, e;
+        two_sum(s, so, t, e);
+        s = t;
+        c = c + co + e;
+    }
+    if (lane == 0) {
+        buf[warp] = s;
+        buf[32 + warp] = c;
+    }
+    __syncthreads();
+    s = lane < nw ? buf[lane] : 0.0;
+    c = lane < nw ? buf[32 + lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double so = __shfl_xor_sync(0xffffffffu, s, o);
+        double co = __shfl_xor_sync(0xffffffffu, c, o);
+        double t, e;
+        two_sum(s, so, t, e);
+        s = t;
+        c = c + co + e;
+    }
+    return s + c;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel argument blocks
+// ---------------------------------------------------------------------------
+struct GeomArgs {
+    int Nm, n1, nm, nmp, nM;
+    const double* prm5;     // [nM][5] general form (A11, A12, A21, A22, b)
+    double D11, D12, D22, kappa, dt;
+    double* M64;            // [nM][5][nmp] mass planes
+    double* S64;            // [nM][5][nmp] M/dt + A + kappa R planes
+    float* S32;             // [nM][5][nmp] S64 rounded to FP32
+    double* lm;             // [nM][nmp]    row sums of M (lumped mass)
+    double* redge;          // [nM][n1]     r = R 1 on the Robin edge nodes
+    double* Rd;             // [nM][n1]     diagonal of R on the edge
+    double* Ru;             // [nM][n1]     coupling of edge node q to q+1
+    DevCtl* ctl;
+};
+
+struct MicroArgs {
+    int n1, nm, nmp, W;     // W = n1 + 2: width of the zero-haloed shared-memory grid
+    int nM;
+    const float* S32;
+    const double* S64;
+    const double* c;        // [nM][nmp] right-hand side without the u term
+    double* v;              // [nM][nmp] in: initial guess, out: solution
+    const double* u;        // [nM] macro iterate
+    const double* redge;    // [nM][n1]
+    double kappa;
+    double tol;             // ||b - S v|| <= tol ||b|| (FP64 residual)
+    double inner_tol;       // mixed: relative tolerance of the FP32 inner solve
+    int maxit;              // cap on inner iterations per solve
+    int max_sweeps;         // mixed: cap on refinement sweeps
+    double* rho;            // [nM] out: r_i^T v_i
+    int* inst_iters;        // [nM] out: inner iterations of this solve
+    DevCtl* ctl;
+};
+
+struct PrologueArgs {
+    int n1, nm, nmp, nM;
+    double dt;
+    const double* M64;
+    const double* v;        // [nM][nmp] state v^n
+    const double* fv;       // [nM][nmp] or nullptr
+    const double* g;        // [nM][n1] or nullptr
+    const double* redge;
+    const double* Rd;
+    const double* Ru;
+    double* c;              // [nM][nmp] out
+    double* G;              // [nM] out: r_i^T g_i (0 if no g)
+};
+
+struct MacroArgs {
+    int NM, N1, nM, bc;
+    double H, dt, Du, kappa;
+    const double* gam;      // [nM] |Gamma_i|
+    const double* cH;       // [nM] macro right-hand side without the coupling term
+    const double* rho;      // [nM]
+    double* uk;             // [nM] macro iterate (in: previous, out: new)
+    double* u;              // [nM] committed state (written when the loop ends)
+    double* x; double* r; double* z; double* zo; double* p; double* q;  // [nM] scratch
+    double tol;
+    int maxit;
+    double coupling_tol;
+    int coupling_maxit;
+    int use_dct;            // fast-diagonalisation preconditioner (else Jacobi)
+    int set_cond;           // call cudaGraphSetConditional
+    cudaGraphConditionalHandle cond;
+    DevCtl* ctl;
+};
+
+struct MacroPrologueArgs {
+    int NM, N1, nM, bc;
+    double H, dt;
+    const double* u;        // committed state u^n
+    const double* fu;       // [nM] or nullptr
+    const double* ud;       // [nM] or nullptr
+    const double* G;        // [nM]
+    double* cH;             // out
+    double* uk;             // out: initial iterate (Dirichlet values applied)
+    DevCtl* ctl;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files; all enqueue on `stream`)
+// ---------------------------------------------------------------------------
+cudaError_t launch_expand_params(int family, int nparam, const double* in, double* prm5, int nM, cudaStream_t s);
+cudaError_t launch_geometry(const GeomArgs& a, cudaStream_t s);
+cudaError_t launch_instance_sums(int n1, int nm, int nmp, int nM, const double* lm, const double* redge,
+                                 double* gam, double* vol, cudaStream_t s);
+cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s);
+cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int K, cudaStream_t s);
+size_t micro_smem_bytes(int n1, int precision);
+int micro_threads(int nm, int K);
+cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s);
+cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s);
+size_t macro_smem_bytes(int N1, int bc, int use_dct);
+cudaError_t launch_vbar(int nm, int nmp, int nM, const double* lm, const double* vol, const double* v,
+                        double* vbar, cudaStream_t s);
+cudaError_t launch_flux(int n1, int nm, int nmp, int nM, double kappa, const double* gam, const double* u,
+                        const double* v, const double* redge, const double* g, double* flux, cudaStream_t s);
+cudaError_t configure_micro_kernels(int smem_optin);
+cudaError_t configure_macro_kernels(int smem_optin);
+
+}  // namespace tsf

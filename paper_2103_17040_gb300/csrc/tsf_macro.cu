@@ -1,0 +1,391 @@
+// tsf_macro.cu -- the macro solve that closes each coupling iteration, and the
+// coupling-loop control.
+//
+// Macro problem (first line of Eq. (17) with a time derivative, the coupling
+// integral lumped at the collocation nodes):
+//     (M_H/dt + Du K_H + kappa L Gam) u = M_H (u^n/dt + fu) - L G + kappa L rho
+// on a uniform NM x NM Q1 mesh of [0,1]^2.  The operator is applied matrix-free
+// from the node position alone: on a uniform square mesh every Q1 cell has the
+// same element matrices, so an entry of M_H or K_H is (number of cells shared
+// by the two nodes) x (the element entry), and L = diag(row sums of M_H) is
+// H^2 (cells around the node)/4.
+//
+// Solver: flexible preconditioned CG in FP64 (Sec. 3.5: CG for every system).
+// Preconditioner: exact fast diagonalisation of
+//     P = M_H/dt + Du K_H + kappa gamma_bar L
+// in FP32.  On a uniform mesh the 1D Q1 matrices M1, K1 and the lumped mass
+// H W are all diagonalised by the same cosine basis cos(pi j k/NM) (Neumann;
+// sine basis on the interior nodes for Dirichlet), so P^-1 is four dense
+// n x n transforms and one diagonal scaling.  With |Gamma_i| equal for all
+// nodes (bump families) P is the operator itself up to FP32 rounding and CG
+// needs two or three iterations.  Meshes too large for the shared-memory
+// transforms fall back to Jacobi.
+//
+// The macro problem is tiny (4225 unknowns for a 64x64 mesh), so it runs in a
+// single thread block; its cost is latency, not bandwidth.
+#include "tsf_internal.cuh"
+
+namespace tsf {
+
+__device__ __forceinline__ bool is_dir_node(int bc, int N, int p, int q) {
+    return bc == 1 && (p == 0 || q == 0 || p == N || q == N);
+}
+
+// (M_H/dt + Du K_H) x + kappa gam_k m_k x_k at node k = (p, q)
+__device__ __forceinline__ double macro_apply(const MacroArgs& a, const double* x, int k, int p, int q) {
+    const int N = a.NM, n1 = a.N1;
+    const double cx = (p == 0 || p == N) ? 1.0 : 2.0, cy = (q == 0 || q == N) ? 1.0 : 2.0;
+    const bool e = p < N, w = p > 0, nn = q < N, s = q > 0;
+    const double xc = x[k];
+    const double ew = (e ? x[k + 1] : 0.0) + (w ? x[k - 1] : 0.0);
+    const double ns = (nn ? x[k + n1] : 0.0) + (s ? x[k - n1] : 0.0);
+    const double dg = ((e && nn) ? x[k + n1 + 1] : 0.0) + ((w && nn) ? x[k + n1 - 1] : 0.0) +
+                      ((e && s) ? x[k - n1 + 1] : 0.0) + ((w && s) ? x[k - n1 - 1] : 0.0);
+    const double H2 = a.H * a.H;
+    const double Mx = (H2 / 36.0) * (4.0 * cx * cy * xc + 2.0 * cy * ew + 2.0 * cx * ns + dg);
+    const double Kx = (4.0 * cx * cy * xc - cy * ew - cx * ns - 2.0 * dg) / 6.0;
+    return Mx / a.dt + a.Du * Kx + a.kappa * a.gam[k] * (cx * cy * 0.25 * H2) * xc;
+}
+
+__device__ __forceinline__ double macro_diag(const MacroArgs& a, int k, int p, int q) {
+    const int N = a.NM;
+    const double cx = (p == 0 || p == N) ? 1.0 : 2.0, cy = (q == 0 || q == N) ? 1.0 : 2.0;
+    const double H2 = a.H * a.H;
+    return (H2 / 9.0) * cx * cy / a.dt + a.Du * (2.0 / 3.0) * cx * cy + a.kappa * a.gam[k] * cx * cy * 0.25 * H2;
+}
+
+// out = in * V (right) or V * in (left); np x np row-major, np even, 2x2
+// register blocks, V symmetric.
+__device__ void mm_pass(const float* __restrict__ in, float* __restrict__ out, const float* __restrict__ V, int np,
+                        bool left) {
+    const int nb = np >> 1, nblk = nb * nb;
+    for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
+        const int r0 = (blk / nb) * 2, c0 = (blk % nb) * 2;
+        float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+        if (!left) {
+            const float* x0 = in + r0 * np;
+            const float* x1 = x0 + np;
+            for (int m = 0; m < np; ++m) {
+                const float2 v = *reinterpret_cast<const float2*>(V + m * np + c0);
+                const float u0 = x0[m], u1 = x1[m];
+                a00 = fmaf(u0, v.x, a00);
+                a01 = fmaf(u0, v.y, a01);
+                a10 = fmaf(u1, v.x, a10);
+                a11 = fmaf(u1, v.y, a11);
+            }
+        } else {
+            const float* v0 = V + r0 * np;
+            const float* v1 = v0 + np;
+            for (int m = 0; m < np; ++m) {
+                const float2 x = *reinterpret_cast<const float2*>(in + m * np + c0);
+                const float w0 = v0[m], w1 = v1[m];
+                a00 = fmaf(w0, x.x, a00);
+                a01 = fmaf(w0, x.y, a01);
+                a10 = fmaf(w1, x.x, a10);
+                a11 = fmaf(w1, x.y, a11);
+            }
+        }
+        *reinterpret_cast<float2*>(out + r0 * np + c0) = make_float2(a00, a01);
+        *reinterpret_cast<float2*>(out + (r0 + 1) * np + c0) = make_float2(a10, a11);
+    }
+}
+
+struct DctView {
+    int n, np, off;     // transform size, padded size, node offset (1 for Dirichlet interior)
+    float *X0, *X1, *V, *lamM, *lamK, *Dn;
+    float gterm;        // kappa * gamma_bar * H^2
+};
+
+// z = P^{-1} r (fast diagonalisation, FP32 transforms).  All threads.
+__device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* r, double* z) {
+    const int n = d.n, np = d.np, n1 = a.N1;
+    for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+        const int rr = e / np, cc = e % np;
+        float val = 0.f;
+        if (rr < n && cc < n) val = (float)r[(cc + d.off) + n1 * (rr + d.off)];
+        d.X0[e] = val;
+    }
+    __syncthreads();
+    mm_pass(d.X0, d.X1, d.V, np, false);
+    __syncthreads();
+    mm_pass(d.X1, d.X0, d.V, np, true);
+    __syncthreads();
+    const float idt = (float)(1.0 / a.dt), Du = (float)a.Du;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int l = e / n, k = e % n;
+        const float lam = d.lamM[k] * d.lamM[l] * idt + Du * (d.lamK[k] * d.lamM[l] + d.lamM[k] * d.lamK[l]) +
+                          d.gterm;
+        d.X0[l * np + k] *= 1.0f / (d.Dn[l] * d.Dn[k] * lam);
+    }
+    __syncthreads();
+    mm_pass(d.X0, d.X1, d.V, np, false);
+    __syncthreads();
+    mm_pass(d.X1, d.X0, d.V, np, true);
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.nM; k += blockDim.x) {
+        const int p = k % n1, q = k / n1;
+        const int cc = p - d.off, rr = q - d.off;
+        z[k] = (cc >= 0 && rr >= 0 && cc < n && rr < n) ? (double)d.X0[rr * np + cc] : 0.0;
+    }
+    __syncthreads();
+}
+
+size_t macro_smem_bytes(int N1, int bc, int use_dct) {
+    size_t b = 4 * 96 * sizeof(double);
+    if (use_dct) {
+        const int n = bc ? N1 - 2 : N1;
+        const int np = (n + 1) & ~1;
+        b += (3 * (size_t)np * np + 3 * (size_t)np) * sizeof(float);
+    }
+    return b;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* red = reinterpret_cast<double*>(smem);  // 4 x 96
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int nM = a.nM, n1 = a.N1, N = a.NM;
+    int rb = 0;
+    auto nextbuf = [&]() { double* b = red + 96 * rb; rb = (rb + 1) & 3; return b; };
+    const int my_iter = a.ctl->coupling_iter;
+
+    DctView d{};
+    if (a.use_dct) {
+        d.n = a.bc ? N - 1 : N + 1;
+        d.off = a.bc ? 1 : 0;
+        d.np = (d.n + 1) & ~1;
+        float* f = reinterpret_cast<float*>(red + 4 * 96);
+        d.X0 = f;
+        d.X1 = f + d.np * d.np;
+        d.V = f + 2 * d.np * d.np;
+        d.lamM = f + 3 * d.np * d.np;
+        d.lamK = d.lamM + d.np;
+        d.Dn = d.lamK + d.np;
+        // basis: cos (Neumann) or sin (Dirichlet interior) of pi (a+off)(b+off)/N
+        for (int e = tid; e < d.np * d.np; e += T) {
+            const int r = e / d.np, c = e % d.np;
+            float v = 0.f;
+            if (r < d.n && c < d.n) {
+                const int m = ((r + d.off) * (c + d.off)) % (2 * N);
+                v = a.bc ? sinpif((float)m / (float)N) : cospif((float)m / (float)N);
+            }
+            d.V[e] = v;
+        }
+        const float H = (float)a.H;
+        for (int k = tid; k < d.n; k += T) {
+            const float ck = cospif((float)(k + d.off) / (float)N);
+            d.lamM[k] = (H / 6.f) * (4.f + 2.f * ck);
+            d.lamK[k] = (2.f / H) * (1.f - ck);
+            // sum_j w_j basis_j^2: N/2, doubled for the constant and alternating cosines
+            d.Dn[k] = 0.5f * (float)N * ((!a.bc && (k == 0 || k == N)) ? 2.f : 1.f);
+        }
+    }
+    // gamma_bar: mean |Gamma| over unknown (non-Dirichlet) nodes
+    {
+        double sg = 0.0, cnt = 0.0;
+        for (int k = tid; k < nM; k += T) {
+            if (!is_dir_node(a.bc, N, k % n1, k / n1)) {
+                sg += a.gam[k];
+                cnt += 1.0;
+            }
+        }
+        double t[2] = {sg, cnt};
+        block_allreduce<double, 2>(t, nextbuf());
+        d.gterm = (float)(a.kappa * (t[1] > 0 ? t[0] / t[1] : 1.0) * a.H * a.H);
+    }
+    // right-hand side and initial guess; b kept in q until the residual is formed
+    for (int k = tid; k < nM; k += T) {
+        const int p = k % n1, q = k / n1;
+        const double H2 = a.H * a.H;
+        const double cx = (p == 0 || p == N) ? 1.0 : 2.0, cy = (q == 0 || q == N) ? 1.0 : 2.0;
+        const double b = is_dir_node(a.bc, N, p, q) ? a.uk[k] : a.cH[k] + a.kappa * (cx * cy * 0.25 * H2) * a.rho[k];
+        a.q[k] = b;
+        a.x[k] = a.uk[k];
+    }
+    __syncthreads();
+    double bn2 = 0.0, rr = 0.0;
+    for (int k = tid; k < nM; k += T) {
+        const int p = k % n1, q = k / n1;
+        const double b = a.q[k];
+        const double res = is_dir_node(a.bc, N, p, q) ? 0.0 : b - macro_apply(a, a.x, k, p, q);
+        a.r[k] = res;
+        bn2 = fma(b, b, bn2);
+        rr = fma(res, res, rr);
+    }
+    {
+        double t[2] = {bn2, rr};
+        block_allreduce<double, 2>(t, nextbuf());
+        bn2 = t[0];
+        rr = t[1];
+    }
+    const double stop2 = a.tol * a.tol * bn2;
+    int it = 0;
+    bool fail = false;
+    if (rr > stop2 && bn2 > 0.0) {
+        // z = P r, p = z
+        if (a.use_dct) {
+            dct_precond(a, d, a.r, a.z);
+        } else {
+            for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, k, k % n1, k / n1);
+            __syncthreads();
+        }
+        double rz = 0.0;
+        for (int k = tid; k < nM; k += T) {
+            a.p[k] = a.z[k];
+            rz = fma(a.r[k], a.z[k], rz);
+        }
+        {
+            double t[1] = {rz};
+            block_allreduce<double, 1>(t, nextbuf());
+            rz = t[0];
+        }
+        while (it < a.maxit) {
+            double pq = 0.0;
+            for (int k = tid; k < nM; k += T) {
+                const int p = k % n1, q = k / n1;
+                const double y = is_dir_node(a.bc, N, p, q) ? 0.0 : macro_apply(a, a.p, k, p, q);
+                a.q[k] = y;
+                pq = fma(a.p[k], y, pq);
+            }
+            {
+                double t[1] = {pq};
+                block_allreduce<double, 1>(t, nextbuf());
+                pq = t[0];
+            }
+            ++it;
+            if (!(pq > 0.0)) {
+                fail = true;
+                break;
+            }
+            const double alpha = rz / pq;
+            rr = 0.0;
+            for (int k = tid; k < nM; k += T) {
+                a.x[k] = fma(alpha, a.p[k], a.x[k]);
+                const double rn = fma(-alpha, a.q[k], a.r[k]);
+                a.r[k] = rn;
+                a.zo[k] = a.z[k];
+                rr = fma(rn, rn, rr);
+            }
+            {
+                double t[1] = {rr};
+                block_allreduce<double, 1>(t, nextbuf());
+                rr = t[0];
+            }
+            if (!(rr == rr)) {
+                fail = true;
+                break;
+            }
+            if (rr <= stop2) break;
+            if (a.use_dct) {
+                dct_precond(a, d, a.r, a.z);
+            } else {
+                for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, k, k % n1, k / n1);
+                __syncthreads();
+            }
+            // flexible (Polak-Ribiere) beta: robust to the FP32 preconditioner
+            double rzn = 0.0, rzo = 0.0;
+            for (int k = tid; k < nM; k += T) {
+                rzn = fma(a.r[k], a.z[k], rzn);
+                rzo = fma(a.r[k], a.zo[k], rzo);
+            }
+            {
+                double t[2] = {rzn, rzo};
+                block_allreduce<double, 2>(t, nextbuf());
+                rzn = t[0];
+                rzo = t[1];
+            }
+            const double beta = (rzn - rzo) / rz;
+            rz = rzn;
+            for (int k = tid; k < nM; k += T) a.p[k] = fma(beta, a.p[k], a.z[k]);
+            __syncthreads();
+        }
+        if (!fail && rr > stop2) fail = true;
+    }
+
+    // coupling control: relative change of the macro iterate
+    double dn2 = 0.0, un2 = 0.0;
+    for (int k = tid; k < nM; k += T) {
+        const double xn = a.x[k];
+        const double dd = xn - a.uk[k];
+        dn2 = fma(dd, dd, dn2);
+        un2 = fma(xn, xn, un2);
+    }
+    {
+        double t[2] = {dn2, un2};
+        block_allreduce<double, 2>(t, nextbuf());
+        dn2 = t[0];
+        un2 = t[1];
+    }
+    const double change = un2 > 0.0 ? sqrt(dn2 / un2) : sqrt(dn2);
+    const int iter = my_iter + 1;
+    const bool converged = change <= a.coupling_tol;
+    const bool last = converged || iter >= a.coupling_maxit || !(change == change);
+    for (int k = tid; k < nM; k += T) {
+        const double xn = a.x[k];
+        a.uk[k] = xn;
+        if (last) a.u[k] = xn;
+    }
+    if (tid == 0) {
+        DevCtl* c = a.ctl;
+        c->macro_iters += (unsigned long long)it;
+        c->coupling_iter = iter;
+        c->change = change;
+        if (fail) set_status(c, kNotConverged);
+        if (!(change == change)) set_status(c, kNaN);
+        if (last) {
+            c->coupling_iters_last = iter;
+            c->coupling_iters_total += iter;
+            c->steps += 1;
+            if (!converged) set_status(c, kNotConverged);
+            c->cont = 0;
+        } else {
+            c->cont = 1;
+        }
+        if (a.set_cond) cudaGraphSetConditional(a.cond, last ? 0u : 1u);
+    }
+}
+
+cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s) {
+    const size_t sm = macro_smem_bytes(a.N1, a.bc, a.use_dct);
+    k_macro_solve<<<1, 1024, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t configure_macro_kernels(int smem_optin) {
+    return cudaFuncSetAttribute(k_macro_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+}
+
+// cH = M_H (u^n/dt + fu) - L G ; initial macro iterate with the Dirichlet values;
+// resets the per-step coupling counter.  One thread per macro node.
+__global__ void k_macro_prologue(MacroPrologueArgs a) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) {
+        a.ctl->coupling_iter = 0;
+        a.ctl->cont = 1;
+    }
+    if (k >= a.nM) return;
+    const int N = a.NM, n1 = a.N1;
+    const int p = k % n1, q = k / n1;
+    const double idt = 1.0 / a.dt;
+    auto w = [&](int l) { return a.fu ? fma(a.u[l], idt, a.fu[l]) : a.u[l] * idt; };
+    const double cx = (p == 0 || p == N) ? 1.0 : 2.0, cy = (q == 0 || q == N) ? 1.0 : 2.0;
+    const bool e = p < N, wst = p > 0, nn = q < N, s = q > 0;
+    const double ew = (e ? w(k + 1) : 0.0) + (wst ? w(k - 1) : 0.0);
+    const double ns = (nn ? w(k + n1) : 0.0) + (s ? w(k - n1) : 0.0);
+    const double dg = ((e && nn) ? w(k + n1 + 1) : 0.0) + ((wst && nn) ? w(k + n1 - 1) : 0.0) +
+                      ((e && s) ? w(k - n1 + 1) : 0.0) + ((wst && s) ? w(k - n1 - 1) : 0.0);
+    const double H2 = a.H * a.H;
+    const double Mw = (H2 / 36.0) * (4.0 * cx * cy * w(k) + 2.0 * cy * ew + 2.0 * cx * ns + dg);
+    const double m = cx * cy * 0.25 * H2;
+    a.cH[k] = Mw - m * a.G[k];
+    double uk = a.u[k];
+    if (is_dir_node(a.bc, N, p, q) && a.ud) uk = a.ud[k];
+    a.uk[k] = uk;
+}
+
+cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s) {
+    k_macro_prologue<<<(a.nM + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace tsf

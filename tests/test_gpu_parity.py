@@ -1,0 +1,279 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L2 over all nodes, u and v separately): 1e-10 for the
+FP64 path, 1e-8 for FP32 inner solves with FP64 refinement, both sides
+solving to a relative residual far below that.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-8
+
+
+def _T():
+    import paper_2103_17040_gb300 as T
+    T.load_library()
+    return T
+
+
+def rel(a, b):
+    a = np.ravel(np.asarray(a))
+    b = np.ravel(np.asarray(b))
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _pair(Nm, NM, family, prm, bc=0, D=(1.0, 0.0, 1.0), kappa=1.0, Du=1.0, precision=0, **opts):
+    T = _T()
+    o = dict(cg_tol=1e-13 if precision == 0 else 1e-11, coupling_tol=1e-13, macro_tol=1e-13)
+    o.update(opts)
+    P = T.TwoScale(Nm, NM, bc=bc, precision=precision, **o)
+    P.set_physics(D, kappa, Du)
+    P.set_deformation(family, prm)
+    R = oracle.Problem(Nm, NM, bc, family, prm, D=D, kappa=kappa, Du=Du)
+    return P, R
+
+
+GEOM_CASES = [(W.FAMILY_IDENTITY, 4), (W.FAMILY_BUMP, 6), (W.FAMILY_SHEAR_BUMP, 5), (W.FAMILY_AFFINE, 3),
+              (W.FAMILY_AFFINE_BUMP, 7)]
+
+
+@pytest.mark.parametrize("family,Nm", GEOM_CASES)
+def test_geometry_matches_oracle(family, Nm):
+    NM = 3
+    nM = (NM + 1) ** 2
+    prm = W.random_params(family, nM, seed=family)
+    P, R = _pair(Nm, NM, family, prm, D=(0.9, 0.1, 0.6), kappa=1.3)
+    gam, vol = P.geometry()
+    gr, vr, _ = R.geometry()
+    assert np.max(np.abs(gam - gr)) < 1e-13
+    assert np.max(np.abs(vol - vr)) < 1e-13
+
+
+STEP_CASES = [
+    # family, Nm, NM, bc, D, kappa, Du, nsteps
+    (W.FAMILY_BUMP, 8, 4, 0, (1.0, 0.0, 1.0), 1.0, 1.0, 2),
+    (W.FAMILY_SHEAR_BUMP, 7, 5, 0, (1.0, 0.0, 0.1), 1.5, 0.7, 2),     # ragged micro mesh, odd sizes
+    (W.FAMILY_AFFINE_BUMP, 13, 3, 1, (0.8, 0.2, 1.1), 0.5, 1.0, 2),  # Dirichlet macro, 196 DoFs
+    (W.FAMILY_AFFINE, 33, 2, 0, (1.0, 0.0, 1.0), 2.0, 1.3, 1),       # 1156 DoFs: several warps, K > 1
+    (W.FAMILY_BUMP, 1, 1, 0, (1.0, 0.0, 1.0), 1.0, 1.0, 1),          # degenerate: one cell on both scales
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", STEP_CASES)
+def test_step_matches_oracle(case, precision):
+    family, Nm, NM, bc, D, kappa, Du, nsteps = case
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(family, nM, seed=20 + Nm)
+    P, R = _pair(Nm, NM, family, prm, bc=bc, D=D, kappa=kappa, Du=Du, precision=precision)
+    u0, v0 = W.random_state(nM, nm, seed=5)
+    P.set_state(u0, v0)
+    R.set_state(u0, v0)
+    if bc == 1:
+        ud = W.rng(3).uniform(0.5, 1.5, nM)
+        P.set_sources(ud=ud)
+        R.set_sources(ud=ud)
+    dt = 0.01
+    P.step(dt, nsteps)
+    P.synchronize()
+    R.step(dt, nsteps, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13)
+    tol = FP64_TOL if precision == 0 else MIXED_TOL
+    assert rel(P.u(), R.u) < tol
+    assert rel(P.v(), R.v) < tol
+    assert rel(P.vbar(), R.vbar) < tol
+    assert rel(P.flux(), R.flux) < max(tol * 1e3, 1e-7) or np.max(np.abs(P.flux() - R.flux)) < 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_manufactured_config_matches_oracle(precision):
+    """8x8 macro / 8x8 micro, Dirichlet, bump a = 0.1 x1, manufactured sources,
+    dt = 0.01 x 10 steps (the plain FP64 workload)."""
+    from workloads import mms
+    w = W.c1()
+    a = w.params[:, 0]
+    P, R = _pair(w.Nm, w.NM, w.family, w.params, bc=1, precision=precision)
+    d0 = mms.nodal_data(w.NM, w.Nm, a, 0.0)
+    P.set_state(d0["u"], d0["v"].ravel())
+    R.set_state(d0["u"], d0["v"].ravel())
+    for n in range(w.nsteps):
+        d = mms.nodal_data(w.NM, w.Nm, a, (n + 1) * w.dt)
+        src = dict(fv=d["fv"].ravel(), g=d["g"].ravel(), fu=d["fu"], ud=d["ud"])
+        P.set_sources(**src)
+        R.set_sources(**src)
+        P.step(w.dt, 1)
+        R.step(w.dt, 1, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13)
+    P.synchronize()
+    tol = FP64_TOL if precision == 0 else MIXED_TOL
+    assert rel(P.u(), R.u) < tol
+    assert rel(P.v(), R.v) < tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_identity_instances_bitwise_identical(precision):
+    """Identity map, same initial micro field everywhere, kappa = 0 (the micro
+    right-hand sides do not see u): every micro problem does the same
+    arithmetic in the same order, so all instances agree bit for bit.  With
+    coupling, u is uniform only up to the rounding of the macro solve, and the
+    instances agree to that level."""
+    Nm, NM = 16, 6
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    T = _T()
+    yh1, _ = W.micro_coords(Nm)
+    for kappa in (0.0, 1.0):
+        P = T.TwoScale(Nm, NM, precision=precision, cg_tol=1e-12, coupling_tol=1e-12)
+        P.set_physics((1.0, 0.0, 1.0), kappa, 1.0)
+        P.set_deformation(W.FAMILY_IDENTITY, None)
+        P.set_state(np.full(nM, 0.7), np.tile(np.cos(np.pi * yh1), nM))
+        P.step(0.01, 3)
+        P.synchronize()
+        V = P.v()
+        u = P.u()
+        if kappa == 0.0:
+            assert np.array_equal(V, np.broadcast_to(V[0], V.shape))
+        else:
+            assert np.max(np.abs(V - V[0])) < 1e-12
+        assert np.max(np.abs(u - u[0])) < 1e-13 * abs(u[0])
+
+
+def test_graph_and_plain_launches_agree_bitwise():
+    NM, Nm = 4, 9
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_BUMP, nM, seed=3)
+    u0, v0 = W.random_state(nM, nm, seed=2)
+    T = _T()
+    out = []
+    for g in (1, 0):
+        P = T.TwoScale(Nm, NM, precision=1, use_graph=g, tiling=1)
+        P.set_deformation(W.FAMILY_BUMP, prm)
+        P.set_state(u0, v0)
+        P.step(0.005, 3)
+        P.synchronize()
+        out.append((P.u(), P.v(), P.stats()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2]["inner_iters"] == out[1][2]["inner_iters"]
+    assert out[0][2]["coupling_iters_total"] == out[1][2]["coupling_iters_total"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_all_tilings_agree(precision):
+    Nm, NM = 20, 3
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_SHEAR_BUMP, nM, seed=8)
+    u0, v0 = W.random_state(nM, nm, seed=9)
+    T = _T()
+    res = []
+    for t in range(4):
+        P = T.TwoScale(Nm, NM, precision=precision, tiling=t, cg_tol=1e-12, coupling_tol=1e-12)
+        P.set_deformation(W.FAMILY_SHEAR_BUMP, prm)
+        P.set_state(u0, v0)
+        P.step(0.01, 2)
+        P.synchronize()
+        assert P.stats()["tiling"] == 1 << t
+        res.append(P.v())
+    for r in res[1:]:
+        assert rel(r, res[0]) < 1e-9
+
+
+def test_mass_balance_on_gpu():
+    NM, Nm = 6, 10
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_SHEAR_BUMP, nM, seed=4)
+    P, R = _pair(Nm, NM, W.FAMILY_SHEAR_BUMP, prm, D=(1.0, 0.0, 0.1), kappa=1.2, precision=0)
+    u0, v0 = W.random_state(nM, nm, seed=6)
+    P.set_state(u0, v0)
+    _, vol = P.geometry()
+    _, _, mH = R.geometry()   # lumped macro mass (a closed form: H^2 cells/4)
+
+    def mass():
+        return mH @ P.u() + np.sum(mH * vol * P.vbar())
+
+    m0 = mass()
+    P.step(0.01, 4)
+    P.synchronize()
+    assert abs(mass() - m0) < 1e-11 * abs(m0)
+
+
+def test_full_size_step_matches_oracle():
+    """The benchmark workload at full size (64x64 macro, 32x32 micro, 4.6M
+    micro DoFs), mixed precision as timed by bench.py: one step against the
+    oracle on all outputs."""
+    w = W.c2()
+    T = _T()
+    P = T.TwoScale(w.Nm, w.NM, precision=T.TSF_MIXED, cg_tol=w.tol, coupling_tol=w.coupling_tol)
+    P.set_deformation(w.family, w.params)
+    P.set_state(w.u0, None)
+    P.step(w.dt, 1)
+    P.synchronize()
+    R = oracle.Problem(w.Nm, w.NM, w.bc, w.family, w.params)
+    R.set_state(w.u0, None)
+    R.step(w.dt, 1, cg_tol=1e-12, coupling_tol=1e-12, macro_tol=1e-13)
+    assert rel(P.u(), R.u) < 1e-8
+    assert rel(P.v(), R.v) < 1e-7
+    assert rel(P.vbar(), R.vbar) < 1e-7
+
+
+def test_bad_jacobian_is_rejected():
+    T = _T()
+    P = T.TwoScale(4, 2)
+    with pytest.raises(T.TsfError) as ei:
+        P.set_deformation(W.FAMILY_BUMP, np.full(9, 0.4))
+    assert ei.value.status == T.TSF_E_BAD_JACOBIAN
+
+
+def test_iteration_cap_reports_not_converged():
+    T = _T()
+    NM, Nm = 3, 12
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    P = T.TwoScale(Nm, NM, precision=0, cg_maxit=2, cg_tol=1e-14)
+    P.set_deformation(W.FAMILY_BUMP, W.random_params(1, nM, seed=1))
+    P.set_state(*W.random_state(nM, nm, seed=1))
+    P.step(0.01, 1)
+    with pytest.raises(T.TsfError) as ei:
+        P.synchronize()
+    assert ei.value.status == T.TSF_E_NOT_CONVERGED
+
+
+def test_argument_errors():
+    T = _T()
+    ctx = T.tsf_create(T.tsf_default_options())
+    try:
+        with pytest.raises(T.TsfError):
+            T.tsf_set_micro_mesh(ctx, 0, 0, 0)
+        with pytest.raises(T.TsfError):
+            T.tsf_set_micro_mesh(ctx, 4, 5, 0)
+        with pytest.raises(T.TsfError):
+            T.tsf_step(ctx, 0.01, 1)          # no meshes yet
+        T.tsf_set_micro_mesh(ctx, 4, 4, 0)
+        T.tsf_set_macro_mesh(ctx, 2, 2, 0, None)
+        with pytest.raises(T.TsfError):
+            T.tsf_set_physics(ctx, (1.0, 2.0, 1.0), 1.0, 1.0)   # D not SPD
+        with pytest.raises(T.TsfError):
+            T.tsf_set_deformation(ctx, 1, 2, np.zeros(18))      # wrong nparam
+    finally:
+        T.tsf_destroy(ctx)
+
+
+def test_device_tensors_in_and_out():
+    import torch
+    T = _T()
+    NM, Nm = 3, 5
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(1, nM, seed=2)
+    u0, v0 = W.random_state(nM, nm, seed=3)
+    A = T.TwoScale(Nm, NM, precision=0)
+    A.set_deformation(1, torch.tensor(prm, device="cuda"))
+    A.set_state(torch.tensor(u0, device="cuda"), torch.tensor(v0, device="cuda"))
+    A.step(0.01, 1)
+    out = torch.empty(nM, dtype=torch.float64, device="cuda")
+    A.u(out)
+    B = T.TwoScale(Nm, NM, precision=0, workspace=None)
+    B.set_deformation(1, prm)
+    B.set_state(u0, v0)
+    B.step(0.01, 1)
+    assert np.array_equal(out.cpu().numpy(), B.u())
