@@ -224,7 +224,7 @@ def run_gb300(args):
         "inner_iters_per_solve": st["inner_iters"] / max(st["micro_solves"], 1),
         "refine_sweeps_per_solve": st["refine_sweeps"] / max(st["micro_solves"], 1),
         "macro_iters_per_solve": st["macro_iters"] / max(st["coupling_iters_total"], 1),
-        "tiling_nodes_per_thread": st["tiling"],
+        "tiling": st["tiling"],
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -234,7 +234,7 @@ def run_gb300(args):
     opts.precision = T.TSF_MIXED if args.precision == "mixed" else T.TSF_FP64
     opts.cg_tol, opts.coupling_tol = w.tol, w.coupling_tol
     opts.use_graph, opts.profile = 0, 1
-    opts.tiling = {1: 0, 2: 1, 4: 2, 8: 3}[st["tiling"]]
+    opts.tiling = st["tiling"]
     opts.cuda_stream = stream.cuda_stream
     T.tsf_set_options(P.ctx, opts)
     P.reset_stats()

@@ -63,6 +63,7 @@ struct tsf_ctx {
     double *u = nullptr, *uk = nullptr, *cH = nullptr, *fu = nullptr, *ud = nullptr, *rho = nullptr,
            *out = nullptr;
     double *mx = nullptr, *mr = nullptr, *mz = nullptr, *mzo = nullptr, *mp = nullptr, *mq = nullptr;
+    double *res = nullptr, *res2 = nullptr, *u_used = nullptr, *uu2 = nullptr, *bnorm = nullptr;
     int* inst_iters = nullptr;
     DevCtl* ctl = nullptr;
     DevCtl* ctl_host = nullptr;  // pinned
@@ -72,8 +73,9 @@ struct tsf_ctx {
     double ops_dt = -1.0;
     bool ops_valid = false;
     bool has_fv = false, has_g = false, has_fu = false, has_ud = false;
-    int K = 0;                   // micro tiling (nodes per thread), 0 = not chosen
-    int K_prec = -1;             // precision the tiling was chosen for
+    int tiling = -1;             // micro-solve variant in use, -1 = not chosen
+    int tiling_prec = -1;        // precision it was chosen for
+    float tune_ms[kNumTilings] = {0};
     bool use_dct = false;
     // graph
     cudaGraph_t graph = nullptr;
@@ -119,7 +121,7 @@ static bool options_ok(const tsf_options* o) {
     return o && (o->precision == TSF_FP64 || o->precision == TSF_MIXED) && o->cg_tol >= 0 && o->inner_tol > 0 &&
            o->inner_tol < 1 && o->macro_tol >= 0 && o->coupling_tol >= 0 && o->cg_maxit > 0 && o->max_sweeps > 0 &&
            o->macro_maxit > 0 && o->coupling_maxit > 0 &&
-           (o->tiling == -1 || (o->tiling >= 0 && o->tiling <= 3));
+           (o->tiling == -1 || (o->tiling >= 0 && o->tiling < kNumTilings));
 }
 
 extern "C" {
@@ -185,7 +187,7 @@ tsf_status tsf_set_options(tsf_ctx* ctx, const tsf_options* opt) {
     const bool prec_changed = opt->precision != ctx->opt.precision;
     ctx->opt = *opt;
     ctx->opt.cuda_stream = keep;
-    if (prec_changed || opt->tiling >= 0) ctx->K = 0;
+    if (prec_changed || opt->tiling >= 0) ctx->tiling = -1;
     invalidate_graph(ctx);
     return TSF_OK;
 }
@@ -214,7 +216,7 @@ tsf_status tsf_set_micro_mesh(tsf_ctx* ctx, int nx, int ny, int robin_edge) {
     ctx->micro_set = true;
     ctx->ws_valid = false;
     ctx->geom_set = ctx->state_set = ctx->ops_valid = false;
-    ctx->K = 0;
+    ctx->tiling = -1;
     invalidate_graph(ctx);
     return TSF_OK;
 }
@@ -273,6 +275,11 @@ static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
     off[k++] = A.take(nM * n1 * sizeof(double));                 // g
     off[k++] = A.take(nM * sizeof(double));                      // G
     for (int r = 0; r < 13; ++r) off[k++] = A.take(nM * sizeof(double));  // u uk cH fu ud rho out mx mr mz mzo mp mq
+    off[k++] = A.take(nM * pl * sizeof(double));                 // res
+    off[k++] = A.take(nM * pl * sizeof(double));                 // res2 (tuning scratch)
+    off[k++] = A.take(nM * sizeof(double));                      // u_used
+    off[k++] = A.take(nM * sizeof(double));                      // uu2 (tuning scratch)
+    off[k++] = A.take(nM * 3 * sizeof(double));                  // bnorm
     off[k++] = A.take(nM * sizeof(int));                         // inst_iters
     off[k++] = A.take(sizeof(DevCtl));                           // ctl
 }
@@ -299,11 +306,16 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     double** r[13] = {&ctx->u, &ctx->uk, &ctx->cH, &ctx->fu, &ctx->ud, &ctx->rho, &ctx->out,
                       &ctx->mx, &ctx->mr, &ctx->mz, &ctx->mzo, &ctx->mp, &ctx->mq};
     for (int i = 0; i < 13; ++i) *r[i] = (double*)(b + off[k++]);
+    ctx->res = (double*)(b + off[k++]);
+    ctx->res2 = (double*)(b + off[k++]);
+    ctx->u_used = (double*)(b + off[k++]);
+    ctx->uu2 = (double*)(b + off[k++]);
+    ctx->bnorm = (double*)(b + off[k++]);
     ctx->inst_iters = (int*)(b + off[k++]);
     ctx->ctl = (DevCtl*)(b + off[k++]);
 }
 
-static constexpr int kNumBuffers = 16 + 13 + 2;
+static constexpr int kNumBuffers = 16 + 13 + 5 + 2;
 
 tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return TSF_E_ARG;
@@ -512,6 +524,9 @@ static MicroArgs micro_args(tsf_ctx* ctx, double* v) {
     a.rho = ctx->rho;
     a.inst_iters = ctx->inst_iters;
     a.ctl = ctx->ctl;
+    a.res = ctx->res;
+    a.u_used = ctx->u_used;
+    a.bnorm = ctx->bnorm;
     return a;
 }
 
@@ -548,58 +563,58 @@ static MacroArgs macro_args(tsf_ctx* ctx, double dt, bool set_cond, cudaGraphCon
 }
 
 static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt) {
+    MacroPrologueArgs m{};
+    m.NM = ctx->NM;
+    m.N1 = ctx->N1;
+    m.nM = ctx->nM;
+    m.bc = ctx->bc;
+    m.n1m = ctx->n1;
+    m.H = 1.0 / ctx->NM;
+    m.dt = dt;
+    m.u = ctx->u;
+    m.fu = ctx->has_fu ? ctx->fu : nullptr;
+    m.ud = ctx->has_ud ? ctx->ud : nullptr;
+    m.g = ctx->has_g ? ctx->g : nullptr;
+    m.redge = ctx->redge;
+    m.G = ctx->G;
+    m.cH = ctx->cH;
+    m.uk = ctx->uk;
+    m.ctl = ctx->ctl;
+    CU(launch_macro_prologue(m, ctx->stream));
     PrologueArgs p{};
     p.n1 = ctx->n1;
     p.nm = ctx->nm;
     p.nmp = ctx->nmp;
     p.nM = ctx->nM;
     p.dt = dt;
+    p.kappa = ctx->kappa;
     p.M64 = ctx->M64;
+    p.S64 = ctx->S64;
     p.v = ctx->v;
     p.fv = ctx->has_fv ? ctx->fv : nullptr;
     p.g = ctx->has_g ? ctx->g : nullptr;
     p.redge = ctx->redge;
     p.Rd = ctx->Rd;
     p.Ru = ctx->Ru;
+    p.u = ctx->uk;
     p.c = ctx->c;
-    p.G = ctx->G;
+    p.res = ctx->res;
+    p.u_used = ctx->u_used;
+    p.bnorm = ctx->bnorm;
     CU(launch_micro_prologue(p, ctx->stream));
-    MacroPrologueArgs m{};
-    m.NM = ctx->NM;
-    m.N1 = ctx->N1;
-    m.nM = ctx->nM;
-    m.bc = ctx->bc;
-    m.H = 1.0 / ctx->NM;
-    m.dt = dt;
-    m.u = ctx->u;
-    m.fu = ctx->has_fu ? ctx->fu : nullptr;
-    m.ud = ctx->has_ud ? ctx->ud : nullptr;
-    m.G = ctx->G;
-    m.cH = ctx->cH;
-    m.uk = ctx->uk;
-    m.ctl = ctx->ctl;
-    CU(launch_macro_prologue(m, ctx->stream));
     return TSF_OK;
 }
 
-static int tiling_K(int t) { return 1 << t; }  // tiling index -> nodes per thread
-
-static bool tiling_ok(tsf_ctx* ctx, int K) {
-    const int T = micro_threads(ctx->nm, K);
-    const int maxT = K <= 2 ? 1024 : (K == 4 ? 512 : 544);
-    return T <= maxT;
-}
-
-// Choose the micro tiling (nodes per thread K) by timing one solve of every
-// admissible variant on the actual problem (right-hand side of the current
-// step, warm start from the current state, written to a scratch copy).
+// Choose the micro-solve variant by timing one solve of every admissible
+// variant on the actual problem (right-hand side of the current step, warm
+// start from the current state, results written to scratch copies).
 static tsf_status autotune(tsf_ctx* ctx, double dt) {
     const int prec = ctx->opt.precision;
     if (ctx->opt.tiling >= 0) {
-        const int K = tiling_K(ctx->opt.tiling);
-        if (!tiling_ok(ctx, K)) return fail(ctx, TSF_E_ARG, "tiling %d does not fit this micro mesh", ctx->opt.tiling);
-        ctx->K = K;
-        ctx->K_prec = prec;
+        if (!tiling_fits(ctx->opt.tiling, prec, ctx->n1, ctx->smem_optin))
+            return fail(ctx, TSF_E_ARG, "tiling %d does not fit this micro mesh / precision", ctx->opt.tiling);
+        ctx->tiling = ctx->opt.tiling;
+        ctx->tiling_prec = prec;
         return TSF_OK;
     }
     DevCtl saved;
@@ -610,48 +625,67 @@ static tsf_status autotune(tsf_ctx* ctx, double dt) {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bestK = 0;
+    int best_t = -1;
     const size_t bytes = (size_t)ctx->nM * ctx->nmp * sizeof(double);
-    for (int t = 0; t < 4; ++t) {
-        const int K = tiling_K(t);
-        if (!tiling_ok(ctx, K)) continue;
+    for (int t = 0; t < kNumTilings; ++t) {
+        if (!tiling_fits(t, prec, ctx->n1, ctx->smem_optin)) continue;
         MicroArgs a = micro_args(ctx, ctx->vtmp);
+        a.res = ctx->res2;
+        a.u_used = ctx->uu2;
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {
             CU(cudaMemcpyAsync(ctx->vtmp, ctx->v, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            CU(cudaMemcpyAsync(ctx->res2, ctx->res, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            CU(cudaMemcpyAsync(ctx->uu2, ctx->u_used, ctx->nM * sizeof(double), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
             CU(cudaEventRecord(e0, ctx->stream));
-            CU(launch_micro_solve(a, prec, K, ctx->stream));
+            CU(launch_micro_solve(a, prec, t, ctx->stream));
             CU(cudaEventRecord(e1, ctx->stream));
             CU(cudaEventSynchronize(e1));
             CU(cudaEventElapsedTime(&ms, e0, e1));
         }
+        ctx->tune_ms[t] = ms;
         if (ms < best) {
             best = ms;
-            bestK = K;
+            best_t = t;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CU(cudaMemcpyAsync(ctx->ctl, &saved, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    if (!bestK) return fail(ctx, TSF_E_ARG, "no micro tiling fits this mesh");
-    ctx->K = bestK;
-    ctx->K_prec = prec;
+    if (best_t < 0) return fail(ctx, TSF_E_ARG, "no micro-solve variant fits this mesh");
+    ctx->tiling = best_t;
+    ctx->tiling_prec = prec;
     return TSF_OK;
+}
+
+// A capture that fails part-way can leave the graph (and the conditional
+// node's body) in a state the runtime does not promise to destroy cleanly, so
+// a failed capture abandons its graph instead of destroying it.
+static tsf_status capture_failed(tsf_ctx* ctx, tsf_status st, cudaError_t e, const char* what) {
+    ctx->graph = nullptr;
+    ctx->gexec = nullptr;
+    ctx->graph_valid = false;
+    cudaGetLastError();
+    if (st) return st;
+    return fail(ctx, TSF_E_CUDA, "graph capture failed at %s: %s", what, cudaGetErrorString(e));
 }
 
 static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
     invalidate_graph(ctx);
     CU(cudaGraphCreate(&ctx->graph, 0));
     cudaGraphConditionalHandle cond;
-    CU(cudaGraphConditionalHandleCreate(&cond, ctx->graph, 1, cudaGraphCondAssignDefault));
-    CU(cudaStreamBeginCaptureToGraph(ctx->stream, ctx->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, ctx->graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "conditional handle");
+    e = cudaStreamBeginCaptureToGraph(ctx->stream, ctx->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "begin capture");
     tsf_status st = enqueue_prologue(ctx, dt);
     cudaStreamCaptureStatus cs;
     cudaGraph_t capg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &capg, &deps, nullptr, &ndeps);
+    e = cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &capg, &deps, nullptr, &ndeps);
     cudaGraphNode_t cnode = nullptr;
     cudaGraph_t body = nullptr;
     if (!st && e == cudaSuccess) {
@@ -670,17 +704,17 @@ static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
     }
     cudaGraph_t endg = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &endg);
-    if (st) return st;
-    CU(e);
-    CU(e2);
-    CU(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (st || e != cudaSuccess || e2 != cudaSuccess)
+        return capture_failed(ctx, st, e != cudaSuccess ? e : e2, "prologue / conditional node");
+    e = cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "begin body capture");
     MicroArgs ma = micro_args(ctx, ctx->v);
-    e = launch_micro_solve(ma, ctx->opt.precision, ctx->K, ctx->stream);
+    e = launch_micro_solve(ma, ctx->opt.precision, ctx->tiling, ctx->stream);
     if (e == cudaSuccess) e = launch_macro_solve(macro_args(ctx, dt, true, cond), ctx->stream);
     e2 = cudaStreamEndCapture(ctx->stream, &body);
-    CU(e);
-    CU(e2);
-    CU(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+    if (e != cudaSuccess || e2 != cudaSuccess) return capture_failed(ctx, TSF_OK, e != cudaSuccess ? e : e2, "body");
+    e = cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0);
+    if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "instantiate");
     ctx->graph_valid = true;
     ctx->graph_dt = dt;
     return TSF_OK;
@@ -698,9 +732,12 @@ tsf_status tsf_step(tsf_ctx* ctx, double dt, int nsteps) {
         invalidate_graph(ctx);
     }
     ctx->use_dct = macro_smem_bytes(ctx->N1, ctx->bc, 1) <= (size_t)ctx->smem_optin;
-    if (micro_smem_bytes(ctx->n1, ctx->opt.precision) > (size_t)ctx->smem_optin)
-        return fail(ctx, TSF_E_ARG, "micro mesh too large for one thread block in this precision");
-    if (ctx->K == 0 || ctx->K_prec != ctx->opt.precision) {
+    {
+        bool any = false;
+        for (int t = 0; t < kNumTilings; ++t) any = any || tiling_fits(t, ctx->opt.precision, ctx->n1, ctx->smem_optin);
+        if (!any) return fail(ctx, TSF_E_ARG, "micro mesh too large for one thread block in this precision");
+    }
+    if (ctx->tiling < 0 || ctx->tiling_prec != ctx->opt.precision) {
         tsf_status st = autotune(ctx, dt);
         if (st) return st;
         invalidate_graph(ctx);
@@ -722,7 +759,7 @@ tsf_status tsf_step(tsf_ctx* ctx, double dt, int nsteps) {
         if (st) return st;
         for (int it = 0; it < ctx->opt.coupling_maxit; ++it) {
             if (prof) CU(cudaEventRecord(ctx->ev[0], ctx->stream));
-            CU(launch_micro_solve(micro_args(ctx, ctx->v), ctx->opt.precision, ctx->K, ctx->stream));
+            CU(launch_micro_solve(micro_args(ctx, ctx->v), ctx->opt.precision, ctx->tiling, ctx->stream));
             if (prof) CU(cudaEventRecord(ctx->ev[1], ctx->stream));
             cudaGraphConditionalHandle none{};
             CU(launch_macro_solve(macro_args(ctx, dt, false, none), ctx->stream));
@@ -808,7 +845,7 @@ tsf_status tsf_get_geometry(tsf_ctx* ctx, double* gamma_out, double* vol_out, in
 tsf_status tsf_get_stats(tsf_ctx* ctx, tsf_stats* out) {
     if (!ctx || !out) return TSF_E_ARG;
     memset(out, 0, sizeof *out);
-    out->tiling = ctx->K;
+    out->tiling = ctx->tiling;
     out->micro_launches = ctx->prof_micro_n;
     out->macro_launches = ctx->prof_macro_n;
     out->micro_kernel_ms = ctx->prof_micro_ms;

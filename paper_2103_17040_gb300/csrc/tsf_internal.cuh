@@ -147,20 +147,28 @@ struct MicroArgs {
     double* rho;            // [nM] out: r_i^T v_i
     int* inst_iters;        // [nM] out: inner iterations of this solve
     DevCtl* ctl;
+    // stored-residual protocol of the column-strip kernel:
+    double* res;            // [nM][nmp] FP64 residual b(u_used) - S v of the current iterate
+    double* u_used;         // [nM] macro value the stored residual belongs to
+    const double* bnorm;    // [nM][3] ||c||^2, c^T r, ||r||^2 (so ||b(u)||^2 is a quadratic in u)
 };
 
 struct PrologueArgs {
     int n1, nm, nmp, nM;
-    double dt;
+    double dt, kappa;
     const double* M64;
+    const double* S64;
     const double* v;        // [nM][nmp] state v^n
     const double* fv;       // [nM][nmp] or nullptr
     const double* g;        // [nM][n1] or nullptr
     const double* redge;
     const double* Rd;
     const double* Ru;
-    double* c;              // [nM][nmp] out
-    double* G;              // [nM] out: r_i^T g_i (0 if no g)
+    const double* u;        // [nM] initial macro iterate of the step
+    double* c;              // [nM][nmp] out: M (v/dt + fv) + R g
+    double* res;            // [nM][nmp] out: c + kappa u r - S v
+    double* u_used;         // [nM] out: u
+    double* bnorm;          // [nM][3] out
 };
 
 struct MacroArgs {
@@ -183,12 +191,14 @@ struct MacroArgs {
 };
 
 struct MacroPrologueArgs {
-    int NM, N1, nM, bc;
+    int NM, N1, nM, bc, n1m;  // n1m: micro nodes per side (Robin edge length in nodes)
     double H, dt;
     const double* u;        // committed state u^n
     const double* fu;       // [nM] or nullptr
     const double* ud;       // [nM] or nullptr
-    const double* G;        // [nM]
+    const double* g;        // [nM][n1m] Robin data or nullptr
+    const double* redge;    // [nM][n1m]
+    double* G;              // out: r_i^T g_i (compensated; 0 without g)
     double* cH;             // out
     double* uk;             // out: initial iterate (Dirichlet values applied)
     DevCtl* ctl;
@@ -202,9 +212,13 @@ cudaError_t launch_geometry(const GeomArgs& a, cudaStream_t s);
 cudaError_t launch_instance_sums(int n1, int nm, int nmp, int nM, const double* lm, const double* redge,
                                  double* gam, double* vol, cudaStream_t s);
 cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s);
-cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int K, cudaStream_t s);
-size_t micro_smem_bytes(int n1, int precision);
-int micro_threads(int nm, int K);
+// Micro-solve variants ("tilings"):
+//   0..3  shared-memory stencil, K = 1, 2, 4, 8 nodes per thread (strided), FP64 or mixed
+//   4..6  column strips of R = 2, 4, 6 nodes with register stencils, mixed only
+constexpr int kNumTilings = 7;
+bool tiling_fits(int tiling, int precision, int n1, int smem_optin);
+cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cudaStream_t s);
+bool tiling_uses_stored_residual(int tiling);
 cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s);
 cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s);
 size_t macro_smem_bytes(int N1, int bc, int use_dct);

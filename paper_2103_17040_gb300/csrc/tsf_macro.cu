@@ -31,27 +31,38 @@ __device__ __forceinline__ bool is_dir_node(int bc, int N, int p, int q) {
     return bc == 1 && (p == 0 || q == 0 || p == N || q == N);
 }
 
-// (M_H/dt + Du K_H) x + kappa gam_k m_k x_k at node k = (p, q)
-__device__ __forceinline__ double macro_apply(const MacroArgs& a, const double* x, int k, int p, int q) {
+// Entries of M_H/dt + Du K_H on the uniform mesh: with Me = H^2/36 [4 2 2 1]
+// and Ke = 1/6 [4 -1 -1 -2] (self, edge neighbour, edge neighbour, diagonal
+// neighbour of a cell), a node shared by cx x cy cells gets
+//   cx cy A0 on the diagonal, cy A1 to E/W, cx A1 to N/S, A2 to diagonals,
+// plus kappa |Gam_k| m_k with the lumped mass m_k = cx cy H^2 / 4.
+struct MacroCoef {
+    double A0, A1, A2, km;
+};
+
+__device__ __forceinline__ MacroCoef macro_coef(const MacroArgs& a) {
+    const double h36 = a.H * a.H / (36.0 * a.dt);
+    return {4.0 * h36 + (4.0 / 6.0) * a.Du, 2.0 * h36 - a.Du / 6.0, h36 - a.Du / 3.0, 0.25 * a.kappa * a.H * a.H};
+}
+
+// (M_H/dt + Du K_H + kappa L Gam) x at node k = (p, q)
+__device__ __forceinline__ double macro_apply(const MacroArgs& a, const MacroCoef& m, const double* x, int k, int p,
+                                              int q) {
     const int N = a.NM, n1 = a.N1;
     const double cx = (p == 0 || p == N) ? 1.0 : 2.0, cy = (q == 0 || q == N) ? 1.0 : 2.0;
     const bool e = p < N, w = p > 0, nn = q < N, s = q > 0;
-    const double xc = x[k];
     const double ew = (e ? x[k + 1] : 0.0) + (w ? x[k - 1] : 0.0);
     const double ns = (nn ? x[k + n1] : 0.0) + (s ? x[k - n1] : 0.0);
     const double dg = ((e && nn) ? x[k + n1 + 1] : 0.0) + ((w && nn) ? x[k + n1 - 1] : 0.0) +
                       ((e && s) ? x[k - n1 + 1] : 0.0) + ((w && s) ? x[k - n1 - 1] : 0.0);
-    const double H2 = a.H * a.H;
-    const double Mx = (H2 / 36.0) * (4.0 * cx * cy * xc + 2.0 * cy * ew + 2.0 * cx * ns + dg);
-    const double Kx = (4.0 * cx * cy * xc - cy * ew - cx * ns - 2.0 * dg) / 6.0;
-    return Mx / a.dt + a.Du * Kx + a.kappa * a.gam[k] * (cx * cy * 0.25 * H2) * xc;
+    const double diag = cx * cy * fma(m.km, a.gam[k], m.A0);
+    return fma(diag, x[k], fma(m.A1, fma(cy, ew, cx * ns), m.A2 * dg));
 }
 
-__device__ __forceinline__ double macro_diag(const MacroArgs& a, int k, int p, int q) {
+__device__ __forceinline__ double macro_diag(const MacroArgs& a, const MacroCoef& m, int k, int p, int q) {
     const int N = a.NM;
     const double cx = (p == 0 || p == N) ? 1.0 : 2.0, cy = (q == 0 || q == N) ? 1.0 : 2.0;
-    const double H2 = a.H * a.H;
-    return (H2 / 9.0) * cx * cy / a.dt + a.Du * (2.0 / 3.0) * cx * cy + a.kappa * a.gam[k] * cx * cy * 0.25 * H2;
+    return cx * cy * fma(m.km, a.gam[k], m.A0);
 }
 
 // out = in * V (right) or V * in (left); np x np row-major, np even, 2x2
@@ -130,6 +141,9 @@ __device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* 
     __syncthreads();
 }
 
+// one block of this many threads runs the macro solve (launch and launch bounds)
+constexpr int kMacroThreads = 512;
+
 size_t macro_smem_bytes(int N1, int bc, int use_dct) {
     size_t b = 4 * 96 * sizeof(double);
     if (use_dct) {
@@ -140,7 +154,7 @@ size_t macro_smem_bytes(int N1, int bc, int use_dct) {
     return b;
 }
 
-__global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
+__global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     double* red = reinterpret_cast<double*>(smem);  // 4 x 96
     const int tid = threadIdx.x, T = blockDim.x;
@@ -148,6 +162,7 @@ __global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
     int rb = 0;
     auto nextbuf = [&]() { double* b = red + 96 * rb; rb = (rb + 1) & 3; return b; };
     const int my_iter = a.ctl->coupling_iter;
+    const MacroCoef mc = macro_coef(a);
 
     DctView d{};
     if (a.use_dct) {
@@ -180,18 +195,19 @@ __global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
             d.Dn[k] = 0.5f * (float)N * ((!a.bc && (k == 0 || k == N)) ? 2.f : 1.f);
         }
     }
-    // gamma_bar: mean |Gamma| over unknown (non-Dirichlet) nodes
+    // gamma_bar: mean |Gamma| over unknown (non-Dirichlet) nodes (FP32: it
+    // only enters the preconditioner)
     {
-        double sg = 0.0, cnt = 0.0;
+        float sg = 0.f, cnt = 0.f;
         for (int k = tid; k < nM; k += T) {
             if (!is_dir_node(a.bc, N, k % n1, k / n1)) {
-                sg += a.gam[k];
-                cnt += 1.0;
+                sg += (float)a.gam[k];
+                cnt += 1.f;
             }
         }
-        double t[2] = {sg, cnt};
-        block_allreduce<double, 2>(t, nextbuf());
-        d.gterm = (float)(a.kappa * (t[1] > 0 ? t[0] / t[1] : 1.0) * a.H * a.H);
+        float t[2] = {sg, cnt};
+        block_allreduce<float, 2>(t, reinterpret_cast<float*>(nextbuf()));
+        d.gterm = (float)a.kappa * (t[1] > 0.f ? t[0] / t[1] : 1.f) * (float)(a.H * a.H);
     }
     // right-hand side and initial guess; b kept in q until the residual is formed
     for (int k = tid; k < nM; k += T) {
@@ -203,30 +219,32 @@ __global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
         a.x[k] = a.uk[k];
     }
     __syncthreads();
-    double bn2 = 0.0, rr = 0.0;
+    // stopping norms in FP32 (they only decide when to stop; vectors, operator
+    // and CG coefficients stay FP64)
+    float bn2 = 0.f, rr = 0.f;
     for (int k = tid; k < nM; k += T) {
         const int p = k % n1, q = k / n1;
         const double b = a.q[k];
-        const double res = is_dir_node(a.bc, N, p, q) ? 0.0 : b - macro_apply(a, a.x, k, p, q);
+        const double res = is_dir_node(a.bc, N, p, q) ? 0.0 : b - macro_apply(a, mc, a.x, k, p, q);
         a.r[k] = res;
-        bn2 = fma(b, b, bn2);
-        rr = fma(res, res, rr);
+        bn2 = fmaf((float)b, (float)b, bn2);
+        rr = fmaf((float)res, (float)res, rr);
     }
     {
-        double t[2] = {bn2, rr};
-        block_allreduce<double, 2>(t, nextbuf());
+        float t[2] = {bn2, rr};
+        block_allreduce<float, 2>(t, reinterpret_cast<float*>(nextbuf()));
         bn2 = t[0];
         rr = t[1];
     }
-    const double stop2 = a.tol * a.tol * bn2;
+    const float stop2 = (float)(a.tol * a.tol) * bn2;
     int it = 0;
     bool fail = false;
-    if (rr > stop2 && bn2 > 0.0) {
+    if (rr > stop2 && bn2 > 0.f) {
         // z = P r, p = z
         if (a.use_dct) {
             dct_precond(a, d, a.r, a.z);
         } else {
-            for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, k, k % n1, k / n1);
+            for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, mc, k, k % n1, k / n1);
             __syncthreads();
         }
         double rz = 0.0;
@@ -243,7 +261,7 @@ __global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
             double pq = 0.0;
             for (int k = tid; k < nM; k += T) {
                 const int p = k % n1, q = k / n1;
-                const double y = is_dir_node(a.bc, N, p, q) ? 0.0 : macro_apply(a, a.p, k, p, q);
+                const double y = is_dir_node(a.bc, N, p, q) ? 0.0 : macro_apply(a, mc, a.p, k, p, q);
                 a.q[k] = y;
                 pq = fma(a.p[k], y, pq);
             }
@@ -258,17 +276,17 @@ __global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
                 break;
             }
             const double alpha = rz / pq;
-            rr = 0.0;
+            rr = 0.f;
             for (int k = tid; k < nM; k += T) {
                 a.x[k] = fma(alpha, a.p[k], a.x[k]);
                 const double rn = fma(-alpha, a.q[k], a.r[k]);
                 a.r[k] = rn;
                 a.zo[k] = a.z[k];
-                rr = fma(rn, rn, rr);
+                rr = fmaf((float)rn, (float)rn, rr);
             }
             {
-                double t[1] = {rr};
-                block_allreduce<double, 1>(t, nextbuf());
+                float t[1] = {rr};
+                block_allreduce<float, 1>(t, reinterpret_cast<float*>(nextbuf()));
                 rr = t[0];
             }
             if (!(rr == rr)) {
@@ -279,7 +297,7 @@ __global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
             if (a.use_dct) {
                 dct_precond(a, d, a.r, a.z);
             } else {
-                for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, k, k % n1, k / n1);
+                for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, mc, k, k % n1, k / n1);
                 __syncthreads();
             }
             // flexible (Polak-Ribiere) beta: robust to the FP32 preconditioner
@@ -303,20 +321,20 @@ __global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
     }
 
     // coupling control: relative change of the macro iterate
-    double dn2 = 0.0, un2 = 0.0;
+    float dn2 = 0.f, un2 = 0.f;
     for (int k = tid; k < nM; k += T) {
         const double xn = a.x[k];
-        const double dd = xn - a.uk[k];
-        dn2 = fma(dd, dd, dn2);
-        un2 = fma(xn, xn, un2);
+        const float dd = (float)(xn - a.uk[k]);
+        dn2 = fmaf(dd, dd, dn2);
+        un2 = fmaf((float)xn, (float)xn, un2);
     }
     {
-        double t[2] = {dn2, un2};
-        block_allreduce<double, 2>(t, nextbuf());
+        float t[2] = {dn2, un2};
+        block_allreduce<float, 2>(t, reinterpret_cast<float*>(nextbuf()));
         dn2 = t[0];
         un2 = t[1];
     }
-    const double change = un2 > 0.0 ? sqrt(dn2 / un2) : sqrt(dn2);
+    const double change = un2 > 0.f ? sqrt((double)dn2 / (double)un2) : sqrt((double)dn2);
     const int iter = my_iter + 1;
     const bool converged = change <= a.coupling_tol;
     const bool last = converged || iter >= a.coupling_maxit || !(change == change);
@@ -347,7 +365,7 @@ __global__ void __launch_bounds__(1024, 1) k_macro_solve(MacroArgs a) {
 
 cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s) {
     const size_t sm = macro_smem_bytes(a.N1, a.bc, a.use_dct);
-    k_macro_solve<<<1, 1024, sm, s>>>(a);
+    k_macro_solve<<<1, kMacroThreads, sm, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -377,7 +395,22 @@ __global__ void k_macro_prologue(MacroPrologueArgs a) {
     const double H2 = a.H * a.H;
     const double Mw = (H2 / 36.0) * (4.0 * cx * cy * w(k) + 2.0 * cy * ew + 2.0 * cx * ns + dg);
     const double m = cx * cy * 0.25 * H2;
-    a.cH[k] = Mw - m * a.G[k];
+    // G_k = int_Gamma g = r_k^T g_k (compensated sum over the Robin-edge nodes)
+    double G = 0.0;
+    if (a.g) {
+        const double* r = a.redge + (size_t)k * a.n1m;
+        const double* g = a.g + (size_t)k * a.n1m;
+        double c = 0.0;
+        for (int j = 0; j < a.n1m; ++j) {
+            double sum, err;
+            two_sum(G, r[j] * g[j], sum, err);
+            G = sum;
+            c += err + fma(r[j], g[j], -(r[j] * g[j]));
+        }
+        G += c;
+    }
+    a.G[k] = G;
+    a.cH[k] = Mw - m * G;
     double uk = a.u[k];
     if (is_dir_node(a.bc, N, p, q) && a.ud) uk = a.ud[k];
     a.uk[k] = uk;

@@ -346,12 +346,12 @@ __global__ void __launch_bounds__(MaxThreads<K>::value) k_micro_solve(MicroArgs 
 #undef JJ
 }
 
-int micro_threads(int nm, int K) {
+static int smem_threads(int nm, int K) {
     int t = (nm + K - 1) / K;
     return (t + 31) / 32 * 32;
 }
 
-size_t micro_smem_bytes(int n1, int precision) {
+static size_t smem_kernel_bytes(int n1, int precision) {
     const size_t W = (size_t)n1 + 2;
     const size_t ti = precision == 0 ? sizeof(double) : sizeof(float);
     size_t off = (kPlanes + 1) * W * W * ti;
@@ -360,12 +360,410 @@ size_t micro_smem_bytes(int n1, int precision) {
 }
 
 template <typename TI, bool MIXED, int K>
-static cudaError_t launch_one(const MicroArgs& a, cudaStream_t s) {
-    const int T = micro_threads(a.nm, K);
+static cudaError_t launch_smem(const MicroArgs& a, cudaStream_t s) {
+    const int T = smem_threads(a.nm, K);
     if (T > MaxThreads<K>::value) return cudaErrorInvalidConfiguration;
-    const size_t sm = micro_smem_bytes(a.n1, MIXED ? 1 : 0);
-    k_micro_solve<TI, MIXED, K><<<a.nM, T, sm, s>>>(a);
+    k_micro_solve<TI, MIXED, K><<<a.nM, T, smem_kernel_bytes(a.n1, MIXED ? 1 : 0), s>>>(a);
     return cudaGetLastError();
+}
+
+// ===========================================================================
+// Column-strip variant (mixed precision).
+//
+// Thread t owns R consecutive nodes of one column of the micro grid:
+// p = t mod n1, rows q0 .. q0+R-1 with q0 = R (t div n1).  The inner FP32 CG
+// runs on the symmetrically Jacobi-scaled operator  S^ = D^-1/2 S D^-1/2
+// (unit diagonal, so the Jacobi preconditioner becomes the identity and
+// z = r): the eight off-diagonal couplings of every node, scaled once with
+// the diagonals of both end nodes, sit in registers for the whole solve, and
+// the search direction of a CG iteration reaches the neighbours through one
+// zero-haloed shared-memory plane: per iteration a thread stores R values and
+// loads its two neighbour columns (2R + 4 values) plus two halo values of its
+// own column, about 3 shared loads per node.
+//
+// FP64 refinement without recomputing b - S v from scratch: the residual of
+// the current iterate is kept in global memory (written by the step prologue
+// and by every solve), so a solve starts from
+//     r = res + kappa (u_i - u_used_i) r_i          (only Robin-edge nodes change)
+// and after each FP32 correction d updates it in FP64 as r -= S64 d, v += d.
+// A micro problem whose residual already meets the tolerance returns before
+// staging anything.  ||b(u)||^2 = ||c||^2 + 2 kappa u c^T r + kappa^2 u^2 ||r||^2
+// comes from three per-instance scalars of the prologue.  Convergence tests
+// use norms accumulated in FP32 from the FP64 residual values (a norm only
+// decides when to stop; the residual itself stays FP64).
+// ===========================================================================
+template <int R>
+struct StripMaxThreads {
+    static constexpr int value = R <= 2 ? 640 : 512;
+};
+
+__host__ __device__ inline int strip_rows(int n1, int R) { return (n1 + R - 1) / R; }
+
+static int strip_threads(int n1, int R) {
+    const int t = n1 * strip_rows(n1, R);
+    return (t + 31) / 32 * 32;
+}
+
+static size_t strip_smem_bytes(int n1, int R) {
+    const size_t W = (size_t)n1 + 2, H = (size_t)strip_rows(n1, R) * R + 2;
+    size_t off = (W * H * sizeof(float) + 15) & ~(size_t)15;
+    return off + 4 * 64 * sizeof(float);
+}
+
+// The eight scaled off-diagonal couplings of one node.
+struct Couple8 {
+    float E, W, N, S, NE, NW, SE, SW;
+};
+
+// y_k = (S^ x)_k = x_k + off-diagonal part, for the R nodes of a strip: x of
+// the own column in registers, neighbour columns and the own column's halo
+// from the shared plane P.
+template <int R>
+__device__ __forceinline__ void strip_apply(const Couple8 (&c)[R], const float (&x)[R], const float* P, int Wd,
+                                            int p, int q0, float (&y)[R]) {
+    float L[R + 2], Rt[R + 2];
+#pragma unroll
+    for (int m = 0; m < R + 2; ++m) {
+        const float* row = P + (q0 + m) * Wd + p;  // plane row of grid row q0-1+m, column p-1
+        L[m] = row[0];
+        Rt[m] = row[2];
+    }
+    const float xm = P[q0 * Wd + p + 1];            // (p, q0-1)
+    const float xp = P[(q0 + R + 1) * Wd + p + 1];  // (p, q0+R)
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float up = (k + 1 < R) ? x[k + 1] : xp;
+        const float dn = (k > 0) ? x[k - 1] : xm;
+        float t = fmaf(c[k].E, Rt[k + 1], x[k]);
+        t = fmaf(c[k].W, L[k + 1], t);
+        t = fmaf(c[k].N, up, t);
+        t = fmaf(c[k].S, dn, t);
+        t = fmaf(c[k].NE, Rt[k + 2], t);
+        t = fmaf(c[k].NW, L[k + 2], t);
+        t = fmaf(c[k].SE, Rt[k], t);
+        t = fmaf(c[k].SW, L[k], t);
+        y[k] = t;
+    }
+}
+
+// Plain CG on the scaled operator (Jacobi-PCG on S); x = 0 on entry, r = rhs.
+// Stops at ||r||^2 <= stop2 or after maxit iterations; returns the count.
+template <int R>
+__device__ int strip_cg(const Couple8 (&c)[R], const bool (&valid)[R], float (&x)[R], float (&r)[R], float rr,
+                        float* P, int Wd, int p, int q0, float stop2, int maxit, float* redA, float* redB,
+                        int* flag) {
+    float pv[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) pv[k] = r[k];
+    int it = 0;
+    while (it < maxit) {
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (valid[k]) P[(q0 + k + 1) * Wd + p + 1] = pv[k];
+        __syncthreads();
+        float q[R];
+        strip_apply<R>(c, pv, P, Wd, p, q0, q);
+        float pq = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) pq = fmaf(pv[k], q[k], pq);
+        {
+            float t[1] = {pq};
+            block_allreduce<float, 1>(t, redA);
+            pq = t[0];
+        }
+        ++it;
+        if (!(pq > 0.f)) {
+            *flag = (pq == pq) ? kBreakdown : kNaN;
+            break;
+        }
+        const float alpha = rr / pq;
+        float rn = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            x[k] = fmaf(alpha, pv[k], x[k]);
+            r[k] = fmaf(-alpha, q[k], r[k]);
+            rn = fmaf(r[k], r[k], rn);
+        }
+        {
+            float t[1] = {rn};
+            block_allreduce<float, 1>(t, redB);
+            rn = t[0];
+        }
+        if (!(rn == rn)) {
+            *flag = kNaN;
+            break;
+        }
+        if (rn <= stop2) break;
+        const float beta = rn / rr;
+        rr = rn;
+#pragma unroll
+        for (int k = 0; k < R; ++k) pv[k] = fmaf(beta, pv[k], r[k]);
+    }
+    return it;
+}
+
+template <int R>
+__global__ void __launch_bounds__(StripMaxThreads<R>::value) k_micro_strip(MicroArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n1 = a.n1, Wd = n1 + 2;
+    const int Hd = strip_rows(n1, R) * R + 2;
+    float* P = reinterpret_cast<float*>(smem);
+    size_t off = ((size_t)Wd * Hd * sizeof(float) + 15) & ~(size_t)15;
+    float* red = reinterpret_cast<float*>(smem + off);  // 4 x 64 floats in rotation
+
+    const int i = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+    const bool active = tid < n1 * strip_rows(n1, R);
+    const int p = active ? tid % n1 : 0;
+    const int q0 = active ? (tid / n1) * R : 0;
+    const size_t pl = (size_t)a.nmp;
+    double* res = a.res + (size_t)i * pl;
+    double* v = a.v + (size_t)i * pl;
+    const double* re = a.redge + (size_t)i * n1;
+    int nb = 0;
+    auto buf = [&]() { float* b = red + 64 * nb; nb = (nb + 1) & 3; return b; };
+
+    bool valid[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) valid[k] = active && (q0 + k) < n1;
+
+    // residual of the current iterate for the new macro value u_i
+    const double ui = a.u[i];
+    const double kdu = a.kappa * (ui - a.u_used[i]);
+    const bool edge = p == n1 - 1;
+    double r64[R];
+    float rr = 0.f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        double r = 0.0;
+        if (valid[k]) {
+            const int q = q0 + k;
+            r = res[p + n1 * q];
+            if (edge) r = fma(kdu, re[q], r);
+        }
+        r64[k] = r;
+        rr = fmaf((float)r, (float)r, rr);
+    }
+    const double* bn = a.bnorm + (size_t)i * 3;
+    const double ku = a.kappa * ui;
+    const double bn2 = fma(ku * ku, bn[2], fma(2.0 * ku, bn[1], bn[0]));
+    {
+        float t[1] = {rr};
+        block_allreduce<float, 1>(t, buf());
+        rr = t[0];
+    }
+    const float stop2 = (float)(a.tol * a.tol * bn2);
+    int inner = 0, sweeps = 0, flag = 0;
+    bool solved = false;
+    if (!(rr == rr)) flag = kNaN;
+    if (bn2 == 0.0) {  // zero right-hand side: the solution is zero
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            r64[k] = 0.0;
+            if (valid[k]) v[p + n1 * (q0 + k)] = 0.0;
+        }
+        solved = true;
+    } else if (!flag && rr > stop2) {
+        solved = true;
+        // zero the plane (halo stays zero); scaled couplings into registers:
+        // c^_jl = c_jl / sqrt(C_j C_l), sc_j = 1 / sqrt(C_j)
+        for (int e = tid; e < Wd * Hd; e += T) P[e] = 0.f;
+        const float* S = a.S32 + (size_t)i * kPlanes * pl;
+        Couple8 c[R];
+        float sc[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            Couple8 s{0, 0, 0, 0, 0, 0, 0, 0};
+            float d0 = 1.f;
+            if (valid[k]) {
+                const int q = q0 + k, j = p + n1 * q;
+                const bool w = p > 0, e = p + 1 < n1, sd = q > 0, nd = q + 1 < n1;
+                d0 = rsqrtf(S[j]);
+                auto dg = [&](int l) { return rsqrtf(S[l]); };
+                if (e) s.E = S[pl + j] * dg(j + 1);
+                if (w) s.W = S[pl + j - 1] * dg(j - 1);
+                if (nd) s.N = S[2 * pl + j] * dg(j + n1);
+                if (sd) s.S = S[2 * pl + j - n1] * dg(j - n1);
+                if (e && nd) s.NE = S[3 * pl + j] * dg(j + n1 + 1);
+                if (w && nd) s.NW = S[4 * pl + j] * dg(j + n1 - 1);
+                if (e && sd) s.SE = S[4 * pl + j - n1 + 1] * dg(j - n1 + 1);
+                if (w && sd) s.SW = S[3 * pl + j - n1 - 1] * dg(j - n1 - 1);
+                s.E *= d0; s.W *= d0; s.N *= d0; s.S *= d0;
+                s.NE *= d0; s.NW *= d0; s.SE *= d0; s.SW *= d0;
+            }
+            c[k] = s;
+            sc[k] = valid[k] ? d0 : 0.f;
+        }
+        __syncthreads();
+        const double* S64 = a.S64 + (size_t)i * kPlanes * pl;
+        for (;;) {
+            if (sweeps >= a.max_sweeps || inner >= a.maxit) {
+                flag = kNotConverged;
+                break;
+            }
+            // FP32 correction on the scaled system S^ y = D^-1/2 r, d = D^-1/2 y,
+            // to inner_tol relative, but no further than half the outer
+            // tolerance requires
+            float y[R], r[R];
+            float rs = 0.f;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                y[k] = 0.f;
+                r[k] = sc[k] * (float)r64[k];
+                rs = fmaf(r[k], r[k], rs);
+            }
+            {
+                float t[1] = {rs};
+                block_allreduce<float, 1>(t, buf());
+                rs = t[0];
+            }
+            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, 0.25f * stop2 / rr);
+            inner += strip_cg<R>(c, valid, y, r, rs, P, Wd, p, q0, rel2 * rs, a.maxit - inner, buf(), buf(),
+                                 &flag);
+            if (flag == kNaN) break;
+            flag = 0;
+            // v += d and r -= S64 d in FP64 (d is exact in FP64)
+            float d[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                d[k] = sc[k] * y[k];
+                if (valid[k]) P[(q0 + k + 1) * Wd + p + 1] = d[k];
+            }
+            __syncthreads();
+            float L[R + 2], Rt[R + 2];
+#pragma unroll
+            for (int m = 0; m < R + 2; ++m) {
+                const float* row = P + (q0 + m) * Wd + p;
+                L[m] = row[0];
+                Rt[m] = row[2];
+            }
+            const float dm = P[q0 * Wd + p + 1];
+            const float dp = P[(q0 + R + 1) * Wd + p + 1];
+            rr = 0.f;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if (!valid[k]) continue;
+                const int q = q0 + k, j = p + n1 * q;
+                const bool w = p > 0, e = p + 1 < n1, sd = q > 0;
+                const double up = (k + 1 < R) ? d[k + 1] : dp;
+                const double dn = (k > 0) ? d[k - 1] : dm;
+                double yv = S64[j] * (double)d[k];
+                yv = fma(S64[pl + j], (double)Rt[k + 1], yv);
+                if (w) yv = fma(S64[pl + j - 1], (double)L[k + 1], yv);
+                yv = fma(S64[2 * pl + j], up, yv);
+                if (sd) yv = fma(S64[2 * pl + j - n1], dn, yv);
+                yv = fma(S64[3 * pl + j], (double)Rt[k + 2], yv);
+                yv = fma(S64[4 * pl + j], (double)L[k + 2], yv);
+                if (e && sd) yv = fma(S64[4 * pl + j - n1 + 1], (double)Rt[k], yv);
+                if (w && sd) yv = fma(S64[3 * pl + j - n1 - 1], (double)L[k], yv);
+                r64[k] -= yv;
+                const float rf = (float)r64[k];
+                rr = fmaf(rf, rf, rr);
+                v[j] += (double)d[k];
+            }
+            {
+                float t[1] = {rr};
+                block_allreduce<float, 1>(t, buf());
+                rr = t[0];
+            }
+            ++sweeps;
+            if (!(rr == rr)) {
+                flag = kNaN;
+                break;
+            }
+            if (rr <= stop2) break;
+        }
+    }
+    // store the residual of the new iterate (only Robin-edge values change
+    // when no correction was needed)
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if (valid[k] && (solved || (edge && kdu != 0.0))) res[p + n1 * (q0 + k)] = r64[k];
+    __syncthreads();
+    // flux integral rho_i = r_i^T v_i over the Robin-edge nodes, one warp,
+    // compensated (TwoSum) FP64
+    if (tid < 32) {
+        double s = 0.0, cpen = 0.0;
+        for (int q = tid; q < n1; q += 32) {
+            const double t = re[q] * v[(n1 - 1) + n1 * q];
+            double su, er;
+            two_sum(s, t, su, er);
+            s = su;
+            cpen += er;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double so = __shfl_xor_sync(0xffffffffu, s, o);
+            const double co = __shfl_xor_sync(0xffffffffu, cpen, o);
+            double su, er;
+            two_sum(s, so, su, er);
+            s = su;
+            cpen += co + er;
+        }
+        if (tid == 0) {
+            a.u_used[i] = ui;
+            a.rho[i] = s + cpen;
+            a.inst_iters[i] = inner;
+            atomicAdd(&a.ctl->inner_iters, (unsigned long long)inner);
+            atomicAdd(&a.ctl->sweeps, (unsigned long long)sweeps);
+            atomicAdd(&a.ctl->micro_solves, 1ull);
+            atomicMax(&a.ctl->max_inner, inner);
+            if (flag) set_status(a.ctl, flag);
+        }
+    }
+}
+
+template <int R>
+static cudaError_t launch_strip(const MicroArgs& a, cudaStream_t s) {
+    const int T = strip_threads(a.n1, R);
+    if (T > StripMaxThreads<R>::value) return cudaErrorInvalidConfiguration;
+    k_micro_strip<R><<<a.nM, T, strip_smem_bytes(a.n1, R), s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// variant table
+// ---------------------------------------------------------------------------
+static const int kSmemK[4] = {1, 2, 4, 8};
+static const int kStripR[3] = {2, 4, 6};
+
+bool tiling_uses_stored_residual(int tiling) { return tiling >= 4; }
+
+bool tiling_fits(int tiling, int precision, int n1, int smem_optin) {
+    const int nm = n1 * n1;
+    if (tiling >= 0 && tiling < 4) {
+        const int K = kSmemK[tiling];
+        const int maxT = K <= 2 ? 1024 : (K == 4 ? 512 : 544);
+        return smem_threads(nm, K) <= maxT && smem_kernel_bytes(n1, precision) <= (size_t)smem_optin;
+    }
+    if (tiling >= 4 && tiling < kNumTilings) {
+        if (precision == 0) return false;
+        const int R = kStripR[tiling - 4];
+        const int maxT = R <= 2 ? 640 : 512;
+        return strip_threads(n1, R) <= maxT && strip_smem_bytes(n1, R) <= (size_t)smem_optin;
+    }
+    return false;
+}
+
+cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cudaStream_t s) {
+    if (precision == 0) {
+        switch (tiling) {
+            case 0: return launch_smem<double, false, 1>(a, s);
+            case 1: return launch_smem<double, false, 2>(a, s);
+            case 2: return launch_smem<double, false, 4>(a, s);
+            case 3: return launch_smem<double, false, 8>(a, s);
+        }
+    } else {
+        switch (tiling) {
+            case 0: return launch_smem<float, true, 1>(a, s);
+            case 1: return launch_smem<float, true, 2>(a, s);
+            case 2: return launch_smem<float, true, 4>(a, s);
+            case 3: return launch_smem<float, true, 8>(a, s);
+            case 4: return launch_strip<2>(a, s);
+            case 5: return launch_strip<4>(a, s);
+            case 6: return launch_strip<6>(a, s);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 // Allow every variant the device's opt-in shared memory (done once, outside
@@ -373,80 +771,87 @@ static cudaError_t launch_one(const MicroArgs& a, cudaStream_t s) {
 cudaError_t configure_micro_kernels(int smem_optin) {
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaSuccess;
-    const void* fns[8] = {(const void*)k_micro_solve<double, false, 1>, (const void*)k_micro_solve<double, false, 2>,
-                          (const void*)k_micro_solve<double, false, 4>, (const void*)k_micro_solve<double, false, 8>,
-                          (const void*)k_micro_solve<float, true, 1>,   (const void*)k_micro_solve<float, true, 2>,
-                          (const void*)k_micro_solve<float, true, 4>,   (const void*)k_micro_solve<float, true, 8>};
-    for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
+    const void* fns[11] = {(const void*)k_micro_solve<double, false, 1>, (const void*)k_micro_solve<double, false, 2>,
+                           (const void*)k_micro_solve<double, false, 4>, (const void*)k_micro_solve<double, false, 8>,
+                           (const void*)k_micro_solve<float, true, 1>,   (const void*)k_micro_solve<float, true, 2>,
+                           (const void*)k_micro_solve<float, true, 4>,   (const void*)k_micro_solve<float, true, 8>,
+                           (const void*)k_micro_strip<2>,                (const void*)k_micro_strip<4>,
+                           (const void*)k_micro_strip<6>};
+    for (int k = 0; k < 11 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
     return e;
 }
 
-cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int K, cudaStream_t s) {
-    if (precision == 0) {
-        switch (K) {
-            case 1: return launch_one<double, false, 1>(a, s);
-            case 2: return launch_one<double, false, 2>(a, s);
-            case 4: return launch_one<double, false, 4>(a, s);
-            case 8: return launch_one<double, false, 8>(a, s);
-        }
-    } else {
-        switch (K) {
-            case 1: return launch_one<float, true, 1>(a, s);
-            case 2: return launch_one<float, true, 2>(a, s);
-            case 4: return launch_one<float, true, 4>(a, s);
-            case 8: return launch_one<float, true, 8>(a, s);
-        }
+// ---------------------------------------------------------------------------
+// Per-step prologue (one block per instance), all FP64:
+//   c   = M (v^n/dt + fv) + R g                (right-hand side without the u term)
+//   res = c + kappa u r - S v^n                (residual of the warm start v^n)
+//   bnorm = (||c||^2, c^T r, ||r||^2)          (||b(u)|| for any u)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double plane_apply(const double* __restrict__ A, size_t pl, const double* __restrict__ x,
+                                              int j, int p, int q, int n1) {
+    double y = A[j] * x[j];
+    const bool e = p + 1 < n1, w = p > 0;
+    if (e) y = fma(A[pl + j], x[j + 1], y);
+    if (w) y = fma(A[pl + j - 1], x[j - 1], y);
+    if (q + 1 < n1) {
+        y = fma(A[2 * pl + j], x[j + n1], y);
+        if (e) y = fma(A[3 * pl + j], x[j + n1 + 1], y);
+        if (w) y = fma(A[4 * pl + j], x[j + n1 - 1], y);
     }
-    return cudaErrorInvalidValue;
+    if (q > 0) {
+        y = fma(A[2 * pl + j - n1], x[j - n1], y);
+        if (w) y = fma(A[3 * pl + j - n1 - 1], x[j - n1 - 1], y);
+        if (e) y = fma(A[4 * pl + j - n1 + 1], x[j - n1 + 1], y);
+    }
+    return y;
 }
 
-// ---------------------------------------------------------------------------
-// Per-step prologue: c_i = M_i (v_i^n/dt + fv_i) + R_i g_i and G_i = r_i^T g_i
-// (right-hand side of the micro equations without the u term, Eq. (17)
-// second line, made parabolic).  One block per instance.
-// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_micro_prologue(PrologueArgs a) {
-    __shared__ double buf[128];
+    __shared__ double buf[3 * 32];
     const int i = blockIdx.x;
     const int n1 = a.n1, nm = a.nm;
     const size_t pl = (size_t)a.nmp;
     const double* M = a.M64 + (size_t)i * kPlanes * pl;
+    const double* S = a.S64 + (size_t)i * kPlanes * pl;
     const double* v = a.v + (size_t)i * pl;
     const double* fv = a.fv ? a.fv + (size_t)i * pl : nullptr;
     const double* g = a.g ? a.g + (size_t)i * n1 : nullptr;
+    const double* re = a.redge + (size_t)i * n1;
     const double idt = 1.0 / a.dt;
+    const double ku = a.kappa * a.u[i];
     double* c = a.c + (size_t)i * pl;
+    double* res = a.res + (size_t)i * pl;
+    double cc = 0.0, cr = 0.0, rr = 0.0;
     for (int j = threadIdx.x; j < nm; j += blockDim.x) {
         const int p = j % n1, q = j / n1;
-        auto w = [&](int l) { return fv ? fma(v[l], idt, fv[l]) : v[l] * idt; };
-        double y = M[j] * w(j);
-        const bool e = p + 1 < n1, wst = p > 0;
-        if (e) y = fma(M[pl + j], w(j + 1), y);
-        if (wst) y = fma(M[pl + j - 1], w(j - 1), y);
-        if (q + 1 < n1) {
-            y = fma(M[2 * pl + j], w(j + n1), y);
-            if (e) y = fma(M[3 * pl + j], w(j + n1 + 1), y);
-            if (wst) y = fma(M[4 * pl + j], w(j + n1 - 1), y);
-        }
-        if (q > 0) {
-            y = fma(M[2 * pl + j - n1], w(j - n1), y);
-            if (wst) y = fma(M[3 * pl + j - n1 - 1], w(j - n1 - 1), y);
-            if (e) y = fma(M[4 * pl + j - n1 + 1], w(j - n1 + 1), y);
-        }
-        if (g && p == n1 - 1) {
-            const double* Rd = a.Rd + (size_t)i * n1;
-            const double* Ru = a.Ru + (size_t)i * n1;
-            y = fma(Rd[q], g[q], y);
-            if (q + 1 < n1) y = fma(Ru[q], g[q + 1], y);
-            if (q > 0) y = fma(Ru[q - 1], g[q - 1], y);
+        double y = plane_apply(M, pl, v, j, p, q, n1) * idt;
+        if (fv) y += plane_apply(M, pl, fv, j, p, q, n1);
+        double rj = 0.0;
+        if (p == n1 - 1) {
+            rj = re[q];
+            if (g) {
+                const double* Rd = a.Rd + (size_t)i * n1;
+                const double* Ru = a.Ru + (size_t)i * n1;
+                y = fma(Rd[q], g[q], y);
+                if (q + 1 < n1) y = fma(Ru[q], g[q + 1], y);
+                if (q > 0) y = fma(Ru[q - 1], g[q - 1], y);
+            }
         }
         c[j] = y;
+        res[j] = fma(ku, rj, y) - plane_apply(S, pl, v, j, p, q, n1);
+        cc = fma(y, y, cc);
+        cr = fma(y, rj, cr);
+        rr = fma(rj, rj, rr);
     }
-    double gl = 0.0;
-    if (g)
-        for (int q = threadIdx.x; q < n1; q += blockDim.x) gl = fma(a.redge[(size_t)i * n1 + q], g[q], gl);
-    const double G = block_sum_compensated(gl, buf);
-    if (threadIdx.x == 0) a.G[i] = G;
+    double t[3] = {cc, cr, rr};
+    block_allreduce<double, 3>(t, buf);
+    if (threadIdx.x == 0) {
+        double* bn = a.bnorm + (size_t)i * 3;
+        bn[0] = t[0];
+        bn[1] = t[1];
+        bn[2] = t[2];
+        a.u_used[i] = a.u[i];
+    }
 }
 
 cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s) {

@@ -168,14 +168,19 @@ def test_all_tilings_agree(precision):
     u0, v0 = W.random_state(nM, nm, seed=9)
     T = _T()
     res = []
-    for t in range(4):
+    for t in range(7):
         P = T.TwoScale(Nm, NM, precision=precision, tiling=t, cg_tol=1e-12, coupling_tol=1e-12)
         P.set_deformation(W.FAMILY_SHEAR_BUMP, prm)
         P.set_state(u0, v0)
-        P.step(0.01, 2)
+        try:
+            P.step(0.01, 2)
+        except T.TsfError as e:       # variant not available for this size / precision
+            assert e.status == T.TSF_E_ARG and (precision == 0 or t < 4)
+            continue
         P.synchronize()
-        assert P.stats()["tiling"] == 1 << t
+        assert P.stats()["tiling"] == t
         res.append(P.v())
+    assert len(res) >= 4  # all four shared-memory variants fit a 21x21 micro grid
     for r in res[1:]:
         assert rel(r, res[0]) < 1e-9
 
