@@ -210,6 +210,46 @@ void tsf_destroy(tsf_ctx *ctx);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int tsf_version(void);
 
+/* ---------------------------------------------------------------------------
+ * Macro solve that allocates no device memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc when they
+ * need a solve -- for example an application that gives all device memory to
+ * its own pool allocator at start-up, a latency-critical loop in which a
+ * device-synchronising allocation is not acceptable, or code that must not
+ * touch the allocator while a stream is being captured.
+ *
+ * It runs the macro-solve kernel of tsf_step once, on caller-owned device
+ * arrays, solving on the NM x NM macro mesh
+ *     (M_H/dt + Du K_H + kappa L Gam) u = cH + kappa L rho
+ * with L = diag(row sums of M_H), Gam = diag(gam), and u = u0 on the whole
+ * boundary when bc = TSF_BC_DIRICHLET; FP64 flexible PCG started from u0
+ * until ||residual||_2 <= tol ||rhs||_2, at most maxit iterations.
+ * Arguments: NM cells per side (1 <= NM <= TSF_NOALLOC_MAX_NM); bc, dt > 0,
+ * macro_diff (Du) > 0, kappa >= 0; gam, cH, rho, u0: device arrays of
+ * nM = (NM+1)^2 doubles, node (p,q) at index p + (NM+1) q, read only;
+ * u_out: device array of nM doubles that receives u (it may be u0 itself);
+ * cuda_stream: cudaStream_t to run on (NULL = legacy default stream);
+ * iters_out: optional host int receiving the PCG iteration count.
+ *
+ * Its scratch (six vectors of the PCG and a control block) is one fixed
+ * device array of the library, sized for TSF_NOALLOC_MAX_NM (about 0.8 MB);
+ * every GPU that loads the library holds it until the process exits.  The
+ * first call on a device looks up that array's device address and sets the
+ * kernel's shared-memory limit, so make the first call on each device before
+ * any stream capture.  All calls on a device share the array (it keeps the
+ * last call's contents; the call clears what must start from zero): calls
+ * that overlap on the GPU, e.g. on two streams at once, race and must not be
+ * issued.  The call returns after the solve has finished (it waits for
+ * cuda_stream).  Errors: TSF_E_ARG (NM outside 1..TSF_NOALLOC_MAX_NM, bad
+ * scalar, NULL array), TSF_E_CUDA (runtime failure), TSF_E_NOT_CONVERGED or
+ * TSF_E_NAN from the solve; there is no context, so tsf_last_error does not
+ * apply.
+ * ------------------------------------------------------------------------- */
+#define TSF_NOALLOC_MAX_NM 128
+tsf_status tsf_macro_solve_noalloc(int NM, int bc, double dt, double macro_diff, double kappa, const double *gam,
+                                   const double *cH, const double *rho, const double *u0, double *u_out,
+                                   double tol, int maxit, void *cuda_stream, int *iters_out);
+
 #ifdef __cplusplus
 }
 #endif

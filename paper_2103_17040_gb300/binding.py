@@ -30,7 +30,8 @@ EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micr
            "tsf_set_physics", "tsf_set_deformation", "tsf_set_state", "tsf_set_sources", "tsf_step",
            "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux",
            "tsf_get_geometry", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
-           "tsf_last_error", "tsf_destroy", "tsf_version"]
+           "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc"]
+TSF_NOALLOC_MAX_NM = 128
 
 
 class tsf_options(ctypes.Structure):
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH):
     L.tsf_destroy.argtypes = [vp]
     L.tsf_destroy.restype = None
     L.tsf_version.argtypes = []
+    L.tsf_macro_solve_noalloc.argtypes = [i, i, d, d, d, vp, vp, vp, vp, vp, d, i, vp, ctypes.POINTER(ctypes.c_int)]
     for f in EXPORTS:
         fn = getattr(L, f)
         if f not in ("tsf_default_options", "tsf_last_error", "tsf_destroy"):
@@ -272,6 +274,31 @@ def tsf_last_error(ctx) -> str:
 def tsf_destroy(ctx):
     if ctx and _lib is not None:
         _lib.tsf_destroy(ctx)
+
+
+def tsf_macro_solve_noalloc(NM, bc, dt, macro_diff, kappa, gam, cH, rho, u0, u_out, tol=1e-12, maxit=500,
+                            stream=None):
+    """Macro solve for callers that cannot allocate device memory.
+
+    All arrays are CUDA tensors of (NM+1)^2 float64 values; the library uses a
+    fixed scratch array of its own instead of allocating.  Returns the PCG
+    iteration count; a non-OK status raises TsfError (there is no context, so
+    the message is the status name only)."""
+    L = load_library()
+    arrs = (gam, cH, rho, u0, u_out)
+    n = (int(NM) + 1) ** 2
+    for a in arrs:
+        if not (_is_cuda_tensor(a) and a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()
+                and a.numel() == n):
+            raise ValueError(f"expected contiguous float64 CUDA tensors of {n} values")
+    s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    it = ctypes.c_int(0)
+    st = L.tsf_macro_solve_noalloc(int(NM), int(bc), float(dt), float(macro_diff), float(kappa),
+                                   *[a.data_ptr() for a in arrs], float(tol), int(maxit), s or None,
+                                   ctypes.byref(it))
+    if st != TSF_OK:
+        raise TsfError(st, "tsf_macro_solve_noalloc failed")
+    return it.value
 
 
 # ---------------------------------------------------------------------------
