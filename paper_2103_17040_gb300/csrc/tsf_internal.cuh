@@ -214,7 +214,7 @@ cudaError_t launch_instance_sums(int n1, int nm, int nmp, int nM, const double* 
 cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s);
 // Micro-solve variants ("tilings"):
 //   0..3  shared-memory stencil, K = 1, 2, 4, 8 nodes per thread (strided), FP64 or mixed
-//   4..6  column strips of R = 2, 4, 6 nodes with register stencils, mixed only
+//   4..6  column strips of R = 3, 5, 7 nodes with register stencils, mixed only
 constexpr int kNumTilings = 7;
 bool tiling_fits(int tiling, int precision, int n1, int smem_optin);
 cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cudaStream_t s);

@@ -373,13 +373,16 @@ static cudaError_t launch_smem(const MicroArgs& a, cudaStream_t s) {
 // Thread t owns R consecutive nodes of one column of the micro grid:
 // p = t mod n1, rows q0 .. q0+R-1 with q0 = R (t div n1).  The inner FP32 CG
 // runs on the symmetrically Jacobi-scaled operator  S^ = D^-1/2 S D^-1/2
-// (unit diagonal, so the Jacobi preconditioner becomes the identity and
-// z = r): the eight off-diagonal couplings of every node, scaled once with
-// the diagonals of both end nodes, sit in registers for the whole solve, and
-// the search direction of a CG iteration reaches the neighbours through one
-// zero-haloed shared-memory plane: per iteration a thread stores R values and
-// loads its two neighbour columns (2R + 4 values) plus two halo values of its
-// own column, about 3 shared loads per node.
+// (unit diagonal, so the Jacobi preconditioner becomes the identity): the
+// eight off-diagonal couplings of every node, scaled once with the diagonals
+// of both end nodes, sit in registers for the whole solve, and the vector the
+// operator is applied to reaches the neighbours through one zero-haloed
+// shared-memory plane: per iteration a thread stores R values and loads its
+// two neighbour columns (2R + 4 values) plus two halo values of its own
+// column.  The plane's row stride is padded so that the rows of consecutive
+// strips start in the same bank, which keeps warps that straddle two strips
+// free of bank conflicts.  The CG is the Chronopoulos-Gear form: one operator
+// application and ONE fused reduction (r.r, r.Ar) per iteration.
 //
 // FP64 refinement without recomputing b - S v from scratch: the residual of
 // the current iterate is kept in global memory (written by the step prologue
@@ -392,12 +395,29 @@ static cudaError_t launch_smem(const MicroArgs& a, cudaStream_t s) {
 // use norms accumulated in FP32 from the FP64 residual values (a norm only
 // decides when to stop; the residual itself stays FP64).
 // ===========================================================================
+// Launch bounds per strip height: R = 3 asks for two resident blocks of up to
+// 384 threads (register cap 85), R = 5 and 7 for one block of 512 / 384.
 template <int R>
 struct StripMaxThreads {
-    static constexpr int value = R <= 2 ? 640 : 512;
+    static constexpr int value = R == 3 ? 384 : (R == 5 ? 512 : 384);
+};
+template <int R>
+struct StripMinBlocks {
+    static constexpr int value = R == 3 ? 2 : 1;
 };
 
 __host__ __device__ inline int strip_rows(int n1, int R) { return (n1 + R - 1) / R; }
+
+// Row stride of the shared plane: the smallest W >= n1 + 2 with
+// R W = n1 (mod 32).  Thread t = s n1 + p reads plane word (s R + m) W + p,
+// which is then t + const (mod 32) for every row offset m, so the 32 lanes of
+// a warp hit 32 distinct banks even when the warp straddles two strips.
+// Needs R odd when n1 is odd (R is then invertible mod 32).
+__host__ __device__ inline int strip_stride(int n1, int R) {
+    for (int W = n1 + 2; W < n1 + 2 + 32; ++W)
+        if ((R * W - n1) % 32 == 0) return W;
+    return n1 + 2;  // not reachable for odd R
+}
 
 static int strip_threads(int n1, int R) {
     const int t = n1 * strip_rows(n1, R);
@@ -405,7 +425,7 @@ static int strip_threads(int n1, int R) {
 }
 
 static size_t strip_smem_bytes(int n1, int R) {
-    const size_t W = (size_t)n1 + 2, H = (size_t)strip_rows(n1, R) * R + 2;
+    const size_t W = (size_t)strip_stride(n1, R), H = (size_t)strip_rows(n1, R) * R + 2;
     size_t off = (W * H * sizeof(float) + 15) & ~(size_t)15;
     return off + 4 * 64 * sizeof(float);
 }
@@ -415,101 +435,139 @@ struct Couple8 {
     float E, W, N, S, NE, NW, SE, SW;
 };
 
-// y_k = (S^ x)_k = x_k + off-diagonal part, for the R nodes of a strip: x of
-// the own column in registers, neighbour columns and the own column's halo
-// from the shared plane P.
+// Neighbour values of a strip from the shared plane: L/Rt = columns p-1 / p+1
+// at rows q0-1 .. q0+R, xm / xp = own column at rows q0-1 and q0+R.
 template <int R>
-__device__ __forceinline__ void strip_apply(const Couple8 (&c)[R], const float (&x)[R], const float* P, int Wd,
-                                            int p, int q0, float (&y)[R]) {
-    float L[R + 2], Rt[R + 2];
+struct StripHalo {
+    float L[R + 2], Rt[R + 2], xm, xp;
+    __device__ __forceinline__ void load(const float* P, int Wd, int p, int q0) {
 #pragma unroll
-    for (int m = 0; m < R + 2; ++m) {
-        const float* row = P + (q0 + m) * Wd + p;  // plane row of grid row q0-1+m, column p-1
-        L[m] = row[0];
-        Rt[m] = row[2];
+        for (int m = 0; m < R + 2; ++m) {
+            const float* row = P + (q0 + m) * Wd + p;  // plane row of grid row q0-1+m, column p-1
+            L[m] = row[0];
+            Rt[m] = row[2];
+        }
+        xm = P[q0 * Wd + p + 1];
+        xp = P[(q0 + R + 1) * Wd + p + 1];
     }
-    const float xm = P[q0 * Wd + p + 1];            // (p, q0-1)
-    const float xp = P[(q0 + R + 1) * Wd + p + 1];  // (p, q0+R)
+};
+
+// y = S^ x = x + off-diagonal part for the R nodes of a strip.
+template <int R>
+__device__ __forceinline__ void strip_apply(const Couple8 (&c)[R], const float (&x)[R], const StripHalo<R>& h,
+                                            float (&y)[R]) {
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        const float up = (k + 1 < R) ? x[k + 1] : xp;
-        const float dn = (k > 0) ? x[k - 1] : xm;
-        float t = fmaf(c[k].E, Rt[k + 1], x[k]);
-        t = fmaf(c[k].W, L[k + 1], t);
+        const float up = (k + 1 < R) ? x[k + 1] : h.xp;
+        const float dn = (k > 0) ? x[k - 1] : h.xm;
+        float t = fmaf(c[k].E, h.Rt[k + 1], x[k]);
+        t = fmaf(c[k].W, h.L[k + 1], t);
         t = fmaf(c[k].N, up, t);
         t = fmaf(c[k].S, dn, t);
-        t = fmaf(c[k].NE, Rt[k + 2], t);
-        t = fmaf(c[k].NW, L[k + 2], t);
-        t = fmaf(c[k].SE, Rt[k], t);
-        t = fmaf(c[k].SW, L[k], t);
+        t = fmaf(c[k].NE, h.Rt[k + 2], t);
+        t = fmaf(c[k].NW, h.L[k + 2], t);
+        t = fmaf(c[k].SE, h.Rt[k], t);
+        t = fmaf(c[k].SW, h.L[k], t);
         y[k] = t;
     }
 }
 
-// Plain CG on the scaled operator (Jacobi-PCG on S); x = 0 on entry, r = rhs.
-// Stops at ||r||^2 <= stop2 or after maxit iterations; returns the count.
 template <int R>
-__device__ int strip_cg(const Couple8 (&c)[R], const bool (&valid)[R], float (&x)[R], float (&r)[R], float rr,
-                        float* P, int Wd, int p, int q0, float stop2, int maxit, float* redA, float* redB,
-                        int* flag) {
-    float pv[R];
+__device__ __forceinline__ void strip_store(float* P, int Wd, int p, int q0, const bool (&valid)[R],
+                                            const float (&v)[R]) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) pv[k] = r[k];
+    for (int k = 0; k < R; ++k)
+        if (valid[k]) P[(q0 + k + 1) * Wd + p + 1] = v[k];
+}
+
+// Chronopoulos-Gear CG on the scaled operator (Jacobi-PCG on S); x = 0 on
+// entry, r = rhs.  Stops when ||r||^2 <= rel2 ||r_0||^2 or after maxit
+// iterations; returns the count.  redA/redB: 64-float reduction buffers.
+template <int R>
+__device__ int strip_cg(const Couple8 (&c)[R], const bool (&valid)[R], float (&x)[R], float (&r)[R], float* P,
+                        int Wd, int p, int q0, float rel2, int maxit, float* redA, float* redB, int* flag) {
+    float pv[R], s[R], w[R];
+    StripHalo<R> h;
+    strip_store<R>(P, Wd, p, q0, valid, r);
+    __syncthreads();
+    h.load(P, Wd, p, q0);
+    strip_apply<R>(c, r, h, w);
+    float g = 0.f, dl = 0.f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        g = fmaf(r[k], r[k], g);
+        dl = fmaf(r[k], w[k], dl);
+        pv[k] = r[k];
+        s[k] = w[k];
+    }
+    {
+        float t[2] = {g, dl};
+        block_allreduce<float, 2>(t, redA);
+        g = t[0];
+        dl = t[1];
+    }
+    const float stop = rel2 * g;
+    if (!(dl > 0.f)) {
+        *flag = (dl == dl) ? kBreakdown : kNaN;
+        return 0;
+    }
+    // CG scalars with the fast division (a few ulp): they steer the FP32 inner
+    // solve only, whose result is checked by the FP64 residual
+    float alpha = __fdividef(g, dl);
     int it = 0;
     while (it < maxit) {
 #pragma unroll
-        for (int k = 0; k < R; ++k)
-            if (valid[k]) P[(q0 + k + 1) * Wd + p + 1] = pv[k];
-        __syncthreads();
-        float q[R];
-        strip_apply<R>(c, pv, P, Wd, p, q0, q);
-        float pq = 0.f;
-#pragma unroll
-        for (int k = 0; k < R; ++k) pq = fmaf(pv[k], q[k], pq);
-        {
-            float t[1] = {pq};
-            block_allreduce<float, 1>(t, redA);
-            pq = t[0];
-        }
-        ++it;
-        if (!(pq > 0.f)) {
-            *flag = (pq == pq) ? kBreakdown : kNaN;
-            break;
-        }
-        const float alpha = rr / pq;
-        float rn = 0.f;
-#pragma unroll
         for (int k = 0; k < R; ++k) {
             x[k] = fmaf(alpha, pv[k], x[k]);
-            r[k] = fmaf(-alpha, q[k], r[k]);
-            rn = fmaf(r[k], r[k], rn);
+            r[k] = fmaf(-alpha, s[k], r[k]);
+        }
+        ++it;
+        strip_store<R>(P, Wd, p, q0, valid, r);
+        __syncthreads();
+        h.load(P, Wd, p, q0);
+        strip_apply<R>(c, r, h, w);
+        float gn = 0.f, dn = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            gn = fmaf(r[k], r[k], gn);
+            dn = fmaf(r[k], w[k], dn);
         }
         {
-            float t[1] = {rn};
-            block_allreduce<float, 1>(t, redB);
-            rn = t[0];
+            float t[2] = {gn, dn};
+            block_allreduce<float, 2>(t, (it & 1) ? redB : redA);
+            gn = t[0];
+            dn = t[1];
         }
-        if (!(rn == rn)) {
+        if (!(gn == gn) || !(dn == dn)) {
             *flag = kNaN;
             break;
         }
-        if (rn <= stop2) break;
-        const float beta = rn / rr;
-        rr = rn;
+        if (gn <= stop) break;
+        const float beta = __fdividef(gn, g);
+        const float den = dn - __fdividef(beta * gn, alpha);
+        if (!(den > 0.f)) {
+            *flag = kBreakdown;
+            break;
+        }
+        alpha = __fdividef(gn, den);
+        g = gn;
 #pragma unroll
-        for (int k = 0; k < R; ++k) pv[k] = fmaf(beta, pv[k], r[k]);
+        for (int k = 0; k < R; ++k) {
+            pv[k] = fmaf(beta, pv[k], r[k]);
+            s[k] = fmaf(beta, s[k], w[k]);
+        }
     }
     return it;
 }
 
 template <int R>
-__global__ void __launch_bounds__(StripMaxThreads<R>::value) k_micro_strip(MicroArgs a) {
+__global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::value) k_micro_strip(MicroArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int n1 = a.n1, Wd = n1 + 2;
+    const int n1 = a.n1, Wd = strip_stride(n1, R);
     const int Hd = strip_rows(n1, R) * R + 2;
     float* P = reinterpret_cast<float*>(smem);
     size_t off = ((size_t)Wd * Hd * sizeof(float) + 15) & ~(size_t)15;
-    float* red = reinterpret_cast<float*>(smem + off);  // 4 x 64 floats in rotation
+    float* red = reinterpret_cast<float*>(smem + off);  // 4 x 64 floats
 
     const int i = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
     const bool active = tid < n1 * strip_rows(n1, R);
@@ -519,8 +577,6 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value) k_micro_strip(Micro
     double* res = a.res + (size_t)i * pl;
     double* v = a.v + (size_t)i * pl;
     const double* re = a.redge + (size_t)i * n1;
-    int nb = 0;
-    auto buf = [&]() { float* b = red + 64 * nb; nb = (nb + 1) & 3; return b; };
 
     bool valid[R];
 #pragma unroll
@@ -548,7 +604,7 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value) k_micro_strip(Micro
     const double bn2 = fma(ku * ku, bn[2], fma(2.0 * ku, bn[1], bn[0]));
     {
         float t[1] = {rr};
-        block_allreduce<float, 1>(t, buf());
+        block_allreduce<float, 1>(t, red + 128);
         rr = t[0];
     }
     const float stop2 = (float)(a.tol * a.tol * bn2);
@@ -564,8 +620,8 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value) k_micro_strip(Micro
         solved = true;
     } else if (!flag && rr > stop2) {
         solved = true;
-        // zero the plane (halo stays zero); scaled couplings into registers:
-        // c^_jl = c_jl / sqrt(C_j C_l), sc_j = 1 / sqrt(C_j)
+        // zero the plane (halo and padding stay zero); scaled couplings into
+        // registers: c^_jl = c_jl / sqrt(C_j C_l), sc_j = 1 / sqrt(C_j)
         for (int e = tid; e < Wd * Hd; e += T) P[e] = 0.f;
         const float* S = a.S32 + (size_t)i * kPlanes * pl;
         Couple8 c[R];
@@ -602,67 +658,60 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value) k_micro_strip(Micro
             }
             // FP32 correction on the scaled system S^ y = D^-1/2 r, d = D^-1/2 y,
             // to inner_tol relative, but no further than half the outer
-            // tolerance requires
+            // tolerance requires.  The FP64 residual waits in global memory.
             float y[R], r[R];
-            float rs = 0.f;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 y[k] = 0.f;
                 r[k] = sc[k] * (float)r64[k];
-                rs = fmaf(r[k], r[k], rs);
-            }
-            {
-                float t[1] = {rs};
-                block_allreduce<float, 1>(t, buf());
-                rs = t[0];
+                if (valid[k]) res[p + n1 * (q0 + k)] = r64[k];
             }
             const float rel2 = fmaxf(a.inner_tol * a.inner_tol, 0.25f * stop2 / rr);
-            inner += strip_cg<R>(c, valid, y, r, rs, P, Wd, p, q0, rel2 * rs, a.maxit - inner, buf(), buf(),
-                                 &flag);
+            inner += strip_cg<R>(c, valid, y, r, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 64, &flag);
             if (flag == kNaN) break;
             flag = 0;
             // v += d and r -= S64 d in FP64 (d is exact in FP64)
             float d[R];
 #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                d[k] = sc[k] * y[k];
-                if (valid[k]) P[(q0 + k + 1) * Wd + p + 1] = d[k];
-            }
+            for (int k = 0; k < R; ++k) d[k] = sc[k] * y[k];
+            strip_store<R>(P, Wd, p, q0, valid, d);
             __syncthreads();
-            float L[R + 2], Rt[R + 2];
+            StripHalo<R> h;
+            h.load(P, Wd, p, q0);
+            double L64[R + 2], R64[R + 2], d64[R];
 #pragma unroll
             for (int m = 0; m < R + 2; ++m) {
-                const float* row = P + (q0 + m) * Wd + p;
-                L[m] = row[0];
-                Rt[m] = row[2];
+                L64[m] = (double)h.L[m];
+                R64[m] = (double)h.Rt[m];
             }
-            const float dm = P[q0 * Wd + p + 1];
-            const float dp = P[(q0 + R + 1) * Wd + p + 1];
+#pragma unroll
+            for (int k = 0; k < R; ++k) d64[k] = (double)d[k];
+            const double dm = (double)h.xm, dp = (double)h.xp;
             rr = 0.f;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 if (!valid[k]) continue;
                 const int q = q0 + k, j = p + n1 * q;
                 const bool w = p > 0, e = p + 1 < n1, sd = q > 0;
-                const double up = (k + 1 < R) ? d[k + 1] : dp;
-                const double dn = (k > 0) ? d[k - 1] : dm;
-                double yv = S64[j] * (double)d[k];
-                yv = fma(S64[pl + j], (double)Rt[k + 1], yv);
-                if (w) yv = fma(S64[pl + j - 1], (double)L[k + 1], yv);
+                const double up = (k + 1 < R) ? d64[k + 1] : dp;
+                const double dn = (k > 0) ? d64[k - 1] : dm;
+                double yv = S64[j] * d64[k];
+                yv = fma(S64[pl + j], R64[k + 1], yv);
+                if (w) yv = fma(S64[pl + j - 1], L64[k + 1], yv);
                 yv = fma(S64[2 * pl + j], up, yv);
                 if (sd) yv = fma(S64[2 * pl + j - n1], dn, yv);
-                yv = fma(S64[3 * pl + j], (double)Rt[k + 2], yv);
-                yv = fma(S64[4 * pl + j], (double)L[k + 2], yv);
-                if (e && sd) yv = fma(S64[4 * pl + j - n1 + 1], (double)Rt[k], yv);
-                if (w && sd) yv = fma(S64[3 * pl + j - n1 - 1], (double)L[k], yv);
-                r64[k] -= yv;
+                yv = fma(S64[3 * pl + j], R64[k + 2], yv);
+                yv = fma(S64[4 * pl + j], L64[k + 2], yv);
+                if (e && sd) yv = fma(S64[4 * pl + j - n1 + 1], R64[k], yv);
+                if (w && sd) yv = fma(S64[3 * pl + j - n1 - 1], L64[k], yv);
+                r64[k] = res[j] - yv;
                 const float rf = (float)r64[k];
                 rr = fmaf(rf, rf, rr);
-                v[j] += (double)d[k];
+                v[j] += d64[k];
             }
             {
                 float t[1] = {rr};
-                block_allreduce<float, 1>(t, buf());
+                block_allreduce<float, 1>(t, red + 128 + 64 * (sweeps & 1));
                 rr = t[0];
             }
             ++sweeps;
@@ -724,7 +773,7 @@ static cudaError_t launch_strip(const MicroArgs& a, cudaStream_t s) {
 // variant table
 // ---------------------------------------------------------------------------
 static const int kSmemK[4] = {1, 2, 4, 8};
-static const int kStripR[3] = {2, 4, 6};
+static const int kStripR[3] = {3, 5, 7};
 
 bool tiling_uses_stored_residual(int tiling) { return tiling >= 4; }
 
@@ -738,7 +787,7 @@ bool tiling_fits(int tiling, int precision, int n1, int smem_optin) {
     if (tiling >= 4 && tiling < kNumTilings) {
         if (precision == 0) return false;
         const int R = kStripR[tiling - 4];
-        const int maxT = R <= 2 ? 640 : 512;
+        const int maxT = R == 3 ? 384 : (R == 5 ? 512 : 384);
         return strip_threads(n1, R) <= maxT && strip_smem_bytes(n1, R) <= (size_t)smem_optin;
     }
     return false;
@@ -758,9 +807,9 @@ cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cu
             case 1: return launch_smem<float, true, 2>(a, s);
             case 2: return launch_smem<float, true, 4>(a, s);
             case 3: return launch_smem<float, true, 8>(a, s);
-            case 4: return launch_strip<2>(a, s);
-            case 5: return launch_strip<4>(a, s);
-            case 6: return launch_strip<6>(a, s);
+            case 4: return launch_strip<3>(a, s);
+            case 5: return launch_strip<5>(a, s);
+            case 6: return launch_strip<7>(a, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -775,8 +824,8 @@ cudaError_t configure_micro_kernels(int smem_optin) {
                            (const void*)k_micro_solve<double, false, 4>, (const void*)k_micro_solve<double, false, 8>,
                            (const void*)k_micro_solve<float, true, 1>,   (const void*)k_micro_solve<float, true, 2>,
                            (const void*)k_micro_solve<float, true, 4>,   (const void*)k_micro_solve<float, true, 8>,
-                           (const void*)k_micro_strip<2>,                (const void*)k_micro_strip<4>,
-                           (const void*)k_micro_strip<6>};
+                           (const void*)k_micro_strip<3>,                (const void*)k_micro_strip<5>,
+                           (const void*)k_micro_strip<7>};
     for (int k = 0; k < 11 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
     return e;
 }
