@@ -41,6 +41,14 @@ if ROOT not in sys.path:
 BYTES_PER_DOF_ITER = {"mixed": 64, "fp64": 128}
 BYTES_PER_DOF_SWEEP = 64
 
+KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_micro_solve<8>",
+                "k_micro_strip<3>", "k_micro_strip<5>", "k_micro_strip<7>"]
+# DRAM bytes (read + write) per micro-solve launch, averaged over the four
+# coupling iterations of one step, from the ncu capture summarised in
+# profiles/micro_strip_c2_64x64_32x32.md (column-strip kernel; the strip height
+# does not change the DRAM traffic).  Entries are removed when the kernel changes.
+MICRO_TRAFFIC = {("c2", "mixed", True): 322.3e6}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -250,7 +258,8 @@ def run_gb300(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     line["roofline"] = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": None, "kernel": "k_micro_solve", "bytes_per_launch": bytes_launch,
+        "traffic": MICRO_TRAFFIC.get((args.workload, args.precision, st["tiling"] >= 4)),
+        "kernel": KERNEL_NAMES[st["tiling"]], "bytes_per_launch": bytes_launch,
         "avg_launch_ms": micro_ms, "launches_timed": sp["micro_launches"],
         "macro_kernel_share": sp["macro_kernel_ms"] / max(sp["macro_kernel_ms"] + sp["micro_kernel_ms"], 1e-30),
         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
