@@ -84,6 +84,9 @@ def lib():
         L.or_reset_stats.argtypes = [vp]
         L.or_chi.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]
         L.or_chi_many.argtypes = [ctypes.c_int, _D, ctypes.c_int, _D, _D, _D, _D]
+        L.or_dchi.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]
+        L.or_assemble_q1_dparam.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _D, _I, _I, _D, _D, _D]
+        L.or_assemble_q1.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _I, _I, _D, _D, _D]
         L.or_pullback.argtypes = [_D, _D, _D, _D, _D, _D]
         L.or_unit_normal.argtypes = [_D, _D, _D]
         L.or_pcg.argtypes = [ctypes.c_int, _I, _I, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _I, _D]
@@ -177,6 +180,35 @@ def pcg(A, b, x0=None, tol=1e-12, maxit=10000):
     e = lib().or_pcg(n, _ip(rp), _ip(ci), _dp(val), _dp(bb), _dp(x), float(tol), int(maxit), _dp(work),
                      _ip(it), _dp(rr))
     return x, int(it[0]), float(rr[0]), e
+
+
+def assemble_q1(N, family, prm, D=(1.0, 0.0, 1.0)):
+    """(M, A, R) of one micro problem as scipy CSR matrices (Eq. (17) micro block)."""
+    import scipy.sparse as sp
+    rp, ci = q1_pattern(N)
+    nnz = len(ci)
+    p = _f64(prm if len(np.atleast_1d(prm)) else [0.0])
+    out = [np.zeros(nnz) for _ in range(3)]
+    e = lib().or_assemble_q1(int(N), int(family), _dp(p), _dp(_f64(D, 3)), _ip(rp), _ip(ci), *[_dp(o) for o in out])
+    if e:
+        raise OracleError(e, "assembly failed")
+    n = (N + 1) ** 2
+    return tuple(sp.csr_matrix((o, ci, rp), shape=(n, n)) for o in out)
+
+
+def assemble_q1_dparam(N, family, prm, k, D=(1.0, 0.0, 1.0)):
+    """(dM, dA, dR): derivatives of (M, A, R) with respect to parameter k."""
+    import scipy.sparse as sp
+    rp, ci = q1_pattern(N)
+    nnz = len(ci)
+    p = _f64(prm if len(np.atleast_1d(prm)) else [0.0])
+    out = [np.zeros(nnz) for _ in range(3)]
+    e = lib().or_assemble_q1_dparam(int(N), int(family), _dp(p), int(k), _dp(_f64(D, 3)), _ip(rp), _ip(ci),
+                                    *[_dp(o) for o in out])
+    if e:
+        raise OracleError(e, "derivative assembly failed")
+    n = (N + 1) ** 2
+    return tuple(sp.csr_matrix((o, ci, rp), shape=(n, n)) for o in out)
 
 
 def q1_pattern(N: int):

@@ -280,6 +280,121 @@ int or_assemble_q1(int N, int family, const double *prm, const double D[3],
 }
 
 /* ------------------------------------------------------------------------ */
+/* Parameter derivatives of the pulled-back operators (for the discrete      */
+/* adjoint of the two-scale march).                                          */
+/* ------------------------------------------------------------------------ */
+/* dF/dp_k of the deformation families at one point, row-major.  Returns
+ * OR_E_ARG for k outside the family's parameters. */
+int or_dchi(int family, int k, double y1, double y2, double dF[4])
+{
+    double s1 = sin(OR_PI * y1), c1 = cos(OR_PI * y1);
+    double s2 = sin(OR_PI * y2), c2 = cos(OR_PI * y2);
+    dF[0] = dF[1] = dF[2] = dF[3] = 0.0;
+    if (k < 0 || k >= or_family_nparam(family)) return OR_E_ARG;
+    int bump = (family == 1 && k == 0) || (family == 2 && k == 1) || (family == 4 && k == 4);
+    if (bump) {
+        dF[0] = OR_PI * c1 * s2;
+        dF[1] = OR_PI * s1 * c2;
+        return OR_OK;
+    }
+    if (family == 2 && k == 0) { dF[1] = 1.0; return OR_OK; } /* shear s */
+    if ((family == 3 || family == 4) && k < 4) { dF[k] = 1.0; return OR_OK; } /* A entries */
+    return OR_OK;                                                           /* affine shift c */
+}
+
+/* Derivatives at one point, obtained by differentiating the formulas of
+ * or_pullback: J = det F, C = adj(F) D adj(F)^T / J, s = |adj(F)^T nu|. */
+static void dpullback(const double F[4], const double dF[4], const double D[3], const double nu[2],
+                      double *dJ, double dC[3], double *ds)
+{
+    double J = F[0] * F[3] - F[1] * F[2];
+    double G[4] = {F[3], -F[1], -F[2], F[0]};        /* adj(F) */
+    double dG[4] = {dF[3], -dF[1], -dF[2], dF[0]};   /* adj is linear */
+    double Dm[4] = {D[0], D[1], D[1], D[2]};
+    *dJ = dF[0] * F[3] + F[0] * dF[3] - dF[1] * F[2] - F[1] * dF[2];
+    /* P = G D G^T, dP = dG D G^T + G D dG^T */
+    double GD[4], dGD[4];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            GD[2 * a + b] = G[2 * a] * Dm[b] + G[2 * a + 1] * Dm[2 + b];
+            dGD[2 * a + b] = dG[2 * a] * Dm[b] + dG[2 * a + 1] * Dm[2 + b];
+        }
+    double P[4], dP[4];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            P[2 * a + b] = GD[2 * a] * G[2 * b] + GD[2 * a + 1] * G[2 * b + 1];
+            dP[2 * a + b] = dGD[2 * a] * G[2 * b] + dGD[2 * a + 1] * G[2 * b + 1] +
+                            GD[2 * a] * dG[2 * b] + GD[2 * a + 1] * dG[2 * b + 1];
+        }
+    /* C = P / J  ->  dC = dP / J - P dJ / J^2 */
+    dC[0] = dP[0] / J - P[0] * *dJ / (J * J);
+    dC[1] = dP[1] / J - P[1] * *dJ / (J * J);
+    dC[2] = dP[3] / J - P[3] * *dJ / (J * J);
+    /* w = G^T nu, s = |w|, ds = w . dw / s */
+    double w0 = G[0] * nu[0] + G[2] * nu[1], w1 = G[1] * nu[0] + G[3] * nu[1];
+    double dw0 = dG[0] * nu[0] + dG[2] * nu[1], dw1 = dG[1] * nu[0] + dG[3] * nu[1];
+    *ds = (w0 * dw0 + w1 * dw1) / sqrt(w0 * w0 + w1 * w1);
+}
+
+/* dM, dA, dR: derivatives of the micro matrices of or_assemble_q1 with respect
+ * to parameter k of the deformation (same quadrature, same pattern). */
+int or_assemble_q1_dparam(int N, int family, const double *prm, int k, const double D[3],
+                          const int *rowptr, const int *col, double *dM, double *dA, double *dR)
+{
+    int n1 = N + 1, nnz = rowptr[n1 * n1];
+    double h = 1.0 / N;
+    const double e1[2] = {1.0, 0.0};
+    memset(dM, 0, sizeof(double) * nnz);
+    memset(dA, 0, sizeof(double) * nnz);
+    memset(dR, 0, sizeof(double) * nnz);
+    if (k < 0 || k >= or_family_nparam(family)) return OR_E_ARG;
+    for (int b = 0; b < N; ++b)
+        for (int a = 0; a < N; ++a) {
+            int gl[4] = {a + n1 * b, a + 1 + n1 * b, a + n1 * (b + 1), a + 1 + n1 * (b + 1)};
+            double Me[4][4] = {{0}}, Ae[4][4] = {{0}};
+            for (int qt = 0; qt < 2; ++qt)
+                for (int qs = 0; qs < 2; ++qs) {
+                    double s = gauss_pt(qs), t = gauss_pt(qt);
+                    double chi[2], F[4], dF[4], dJ, dC[3], dsg;
+                    or_chi(family, prm, (a + s) * h, (b + t) * h, chi, F);
+                    or_dchi(family, k, (a + s) * h, (b + t) * h, dF);
+                    dpullback(F, dF, D, e1, &dJ, dC, &dsg);
+                    double phi[4], ds[4], dt[4];
+                    q1_shape(s, t, phi, ds, dt);
+                    for (int i = 0; i < 4; ++i)
+                        for (int j = 0; j < 4; ++j) {
+                            Me[i][j] += 0.25 * h * h * dJ * phi[i] * phi[j];
+                            Ae[i][j] += 0.25 * (ds[i] * (dC[0] * ds[j] + dC[1] * dt[j]) +
+                                                dt[i] * (dC[1] * ds[j] + dC[2] * dt[j]));
+                        }
+                }
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    int kk = csr_pos(rowptr, col, gl[i], gl[j]);
+                    dM[kk] += Me[i][j];
+                    dA[kk] += Ae[i][j];
+                }
+        }
+    for (int b = 0; b < N; ++b) {
+        int gg[2] = {N + n1 * b, N + n1 * (b + 1)};
+        double Re[2][2] = {{0}};
+        for (int qt = 0; qt < 2; ++qt) {
+            double t = gauss_pt(qt);
+            double chi[2], F[4], dF[4], dJ, dC[3], dsg;
+            or_chi(family, prm, 1.0, (b + t) * h, chi, F);
+            or_dchi(family, k, 1.0, (b + t) * h, dF);
+            dpullback(F, dF, D, e1, &dJ, dC, &dsg);
+            double ph[2] = {1 - t, t};
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) Re[i][j] += 0.5 * h * dsg * ph[i] * ph[j];
+        }
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) dR[csr_pos(rowptr, col, gg[i], gg[j])] += Re[i][j];
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sparse kernels and Jacobi-preconditioned CG (Sec. 3.5, last paragraph).   */
 /* ------------------------------------------------------------------------ */
 void or_csr_matvec(int n, const int *rowptr, const int *col, const double *val,
