@@ -193,6 +193,26 @@ tsf_status tsf_get_geometry(tsf_ctx *ctx, double *gamma_out, double *vol_out, in
 tsf_status tsf_get_stats(tsf_ctx *ctx, tsf_stats *out);
 tsf_status tsf_reset_stats(tsf_ctx *ctx);
 
+/* Gradient of the mean macro concentration after a march, by a discrete
+ * adjoint of the implicit two-scale steps (the Eq. (17) step operator
+ * differentiated through the pull-back factors of Eqs. (13)-(16)).
+ *   J = int_Omega u(t_N) dx = sum_k m_k u_k^N   (Omega = [0,1]^2, m = row sums of M_H)
+ * after nsteps steps of size dt from the current state, and dJ/dp for every
+ * per-node deformation parameter of the family given to tsf_set_deformation
+ * (grad_out[i * nparam + k]; parameters that do not change F, such as the
+ * shift of the affine family, get 0).  The forward states are kept at
+ * checkpoints every ckpt_every steps and recomputed segment by segment for
+ * the backward march.  The gradient is that of the discrete march as solved
+ * (use FP64 and tight tolerances when comparing with finite differences).
+ * Requires the Neumann macro boundary and no sources (TSF_E_ARG otherwise).
+ * J_out, grad_out: host (on_device = 0) or device pointers, may be NULL.  On
+ * return the state is the state after the nsteps steps (as after tsf_step)
+ * and the call has synchronised the stream.  The call allocates its own
+ * checkpoint buffers (about (nsteps/ckpt_every + ckpt_every + 3) states) and
+ * frees them before returning; TSF_E_OOM if that fails. */
+tsf_status tsf_adjoint_mean_u(tsf_ctx *ctx, double dt, int nsteps, int ckpt_every, double *J_out, double *grad_out,
+                              int on_device);
+
 /* Device memory: bytes of the workspace the current meshes need, and binding
  * of a caller-owned device buffer of at least that size (256-byte aligned)
  * that the library then uses for all its arrays (e.g. memory from PyTorch's

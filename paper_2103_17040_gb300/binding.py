@@ -30,7 +30,7 @@ EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micr
            "tsf_set_physics", "tsf_set_deformation", "tsf_set_state", "tsf_set_sources", "tsf_step",
            "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux",
            "tsf_get_geometry", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
-           "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc"]
+           "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u"]
 TSF_NOALLOC_MAX_NM = 128
 
 
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
     L.tsf_destroy.restype = None
     L.tsf_version.argtypes = []
     L.tsf_macro_solve_noalloc.argtypes = [i, i, d, d, d, vp, vp, vp, vp, vp, d, i, vp, ctypes.POINTER(ctypes.c_int)]
+    L.tsf_adjoint_mean_u.argtypes = [vp, d, i, i, vp, vp, i]
     for f in EXPORTS:
         fn = getattr(L, f)
         if f not in ("tsf_default_options", "tsf_last_error", "tsf_destroy"):
@@ -257,6 +258,19 @@ def tsf_reset_stats(ctx):
     _check(ctx, _lib.tsf_reset_stats(ctx))
 
 
+def tsf_adjoint_mean_u(ctx, dt, nsteps, ckpt_every, nM, nparam, grad_out=None):
+    """(J, grad [nM * nparam]) of the mean macro concentration after the march."""
+    p, dev, g = _out(grad_out, nM * nparam) if nparam else (None, 0, np.zeros(0))
+    J = np.zeros(1)
+    if dev:
+        import torch
+        Jt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        _check(ctx, _lib.tsf_adjoint_mean_u(ctx, float(dt), int(nsteps), int(ckpt_every), Jt.data_ptr(), p, 1))
+        return float(Jt.item()), g
+    _check(ctx, _lib.tsf_adjoint_mean_u(ctx, float(dt), int(nsteps), int(ckpt_every), J.ctypes.data, p, 0))
+    return float(J[0]), g
+
+
 def tsf_workspace_bytes(ctx) -> int:
     n = ctypes.c_size_t()
     _check(ctx, _lib.tsf_workspace_bytes(ctx, ctypes.byref(n)))
@@ -349,6 +363,7 @@ class TwoScale:
         tsf_set_physics(self.ctx, D, kappa, macro_diff)
 
     def set_deformation(self, family, params):
+        self.family = int(family)
         params = np.zeros((self.nM, 0)) if params is None else params
         nparam = {0: 0, 1: 1, 2: 2, 3: 6, 4: 5}[int(family)]
         tsf_set_deformation(self.ctx, family, nparam, params)
@@ -386,3 +401,9 @@ class TwoScale:
 
     def reset_stats(self):
         tsf_reset_stats(self.ctx)
+
+    def adjoint_mean_u(self, dt, nsteps, ckpt_every=10, family=None):
+        """(J, dJ/dparams [nM, nparam]) after nsteps from the current state."""
+        nparam = {0: 0, 1: 1, 2: 2, 3: 6, 4: 5}[self.family if family is None else family]
+        J, g = tsf_adjoint_mean_u(self.ctx, dt, nsteps, ckpt_every, self.nM, nparam)
+        return J, np.asarray(g).reshape(self.nM, nparam)

@@ -11,6 +11,7 @@
 #include "tsfem.h"
 #include "tsf_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -720,37 +721,29 @@ static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
     return TSF_OK;
 }
 
-tsf_status tsf_step(tsf_ctx* ctx, double dt, int nsteps) {
-    if (!ctx) return TSF_E_ARG;
-    if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(ctx, TSF_E_ARG, "need dt > 0 and nsteps >= 0");
-    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
-    if (!ctx->state_set) return fail(ctx, TSF_E_STATE, "set the state first");
-    if (nsteps == 0) return TSF_OK;
+// Operators for dt, macro preconditioner choice, micro variant (autotuned on
+// first use): everything a step needs besides the state.
+static tsf_status prepare_step(tsf_ctx* ctx, double dt) {
     if (!ctx->ops_valid || ctx->ops_dt != dt) {
         tsf_status st = build_operators(ctx, dt);
         if (st) return st;
         invalidate_graph(ctx);
     }
     ctx->use_dct = macro_smem_bytes(ctx->N1, ctx->bc, 1) <= (size_t)ctx->smem_optin;
-    {
-        bool any = false;
-        for (int t = 0; t < kNumTilings; ++t) any = any || tiling_fits(t, ctx->opt.precision, ctx->n1, ctx->smem_optin);
-        if (!any) return fail(ctx, TSF_E_ARG, "micro mesh too large for one thread block in this precision");
-    }
+    bool any = false;
+    for (int t = 0; t < kNumTilings; ++t) any = any || tiling_fits(t, ctx->opt.precision, ctx->n1, ctx->smem_optin);
+    if (!any) return fail(ctx, TSF_E_ARG, "micro mesh too large for one thread block in this precision");
     if (ctx->tiling < 0 || ctx->tiling_prec != ctx->opt.precision) {
         tsf_status st = autotune(ctx, dt);
         if (st) return st;
         invalidate_graph(ctx);
     }
-    if (ctx->opt.use_graph) {
-        if (!ctx->graph_valid || ctx->graph_dt != dt) {
-            tsf_status st = capture_graph(ctx, dt);
-            if (st) return st;
-        }
-        for (int s = 0; s < nsteps; ++s) CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
-        return TSF_OK;
-    }
-    // plain launches, host-controlled coupling loop
+    return TSF_OK;
+}
+
+// Steps with plain launches and a host-controlled coupling loop, on whatever
+// arrays ctx->u / ctx->v point to.
+static tsf_status run_plain_steps(tsf_ctx* ctx, double dt, int nsteps) {
     const bool prof = ctx->opt.profile != 0;
     if (prof && !ctx->ev[0])
         for (int k = 0; k < 4; ++k) CU(cudaEventCreate(&ctx->ev[k]));
@@ -780,6 +773,162 @@ tsf_status tsf_step(tsf_ctx* ctx, double dt, int nsteps) {
         }
     }
     return TSF_OK;
+}
+
+tsf_status tsf_step(tsf_ctx* ctx, double dt, int nsteps) {
+    if (!ctx) return TSF_E_ARG;
+    if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(ctx, TSF_E_ARG, "need dt > 0 and nsteps >= 0");
+    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
+    if (!ctx->state_set) return fail(ctx, TSF_E_STATE, "set the state first");
+    if (nsteps == 0) return TSF_OK;
+    tsf_status st = prepare_step(ctx, dt);
+    if (st) return st;
+    if (ctx->opt.use_graph) {
+        if (!ctx->graph_valid || ctx->graph_dt != dt) {
+            st = capture_graph(ctx, dt);
+            if (st) return st;
+        }
+        for (int s = 0; s < nsteps; ++s) CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
+        return TSF_OK;
+    }
+    return run_plain_steps(ctx, dt, nsteps);
+}
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint of the march (kernels and derivation in tsf_adjoint.cu).
+// Forward with checkpoints, then segment by segment backwards: recompute the
+// segment's states from its checkpoint, step the scaled adjoint state with
+// the forward solver (W A is symmetric), accumulate the gradient products.
+// ---------------------------------------------------------------------------
+tsf_status tsf_adjoint_mean_u(tsf_ctx* ctx, double dt, int nsteps, int ckpt_every, double* J_out, double* grad_out,
+                              int on_device) {
+    if (!ctx) return TSF_E_ARG;
+    if (!(dt > 0) || !std::isfinite(dt) || nsteps < 1 || ckpt_every < 1)
+        return fail(ctx, TSF_E_ARG, "need dt > 0, nsteps >= 1, ckpt_every >= 1");
+    if (!ctx->ws_valid || !ctx->geom_set || !ctx->state_set)
+        return fail(ctx, TSF_E_STATE, "set meshes, deformation and state first");
+    if (ctx->bc != TSF_BC_NEUMANN) return fail(ctx, TSF_E_ARG, "the adjoint supports the Neumann macro boundary only");
+    if (ctx->has_fv || ctx->has_g || ctx->has_fu)
+        return fail(ctx, TSF_E_ARG, "the adjoint supports problems without sources only");
+    static const int np_of[5] = {0, 1, 2, 6, 5};
+    const int nparam = np_of[ctx->family];
+    tsf_status st = prepare_step(ctx, dt);
+    if (st) return st;
+    const int K = ckpt_every, nck = (nsteps + K - 1) / K;
+    const size_t nM = ctx->nM, nv = nM * ctx->nmp, ns = nM + nv;
+    const size_t cells = (size_t)ctx->Nm * ctx->Nm;
+    const size_t nacc = nM * cells * 16, nea = nM * (size_t)ctx->Nm * 2;
+    const size_t total = (size_t)nck * ns + (size_t)(K + 1) * ns + 2 * ns + nacc + nea + nM * 6 + 8;
+    double* buf = nullptr;
+    cudaError_t e = cudaMalloc((void**)&buf, total * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, TSF_E_OOM, "adjoint buffers (%zu bytes): %s", total * sizeof(double), cudaGetErrorString(e));
+    }
+    double* ck = buf;
+    double* seg = ck + (size_t)nck * ns;
+    double* lam = seg + (size_t)(K + 1) * ns;
+    double* xN = lam + ns;
+    double* acc = xN + ns;
+    double* eacc = acc + nacc;
+    double* grad = eacc + nea;
+    double* Jd = grad + nM * 6;
+    const int saved_graph = ctx->opt.use_graph;
+    ctx->opt.use_graph = 0;
+    invalidate_graph(ctx);
+    double* const u_state = ctx->u;
+    double* const v_state = ctx->v;
+    auto save = [&](double* dst) -> tsf_status {
+        CU(cudaMemcpyAsync(dst, ctx->u, nM * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(dst + nM, ctx->v, nv * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        return TSF_OK;
+    };
+    auto load = [&](const double* src) -> tsf_status {
+        CU(cudaMemcpyAsync(ctx->u, src, nM * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ctx->v, src + nM, nv * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        return TSF_OK;
+    };
+    auto adjoint_step = [&]() -> tsf_status {  // lam <- forward step of lam
+        ctx->u = lam;
+        ctx->v = lam + nM;
+        tsf_status s2 = run_plain_steps(ctx, dt, 1);
+        ctx->u = u_state;
+        ctx->v = v_state;
+        return s2;
+    };
+    auto body = [&]() -> tsf_status {
+        // forward march with checkpoints
+        for (int s = 0; s < nck; ++s) {
+            tsf_status s2 = save(ck + (size_t)s * ns);
+            if (s2) return s2;
+            if ((s2 = run_plain_steps(ctx, dt, std::min(K, nsteps - s * K)))) return s2;
+        }
+        tsf_status s2 = save(xN);
+        if (s2) return s2;
+        CU(launch_mean_u(ctx->u, ctx->nM, ctx->NM, Jd, ctx->stream));
+        // terminal adjoint: A lam~ = (m, 0) = B (dt 1, 0)
+        CU(launch_fill(lam, dt, nM, ctx->stream));
+        CU(launch_fill(lam + nM, 0.0, nv, ctx->stream));
+        if ((s2 = adjoint_step())) return s2;
+        CU(cudaMemsetAsync(acc, 0, (nacc + nea) * sizeof(double), ctx->stream));
+        for (int s = nck - 1; s >= 0; --s) {
+            const int n0 = s * K, nsg = std::min(K, nsteps - n0);
+            CU(cudaMemcpyAsync(seg, ck + (size_t)s * ns, ns * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+            if ((s2 = load(seg))) return s2;
+            for (int j = 1; j <= nsg; ++j) {
+                if ((s2 = run_plain_steps(ctx, dt, 1))) return s2;
+                if ((s2 = save(seg + (size_t)j * ns))) return s2;
+            }
+            for (int j = nsg - 1; j >= 0; --j) {
+                if (n0 + j != nsteps - 1 && (s2 = adjoint_step())) return s2;
+                AdjAccArgs aa{};
+                aa.Nm = ctx->Nm;
+                aa.n1 = ctx->n1;
+                aa.nmp = ctx->nmp;
+                aa.nM = ctx->nM;
+                aa.nu = lam + nM;
+                aa.mu = lam;
+                aa.v1 = seg + (size_t)(j + 1) * ns + nM;
+                aa.v0 = seg + (size_t)j * ns + nM;
+                aa.u1 = seg + (size_t)(j + 1) * ns;
+                aa.inv_dt = 1.0 / dt;
+                aa.acc = acc;
+                aa.eacc = eacc;
+                CU(launch_adj_accumulate(aa, ctx->stream));
+            }
+        }
+        if ((s2 = load(xN))) return s2;
+        AdjGradArgs ga{};
+        ga.Nm = ctx->Nm;
+        ga.nM = ctx->nM;
+        ga.NM = ctx->NM;
+        ga.family = ctx->family;
+        ga.nparam = nparam;
+        ga.prm5 = ctx->prm5;
+        ga.D11 = ctx->D[0];
+        ga.D12 = ctx->D[1];
+        ga.D22 = ctx->D[2];
+        ga.kappa = ctx->kappa;
+        ga.acc = acc;
+        ga.eacc = eacc;
+        ga.grad = grad;
+        if (nparam > 0) CU(launch_adj_gradient(ga, ctx->stream));
+        if (grad_out && nparam > 0)
+            CU(cudaMemcpyAsync(grad_out, grad, nM * nparam * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+        if (J_out)
+            CU(cudaMemcpyAsync(J_out, Jd, sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        return TSF_OK;
+    };
+    st = body();
+    ctx->u = u_state;
+    ctx->v = v_state;
+    ctx->opt.use_graph = saved_graph;
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    return st;
 }
 
 tsf_status tsf_synchronize(tsf_ctx* ctx) {

@@ -229,4 +229,29 @@ cudaError_t launch_flux(int n1, int nm, int nmp, int nM, double kappa, const dou
 cudaError_t configure_micro_kernels(int smem_optin);
 cudaError_t configure_macro_kernels(int smem_optin);
 
+// discrete adjoint (tsf_adjoint.cu)
+struct AdjAccArgs {
+    int Nm, n1, nmp, nM;
+    const double* nu;       // [nM][nmp] scaled adjoint micro state at step n+1
+    const double* mu;       // [nM]      scaled adjoint macro state at step n+1
+    const double* v1;       // [nM][nmp] forward micro state X^{n+1}
+    const double* v0;       // [nM][nmp] forward micro state X^n
+    const double* u1;       // [nM]      forward macro state at n+1
+    double inv_dt;
+    double* acc;            // [nM][Nm*Nm][4 qp][4]: s, T11, T12+T21, T22
+    double* eacc;           // [nM][Nm][2 edge qp]
+};
+struct AdjGradArgs {
+    int Nm, nM, NM, family, nparam;
+    const double* prm5;
+    double D11, D12, D22, kappa;
+    const double* acc;
+    const double* eacc;
+    double* grad;           // [nM][nparam]
+};
+cudaError_t launch_adj_accumulate(const AdjAccArgs& a, cudaStream_t s);
+cudaError_t launch_adj_gradient(const AdjGradArgs& a, cudaStream_t s);
+cudaError_t launch_mean_u(const double* u, int nM, int NM, double* J, cudaStream_t s);
+cudaError_t launch_fill(double* x, double val, size_t n, cudaStream_t s);
+
 }  // namespace tsf
