@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
+    ap.add_argument("--fd-dirs", type=int, default=20, help="c5: finite-difference directions per family")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, e2e, cpu baseline")
     return ap.parse_args()
@@ -387,10 +388,245 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_c5(args):
+    """Differentiation workload: the gradient of J = mean of u at the final time
+    with respect to the per-node deformation parameters, after the 50-step FP64
+    march of the 64x64 macro / 32x32 micro bump workload with checkpoints every
+    10 steps (discrete adjoint on the GPU).  Timed at the workload's
+    tolerances; then checked against central differences (h = 1e-6) of the GPU
+    forward march along seeded unit directions, both sides at tolerance 1e-14
+    with a fixed micro-solve variant, on the bump family and on the
+    shear+bump family (64x64 / 32x32, D = diag(1, 0.1))."""
+    import torch
+    import paper_2103_17040_gb300 as T
+    import workloads as W
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    T.load_library()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    w = W.c5()
+    ckpt = 10
+
+    def ev_time(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    # ---- timing at the workload's tolerances ----
+    P = make_problem(T, w, "fp64", stream)
+    P.step(w.dt, 2)
+    P.set_state(w.u0, None)
+    P.adjoint_mean_u(w.dt, 3, 2)
+    P.set_state(w.u0, None)
+    t_fwd, _ = ev_time(lambda: P.step(w.dt, w.nsteps))
+    t_grad_l = []
+    for _ in range(3):
+        P.set_state(w.u0, None)
+        t, (J, g) = ev_time(lambda: P.adjoint_mean_u(w.dt, w.nsteps, ckpt))
+        t_grad_l.append(t)
+    tiling = P.stats()["tiling"]
+    P.close()
+
+    x1, x2 = W.macro_coords(w.NM)
+    mH = 0.25 * np.where((x1 == 0) | (x1 == 1), 1.0, 2.0) * np.where((x2 == 0) | (x2 == 1), 1.0, 2.0) / w.NM ** 2
+
+    def fd_check(fam, prm, D, ndirs, seed):
+        tight = dict(cg_tol=1e-14, coupling_tol=1e-14, macro_tol=1e-14, tiling=tiling, cg_maxit=20000,
+                     coupling_maxit=100)
+        Q = T.TwoScale(w.Nm, w.NM, bc=w.bc, precision=T.TSF_FP64, stream=stream, **tight)
+        Q.set_physics(D, w.kappa, w.Du)
+
+        def J_at(p):
+            Q.set_deformation(fam, p)
+            Q.set_state(w.u0, None)
+            Q.step(w.dt, w.nsteps)
+            return float(np.dot(mH, Q.u()))
+
+        Q.set_deformation(fam, prm)
+        Q.set_state(w.u0, None)
+        t0 = time.perf_counter()
+        J0, g0 = Q.adjoint_mean_u(w.dt, w.nsteps, ckpt)
+        t_adj = time.perf_counter() - t0
+        # noise floor: change of J when the tolerances are loosened tenfold
+        L = T.TwoScale(w.Nm, w.NM, bc=w.bc, precision=T.TSF_FP64, stream=stream,
+                       **dict(tight, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13))
+        L.set_physics(D, w.kappa, w.Du)
+        L.set_deformation(fam, prm)
+        L.set_state(w.u0, None)
+        L.step(w.dt, w.nsteps)
+        epsJ = abs(float(np.dot(mH, L.u())) - J0)
+        L.close()
+        h = 1e-6
+        rows = []
+        t0 = time.perf_counter()
+        for k in range(ndirs):
+            e = W.rng(1000 + seed + k).standard_normal(prm.shape)
+            e /= np.linalg.norm(e)
+            fd = (J_at(prm + h * e) - J_at(prm - h * e)) / (2 * h)
+            ad = float(np.sum(g0 * e))
+            rows.append((ad, fd))
+        t_fd = time.perf_counter() - t0
+        Q.close()
+        ad = np.array([r[0] for r in rows])
+        fd = np.array([r[1] for r in rows])
+        rel = np.abs(fd - ad) / np.abs(ad)
+        return {"family": fam, "directions": ndirs, "h": h, "J": J0, "grad_norm": float(np.linalg.norm(g0)),
+                "median_abs_directional": float(np.median(np.abs(ad))),
+                "rel_err_max": float(rel.max()), "rel_err_median": float(np.median(rel)),
+                "abs_err_max": float(np.abs(fd - ad).max()),
+                "noise_floor_abs": epsJ / h, "J_change_tol_1e-13_vs_1e-14": epsJ,
+                "adjoint_s": t_adj, "fd_s": t_fd,
+                "per_direction": [[float(a), float(b)] for a, b in rows]}
+
+    bump = fd_check(W.FAMILY_BUMP, w.params, w.D, args.fd_dirs, 0)
+    w3 = W.c3(NM=w.NM, Nm=w.Nm)
+    shear = fd_check(w3.family, w3.params, w3.D, args.fd_dirs, 500)
+    t_grad = statistics.median(t_grad_l)
+    line = {"metric": "gradient wall time (dJ/da, 4225 parameters)", "value": t_grad, "unit": "s",
+            "n_gpus": 1, "steps": w.nsteps, "warmup": 1, "higher_is_better": False, "dtype": "f64",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": f"c5: macro {w.NM}x{w.NM} ({w.nM} micro problems), micro {w.Nm}x{w.Nm}, "
+                                   f"bump a ~ U[0,0.2], FP64, dt={w.dt} x {w.nsteps} steps, checkpoints every "
+                                   f"{ckpt}, tol {w.tol}, coupling tol {w.coupling_tol}"},
+            "forward_s": t_fwd, "gradient_over_forward": t_grad / t_fwd, "J": J, "grad_norm": float(np.linalg.norm(g)),
+            "tiling": tiling, "fd_check": {"bump": bump, "shear_bump": shear}}
+    print(json.dumps(line))
+
+
+def run_c4(args):
+    """32 independent two-scale problems of uneven sizes (macro 16..96 cells,
+    micro 16..48 cells per side, 200M micro DoFs in all), mixed precision,
+    each with its autotuned micro-solve variant; one batch step is one CUDA
+    graph launch with one branch per problem.  Beside the batch: the same
+    problems stepped one after another (one graph per problem and step)."""
+    import torch
+    import paper_2103_17040_gb300 as T
+    import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    T.load_library()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ws = W.c4(seed=rank)
+    dt = ws[0].dt
+    K, Wm = args.steps, args.warmup
+
+    def build():
+        B = T.TwoScaleBatch([(w.Nm, w.NM, w.bc) for w in ws], precision=T.TSF_MIXED, stream=stream,
+                            cg_tol=ws[0].tol, coupling_tol=ws[0].coupling_tol)
+        for k, w in enumerate(ws):
+            B[k].set_physics(w.D, w.kappa, w.Du)
+            B[k].set_deformation(w.family, w.params)
+            B[k].set_state(w.u0, None)
+        return B
+
+    B = build()
+    B.step(dt, Wm)
+    B.synchronize()
+    B.reset_stats()
+    barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
+    clk = Clocks(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.step(dt, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    B.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = B.stats()
+    tilings = [B[k].stats()["tiling"] for k in range(len(ws))]
+    if world > 1:
+        t = torch.tensor([ms, float(st["dof_cg_iters"])], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        ms_max, dof_iters = float(mx[0]), float(t[1])
+    else:
+        ms_max, dof_iters = ms, float(st["dof_cg_iters"])
+
+    # the same problems one after another, each its own graph per step
+    seq_ms = 0.0
+    ks = max(1, min(K, 5))
+    for k in range(len(ws)):
+        P = B[k]
+        e0.record(stream)
+        P.step(dt, ks)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+
+    # per-kernel timing of the micro solves (plain launches, one problem at a time)
+    bytes_total, micro_ms, launches = 0.0, 0.0, 0
+    for k, w in enumerate(ws):
+        P = B[k]
+        o = T.tsf_default_options()
+        o.precision, o.cg_tol, o.coupling_tol = T.TSF_MIXED, w.tol, w.coupling_tol
+        o.use_graph, o.profile, o.tiling = 0, 1, tilings[k]
+        o.cuda_stream = stream.cuda_stream
+        T.tsf_set_options(P.ctx, o)
+        P.reset_stats()
+        P.step(dt, 2)
+        P.synchronize()
+        sp = P.stats()
+        bytes_total += BYTES_PER_DOF_ITER["mixed"] * sp["dof_cg_iters"] + BYTES_PER_DOF_SWEEP * sp["refine_sweeps"] * w.nm
+        micro_ms += sp["micro_kernel_ms"]
+        launches += sp["micro_launches"]
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = bytes_total / (micro_ms / 1e3) / 1e9
+    B.close()
+    ndof = sum(w.nM * w.nm for w in ws)
+    line = {
+        "metric": "micro DOF-CG-iters/s", "value": dof_iters / (ms_max / 1e3), "unit": "DOF-iter/s",
+        "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"c4: {len(ws)} independent two-scale problems, macro 16..96 / micro 16..48 cells "
+                               f"per side, {ndof} micro DoFs, dt={dt}, tol={ws[0].tol}, mixed, one graph per "
+                               f"batch step", "problems": len(ws), "micro_dofs": ndof,
+                   "l2": "working set > L2, no flush"},
+        "batch_steps_per_s": world * K / (ms_max / 1e3),
+        "sequential_ms_per_step": seq_ms / ks, "batch_speedup_vs_sequential": (seq_ms / ks) / (ms / K),
+        "coupling_iters_per_problem_step": st["coupling_iters_total"] / (K * len(ws)),
+        "tilings": tilings, "gpu_launches": 2 * K * len(ws) + 2 * st["coupling_iters_total"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "micro solve (per-problem variant)", "launches_timed": launches,
+                     "avg_launch_ms": micro_ms / max(launches, 1),
+                     "bytes_per_launch": bytes_total / max(launches, 1),
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s"},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_c4(args)
+    elif args.workload == "c5":
+        run_c5(args)
     else:
         run_gb300(args)
 

@@ -230,6 +230,47 @@ void tsf_destroy(tsf_ctx *ctx);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int tsf_version(void);
 
+/* -------------------------------------------------------------------------
+ * Batches of independent two-scale problems (library addition; the paper
+ * solves one problem at a time).  Each instance is an ordinary context: get
+ * it with tsf_batch_instance and configure it with the tsf_set_* calls (its
+ * own micro and macro meshes, physics, deformation, state, sources), read it
+ * with the tsf_get_* calls.  All instances enqueue on the batch's stream.
+ * tsf_batch_step advances every instance by nsteps steps of size dt; with
+ * use_graph = 1 each batch step is ONE CUDA graph launch holding one
+ * independent branch per instance (its prologues and its own device-side
+ * coupling loop), so the instances run concurrently.  The graph is captured
+ * on the first step and again whenever an instance's operators, variant,
+ * workspace or dt change.  Each instance chooses its own micro-solve variant
+ * (timed on its own problem when options.tiling = -1).
+ * ------------------------------------------------------------------------- */
+typedef struct tsf_batch tsf_batch;
+#define TSF_BATCH_MAX 4096
+
+/* Create a batch of ninst (1..TSF_BATCH_MAX) empty instances with options
+ * opt (NULL = defaults; opt->cuda_stream NULL = a stream owned by the batch).
+ * Errors: TSF_E_ARG, TSF_E_CUDA, TSF_E_OOM. */
+tsf_status tsf_batch_create(tsf_batch **out, int ninst, const tsf_options *opt);
+
+/* Borrowed handle of instance inst (0-based); it lives as long as the batch
+ * and must not be passed to tsf_destroy.  Calling tsf_step on it steps that
+ * instance alone. */
+tsf_status tsf_batch_instance(tsf_batch *b, int inst, tsf_ctx **out);
+
+/* Advance every instance by nsteps implicit Euler steps of size dt
+ * (asynchronous on the batch stream; device-side errors are reported by
+ * tsf_batch_synchronize).  TSF_E_STATE if an instance lacks meshes,
+ * deformation or state; instance errors name the instance. */
+tsf_status tsf_batch_step(tsf_batch *b, double dt, int nsteps);
+tsf_status tsf_batch_synchronize(tsf_batch *b);
+
+/* Statistics summed over the instances (coupling_iters_last, max_inner_iters
+ * and coupling_change are maxima; steps counts batch steps; tiling = -1). */
+tsf_status tsf_batch_get_stats(tsf_batch *b, tsf_stats *out);
+tsf_status tsf_batch_reset_stats(tsf_batch *b);
+const char *tsf_batch_last_error(const tsf_batch *b);
+void tsf_batch_destroy(tsf_batch *b);
+
 /* ---------------------------------------------------------------------------
  * Macro solve that allocates no device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc when they

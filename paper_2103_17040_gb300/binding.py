@@ -30,8 +30,11 @@ EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micr
            "tsf_set_physics", "tsf_set_deformation", "tsf_set_state", "tsf_set_sources", "tsf_step",
            "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux",
            "tsf_get_geometry", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
-           "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u"]
+           "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u",
+           "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_synchronize",
+           "tsf_batch_get_stats", "tsf_batch_reset_stats", "tsf_batch_last_error", "tsf_batch_destroy"]
 TSF_NOALLOC_MAX_NM = 128
+TSF_BATCH_MAX = 4096
 
 
 class tsf_options(ctypes.Structure):
@@ -101,9 +104,20 @@ def load_library(path: str = LIB_PATH):
     L.tsf_version.argtypes = []
     L.tsf_macro_solve_noalloc.argtypes = [i, i, d, d, d, vp, vp, vp, vp, vp, d, i, vp, ctypes.POINTER(ctypes.c_int)]
     L.tsf_adjoint_mean_u.argtypes = [vp, d, i, i, vp, vp, i]
+    L.tsf_batch_create.argtypes = [pp, i, ctypes.POINTER(tsf_options)]
+    L.tsf_batch_instance.argtypes = [vp, i, pp]
+    L.tsf_batch_step.argtypes = [vp, d, i]
+    L.tsf_batch_synchronize.argtypes = [vp]
+    L.tsf_batch_get_stats.argtypes = [vp, ctypes.POINTER(tsf_stats)]
+    L.tsf_batch_reset_stats.argtypes = [vp]
+    L.tsf_batch_last_error.argtypes = [vp]
+    L.tsf_batch_last_error.restype = ctypes.c_char_p
+    L.tsf_batch_destroy.argtypes = [vp]
+    L.tsf_batch_destroy.restype = None
     for f in EXPORTS:
         fn = getattr(L, f)
-        if f not in ("tsf_default_options", "tsf_last_error", "tsf_destroy"):
+        if f not in ("tsf_default_options", "tsf_last_error", "tsf_destroy", "tsf_batch_last_error",
+                     "tsf_batch_destroy"):
             fn.restype = ctypes.c_int
     _lib = L
     return L
@@ -258,6 +272,53 @@ def tsf_reset_stats(ctx):
     _check(ctx, _lib.tsf_reset_stats(ctx))
 
 
+def _bcheck(b, status):
+    if status != TSF_OK:
+        raise TsfError(status, _lib.tsf_batch_last_error(b).decode() if b else "")
+
+
+def tsf_batch_create(ninst, opt: tsf_options | None = None) -> int:
+    L = load_library()
+    h = ctypes.c_void_p()
+    st = L.tsf_batch_create(ctypes.byref(h), int(ninst), ctypes.byref(opt) if opt is not None else None)
+    if st != TSF_OK:
+        raise TsfError(st, "tsf_batch_create failed")
+    return h.value
+
+
+def tsf_batch_instance(b, inst) -> int:
+    h = ctypes.c_void_p()
+    _bcheck(b, _lib.tsf_batch_instance(b, int(inst), ctypes.byref(h)))
+    return h.value
+
+
+def tsf_batch_step(b, dt, nsteps=1):
+    _bcheck(b, _lib.tsf_batch_step(b, float(dt), int(nsteps)))
+
+
+def tsf_batch_synchronize(b):
+    _bcheck(b, _lib.tsf_batch_synchronize(b))
+
+
+def tsf_batch_get_stats(b) -> dict:
+    s = tsf_stats()
+    _bcheck(b, _lib.tsf_batch_get_stats(b, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def tsf_batch_reset_stats(b):
+    _bcheck(b, _lib.tsf_batch_reset_stats(b))
+
+
+def tsf_batch_last_error(b) -> str:
+    return _lib.tsf_batch_last_error(b).decode()
+
+
+def tsf_batch_destroy(b):
+    if b:
+        _lib.tsf_batch_destroy(b)
+
+
 def tsf_adjoint_mean_u(ctx, dt, nsteps, ckpt_every, nM, nparam, grad_out=None):
     """(J, grad [nM * nparam]) of the mean macro concentration after the march."""
     p, dev, g = _out(grad_out, nM * nparam) if nparam else (None, 0, np.zeros(0))
@@ -318,6 +379,18 @@ def tsf_macro_solve_noalloc(NM, bc, dt, macro_diff, kappa, gam, cH, rho, u0, u_o
 # ---------------------------------------------------------------------------
 # convenience wrapper (still marshalling only)
 # ---------------------------------------------------------------------------
+def _make_options(precision, stream, opts):
+    o = tsf_default_options()
+    o.precision = int(precision)
+    for k, v in opts.items():
+        setattr(o, k, v)
+    if stream is not None:
+        o.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+        if not o.cuda_stream:
+            raise ValueError("pass a non-default stream (a NULL stream makes the library create its own)")
+    return o
+
+
 class TwoScale:
     """One two-scale problem on the current CUDA device.
 
@@ -326,16 +399,13 @@ class TwoScale:
     PyTorch's caching allocator; ``None`` lets the library allocate it.
     """
 
-    def __init__(self, Nm, NM, bc=TSF_BC_NEUMANN, precision=TSF_MIXED, stream=None, workspace="torch", **opts):
-        o = tsf_default_options()
-        o.precision = int(precision)
-        for k, v in opts.items():
-            setattr(o, k, v)
-        if stream is not None:
-            o.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
-            if not o.cuda_stream:
-                raise ValueError("pass a non-default stream (a NULL stream makes the library create its own)")
-        self.ctx = tsf_create(o)
+    def __init__(self, Nm, NM, bc=TSF_BC_NEUMANN, precision=TSF_MIXED, stream=None, workspace="torch",
+                 _instance=None, **opts):
+        if _instance is None:
+            self.ctx = tsf_create(_make_options(precision, stream, opts))
+            self._owned = True
+        else:
+            self.ctx, self._owned = _instance, False
         self.Nm, self.NM = int(Nm), int(NM)
         self.nm, self.nM = (self.Nm + 1) ** 2, (self.NM + 1) ** 2
         tsf_set_micro_mesh(self.ctx, self.Nm, self.Nm, 0)
@@ -350,7 +420,8 @@ class TwoScale:
 
     def close(self):
         if getattr(self, "ctx", None):
-            tsf_destroy(self.ctx)
+            if self._owned:
+                tsf_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):
@@ -407,3 +478,53 @@ class TwoScale:
         nparam = {0: 0, 1: 1, 2: 2, 3: 6, 4: 5}[self.family if family is None else family]
         J, g = tsf_adjoint_mean_u(self.ctx, dt, nsteps, ckpt_every, self.nM, nparam)
         return J, np.asarray(g).reshape(self.nM, nparam)
+
+
+class TwoScaleBatch:
+    """Independent two-scale problems advanced together: one CUDA graph launch
+    per batch step, one branch per instance.
+
+    ``specs``: sequence of ``(Nm, NM)`` or ``(Nm, NM, bc)``.  ``batch[i]`` is a
+    :class:`TwoScale` view of instance i (configure and read it as usual; it
+    is valid while the batch lives).
+    """
+
+    def __init__(self, specs, precision=TSF_MIXED, stream=None, workspace="torch", **opts):
+        self.b = tsf_batch_create(len(specs), _make_options(precision, stream, opts))
+        self.instances = []
+        for i, sp in enumerate(specs):
+            Nm, NM = int(sp[0]), int(sp[1])
+            bc = int(sp[2]) if len(sp) > 2 else TSF_BC_NEUMANN
+            self.instances.append(TwoScale(Nm, NM, bc, workspace=workspace,
+                                           _instance=tsf_batch_instance(self.b, i)))
+
+    def __len__(self):
+        return len(self.instances)
+
+    def __getitem__(self, i):
+        return self.instances[i]
+
+    def step(self, dt, nsteps=1):
+        tsf_batch_step(self.b, dt, nsteps)
+
+    def synchronize(self):
+        tsf_batch_synchronize(self.b)
+
+    def stats(self):
+        return tsf_batch_get_stats(self.b)
+
+    def reset_stats(self):
+        tsf_batch_reset_stats(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for p in self.instances:
+                p.ctx = None
+            tsf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -83,6 +83,7 @@ struct tsf_ctx {
     cudaGraphExec_t gexec = nullptr;
     bool graph_valid = false;
     double graph_dt = -1.0;
+    uint64_t graph_gen = 0;      // bumped whenever a captured step would go stale
     // per-launch CUDA-event timing of the plain-launch path (options.profile)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t prof_micro_n = 0, prof_macro_n = 0;
@@ -111,6 +112,7 @@ static tsf_status fail(tsf_ctx* ctx, tsf_status st, const char* fmt, ...) {
     } while (0)
 
 static void invalidate_graph(tsf_ctx* ctx) {
+    ctx->graph_gen++;
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     ctx->gexec = nullptr;
@@ -673,15 +675,21 @@ static tsf_status capture_failed(tsf_ctx* ctx, tsf_status st, cudaError_t e, con
     return fail(ctx, TSF_E_CUDA, "graph capture failed at %s: %s", what, cudaGetErrorString(e));
 }
 
-static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
-    invalidate_graph(ctx);
-    CU(cudaGraphCreate(&ctx->graph, 0));
+// Appends one step of ctx to graph G as an independent branch: the macro and
+// micro prologues, then a WHILE conditional node whose body is one coupling
+// iteration (micro solve, macro solve; the macro kernel clears the condition
+// when the coupling test passes).  On failure *what names the stage; the
+// caller abandons G.
+static cudaError_t capture_step_into(tsf_ctx* ctx, cudaGraph_t G, double dt, tsf_status* st, const char** what) {
+    *st = TSF_OK;
     cudaGraphConditionalHandle cond;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, ctx->graph, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "conditional handle");
-    e = cudaStreamBeginCaptureToGraph(ctx->stream, ctx->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "begin capture");
-    tsf_status st = enqueue_prologue(ctx, dt);
+    *what = "conditional handle";
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, G, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    *what = "begin capture";
+    e = cudaStreamBeginCaptureToGraph(ctx->stream, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    *st = enqueue_prologue(ctx, dt);
     cudaStreamCaptureStatus cs;
     cudaGraph_t capg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -689,7 +697,7 @@ static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
     e = cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &capg, &deps, nullptr, &ndeps);
     cudaGraphNode_t cnode = nullptr;
     cudaGraph_t body = nullptr;
-    if (!st && e == cudaSuccess) {
+    if (!*st && e == cudaSuccess) {
         alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
         memset(cpbuf, 0, sizeof cpbuf);
         cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
@@ -705,15 +713,27 @@ static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
     }
     cudaGraph_t endg = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &endg);
-    if (st || e != cudaSuccess || e2 != cudaSuccess)
-        return capture_failed(ctx, st, e != cudaSuccess ? e : e2, "prologue / conditional node");
+    *what = "prologue / conditional node";
+    if (*st) return cudaErrorUnknown;
+    if (e != cudaSuccess || e2 != cudaSuccess) return e != cudaSuccess ? e : e2;
+    *what = "begin body capture";
     e = cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "begin body capture");
+    if (e != cudaSuccess) return e;
     MicroArgs ma = micro_args(ctx, ctx->v);
     e = launch_micro_solve(ma, ctx->opt.precision, ctx->tiling, ctx->stream);
     if (e == cudaSuccess) e = launch_macro_solve(macro_args(ctx, dt, true, cond), ctx->stream);
     e2 = cudaStreamEndCapture(ctx->stream, &body);
-    if (e != cudaSuccess || e2 != cudaSuccess) return capture_failed(ctx, TSF_OK, e != cudaSuccess ? e : e2, "body");
+    *what = "body";
+    return e != cudaSuccess ? e : e2;
+}
+
+static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
+    invalidate_graph(ctx);
+    CU(cudaGraphCreate(&ctx->graph, 0));
+    tsf_status st;
+    const char* what;
+    cudaError_t e = capture_step_into(ctx, ctx->graph, dt, &st, &what);
+    if (e != cudaSuccess) return capture_failed(ctx, st, e, what);
     e = cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0);
     if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "instantiate");
     ctx->graph_valid = true;
@@ -1029,6 +1049,227 @@ tsf_status tsf_reset_stats(tsf_ctx* ctx) {
     CU(cudaMemcpyAsync(&ctx->ctl->steps, zero4, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return TSF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent two-scale problems.  Each instance is an ordinary
+// context on the batch's stream; a batch step is one CUDA graph holding one
+// independent branch per instance (prologues, then that instance's own
+// device-controlled coupling loop), so the instances' micro and macro
+// kernels run concurrently and small instances fill the SMs that large ones
+// leave idle.
+// ---------------------------------------------------------------------------
+struct tsf_batch {
+    std::vector<tsf_ctx*> inst;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int use_graph = 1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_valid = false;
+    double graph_dt = -1.0;
+    std::vector<uint64_t> gen;   // instance graph generations the graph was captured at
+    int steps = 0;
+    std::string err;
+};
+
+static tsf_status bfail(tsf_batch* b, tsf_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    b->err = buf;
+    return st;
+}
+
+static void batch_drop_graph(tsf_batch* b, bool destroy) {
+    if (destroy) {
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+    }
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    b->graph_valid = false;
+}
+
+// An instance error is reported with the instance's index and message.
+static tsf_status inst_fail(tsf_batch* b, int i, tsf_status st) {
+    return bfail(b, st, "instance %d: %s", i, b->inst[i]->err.c_str());
+}
+
+static tsf_status batch_capture(tsf_batch* b, double dt) {
+    batch_drop_graph(b, true);
+    cudaError_t e = cudaGraphCreate(&b->graph, 0);
+    if (e != cudaSuccess) return bfail(b, TSF_E_CUDA, "cudaGraphCreate: %s", cudaGetErrorString(e));
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        tsf_status st;
+        const char* what;
+        e = capture_step_into(b->inst[i], b->graph, dt, &st, &what);
+        if (e != cudaSuccess) {
+            batch_drop_graph(b, false);  // abandoned, as for a single context
+            cudaGetLastError();
+            if (st) return inst_fail(b, (int)i, st);
+            return bfail(b, TSF_E_CUDA, "instance %d: graph capture failed at %s: %s", (int)i, what,
+                         cudaGetErrorString(e));
+        }
+    }
+    e = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+    if (e != cudaSuccess) {
+        batch_drop_graph(b, false);
+        cudaGetLastError();
+        return bfail(b, TSF_E_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    }
+    b->gen.resize(b->inst.size());
+    for (size_t i = 0; i < b->inst.size(); ++i) b->gen[i] = b->inst[i]->graph_gen;
+    b->graph_valid = true;
+    b->graph_dt = dt;
+    return TSF_OK;
+}
+
+extern "C" {
+
+tsf_status tsf_batch_create(tsf_batch** out, int ninst, const tsf_options* opt) {
+    if (!out) return TSF_E_ARG;
+    *out = nullptr;
+    if (ninst < 1 || ninst > TSF_BATCH_MAX) return TSF_E_ARG;
+    tsf_options o;
+    tsf_default_options(&o);
+    if (opt) o = *opt;
+    if (!options_ok(&o)) return TSF_E_ARG;
+    tsf_batch* b = new (std::nothrow) tsf_batch();
+    if (!b) return TSF_E_OOM;
+    b->use_graph = o.use_graph;
+    if (o.cuda_stream) {
+        b->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return TSF_E_CUDA;
+        }
+        b->own_stream = true;
+    }
+    o.cuda_stream = b->stream;
+    for (int i = 0; i < ninst; ++i) {
+        tsf_ctx* c = nullptr;
+        tsf_status st = tsf_create(&c, &o);
+        if (st) {
+            for (tsf_ctx* x : b->inst) tsf_destroy(x);
+            if (b->own_stream) cudaStreamDestroy(b->stream);
+            delete b;
+            return st;
+        }
+        b->inst.push_back(c);
+    }
+    *out = b;
+    return TSF_OK;
+}
+
+tsf_status tsf_batch_instance(tsf_batch* b, int inst, tsf_ctx** out) {
+    if (!b || !out) return TSF_E_ARG;
+    *out = nullptr;
+    if (inst < 0 || inst >= (int)b->inst.size()) return bfail(b, TSF_E_ARG, "instance %d out of range", inst);
+    *out = b->inst[inst];
+    return TSF_OK;
+}
+
+tsf_status tsf_batch_step(tsf_batch* b, double dt, int nsteps) {
+    if (!b) return TSF_E_ARG;
+    if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return bfail(b, TSF_E_ARG, "need dt > 0 and nsteps >= 0");
+    const int n = (int)b->inst.size();
+    for (int i = 0; i < n; ++i) {
+        tsf_ctx* c = b->inst[i];
+        if (!c->ws_valid || !c->geom_set || !c->state_set)
+            return bfail(b, TSF_E_STATE, "instance %d: set meshes, deformation and state first", i);
+    }
+    if (nsteps == 0) return TSF_OK;
+    for (int i = 0; i < n; ++i) {
+        tsf_status st = prepare_step(b->inst[i], dt);
+        if (st) return inst_fail(b, i, st);
+    }
+    if (!b->use_graph) {
+        for (int s = 0; s < nsteps; ++s) {
+            for (int i = 0; i < n; ++i) {
+                tsf_status st = run_plain_steps(b->inst[i], dt, 1);
+                if (st) return inst_fail(b, i, st);
+            }
+            b->steps++;
+        }
+        return TSF_OK;
+    }
+    bool stale = !b->graph_valid || b->graph_dt != dt || b->gen.size() != (size_t)n;
+    for (int i = 0; i < n && !stale; ++i) stale = b->gen[i] != b->inst[i]->graph_gen;
+    if (stale) {
+        tsf_status st = batch_capture(b, dt);
+        if (st) return st;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+        if (e != cudaSuccess) return bfail(b, TSF_E_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+        b->steps++;
+    }
+    return TSF_OK;
+}
+
+tsf_status tsf_batch_synchronize(tsf_batch* b) {
+    if (!b) return TSF_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, TSF_E_CUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+    for (int i = 0; i < (int)b->inst.size(); ++i) {
+        tsf_status st = tsf_synchronize(b->inst[i]);
+        if (st) return inst_fail(b, i, st);
+    }
+    return TSF_OK;
+}
+
+tsf_status tsf_batch_get_stats(tsf_batch* b, tsf_stats* out) {
+    if (!b || !out) return TSF_E_ARG;
+    memset(out, 0, sizeof *out);
+    out->tiling = -1;
+    for (int i = 0; i < (int)b->inst.size(); ++i) {
+        tsf_stats s;
+        tsf_status st = tsf_get_stats(b->inst[i], &s);
+        if (st) return inst_fail(b, i, st);
+        out->inner_iters += s.inner_iters;
+        out->dof_cg_iters += s.dof_cg_iters;
+        out->refine_sweeps += s.refine_sweeps;
+        out->micro_solves += s.micro_solves;
+        out->macro_iters += s.macro_iters;
+        out->coupling_iters_last = std::max(out->coupling_iters_last, s.coupling_iters_last);
+        out->coupling_iters_total += s.coupling_iters_total;
+        out->max_inner_iters = std::max(out->max_inner_iters, s.max_inner_iters);
+        if (!out->status) out->status = s.status;
+        out->coupling_change = std::max(out->coupling_change, s.coupling_change);
+        out->micro_launches += s.micro_launches;
+        out->macro_launches += s.macro_launches;
+        out->micro_kernel_ms += s.micro_kernel_ms;
+        out->macro_kernel_ms += s.macro_kernel_ms;
+    }
+    out->steps = b->steps;
+    return TSF_OK;
+}
+
+tsf_status tsf_batch_reset_stats(tsf_batch* b) {
+    if (!b) return TSF_E_ARG;
+    for (int i = 0; i < (int)b->inst.size(); ++i) {
+        tsf_status st = tsf_reset_stats(b->inst[i]);
+        if (st) return inst_fail(b, i, st);
+    }
+    b->steps = 0;
+    return TSF_OK;
+}
+
+const char* tsf_batch_last_error(const tsf_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void tsf_batch_destroy(tsf_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b, true);
+    for (tsf_ctx* c : b->inst) tsf_destroy(c);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 }  // extern "C"
