@@ -43,11 +43,12 @@ BYTES_PER_DOF_SWEEP = 64
 
 KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_micro_solve<8>",
                 "k_micro_strip<3>", "k_micro_strip<5>", "k_micro_strip<7>"]
-# DRAM bytes (read + write) per micro-solve launch, averaged over the four
-# coupling iterations of one step, from the ncu capture summarised in
-# profiles/micro_strip_c2_64x64_32x32.md (column-strip kernel; the strip height
-# does not change the DRAM traffic).  Entries are removed when the kernel changes.
-MICRO_TRAFFIC = {("c2", "mixed", True): 322.3e6}
+# DRAM bytes (read + write) per micro-solve launch from the ncu captures
+# summarised under profiles/ (column-strip kernel; the strip height does not
+# change the DRAM traffic): partitioned, averaged over the four coupling
+# iterations of a step (micro_strip_c2_64x64_32x32.md).  Keyed by (workload,
+# precision, strip kernel, coupling); entries are removed when the kernel changes.
+MICRO_TRAFFIC = {("c2", "mixed", True, "partitioned"): 322.3e6}
 
 
 def parse():
@@ -59,6 +60,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
     ap.add_argument("--fd-dirs", type=int, default=20, help="c5: finite-difference directions per family")
+    ap.add_argument("--coupling", default="elimination", choices=["elimination", "partitioned"],
+                    help="how each step reaches the coupled solution (the other way is timed beside it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, e2e, cpu baseline")
     return ap.parse_args()
@@ -128,6 +131,9 @@ def measured_peaks():
         return None
 
 
+COUPLING = {"elimination": 1, "partitioned": 0}
+
+
 def make_problem(T, w, precision, stream, **opts):
     prec = T.TSF_MIXED if precision == "mixed" else T.TSF_FP64
     P = T.TwoScale(w.Nm, w.NM, bc=w.bc, precision=prec, stream=stream, cg_tol=w.tol, coupling_tol=w.coupling_tol,
@@ -193,7 +199,8 @@ def run_gb300(args):
     K, Wm = args.steps, args.warmup
 
     # ---- main timed region (graph-launched steps, inputs resident) ----
-    P = make_problem(T, w, args.precision, stream)
+    other = "partitioned" if args.coupling == "elimination" else "elimination"
+    P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling])
     P.step(w.dt, Wm)
     P.synchronize()
     P.reset_stats()
@@ -207,7 +214,8 @@ def run_gb300(args):
     dof_iters = allsum(float(st["dof_cg_iters"]))
     value = dof_iters / (ms_max / 1e3)
     steps_per_s = world * K / (ms_max / 1e3)
-    launches = 2 * K + 2 * st["coupling_iters_total"]
+    # partitioned: 2 prologues + (micro, macro) per coupling iteration; elimination: 5 kernels per step
+    launches = 5 * K if args.coupling == "elimination" else 2 * K + 2 * st["coupling_iters_total"]
 
     line = {
         "metric": "micro DOF-CG-iters/s",
@@ -224,9 +232,10 @@ def run_gb300(args):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: macro {w.NM}x{w.NM} Q1 ({nM} micro problems), micro "
                                f"{w.Nm}x{w.Nm} Q1 ({nm} DoFs each, {nM * nm} micro DoFs), "
-                               f"dt={w.dt}, tol={w.tol}, {args.precision}",
+                               f"dt={w.dt}, tol={w.tol}, {args.precision}, coupling by {args.coupling}",
                    "macro_mesh": w.NM, "micro_mesh": w.Nm, "micro_dofs": nM * nm, "dt": w.dt, "tol": w.tol,
-                   "coupling_tol": w.coupling_tol, "precision": args.precision, "replicas": world,
+                   "coupling_tol": w.coupling_tol, "precision": args.precision, "coupling": args.coupling,
+                   "replicas": world,
                    "l2": "working set > L2 (stencils + vectors ~0.6 GB), no flush"},
         "steps_per_s": steps_per_s,
         "coupling_iters_per_step": st["coupling_iters_total"] / K,
@@ -238,10 +247,34 @@ def run_gb300(args):
         "clocks": clocks,
     }
 
+    # ---- the same steps with the other way of reaching the coupled solution:
+    # exact elimination (one micro solve per step) or the partitioned
+    # iteration of the paper (micro and macro solves until u settles) ----
+    uP, vP = P.u(), P.v()
+    E = make_problem(T, w, args.precision, stream, coupling=COUPLING[other])
+    E.step(w.dt, Wm)
+    E.synchronize()
+    E.reset_stats()
+    msE = timed_steps(torch, E, w, K, barrier)
+    E.synchronize()
+    sE = E.stats()
+    msE_max = allmax(msE)
+    line[other] = {
+        "value": allsum(float(sE["dof_cg_iters"])) / (msE_max / 1e3), "unit": "DOF-iter/s",
+        "ms_per_step": msE_max / K, "steps_per_s": world * K / (msE_max / 1e3),
+        "ms_per_step_ratio_to_main": msE_max / ms_max,
+        "inner_iters_per_solve": sE["inner_iters"] / max(sE["micro_solves"], 1),
+        "rel_diff_vs_main": {"u": float(np.linalg.norm(E.u() - uP) / np.linalg.norm(uP)),
+                             "v": float(np.linalg.norm(E.v() - vP) / np.linalg.norm(vP))},
+        "coupling_iters_per_step": sE["coupling_iters_total"] / K,
+    }
+    E.close()
+
     # ---- per-kernel timing of the micro solve (plain launches, CUDA events) ----
     opts = T.tsf_default_options()
     opts.precision = T.TSF_MIXED if args.precision == "mixed" else T.TSF_FP64
     opts.cg_tol, opts.coupling_tol = w.tol, w.coupling_tol
+    opts.coupling = COUPLING[args.coupling]
     opts.use_graph, opts.profile = 0, 1
     opts.tiling = st["tiling"]
     opts.cuda_stream = stream.cuda_stream
@@ -259,7 +292,7 @@ def run_gb300(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     line["roofline"] = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": MICRO_TRAFFIC.get((args.workload, args.precision, st["tiling"] >= 4)),
+        "traffic": MICRO_TRAFFIC.get((args.workload, args.precision, st["tiling"] >= 4, args.coupling)),
         "kernel": KERNEL_NAMES[st["tiling"]], "bytes_per_launch": bytes_launch,
         "avg_launch_ms": micro_ms, "launches_timed": sp["micro_launches"],
         "macro_kernel_share": sp["macro_kernel_ms"] / max(sp["macro_kernel_ms"] + sp["micro_kernel_ms"], 1e-30),
@@ -270,7 +303,7 @@ def run_gb300(args):
     if not args.no_extras and rank == 0:
         # ---- FP64 path at equal tolerance (comparison) ----
         if args.precision == "mixed":
-            Q = make_problem(T, w, "fp64", stream)
+            Q = make_problem(T, w, "fp64", stream, coupling=COUPLING[args.coupling])
             Q.step(w.dt, 2)
             Q.synchronize()
             Q.reset_stats()
@@ -295,7 +328,7 @@ def run_gb300(args):
 def run_e2e(torch, T, w, args, stream):
     """Each step: pinned host -> device state upload, one step, macro field and
     micro averages back to pinned host memory."""
-    P = make_problem(T, w, args.precision, stream)
+    P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling])
     P.step(w.dt, 2)
     P.synchronize()
     u_h = torch.empty(w.nM, dtype=torch.float64).pin_memory()
@@ -342,7 +375,7 @@ def run_cpu_baseline(T, w, args, stream):
            "kind": "oracle", "sample": f"{n} full-size steps of the workload from u0=1, v0=0 (FP64, CSR Jacobi-PCG, "
                                        f"OpenMP over micro problems), {el:.1f} s",
            "steps_per_s": n / el}
-    P = make_problem(T, w, args.precision, stream)
+    P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling])
     P.step(w.dt, n)
     P.synchronize()
     u, v = P.u(), P.v()
@@ -420,7 +453,7 @@ def run_c5(args):
         return e0.elapsed_time(e1) / 1e3, out
 
     # ---- timing at the workload's tolerances ----
-    P = make_problem(T, w, "fp64", stream)
+    P = make_problem(T, w, "fp64", stream, coupling=COUPLING[args.coupling])
     P.step(w.dt, 2)
     P.set_state(w.u0, None)
     P.adjoint_mean_u(w.dt, 3, 2)
@@ -440,7 +473,8 @@ def run_c5(args):
     def fd_check(fam, prm, D, ndirs, seed):
         tight = dict(cg_tol=1e-14, coupling_tol=1e-14, macro_tol=1e-14, tiling=tiling, cg_maxit=20000,
                      coupling_maxit=100)
-        Q = T.TwoScale(w.Nm, w.NM, bc=w.bc, precision=T.TSF_FP64, stream=stream, **tight)
+        Q = T.TwoScale(w.Nm, w.NM, bc=w.bc, precision=T.TSF_FP64, stream=stream, coupling=COUPLING[args.coupling],
+                       **tight)
         Q.set_physics(D, w.kappa, w.Du)
 
         def J_at(p):
@@ -455,7 +489,7 @@ def run_c5(args):
         J0, g0 = Q.adjoint_mean_u(w.dt, w.nsteps, ckpt)
         t_adj = time.perf_counter() - t0
         # noise floor: change of J when the tolerances are loosened tenfold
-        L = T.TwoScale(w.Nm, w.NM, bc=w.bc, precision=T.TSF_FP64, stream=stream,
+        L = T.TwoScale(w.Nm, w.NM, bc=w.bc, precision=T.TSF_FP64, stream=stream, coupling=COUPLING[args.coupling],
                        **dict(tight, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13))
         L.set_physics(D, w.kappa, w.Du)
         L.set_deformation(fam, prm)
@@ -494,7 +528,7 @@ def run_c5(args):
             "data": "synthetic", "vs_baseline": None,
             "config": {"workload": f"c5: macro {w.NM}x{w.NM} ({w.nM} micro problems), micro {w.Nm}x{w.Nm}, "
                                    f"bump a ~ U[0,0.2], FP64, dt={w.dt} x {w.nsteps} steps, checkpoints every "
-                                   f"{ckpt}, tol {w.tol}, coupling tol {w.coupling_tol}"},
+                                   f"{ckpt}, tol {w.tol}, coupling tol {w.coupling_tol}, coupling by {args.coupling}"},
             "forward_s": t_fwd, "gradient_over_forward": t_grad / t_fwd, "J": J, "grad_norm": float(np.linalg.norm(g)),
             "tiling": tiling, "fd_check": {"bump": bump, "shear_bump": shear}}
     print(json.dumps(line))
@@ -526,7 +560,7 @@ def run_c4(args):
 
     def build():
         B = T.TwoScaleBatch([(w.Nm, w.NM, w.bc) for w in ws], precision=T.TSF_MIXED, stream=stream,
-                            cg_tol=ws[0].tol, coupling_tol=ws[0].coupling_tol)
+                            cg_tol=ws[0].tol, coupling_tol=ws[0].coupling_tol, coupling=COUPLING[args.coupling])
         for k, w in enumerate(ws):
             B[k].set_physics(w.D, w.kappa, w.Du)
             B[k].set_deformation(w.family, w.params)
@@ -579,6 +613,7 @@ def run_c4(args):
         P = B[k]
         o = T.tsf_default_options()
         o.precision, o.cg_tol, o.coupling_tol = T.TSF_MIXED, w.tol, w.coupling_tol
+        o.coupling = COUPLING[args.coupling]
         o.use_graph, o.profile, o.tiling = 0, 1, tilings[k]
         o.cuda_stream = stream.cuda_stream
         T.tsf_set_options(P.ctx, o)
@@ -599,13 +634,15 @@ def run_c4(args):
         "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"c4: {len(ws)} independent two-scale problems, macro 16..96 / micro 16..48 cells "
-                               f"per side, {ndof} micro DoFs, dt={dt}, tol={ws[0].tol}, mixed, one graph per "
-                               f"batch step", "problems": len(ws), "micro_dofs": ndof,
+                               f"per side, {ndof} micro DoFs, dt={dt}, tol={ws[0].tol}, mixed, coupling by "
+                               f"{args.coupling}, one graph per batch step", "problems": len(ws), "micro_dofs": ndof,
                    "l2": "working set > L2, no flush"},
         "batch_steps_per_s": world * K / (ms_max / 1e3),
         "sequential_ms_per_step": seq_ms / ks, "batch_speedup_vs_sequential": (seq_ms / ks) / (ms / K),
         "coupling_iters_per_problem_step": st["coupling_iters_total"] / (K * len(ws)),
-        "tilings": tilings, "gpu_launches": 2 * K * len(ws) + 2 * st["coupling_iters_total"],
+        "tilings": tilings, "coupling": args.coupling,
+        "gpu_launches": (5 * K * len(ws) if args.coupling == "elimination"
+                         else 2 * K * len(ws) + 2 * st["coupling_iters_total"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "micro solve (per-problem variant)", "launches_timed": launches,
                      "avg_launch_ms": micro_ms / max(launches, 1),

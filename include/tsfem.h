@@ -103,7 +103,21 @@ typedef struct tsf_options {
     void *cuda_stream;       /* cudaStream_t to enqueue on, NULL = library-owned stream */
     int profile;             /* 1 (with use_graph = 0): time every micro and macro kernel launch
                                 with CUDA events on the stream; totals in tsf_stats */
+    int coupling;            /* how a step reaches the coupled fixed point:
+                                TSF_COUPLING_PARTITIONED: the partitioned iteration of Sec. 3.3
+                                  (micro solves with the current u, macro solve with the new
+                                  fluxes, until coupling_tol);
+                                TSF_COUPLING_ELIMINATION: exact elimination.  Given u_i the micro
+                                  solution is affine in u_i, v_i = v0_i + u_i phi_i with
+                                  S_i phi_i = kappa r_i independent of the state, so the fluxes
+                                  are rho_i = r_i^T v0_i + u_i r_i^T phi_i and one macro solve with
+                                  the diagonal kappa m_i (|Gam_i| - r_i^T phi_i) gives u; one micro
+                                  solve per step (phi is solved once per geometry and dt, to
+                                  1e-3 cg_tol, at least 1e-13).  Same discrete solution, without
+                                  the coupling tolerance; coupling_tol and coupling_maxit unused. */
 } tsf_options;
+
+enum { TSF_COUPLING_PARTITIONED = 0, TSF_COUPLING_ELIMINATION = 1 };
 
 typedef struct tsf_stats {
     int64_t inner_iters;        /* CG iterations summed over micro instances, solves and steps */
@@ -126,7 +140,7 @@ typedef struct tsf_stats {
 
 /* Fill *opt with defaults: TSF_MIXED, cg_tol 1e-8, inner_tol 1e-5, macro_tol 1e-12,
  * coupling_tol 1e-10, cg_maxit 5000, max_sweeps 20, macro_maxit 500, coupling_maxit 50,
- * tiling -1, use_graph 1, cuda_stream NULL, profile 0. */
+ * tiling -1, use_graph 1, cuda_stream NULL, profile 0, coupling TSF_COUPLING_PARTITIONED. */
 void tsf_default_options(tsf_options *opt);
 
 /* Create a context.  opt may be NULL (defaults).  *out receives the handle.

@@ -22,6 +22,7 @@ TSF_E_NAN, TSF_E_CUDA, TSF_E_OOM, TSF_E_BREAKDOWN = 5, 6, 7, 8
 TSF_FP64, TSF_MIXED = 0, 1
 TSF_FAMILY_IDENTITY, TSF_FAMILY_BUMP, TSF_FAMILY_SHEAR_BUMP, TSF_FAMILY_AFFINE, TSF_FAMILY_AFFINE_BUMP = 0, 1, 2, 3, 4
 TSF_BC_NEUMANN, TSF_BC_DIRICHLET = 0, 1
+TSF_COUPLING_PARTITIONED, TSF_COUPLING_ELIMINATION = 0, 1
 STATUS_NAMES = {0: "TSF_OK", 1: "TSF_E_ARG", 2: "TSF_E_STATE", 3: "TSF_E_BAD_JACOBIAN", 4: "TSF_E_NOT_CONVERGED",
                 5: "TSF_E_NAN", 6: "TSF_E_CUDA", 7: "TSF_E_OOM", 8: "TSF_E_BREAKDOWN"}
 
@@ -42,7 +43,7 @@ class tsf_options(ctypes.Structure):
                 ("macro_tol", ctypes.c_double), ("coupling_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("macro_maxit", ctypes.c_int), ("coupling_maxit", ctypes.c_int),
                 ("tiling", ctypes.c_int), ("use_graph", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("coupling", ctypes.c_int)]
 
 
 class tsf_stats(ctypes.Structure):

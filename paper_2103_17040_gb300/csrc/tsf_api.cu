@@ -65,6 +65,10 @@ struct tsf_ctx {
            *out = nullptr;
     double *mx = nullptr, *mr = nullptr, *mz = nullptr, *mzo = nullptr, *mp = nullptr, *mq = nullptr;
     double *res = nullptr, *res2 = nullptr, *u_used = nullptr, *uu2 = nullptr, *bnorm = nullptr;
+    // exact elimination: phi_i = S_i^-1 kappa r_i, beta_i = r_i^T phi_i,
+    // gam_eff = |Gam| - beta, constant macro vectors 0 and 1
+    double *phi = nullptr, *beta = nullptr, *gam_eff = nullptr, *uzero = nullptr, *uone = nullptr;
+    bool phi_valid = false;
     int* inst_iters = nullptr;
     DevCtl* ctl = nullptr;
     DevCtl* ctl_host = nullptr;  // pinned
@@ -124,6 +128,7 @@ static bool options_ok(const tsf_options* o) {
     return o && (o->precision == TSF_FP64 || o->precision == TSF_MIXED) && o->cg_tol >= 0 && o->inner_tol > 0 &&
            o->inner_tol < 1 && o->macro_tol >= 0 && o->coupling_tol >= 0 && o->cg_maxit > 0 && o->max_sweeps > 0 &&
            o->macro_maxit > 0 && o->coupling_maxit > 0 &&
+           (o->coupling == TSF_COUPLING_PARTITIONED || o->coupling == TSF_COUPLING_ELIMINATION) &&
            (o->tiling == -1 || (o->tiling >= 0 && o->tiling < kNumTilings));
 }
 
@@ -191,6 +196,7 @@ tsf_status tsf_set_options(tsf_ctx* ctx, const tsf_options* opt) {
     ctx->opt = *opt;
     ctx->opt.cuda_stream = keep;
     if (prec_changed || opt->tiling >= 0) ctx->tiling = -1;
+    ctx->phi_valid = false;
     invalidate_graph(ctx);
     return TSF_OK;
 }
@@ -285,6 +291,8 @@ static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
     off[k++] = A.take(nM * 3 * sizeof(double));                  // bnorm
     off[k++] = A.take(nM * sizeof(int));                         // inst_iters
     off[k++] = A.take(sizeof(DevCtl));                           // ctl
+    off[k++] = A.take(nM * pl * sizeof(double));                 // phi
+    for (int r = 0; r < 4; ++r) off[k++] = A.take(nM * sizeof(double));  // beta gam_eff uzero uone
 }
 
 static void assign(tsf_ctx* ctx, const size_t* off) {
@@ -316,9 +324,14 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->bnorm = (double*)(b + off[k++]);
     ctx->inst_iters = (int*)(b + off[k++]);
     ctx->ctl = (DevCtl*)(b + off[k++]);
+    ctx->phi = (double*)(b + off[k++]);
+    ctx->beta = (double*)(b + off[k++]);
+    ctx->gam_eff = (double*)(b + off[k++]);
+    ctx->uzero = (double*)(b + off[k++]);
+    ctx->uone = (double*)(b + off[k++]);
 }
 
-static constexpr int kNumBuffers = 16 + 13 + 5 + 2;
+static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5;
 
 tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return TSF_E_ARG;
@@ -339,6 +352,9 @@ static tsf_status init_workspace(tsf_ctx* ctx) {
     CU(cudaMemsetAsync(ctx->u, 0, (size_t)ctx->nM * sizeof(double), ctx->stream));
     CU(cudaMemsetAsync(ctx->v, 0, (size_t)ctx->nM * ctx->nmp * sizeof(double), ctx->stream));
     CU(cudaMemsetAsync(ctx->G, 0, (size_t)ctx->nM * sizeof(double), ctx->stream));
+    CU(launch_fill(ctx->uzero, 0.0, ctx->nM, ctx->stream));
+    CU(launch_fill(ctx->uone, 1.0, ctx->nM, ctx->stream));
+    ctx->phi_valid = false;
     if (!ctx->dir_vals.empty())
         CU(cudaMemcpyAsync(ctx->ud, ctx->dir_vals.data(), ctx->nM * sizeof(double), cudaMemcpyHostToDevice,
                            ctx->stream));
@@ -428,6 +444,7 @@ static tsf_status build_operators(tsf_ctx* ctx, double dt) {
                             ctx->stream));
     ctx->ops_dt = dt;
     ctx->ops_valid = true;
+    ctx->phi_valid = false;
     return TSF_OK;
 }
 
@@ -565,7 +582,11 @@ static MacroArgs macro_args(tsf_ctx* ctx, double dt, bool set_cond, cudaGraphCon
     return a;
 }
 
-static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt) {
+static bool eliminating(const tsf_ctx* ctx) { return ctx->opt.coupling == TSF_COUPLING_ELIMINATION; }
+
+// Macro and micro prologues of a step.  With elim the micro prologue also
+// replaces v by the warm start v - u phi of v0 (exact elimination).
+static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt, bool elim) {
     MacroPrologueArgs m{};
     m.NM = ctx->NM;
     m.N1 = ctx->N1;
@@ -604,7 +625,74 @@ static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt) {
     p.res = ctx->res;
     p.u_used = ctx->u_used;
     p.bnorm = ctx->bnorm;
+    p.phi = elim ? ctx->phi : nullptr;
+    p.uw = elim ? ctx->u : nullptr;
     CU(launch_micro_prologue(p, ctx->stream));
+    return TSF_OK;
+}
+
+// One step by exact elimination: micro solve S v0 = c (u = 0 in the
+// right-hand side), macro solve with the diagonal kappa m (|Gam| - beta) and
+// the fluxes alpha = r^T v0, then v = v0 + u phi.  ev: optional events around
+// the micro and macro solves.
+static tsf_status enqueue_elimination_step(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
+    tsf_status st = enqueue_prologue(ctx, dt, true);
+    if (st) return st;
+    if (ev) CU(cudaEventRecord(ev[0], ctx->stream));
+    MicroArgs ma = micro_args(ctx, ctx->v);
+    ma.u = ctx->uzero;
+    CU(launch_micro_solve(ma, ctx->opt.precision, ctx->tiling, ctx->stream));
+    if (ev) CU(cudaEventRecord(ev[1], ctx->stream));
+    cudaGraphConditionalHandle none{};
+    MacroArgs mg = macro_args(ctx, dt, false, none);
+    mg.gam = ctx->gam_eff;
+    mg.coupling_tol = HUGE_VAL;  // one macro solve ends the step
+    mg.coupling_maxit = 1;
+    CU(launch_macro_solve(mg, ctx->stream));
+    if (ev) CU(cudaEventRecord(ev[2], ctx->stream));
+    CU(launch_commit(ctx->nm, ctx->nmp, ctx->nM, ctx->u, ctx->phi, ctx->v, ctx->stream));
+    return TSF_OK;
+}
+
+static double phi_tol(double cg_tol) { return std::max(1e-3 * cg_tol, 1e-13); }
+
+// phi_i = S_i^-1 kappa r_i for every micro problem (with the variant in use),
+// beta_i = r_i^T phi_i and gam_eff = |Gam| - beta.  The counters of the
+// control block are left as they were.
+static tsf_status compute_phi(tsf_ctx* ctx) {
+    DevCtl saved;
+    CU(cudaMemcpyAsync(&saved, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    PhiSetupArgs ps{};
+    ps.n1 = ctx->n1;
+    ps.nm = ctx->nm;
+    ps.nmp = ctx->nmp;
+    ps.nM = ctx->nM;
+    ps.kappa = ctx->kappa;
+    ps.redge = ctx->redge;
+    ps.phi = ctx->phi;
+    ps.cz = ctx->vtmp;
+    ps.res = ctx->res;
+    ps.u_used = ctx->u_used;
+    ps.bnorm = ctx->bnorm;
+    CU(launch_phi_setup(ps, ctx->stream));
+    CU(cudaMemsetAsync(&ctx->ctl->status, 0, sizeof(int), ctx->stream));
+    MicroArgs a = micro_args(ctx, ctx->phi);
+    a.c = ctx->vtmp;
+    a.u = ctx->uone;
+    a.tol = phi_tol(ctx->opt.cg_tol);
+    a.rho = ctx->beta;
+    CU(launch_micro_solve(a, ctx->opt.precision, ctx->tiling, ctx->stream));
+    CU(launch_sub(ctx->gam, ctx->beta, ctx->gam_eff, ctx->nM, ctx->stream));
+    int status = 0;
+    CU(cudaMemcpyAsync(&status, &ctx->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(ctx->ctl, &saved, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (status)
+        return fail(ctx, (tsf_status)status, "solving for the elimination vectors S phi = kappa r failed (status %d)",
+                    status);
+    ctx->phi_valid = true;
     return TSF_OK;
 }
 
@@ -622,7 +710,7 @@ static tsf_status autotune(tsf_ctx* ctx, double dt) {
     }
     DevCtl saved;
     CU(cudaMemcpyAsync(&saved, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
-    tsf_status st = enqueue_prologue(ctx, dt);
+    tsf_status st = enqueue_prologue(ctx, dt, false);
     if (st) return st;
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
@@ -682,14 +770,27 @@ static tsf_status capture_failed(tsf_ctx* ctx, tsf_status st, cudaError_t e, con
 // caller abandons G.
 static cudaError_t capture_step_into(tsf_ctx* ctx, cudaGraph_t G, double dt, tsf_status* st, const char** what) {
     *st = TSF_OK;
+    cudaError_t e;
+    if (eliminating(ctx)) {  // a straight sequence of kernels, no coupling loop
+        *what = "begin capture";
+        e = cudaStreamBeginCaptureToGraph(ctx->stream, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        *st = enqueue_elimination_step(ctx, dt, nullptr);
+        cudaGraph_t endg = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &endg);
+        *what = "elimination step";
+        if (*st) return cudaErrorUnknown;
+        return e2;
+    }
+    // (a conditional handle must belong to a conditional node of G)
     cudaGraphConditionalHandle cond;
     *what = "conditional handle";
-    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, G, 1, cudaGraphCondAssignDefault);
+    e = cudaGraphConditionalHandleCreate(&cond, G, 1, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) return e;
     *what = "begin capture";
     e = cudaStreamBeginCaptureToGraph(ctx->stream, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    *st = enqueue_prologue(ctx, dt);
+    *st = enqueue_prologue(ctx, dt, false);
     cudaStreamCaptureStatus cs;
     cudaGraph_t capg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -758,6 +859,10 @@ static tsf_status prepare_step(tsf_ctx* ctx, double dt) {
         if (st) return st;
         invalidate_graph(ctx);
     }
+    if (eliminating(ctx) && !ctx->phi_valid) {
+        tsf_status st = compute_phi(ctx);
+        if (st) return st;
+    }
     return TSF_OK;
 }
 
@@ -767,8 +872,25 @@ static tsf_status run_plain_steps(tsf_ctx* ctx, double dt, int nsteps) {
     const bool prof = ctx->opt.profile != 0;
     if (prof && !ctx->ev[0])
         for (int k = 0; k < 4; ++k) CU(cudaEventCreate(&ctx->ev[k]));
+    if (eliminating(ctx)) {
+        for (int s = 0; s < nsteps; ++s) {
+            tsf_status st = enqueue_elimination_step(ctx, dt, prof ? ctx->ev : nullptr);
+            if (st) return st;
+            if (prof) {
+                float a = 0.f, b = 0.f;
+                CU(cudaEventSynchronize(ctx->ev[2]));
+                CU(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
+                CU(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+                ctx->prof_micro_ms += a;
+                ctx->prof_macro_ms += b;
+                ctx->prof_micro_n += 1;
+                ctx->prof_macro_n += 1;
+            }
+        }
+        return TSF_OK;
+    }
     for (int s = 0; s < nsteps; ++s) {
-        tsf_status st = enqueue_prologue(ctx, dt);
+        tsf_status st = enqueue_prologue(ctx, dt, false);
         if (st) return st;
         for (int it = 0; it < ctx->opt.coupling_maxit; ++it) {
             if (prof) CU(cudaEventRecord(ctx->ev[0], ctx->stream));

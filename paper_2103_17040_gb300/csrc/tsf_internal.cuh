@@ -158,7 +158,7 @@ struct PrologueArgs {
     double dt, kappa;
     const double* M64;
     const double* S64;
-    const double* v;        // [nM][nmp] state v^n
+    double* v;              // [nM][nmp] state v^n (replaced by the warm start of v0 under elimination)
     const double* fv;       // [nM][nmp] or nullptr
     const double* g;        // [nM][n1] or nullptr
     const double* redge;
@@ -169,6 +169,24 @@ struct PrologueArgs {
     double* res;            // [nM][nmp] out: c + kappa u r - S v
     double* u_used;         // [nM] out: u
     double* bnorm;          // [nM][3] out
+    // exact elimination (nullptr otherwise): v is replaced in place by the
+    // warm start v - uw phi of v0, and res = c - S v, u_used = 0
+    const double* phi;      // [nM][nmp] S^-1 kappa r
+    const double* uw;       // [nM] macro values of the state v
+};
+
+// One-off set-up of the solve S phi = kappa r with the stored-residual
+// protocol (c = 0, u = 1, phi = 0): res = kappa r on the Robin edge,
+// u_used = 1, bnorm = (0, 0, ||r||^2); zeroes phi and cz.
+struct PhiSetupArgs {
+    int n1, nm, nmp, nM;
+    double kappa;
+    const double* redge;
+    double* phi;
+    double* cz;             // [nM][nmp] zero right-hand side for the variants that read c
+    double* res;
+    double* u_used;
+    double* bnorm;
 };
 
 struct MacroArgs {
@@ -212,6 +230,11 @@ cudaError_t launch_geometry(const GeomArgs& a, cudaStream_t s);
 cudaError_t launch_instance_sums(int n1, int nm, int nmp, int nM, const double* lm, const double* redge,
                                  double* gam, double* vol, cudaStream_t s);
 cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s);
+cudaError_t launch_phi_setup(const PhiSetupArgs& a, cudaStream_t s);
+// v_i += u_i phi_i on every micro DoF
+cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double* phi, double* v, cudaStream_t s);
+// out = a - b elementwise
+cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);
 // Micro-solve variants ("tilings"):
 //   0..3  shared-memory stencil, K = 1, 2, 4, 8 nodes per thread (strided), FP64 or mixed
 //   4..6  column strips of R = 3, 5, 7 nodes with register stencils, mixed only

@@ -887,10 +887,23 @@ __global__ void __launch_bounds__(256) k_micro_prologue(PrologueArgs a) {
             }
         }
         c[j] = y;
-        res[j] = fma(ku, rj, y) - plane_apply(S, pl, v, j, p, q, n1);
+        if (!a.phi) res[j] = fma(ku, rj, y) - plane_apply(S, pl, v, j, p, q, n1);
         cc = fma(y, y, cc);
         cr = fma(y, rj, cr);
         rr = fma(rj, rj, rr);
+    }
+    if (a.phi) {
+        // exact elimination: the unknown is v0 with S v0 = c; its warm start
+        // is v^n - u^n phi (= the previous step's v0 when v^n was committed
+        // as v0 + u^n phi)
+        const double* ph = a.phi + (size_t)i * pl;
+        double* vw = a.v + (size_t)i * pl;
+        const double uw = a.uw[i];
+        __syncthreads();  // every thread has read v^n for c
+        for (int j = threadIdx.x; j < nm; j += blockDim.x) vw[j] = fma(-uw, ph[j], vw[j]);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nm; j += blockDim.x)
+            res[j] = c[j] - plane_apply(S, pl, v, j, j % n1, j / n1, n1);
     }
     double t[3] = {cc, cr, rr};
     block_allreduce<double, 3>(t, buf);
@@ -899,8 +912,64 @@ __global__ void __launch_bounds__(256) k_micro_prologue(PrologueArgs a) {
         bn[0] = t[0];
         bn[1] = t[1];
         bn[2] = t[2];
-        a.u_used[i] = a.u[i];
+        a.u_used[i] = a.phi ? 0.0 : a.u[i];
     }
+}
+
+__global__ void __launch_bounds__(128) k_phi_setup(PhiSetupArgs a) {
+    __shared__ double buf[32];
+    const int i = blockIdx.x, n1 = a.n1;
+    const size_t pl = (size_t)a.nmp;
+    const double* re = a.redge + (size_t)i * n1;
+    double rr = 0.0;
+    for (int j = threadIdx.x; j < a.nmp; j += blockDim.x) {
+        const int p = j % n1, q = j / n1;
+        const bool edge = j < a.nm && p == n1 - 1;
+        const double rj = edge ? re[q] : 0.0;
+        a.phi[i * pl + j] = 0.0;
+        a.cz[i * pl + j] = 0.0;
+        a.res[i * pl + j] = a.kappa * rj;
+        rr = fma(rj, rj, rr);
+    }
+    double t[1] = {rr};
+    block_allreduce<double, 1>(t, buf);
+    if (threadIdx.x == 0) {
+        a.bnorm[(size_t)i * 3] = 0.0;
+        a.bnorm[(size_t)i * 3 + 1] = 0.0;
+        a.bnorm[(size_t)i * 3 + 2] = t[0];
+        a.u_used[i] = 1.0;
+    }
+}
+
+cudaError_t launch_phi_setup(const PhiSetupArgs& a, cudaStream_t s) {
+    k_phi_setup<<<a.nM, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// v_i += u_i phi_i, one thread per (instance, DoF)
+__global__ void __launch_bounds__(256) k_commit(int nm, int nmp, const double* __restrict__ u,
+                                                const double* __restrict__ phi, double* __restrict__ v) {
+    const int i = blockIdx.x;  // instances on grid.x (up to 2^31 - 1)
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    if (j >= nm) return;
+    const size_t o = (size_t)i * nmp + j;
+    v[o] = fma(u[i], phi[o], v[o]);
+}
+
+cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double* phi, double* v, cudaStream_t s) {
+    dim3 grid(nM, (nm + 255) / 256);
+    k_commit<<<grid, 256, 0, s>>>(nm, nmp, u, phi, v);
+    return cudaGetLastError();
+}
+
+__global__ void k_sub(const double* a, const double* b, double* out, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = a[k] - b[k];
+}
+
+cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s) {
+    k_sub<<<(n + 255) / 256, 256, 0, s>>>(a, b, out, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s) {

@@ -62,8 +62,9 @@ def test_options_struct_layout_matches_header():
 #include <stddef.h>
 #include "tsfem.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(tsf_options), offsetof(tsf_options, cuda_stream),
-         sizeof(tsf_stats), offsetof(tsf_stats, coupling_change), offsetof(tsf_stats, steps));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tsf_options), offsetof(tsf_options, cuda_stream),
+         offsetof(tsf_options, coupling), sizeof(tsf_stats), offsetof(tsf_stats, coupling_change),
+         offsetof(tsf_stats, steps));
   return 0;
 }'''
     src = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"tsf_layout_{os.getpid()}.c")
@@ -73,6 +74,6 @@ int main(void) {
     out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     os.remove(src)
     os.remove(exe)
-    exp = [ctypes.sizeof(T.tsf_options), T.tsf_options.cuda_stream.offset, ctypes.sizeof(T.tsf_stats),
-           T.tsf_stats.coupling_change.offset, T.tsf_stats.steps.offset]
+    exp = [ctypes.sizeof(T.tsf_options), T.tsf_options.cuda_stream.offset, T.tsf_options.coupling.offset,
+           ctypes.sizeof(T.tsf_stats), T.tsf_stats.coupling_change.offset, T.tsf_stats.steps.offset]
     assert [int(x) for x in out] == exp

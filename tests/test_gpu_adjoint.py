@@ -17,15 +17,15 @@ def _T():
     return T
 
 
-def _gpu(T, Nm, NM, family, prm, D, kappa, Du, precision=0):
-    P = T.TwoScale(Nm, NM, precision=precision, **OPTS)
+def _gpu(T, Nm, NM, family, prm, D, kappa, Du, precision=0, coupling=0):
+    P = T.TwoScale(Nm, NM, precision=precision, coupling=coupling, **OPTS)
     P.set_physics(D, kappa, Du)
     P.set_deformation(family, prm)
     return P
 
 
-@pytest.mark.parametrize("family", [1, 2, 4])
-def test_gradient_matches_oracle_adjoint(family):
+@pytest.mark.parametrize("family,coupling", [(1, 0), (2, 0), (4, 0), (2, 1)])
+def test_gradient_matches_oracle_adjoint(family, coupling):
     NM, Nm, dt, nsteps = 3, 4, 0.02, 4
     nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
     prm = W.random_params(family, nM, seed=60 + family)
@@ -33,7 +33,7 @@ def test_gradient_matches_oracle_adjoint(family):
     u0, v0 = W.random_state(nM, nm, seed=7)
     Jo, go = TwoScaleAdjoint(Nm, NM, 0, family, prm, D=D, kappa=kappa, Du=Du).gradient(u0, v0, dt, nsteps)
     T = _T()
-    P = _gpu(T, Nm, NM, family, prm, D, kappa, Du)
+    P = _gpu(T, Nm, NM, family, prm, D, kappa, Du, coupling=coupling)
     P.set_state(u0, v0)
     J, g = P.adjoint_mean_u(dt, nsteps, ckpt_every=3)
     assert abs(J - Jo) < 1e-12 * abs(Jo)

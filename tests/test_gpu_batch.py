@@ -33,10 +33,11 @@ def _configure(p, k, spec):
     return prm, u0, v0
 
 
+@pytest.mark.parametrize("coupling", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_matches_oracle(precision):
+def test_batch_matches_oracle(precision, coupling):
     T = _T()
-    B = T.TwoScaleBatch([(s[0], s[1]) for s in SPECS], precision=precision, **TIGHT)
+    B = T.TwoScaleBatch([(s[0], s[1]) for s in SPECS], precision=precision, coupling=coupling, **TIGHT)
     inputs = [_configure(B[k], k, s) for k, s in enumerate(SPECS)]
     dt, n = 0.01, 3
     B.step(dt, n)

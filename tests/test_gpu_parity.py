@@ -65,13 +65,16 @@ STEP_CASES = [
 ]
 
 
+@pytest.mark.parametrize("coupling", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("case", STEP_CASES)
-def test_step_matches_oracle(case, precision):
+def test_step_matches_oracle(case, precision, coupling):
+    """coupling 0: the partitioned iteration; 1: exact elimination of the
+    coupling (one micro solve per step) -- the same discrete solution."""
     family, Nm, NM, bc, D, kappa, Du, nsteps = case
     nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
     prm = W.random_params(family, nM, seed=20 + Nm)
-    P, R = _pair(Nm, NM, family, prm, bc=bc, D=D, kappa=kappa, Du=Du, precision=precision)
+    P, R = _pair(Nm, NM, family, prm, bc=bc, D=D, kappa=kappa, Du=Du, precision=precision, coupling=coupling)
     u0, v0 = W.random_state(nM, nm, seed=5)
     P.set_state(u0, v0)
     R.set_state(u0, v0)
@@ -90,14 +93,15 @@ def test_step_matches_oracle(case, precision):
     assert rel(P.flux(), R.flux) < max(tol * 1e3, 1e-7) or np.max(np.abs(P.flux() - R.flux)) < 1e-9
 
 
+@pytest.mark.parametrize("coupling", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_manufactured_config_matches_oracle(precision):
+def test_manufactured_config_matches_oracle(precision, coupling):
     """8x8 macro / 8x8 micro, Dirichlet, bump a = 0.1 x1, manufactured sources,
     dt = 0.01 x 10 steps (the plain FP64 workload)."""
     from workloads import mms
     w = W.c1()
     a = w.params[:, 0]
-    P, R = _pair(w.Nm, w.NM, w.family, w.params, bc=1, precision=precision)
+    P, R = _pair(w.Nm, w.NM, w.family, w.params, bc=1, precision=precision, coupling=coupling)
     d0 = mms.nodal_data(w.NM, w.Nm, a, 0.0)
     P.set_state(d0["u"], d0["v"].ravel())
     R.set_state(d0["u"], d0["v"].ravel())
@@ -141,7 +145,8 @@ def test_identity_instances_bitwise_identical(precision):
         assert np.max(np.abs(u - u[0])) < 1e-13 * abs(u[0])
 
 
-def test_graph_and_plain_launches_agree_bitwise():
+@pytest.mark.parametrize("coupling", [0, 1])
+def test_graph_and_plain_launches_agree_bitwise(coupling):
     NM, Nm = 4, 9
     nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
     prm = W.random_params(W.FAMILY_BUMP, nM, seed=3)
@@ -149,7 +154,7 @@ def test_graph_and_plain_launches_agree_bitwise():
     T = _T()
     out = []
     for g in (1, 0):
-        P = T.TwoScale(Nm, NM, precision=1, use_graph=g, tiling=1)
+        P = T.TwoScale(Nm, NM, precision=1, use_graph=g, tiling=1, coupling=coupling)
         P.set_deformation(W.FAMILY_BUMP, prm)
         P.set_state(u0, v0)
         P.step(0.005, 3)
@@ -185,11 +190,12 @@ def test_all_tilings_agree(precision):
         assert rel(r, res[0]) < 1e-9
 
 
-def test_mass_balance_on_gpu():
+@pytest.mark.parametrize("coupling", [0, 1])
+def test_mass_balance_on_gpu(coupling):
     NM, Nm = 6, 10
     nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
     prm = W.random_params(W.FAMILY_SHEAR_BUMP, nM, seed=4)
-    P, R = _pair(Nm, NM, W.FAMILY_SHEAR_BUMP, prm, D=(1.0, 0.0, 0.1), kappa=1.2, precision=0)
+    P, R = _pair(Nm, NM, W.FAMILY_SHEAR_BUMP, prm, D=(1.0, 0.0, 0.1), kappa=1.2, precision=0, coupling=coupling)
     u0, v0 = W.random_state(nM, nm, seed=6)
     P.set_state(u0, v0)
     _, vol = P.geometry()
@@ -204,13 +210,14 @@ def test_mass_balance_on_gpu():
     assert abs(mass() - m0) < 1e-11 * abs(m0)
 
 
-def test_full_size_step_matches_oracle():
+@pytest.mark.parametrize("coupling", [0, 1])
+def test_full_size_step_matches_oracle(coupling):
     """The benchmark workload at full size (64x64 macro, 32x32 micro, 4.6M
     micro DoFs), mixed precision as timed by bench.py: one step against the
     oracle on all outputs."""
     w = W.c2()
     T = _T()
-    P = T.TwoScale(w.Nm, w.NM, precision=T.TSF_MIXED, cg_tol=w.tol, coupling_tol=w.coupling_tol)
+    P = T.TwoScale(w.Nm, w.NM, precision=T.TSF_MIXED, cg_tol=w.tol, coupling_tol=w.coupling_tol, coupling=coupling)
     P.set_deformation(w.family, w.params)
     P.set_state(w.u0, None)
     P.step(w.dt, 1)
@@ -282,3 +289,28 @@ def test_device_tensors_in_and_out():
     B.set_state(u0, v0)
     B.step(0.01, 1)
     assert np.array_equal(out.cpu().numpy(), B.u())
+
+
+def test_elimination_matches_partitioned_over_many_steps():
+    """Both ways of reaching the coupled solution, 20 steps of a 12x12 / 16x16
+    shear+bump problem in FP64 at tight tolerances, and the elimination's
+    statistics: one micro solve per problem and step."""
+    NM, Nm = 12, 16
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_SHEAR_BUMP, nM, seed=11)
+    u0, v0 = W.random_state(nM, nm, seed=12)
+    T = _T()
+    out = []
+    for coupling in (0, 1):
+        P = T.TwoScale(Nm, NM, precision=0, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13, coupling=coupling)
+        P.set_physics((1.0, 0.1, 0.5), 1.4, 0.9)
+        P.set_deformation(W.FAMILY_SHEAR_BUMP, prm)
+        P.set_state(u0, v0)
+        P.step(0.005, 20)
+        P.synchronize()
+        out.append((P.u(), P.v(), P.stats()))
+    assert rel(out[1][0], out[0][0]) < 1e-11
+    assert rel(out[1][1], out[0][1]) < 1e-11
+    st = out[1][2]
+    assert st["micro_solves"] == 20 * nM and st["coupling_iters_total"] == 20
+    assert out[0][2]["micro_solves"] > st["micro_solves"]
