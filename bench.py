@@ -46,9 +46,11 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # DRAM bytes (read + write) per micro-solve launch from the ncu captures
 # summarised under profiles/ (column-strip kernel; the strip height does not
 # change the DRAM traffic): partitioned, averaged over the four coupling
-# iterations of a step (micro_strip_c2_64x64_32x32.md).  Keyed by (workload,
+# iterations of a step (micro_strip_c2_64x64_32x32.md);  Keyed by (workload,
 # precision, strip kernel, coupling); entries are removed when the kernel changes.
-MICRO_TRAFFIC = {("c2", "mixed", True, "partitioned"): 322.3e6}
+MICRO_TRAFFIC = {("c2", "mixed", True, "partitioned"): 322.3e6,
+                 # elimination: one full solve per launch (step_elimination_c2_64x64_32x32.md)
+                 ("c2", "mixed", True, "elimination"): 410.9e6}
 
 
 def parse():
@@ -159,6 +161,27 @@ def timed_steps(torch, P, w, steps, barrier):
     return e0.elapsed_time(e1)
 
 
+def other_coupling(torch, T, E, w, args, uP, vP, barrier, allmax, allsum, K, Wm):
+    """The same steps with the other way of reaching the coupled solution."""
+    E.step(w.dt, Wm)
+    E.synchronize()
+    E.reset_stats()
+    msE = timed_steps(torch, E, w, K, barrier)
+    E.synchronize()
+    sE = E.stats()
+    msE_max = allmax(msE)
+    out = {
+        "value": allsum(float(sE["dof_cg_iters"])) / (msE_max / 1e3), "unit": "DOF-iter/s",
+        "ms_per_step": msE_max / K, "steps_per_s": int(os.environ.get("WORLD_SIZE", "1")) * K / (msE_max / 1e3),
+        "inner_iters_per_solve": sE["inner_iters"] / max(sE["micro_solves"], 1),
+        "coupling_iters_per_step": sE["coupling_iters_total"] / K,
+        "rel_diff_vs_main": {"u": float(np.linalg.norm(E.u() - uP) / np.linalg.norm(uP)),
+                             "v": float(np.linalg.norm(E.v() - vP) / np.linalg.norm(vP))},
+    }
+    E.close()
+    return out
+
+
 def run_gb300(args):
     import torch
     import torch.distributed as dist
@@ -251,24 +274,9 @@ def run_gb300(args):
     # exact elimination (one micro solve per step) or the partitioned
     # iteration of the paper (micro and macro solves until u settles) ----
     uP, vP = P.u(), P.v()
-    E = make_problem(T, w, args.precision, stream, coupling=COUPLING[other])
-    E.step(w.dt, Wm)
-    E.synchronize()
-    E.reset_stats()
-    msE = timed_steps(torch, E, w, K, barrier)
-    E.synchronize()
-    sE = E.stats()
-    msE_max = allmax(msE)
-    line[other] = {
-        "value": allsum(float(sE["dof_cg_iters"])) / (msE_max / 1e3), "unit": "DOF-iter/s",
-        "ms_per_step": msE_max / K, "steps_per_s": world * K / (msE_max / 1e3),
-        "ms_per_step_ratio_to_main": msE_max / ms_max,
-        "inner_iters_per_solve": sE["inner_iters"] / max(sE["micro_solves"], 1),
-        "rel_diff_vs_main": {"u": float(np.linalg.norm(E.u() - uP) / np.linalg.norm(uP)),
-                             "v": float(np.linalg.norm(E.v() - vP) / np.linalg.norm(vP))},
-        "coupling_iters_per_step": sE["coupling_iters_total"] / K,
-    }
-    E.close()
+    E = make_problem(T, w, args.precision, stream, coupling=COUPLING[other]) if not args.no_extras else None
+    if E is not None:
+        line[other] = other_coupling(torch, T, E, w, args, uP, vP, barrier, allmax, allsum, K, Wm)
 
     # ---- per-kernel timing of the micro solve (plain launches, CUDA events) ----
     opts = T.tsf_default_options()
