@@ -42,7 +42,8 @@ BYTES_PER_DOF_ITER = {"mixed": 64, "fp64": 128}
 BYTES_PER_DOF_SWEEP = 64
 
 KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_micro_solve<8>",
-                "k_micro_strip<3>", "k_micro_strip<5>", "k_micro_strip<7>"]
+                "k_micro_strip<3>", "k_micro_strip<5>", "k_micro_strip<7>",
+                "k_micro_strip_tall<9>", "k_micro_strip_tall<11>", "k_micro_strip_tall<13>"]
 # DRAM bytes (read + write) per micro-solve launch from the ncu captures
 # summarised under profiles/ (column-strip kernel; the strip height does not
 # change the DRAM traffic): partitioned, averaged over the four coupling
@@ -300,7 +301,7 @@ def run_gb300(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     line["roofline"] = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": MICRO_TRAFFIC.get((args.workload, args.precision, st["tiling"] >= 4, args.coupling)),
+        "traffic": MICRO_TRAFFIC.get((args.workload, args.precision, st["tiling"] in (4, 5, 6), args.coupling)),
         "kernel": KERNEL_NAMES[st["tiling"]], "bytes_per_launch": bytes_launch,
         "avg_launch_ms": micro_ms, "launches_timed": sp["micro_launches"],
         "macro_kernel_share": sp["macro_kernel_ms"] / max(sp["macro_kernel_ms"] + sp["micro_kernel_ms"], 1e-30),

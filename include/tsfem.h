@@ -130,7 +130,11 @@ typedef struct tsf_stats {
     int max_inner_iters;        /* largest inner-iteration count of a single micro solve */
     int steps;                  /* steps taken since the last tsf_reset_stats */
     int status;                 /* first device-side error (tsf_status), TSF_OK if none */
-    int tiling;                 /* micro-kernel variant in use */
+    int tiling;                 /* micro-kernel variant in use: 0..3 shared-memory stencil with
+                                   1, 2, 4, 8 nodes per thread (FP64 or mixed); 4..6 column strips
+                                   of 3, 5, 7 nodes with the stencil in registers (mixed); 7..9
+                                   column strips of 9, 11, 13 nodes with the stencil in shared
+                                   memory (mixed) */
     double coupling_change;     /* final ||du|| / ||u|| of the last step */
     int64_t micro_launches;     /* profiled micro-solve kernel launches */
     int64_t macro_launches;     /* profiled macro-solve kernel launches */

@@ -238,7 +238,8 @@ cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cud
 // Micro-solve variants ("tilings"):
 //   0..3  shared-memory stencil, K = 1, 2, 4, 8 nodes per thread (strided), FP64 or mixed
 //   4..6  column strips of R = 3, 5, 7 nodes with register stencils, mixed only
-constexpr int kNumTilings = 7;
+//   7..9  column strips of R = 9, 11, 13 nodes with the stencil in shared memory, mixed only
+constexpr int kNumTilings = 10;
 bool tiling_fits(int tiling, int precision, int n1, int smem_optin);
 cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cudaStream_t s);
 bool tiling_uses_stored_residual(int tiling);

@@ -396,7 +396,9 @@ static cudaError_t launch_smem(const MicroArgs& a, cudaStream_t s) {
 // decides when to stop; the residual itself stays FP64).
 // ===========================================================================
 // Launch bounds per strip height: R = 3 asks for two resident blocks of up to
-// 384 threads (register cap 85), R = 5 and 7 for one block of 512 / 384.
+// 384 threads (register cap 85), R = 5 and 7 for one block of 512 / 384; the
+// tall strips (R = 9, 11, 13, couplings in shared memory) take up to 384
+// threads at kTallStripRegs registers.
 template <int R>
 struct StripMaxThreads {
     static constexpr int value = R == 3 ? 384 : (R == 5 ? 512 : 384);
@@ -424,15 +426,50 @@ static int strip_threads(int n1, int R) {
     return (t + 31) / 32 * 32;
 }
 
-static size_t strip_smem_bytes(int n1, int R) {
+// Shared memory of a strip block: the plane, 4 x 64 reduction floats and,
+// with couplings in shared memory (sc), two float4 per node of the padded
+// strip grid (n1 columns x strip_rows * R rows).
+static size_t strip_smem_bytes(int n1, int R, bool sc) {
     const size_t W = (size_t)strip_stride(n1, R), H = (size_t)strip_rows(n1, R) * R + 2;
     size_t off = (W * H * sizeof(float) + 15) & ~(size_t)15;
-    return off + 4 * 64 * sizeof(float);
+    off += 4 * 64 * sizeof(float);
+    if (sc) off += 2 * (size_t)n1 * strip_rows(n1, R) * R * sizeof(float4);
+    return off;
 }
 
 // The eight scaled off-diagonal couplings of one node.
 struct Couple8 {
     float E, W, N, S, NE, NW, SE, SW;
+};
+
+// Where a strip's couplings live: in registers (short strips) ...
+template <int R>
+struct RegCouplings {
+    Couple8 c[R];
+    __device__ __forceinline__ Couple8 get(int k) const { return c[k]; }
+};
+// ... or in shared memory as two float4 per node, (E, W, N, S) and
+// (NE, NW, SE, SW), node (p, q) at index p + n1 q of the padded strip grid
+// (tall strips).
+// (The loads are volatile so that the compiler re-reads the couplings at
+// every operator application instead of hoisting them into registers.)
+__device__ __forceinline__ float4 lds_f4(const float4* p) {
+    float4 v;
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+struct SmemCouplings {
+    const float4* A;
+    const float4* B;
+    int j0, n1;
+    __device__ __forceinline__ Couple8 get(int k) const {
+        const float4 a = lds_f4(A + j0 + k * n1), b = lds_f4(B + j0 + k * n1);
+        return Couple8{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    }
 };
 
 // Neighbour values of a strip from the shared plane: L/Rt = columns p-1 / p+1
@@ -453,21 +490,55 @@ struct StripHalo {
 };
 
 // y = S^ x = x + off-diagonal part for the R nodes of a strip.
-template <int R>
-__device__ __forceinline__ void strip_apply(const Couple8 (&c)[R], const float (&x)[R], const StripHalo<R>& h,
+// y = S^ x reading the neighbour columns from the plane with a sliding
+// window of three rows (fewer live registers than a loaded halo for tall
+// strips).  The plane must hold x.  Entries of nodes outside the mesh (and
+// of threads without a strip, whose coupling reads point at node (0, k)) are
+// set to zero, so that they stay out of the dot products.
+template <int R, class CS>
+__device__ __forceinline__ void strip_apply_plane(const CS& cs, const float (&x)[R], const float* P, int Wd, int p,
+                                                  int q0, const bool (&valid)[R], float (&y)[R]) {
+    const float* cl = P + q0 * Wd + p;  // plane column of grid column p-1, from grid row q0-1
+    float l0 = cl[0], l1 = cl[Wd], r0 = cl[2], r1 = cl[Wd + 2];
+    const float xm = cl[1], xp = cl[(R + 1) * Wd + 1];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float l2 = cl[(k + 2) * Wd], r2 = cl[(k + 2) * Wd + 2];
+        const Couple8 c = cs.get(k);
+        const float up = (k + 1 < R) ? x[k + 1] : xp;
+        const float dn = (k > 0) ? x[k - 1] : xm;
+        float t = fmaf(c.E, r1, x[k]);
+        t = fmaf(c.W, l1, t);
+        t = fmaf(c.N, up, t);
+        t = fmaf(c.S, dn, t);
+        t = fmaf(c.NE, r2, t);
+        t = fmaf(c.NW, l2, t);
+        t = fmaf(c.SE, r0, t);
+        t = fmaf(c.SW, l0, t);
+        y[k] = valid[k] ? t : 0.f;
+        l0 = l1;
+        l1 = l2;
+        r0 = r1;
+        r1 = r2;
+    }
+}
+
+template <int R, class CS>
+__device__ __forceinline__ void strip_apply(const CS& cs, const float (&x)[R], const StripHalo<R>& h,
                                             float (&y)[R]) {
 #pragma unroll
     for (int k = 0; k < R; ++k) {
+        const Couple8 c = cs.get(k);
         const float up = (k + 1 < R) ? x[k + 1] : h.xp;
         const float dn = (k > 0) ? x[k - 1] : h.xm;
-        float t = fmaf(c[k].E, h.Rt[k + 1], x[k]);
-        t = fmaf(c[k].W, h.L[k + 1], t);
-        t = fmaf(c[k].N, up, t);
-        t = fmaf(c[k].S, dn, t);
-        t = fmaf(c[k].NE, h.Rt[k + 2], t);
-        t = fmaf(c[k].NW, h.L[k + 2], t);
-        t = fmaf(c[k].SE, h.Rt[k], t);
-        t = fmaf(c[k].SW, h.L[k], t);
+        float t = fmaf(c.E, h.Rt[k + 1], x[k]);
+        t = fmaf(c.W, h.L[k + 1], t);
+        t = fmaf(c.N, up, t);
+        t = fmaf(c.S, dn, t);
+        t = fmaf(c.NE, h.Rt[k + 2], t);
+        t = fmaf(c.NW, h.L[k + 2], t);
+        t = fmaf(c.SE, h.Rt[k], t);
+        t = fmaf(c.SW, h.L[k], t);
         y[k] = t;
     }
 }
@@ -483,15 +554,19 @@ __device__ __forceinline__ void strip_store(float* P, int Wd, int p, int q0, con
 // Chronopoulos-Gear CG on the scaled operator (Jacobi-PCG on S); x = 0 on
 // entry, r = rhs.  Stops when ||r||^2 <= rel2 ||r_0||^2 or after maxit
 // iterations; returns the count.  redA/redB: 64-float reduction buffers.
-template <int R>
-__device__ int strip_cg(const Couple8 (&c)[R], const bool (&valid)[R], float (&x)[R], float (&r)[R], float* P,
+template <int R, class CS>
+__device__ int strip_cg(const CS& c, const bool (&valid)[R], float (&x)[R], float (&r)[R], float* P,
                         int Wd, int p, int q0, float rel2, int maxit, float* redA, float* redB, int* flag) {
     float pv[R], s[R], w[R];
     StripHalo<R> h;
     strip_store<R>(P, Wd, p, q0, valid, r);
     __syncthreads();
-    h.load(P, Wd, p, q0);
-    strip_apply<R>(c, r, h, w);
+    if constexpr (R >= 9) {
+        strip_apply_plane<R>(c, r, P, Wd, p, q0, valid, w);
+    } else {
+        h.load(P, Wd, p, q0);
+        strip_apply<R>(c, r, h, w);
+    }
     float g = 0.f, dl = 0.f;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
@@ -524,8 +599,12 @@ __device__ int strip_cg(const Couple8 (&c)[R], const bool (&valid)[R], float (&x
         ++it;
         strip_store<R>(P, Wd, p, q0, valid, r);
         __syncthreads();
-        h.load(P, Wd, p, q0);
-        strip_apply<R>(c, r, h, w);
+        if constexpr (R >= 9) {
+            strip_apply_plane<R>(c, r, P, Wd, p, q0, valid, w);
+        } else {
+            h.load(P, Wd, p, q0);
+            strip_apply<R>(c, r, h, w);
+        }
         float gn = 0.f, dn = 0.f;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -560,14 +639,18 @@ __device__ int strip_cg(const Couple8 (&c)[R], const bool (&valid)[R], float (&x
     return it;
 }
 
-template <int R>
-__global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::value) k_micro_strip(MicroArgs a) {
+template <int R, bool SC>
+__device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n1 = a.n1, Wd = strip_stride(n1, R);
     const int Hd = strip_rows(n1, R) * R + 2;
     float* P = reinterpret_cast<float*>(smem);
     size_t off = ((size_t)Wd * Hd * sizeof(float) + 15) & ~(size_t)15;
     float* red = reinterpret_cast<float*>(smem + off);  // 4 x 64 floats
+    // SC: scaled couplings of the padded strip grid (n1 x strip_rows * R nodes)
+    const int ncg = n1 * strip_rows(n1, R) * R;
+    float4* cA = reinterpret_cast<float4*>(smem + off + 4 * 64 * sizeof(float));
+    float4* cB = cA + ncg;
 
     const int i = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
     const bool active = tid < n1 * strip_rows(n1, R);
@@ -624,7 +707,7 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::
         // registers: c^_jl = c_jl / sqrt(C_j C_l), sc_j = 1 / sqrt(C_j)
         for (int e = tid; e < Wd * Hd; e += T) P[e] = 0.f;
         const float* S = a.S32 + (size_t)i * kPlanes * pl;
-        Couple8 c[R];
+        RegCouplings<R> c;
         float sc[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -646,10 +729,16 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::
                 s.E *= d0; s.W *= d0; s.N *= d0; s.S *= d0;
                 s.NE *= d0; s.NW *= d0; s.SE *= d0; s.SW *= d0;
             }
-            c[k] = s;
+            c.c[k] = s;
             sc[k] = valid[k] ? d0 : 0.f;
+            if (SC && active) {  // padding rows of the last strip get zero couplings
+                const int j = p + n1 * (q0 + k);
+                cA[j] = make_float4(s.E, s.W, s.N, s.S);
+                cB[j] = make_float4(s.NE, s.NW, s.SE, s.SW);
+            }
         }
         __syncthreads();
+        const SmemCouplings cs{cA, cB, p + n1 * q0, n1};
         const double* S64 = a.S64 + (size_t)i * kPlanes * pl;
         for (;;) {
             if (sweeps >= a.max_sweeps || inner >= a.maxit) {
@@ -667,7 +756,10 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::
                 if (valid[k]) res[p + n1 * (q0 + k)] = r64[k];
             }
             const float rel2 = fmaxf(a.inner_tol * a.inner_tol, 0.25f * stop2 / rr);
-            inner += strip_cg<R>(c, valid, y, r, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 64, &flag);
+            if (SC)
+                inner += strip_cg<R>(cs, valid, y, r, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 64, &flag);
+            else
+                inner += strip_cg<R>(c, valid, y, r, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 64, &flag);
             if (flag == kNaN) break;
             flag = 0;
             // v += d and r -= S64 d in FP64 (d is exact in FP64)
@@ -678,36 +770,28 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::
             __syncthreads();
             StripHalo<R> h;
             h.load(P, Wd, p, q0);
-            double L64[R + 2], R64[R + 2], d64[R];
-#pragma unroll
-            for (int m = 0; m < R + 2; ++m) {
-                L64[m] = (double)h.L[m];
-                R64[m] = (double)h.Rt[m];
-            }
-#pragma unroll
-            for (int k = 0; k < R; ++k) d64[k] = (double)d[k];
-            const double dm = (double)h.xm, dp = (double)h.xp;
             rr = 0.f;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 if (!valid[k]) continue;
                 const int q = q0 + k, j = p + n1 * q;
                 const bool w = p > 0, e = p + 1 < n1, sd = q > 0;
-                const double up = (k + 1 < R) ? d64[k + 1] : dp;
-                const double dn = (k > 0) ? d64[k - 1] : dm;
-                double yv = S64[j] * d64[k];
-                yv = fma(S64[pl + j], R64[k + 1], yv);
-                if (w) yv = fma(S64[pl + j - 1], L64[k + 1], yv);
+                // FP32 values converted as they are used (exact in FP64)
+                const double up = (double)((k + 1 < R) ? d[k + 1] : h.xp);
+                const double dn = (double)((k > 0) ? d[k - 1] : h.xm);
+                double yv = S64[j] * (double)d[k];
+                yv = fma(S64[pl + j], (double)h.Rt[k + 1], yv);
+                if (w) yv = fma(S64[pl + j - 1], (double)h.L[k + 1], yv);
                 yv = fma(S64[2 * pl + j], up, yv);
                 if (sd) yv = fma(S64[2 * pl + j - n1], dn, yv);
-                yv = fma(S64[3 * pl + j], R64[k + 2], yv);
-                yv = fma(S64[4 * pl + j], L64[k + 2], yv);
-                if (e && sd) yv = fma(S64[4 * pl + j - n1 + 1], R64[k], yv);
-                if (w && sd) yv = fma(S64[3 * pl + j - n1 - 1], L64[k], yv);
+                yv = fma(S64[3 * pl + j], (double)h.Rt[k + 2], yv);
+                yv = fma(S64[4 * pl + j], (double)h.L[k + 2], yv);
+                if (e && sd) yv = fma(S64[4 * pl + j - n1 + 1], (double)h.Rt[k], yv);
+                if (w && sd) yv = fma(S64[3 * pl + j - n1 - 1], (double)h.L[k], yv);
                 r64[k] = res[j] - yv;
                 const float rf = (float)r64[k];
                 rr = fmaf(rf, rf, rr);
-                v[j] += d64[k];
+                v[j] += (double)d[k];
             }
             {
                 float t[1] = {rr};
@@ -761,11 +845,26 @@ __global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::
     }
 }
 
+// Short strips (couplings in registers) and tall strips (couplings in shared
+// memory, register budget capped so that several blocks share an SM).
 template <int R>
+__global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::value) k_micro_strip(MicroArgs a) {
+    micro_strip_body<R, false>(a);
+}
+constexpr int kTallStripRegs = 160;
+template <int R>
+__global__ void __maxnreg__(kTallStripRegs) k_micro_strip_tall(MicroArgs a) {
+    micro_strip_body<R, true>(a);
+}
+
+template <int R, bool SC>
 static cudaError_t launch_strip(const MicroArgs& a, cudaStream_t s) {
     const int T = strip_threads(a.n1, R);
     if (T > StripMaxThreads<R>::value) return cudaErrorInvalidConfiguration;
-    k_micro_strip<R><<<a.nM, T, strip_smem_bytes(a.n1, R), s>>>(a);
+    if constexpr (SC)
+        k_micro_strip_tall<R><<<a.nM, T, strip_smem_bytes(a.n1, R, SC), s>>>(a);
+    else
+        k_micro_strip<R><<<a.nM, T, strip_smem_bytes(a.n1, R, SC), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -773,7 +872,7 @@ static cudaError_t launch_strip(const MicroArgs& a, cudaStream_t s) {
 // variant table
 // ---------------------------------------------------------------------------
 static const int kSmemK[4] = {1, 2, 4, 8};
-static const int kStripR[3] = {3, 5, 7};
+static const int kStripR[6] = {3, 5, 7, 9, 11, 13};  // 3..7 couplings in registers, 9..13 in shared memory
 
 bool tiling_uses_stored_residual(int tiling) { return tiling >= 4; }
 
@@ -787,8 +886,9 @@ bool tiling_fits(int tiling, int precision, int n1, int smem_optin) {
     if (tiling >= 4 && tiling < kNumTilings) {
         if (precision == 0) return false;
         const int R = kStripR[tiling - 4];
+        const bool sc = R >= 9;
         const int maxT = R == 3 ? 384 : (R == 5 ? 512 : 384);
-        return strip_threads(n1, R) <= maxT && strip_smem_bytes(n1, R) <= (size_t)smem_optin;
+        return strip_threads(n1, R) <= maxT && strip_smem_bytes(n1, R, sc) <= (size_t)smem_optin;
     }
     return false;
 }
@@ -807,9 +907,12 @@ cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cu
             case 1: return launch_smem<float, true, 2>(a, s);
             case 2: return launch_smem<float, true, 4>(a, s);
             case 3: return launch_smem<float, true, 8>(a, s);
-            case 4: return launch_strip<3>(a, s);
-            case 5: return launch_strip<5>(a, s);
-            case 6: return launch_strip<7>(a, s);
+            case 4: return launch_strip<3, false>(a, s);
+            case 5: return launch_strip<5, false>(a, s);
+            case 6: return launch_strip<7, false>(a, s);
+            case 7: return launch_strip<9, true>(a, s);
+            case 8: return launch_strip<11, true>(a, s);
+            case 9: return launch_strip<13, true>(a, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -820,13 +923,14 @@ cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cu
 cudaError_t configure_micro_kernels(int smem_optin) {
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaSuccess;
-    const void* fns[11] = {(const void*)k_micro_solve<double, false, 1>, (const void*)k_micro_solve<double, false, 2>,
+    const void* fns[14] = {(const void*)k_micro_solve<double, false, 1>, (const void*)k_micro_solve<double, false, 2>,
                            (const void*)k_micro_solve<double, false, 4>, (const void*)k_micro_solve<double, false, 8>,
                            (const void*)k_micro_solve<float, true, 1>,   (const void*)k_micro_solve<float, true, 2>,
                            (const void*)k_micro_solve<float, true, 4>,   (const void*)k_micro_solve<float, true, 8>,
                            (const void*)k_micro_strip<3>,                (const void*)k_micro_strip<5>,
-                           (const void*)k_micro_strip<7>};
-    for (int k = 0; k < 11 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
+                           (const void*)k_micro_strip<7>,                (const void*)k_micro_strip_tall<9>,
+                           (const void*)k_micro_strip_tall<11>,          (const void*)k_micro_strip_tall<13>};
+    for (int k = 0; k < 14 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
     return e;
 }
 
