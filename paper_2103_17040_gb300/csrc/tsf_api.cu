@@ -69,6 +69,8 @@ struct tsf_ctx {
     // gam_eff = |Gam| - beta, constant macro vectors 0 and 1
     double *phi = nullptr, *beta = nullptr, *gam_eff = nullptr, *uzero = nullptr, *uone = nullptr;
     bool phi_valid = false;
+    double* hist = nullptr;      // [3][nM][nmp] past v0 fields (warm-start extrapolation)
+    bool extrap = true;          // off while the adjoint replays states out of order
     int* inst_iters = nullptr;
     DevCtl* ctl = nullptr;
     DevCtl* ctl_host = nullptr;  // pinned
@@ -114,6 +116,11 @@ static tsf_status fail(tsf_ctx* ctx, tsf_status st, const char* fmt, ...) {
             return fail(ctx, e_ == cudaErrorMemoryAllocation ? TSF_E_OOM : TSF_E_CUDA, "%s: %s (%s:%d)", \
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
     } while (0)
+
+// Forget the warm-start history (after a new state or new operators).
+static cudaError_t reset_history(tsf_ctx* ctx) {
+    return cudaMemsetAsync(&ctx->ctl->hist_level, 0, sizeof(int), ctx->stream);
+}
 
 static void invalidate_graph(tsf_ctx* ctx) {
     ctx->graph_gen++;
@@ -293,6 +300,7 @@ static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
     off[k++] = A.take(sizeof(DevCtl));                           // ctl
     off[k++] = A.take(nM * pl * sizeof(double));                 // phi
     for (int r = 0; r < 4; ++r) off[k++] = A.take(nM * sizeof(double));  // beta gam_eff uzero uone
+    off[k++] = A.take(3 * nM * pl * sizeof(double));             // hist
 }
 
 static void assign(tsf_ctx* ctx, const size_t* off) {
@@ -329,9 +337,10 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->gam_eff = (double*)(b + off[k++]);
     ctx->uzero = (double*)(b + off[k++]);
     ctx->uone = (double*)(b + off[k++]);
+    ctx->hist = (double*)(b + off[k++]);
 }
 
-static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5;
+static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5 + 1;
 
 tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return TSF_E_ARG;
@@ -492,6 +501,7 @@ tsf_status tsf_set_state(tsf_ctx* ctx, const double* u, const double* v, int on_
     } else {
         CU(cudaMemsetAsync(ctx->v, 0, (size_t)ctx->nM * ctx->nmp * sizeof(double), ctx->stream));
     }
+    CU(reset_history(ctx));
     ctx->state_set = true;
     return TSF_OK;
 }
@@ -627,6 +637,8 @@ static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt, bool elim) {
     p.bnorm = ctx->bnorm;
     p.phi = elim ? ctx->phi : nullptr;
     p.uw = elim ? ctx->u : nullptr;
+    p.hist = elim && ctx->extrap ? ctx->hist : nullptr;
+    p.ctl = ctx->ctl;
     CU(launch_micro_prologue(p, ctx->stream));
     return TSF_OK;
 }
@@ -650,7 +662,8 @@ static tsf_status enqueue_elimination_step(tsf_ctx* ctx, double dt, cudaEvent_t*
     mg.coupling_maxit = 1;
     CU(launch_macro_solve(mg, ctx->stream));
     if (ev) CU(cudaEventRecord(ev[2], ctx->stream));
-    CU(launch_commit(ctx->nm, ctx->nmp, ctx->nM, ctx->u, ctx->phi, ctx->v, ctx->stream));
+    CU(launch_commit(ctx->nm, ctx->nmp, ctx->nM, ctx->u, ctx->phi, ctx->v, ctx->extrap ? ctx->ctl : nullptr,
+                     ctx->stream));
     return TSF_OK;
 }
 
@@ -692,6 +705,8 @@ static tsf_status compute_phi(tsf_ctx* ctx) {
     if (status)
         return fail(ctx, (tsf_status)status, "solving for the elimination vectors S phi = kappa r failed (status %d)",
                     status);
+    CU(reset_history(ctx));  // past v0 fields belong to the old phi
+    CU(cudaStreamSynchronize(ctx->stream));
     ctx->phi_valid = true;
     return TSF_OK;
 }
@@ -977,6 +992,7 @@ tsf_status tsf_adjoint_mean_u(tsf_ctx* ctx, double dt, int nsteps, int ckpt_ever
     double* Jd = grad + nM * 6;
     const int saved_graph = ctx->opt.use_graph;
     ctx->opt.use_graph = 0;
+    ctx->extrap = false;  // the replayed steps start from checkpoints: no warm-start history
     invalidate_graph(ctx);
     double* const u_state = ctx->u;
     double* const v_state = ctx->v;
@@ -1068,6 +1084,9 @@ tsf_status tsf_adjoint_mean_u(tsf_ctx* ctx, double dt, int nsteps, int ckpt_ever
     ctx->u = u_state;
     ctx->v = v_state;
     ctx->opt.use_graph = saved_graph;
+    ctx->extrap = true;
+    reset_history(ctx);
+    invalidate_graph(ctx);
     cudaStreamSynchronize(ctx->stream);
     cudaFree(buf);
     return st;

@@ -35,6 +35,9 @@ struct DevCtl {
     int cont;                         // 1 while the coupling loop must go on
     double change;                    // last relative change of u
     double gamma_bar;                 // preconditioner value of |Gamma| (macro)
+    // exact elimination: history of past v0 fields for the warm start
+    int hist_level;                   // number of valid past fields (0..2); reset with the state
+    int hist_step;                    // ring position: the current step writes slot hist_step % 3
 };
 
 __device__ __forceinline__ void set_status(DevCtl* ctl, int code) {
@@ -173,6 +176,8 @@ struct PrologueArgs {
     // warm start v - uw phi of v0, and res = c - S v, u_used = 0
     const double* phi;      // [nM][nmp] S^-1 kappa r
     const double* uw;       // [nM] macro values of the state v
+    double* hist;           // [3][nM][nmp] ring of past v0 fields (nullptr: no extrapolation)
+    const DevCtl* ctl;      // hist_level, hist_step
 };
 
 // One-off set-up of the solve S phi = kappa r with the stored-residual
@@ -231,8 +236,10 @@ cudaError_t launch_instance_sums(int n1, int nm, int nmp, int nM, const double* 
                                  double* gam, double* vol, cudaStream_t s);
 cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s);
 cudaError_t launch_phi_setup(const PhiSetupArgs& a, cudaStream_t s);
-// v_i += u_i phi_i on every micro DoF
-cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double* phi, double* v, cudaStream_t s);
+// v_i += u_i phi_i on every micro DoF; with ctl, also advances the warm-start
+// history (hist_step += 1, hist_level up to 2)
+cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double* phi, double* v, DevCtl* ctl,
+                          cudaStream_t s);
 // out = a - b elementwise
 cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);
 // Micro-solve variants ("tilings"):

@@ -314,3 +314,25 @@ def test_elimination_matches_partitioned_over_many_steps():
     st = out[1][2]
     assert st["micro_solves"] == 20 * nM and st["coupling_iters_total"] == 20
     assert out[0][2]["micro_solves"] > st["micro_solves"]
+
+
+def test_elimination_history_is_reset_by_set_state():
+    """Exact elimination extrapolates its warm start from the past steps; a new
+    state forgets that history, so a context that marched before and one that
+    did not give bit-identical steps from the same state."""
+    NM, Nm = 5, 12
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_BUMP, nM, seed=21)
+    u0, v0 = W.random_state(nM, nm, seed=22)
+    T = _T()
+    A = T.TwoScale(Nm, NM, precision=1, coupling=1, tiling=5)
+    B = T.TwoScale(Nm, NM, precision=1, coupling=1, tiling=5)
+    for P in (A, B):
+        P.set_deformation(W.FAMILY_BUMP, prm)
+    A.set_state(*W.random_state(nM, nm, seed=23))
+    A.step(0.01, 6)
+    A.set_state(u0, v0)
+    B.set_state(u0, v0)
+    A.step(0.01, 4)
+    B.step(0.01, 4)
+    assert np.array_equal(A.u(), B.u()) and np.array_equal(A.v(), B.v())
