@@ -183,14 +183,39 @@ def other_coupling(torch, T, E, w, args, uP, vP, barrier, allmax, allsum, K, Wm)
     return out
 
 
+def rank_env():
+    """(world, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def reduce_over_ranks(x, op, world, device="cpu"):
+    """All-reduce one number over the ranks ("max" or "sum"); the identity at
+    world size 1.  Every rank runs its own replica of the workload, so the
+    only collectives are these two on the timing and the work counters."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms_per_rank, world, device="cpu"):
+    """Whole-job throughput: the units all ranks processed divided by the
+    slowest rank's time; also returns (slowest ms, total units)."""
+    ms_max = reduce_over_ranks(ms_per_rank, "max", world, device)
+    total = reduce_over_ranks(units_per_rank, "sum", world, device)
+    return total / (ms_max / 1e3), ms_max, total
+
+
 def run_gb300(args):
     import torch
     import torch.distributed as dist
     import paper_2103_17040_gb300 as T
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
@@ -201,18 +226,10 @@ def run_gb300(args):
             dist.barrier()
 
     def allmax(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", world, "cuda")
 
     def allsum(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(x, "sum", world, "cuda")
 
     # the library enqueues on this (non-default) torch stream, so torch's CUDA
     # events on it bracket exactly the library's work
@@ -234,9 +251,7 @@ def run_gb300(args):
     clocks = clk.stop()
     P.synchronize()
     st = P.stats()
-    ms_max = allmax(ms)
-    dof_iters = allsum(float(st["dof_cg_iters"]))
-    value = dof_iters / (ms_max / 1e3)
+    value, ms_max, dof_iters = whole_job_rate(float(st["dof_cg_iters"]), ms, world, "cuda")
     steps_per_s = world * K / (ms_max / 1e3)
     # partitioned: 2 prologues + (micro, macro) per coupling iteration; elimination: 5 kernels per step
     launches = 5 * K if args.coupling == "elimination" else 2 * K + 2 * st["coupling_iters_total"]
