@@ -69,8 +69,15 @@ struct tsf_ctx {
     // gam_eff = |Gam| - beta, constant macro vectors 0 and 1
     double *phi = nullptr, *beta = nullptr, *gam_eff = nullptr, *uzero = nullptr, *uone = nullptr;
     bool phi_valid = false;
-    double* hist = nullptr;      // [3][nM][nmp] past v0 fields (warm-start extrapolation)
-    bool extrap = true;          // off while the adjoint replays states out of order
+    double* hist = nullptr;      // [3][nM][nmp] ring of the last solves' z (warm-start extrapolation)
+    double *Z = nullptr, *cpre = nullptr, *mphi = nullptr;  // pipelined elimination (tsf_elim.cu)
+    double* yhist = nullptr;     // [3][nM][nmp] ring of S z of the last solves
+    double *pnorm = nullptr, *mnorm = nullptr;  // [nM][3] prepared norms
+    bool extrap = true;          // pipelined elimination with extrapolated warm starts; off while the
+                                 // adjoint replays states out of order
+    cudaStream_t side = nullptr; // second stream of the pipelined step (prepares the next step)
+    int prio_hi = 0, prio_lo = 0; // launch priorities: macro solve first, preparation after
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     int* inst_iters = nullptr;
     DevCtl* ctl = nullptr;
     DevCtl* ctl_host = nullptr;  // pinned
@@ -117,9 +124,12 @@ static tsf_status fail(tsf_ctx* ctx, tsf_status st, const char* fmt, ...) {
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
     } while (0)
 
-// Forget the warm-start history (after a new state or new operators).
+// Forget the warm-start history and the prepared next step (after a new
+// state or new operators).
 static cudaError_t reset_history(tsf_ctx* ctx) {
-    return cudaMemsetAsync(&ctx->ctl->hist_level, 0, sizeof(int), ctx->stream);
+    cudaError_t e = cudaMemsetAsync(&ctx->ctl->hist_level, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&ctx->ctl->prep_ok, 0, sizeof(int), ctx->stream);
+    return e;
 }
 
 static void invalidate_graph(tsf_ctx* ctx) {
@@ -182,10 +192,17 @@ tsf_status tsf_create(tsf_ctx** out, const tsf_options* opt) {
             ctx->own_stream = (e == cudaSuccess);
         }
     }
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&ctx->prio_lo, &ctx->prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = configure_micro_kernels(ctx->smem_optin);
     if (e == cudaSuccess) e = configure_macro_kernels(ctx->smem_optin);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->ctl_host, sizeof(DevCtl));
     if (e != cudaSuccess) {
+        if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+        if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+        if (ctx->side) cudaStreamDestroy(ctx->side);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
         return TSF_E_CUDA;
@@ -211,9 +228,13 @@ tsf_status tsf_set_options(tsf_ctx* ctx, const tsf_options* opt) {
 void tsf_destroy(tsf_ctx* ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
     invalidate_graph(ctx);
     for (int k = 0; k < 4; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
     if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -301,6 +322,10 @@ static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
     off[k++] = A.take(nM * pl * sizeof(double));                 // phi
     for (int r = 0; r < 4; ++r) off[k++] = A.take(nM * sizeof(double));  // beta gam_eff uzero uone
     off[k++] = A.take(3 * nM * pl * sizeof(double));             // hist
+    for (int r = 0; r < 3; ++r) off[k++] = A.take(nM * pl * sizeof(double));  // Z cpre mphi
+    off[k++] = A.take(3 * nM * pl * sizeof(double));             // yhist
+    off[k++] = A.take(nM * 3 * sizeof(double));                  // pnorm
+    off[k++] = A.take(nM * 3 * sizeof(double));                  // mnorm
 }
 
 static void assign(tsf_ctx* ctx, const size_t* off) {
@@ -338,9 +363,15 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->uzero = (double*)(b + off[k++]);
     ctx->uone = (double*)(b + off[k++]);
     ctx->hist = (double*)(b + off[k++]);
+    ctx->Z = (double*)(b + off[k++]);
+    ctx->cpre = (double*)(b + off[k++]);
+    ctx->mphi = (double*)(b + off[k++]);
+    ctx->yhist = (double*)(b + off[k++]);
+    ctx->pnorm = (double*)(b + off[k++]);
+    ctx->mnorm = (double*)(b + off[k++]);
 }
 
-static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5 + 1;
+static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5 + 1 + 3 + 1 + 2;
 
 tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return TSF_E_ARG;
@@ -594,9 +625,7 @@ static MacroArgs macro_args(tsf_ctx* ctx, double dt, bool set_cond, cudaGraphCon
 
 static bool eliminating(const tsf_ctx* ctx) { return ctx->opt.coupling == TSF_COUPLING_ELIMINATION; }
 
-// Macro and micro prologues of a step.  With elim the micro prologue also
-// replaces v by the warm start v - u phi of v0 (exact elimination).
-static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt, bool elim) {
+static tsf_status enqueue_macro_prologue(tsf_ctx* ctx, double dt) {
     MacroPrologueArgs m{};
     m.NM = ctx->NM;
     m.N1 = ctx->N1;
@@ -615,6 +644,14 @@ static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt, bool elim) {
     m.uk = ctx->uk;
     m.ctl = ctx->ctl;
     CU(launch_macro_prologue(m, ctx->stream));
+    return TSF_OK;
+}
+
+// Macro and micro prologues of a step.  With elim the micro prologue also
+// replaces v by the warm start v - u phi of v0 (exact elimination).
+static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt, bool elim) {
+    tsf_status st = enqueue_macro_prologue(ctx, dt);
+    if (st) return st;
     PrologueArgs p{};
     p.n1 = ctx->n1;
     p.nm = ctx->nm;
@@ -637,8 +674,6 @@ static tsf_status enqueue_prologue(tsf_ctx* ctx, double dt, bool elim) {
     p.bnorm = ctx->bnorm;
     p.phi = elim ? ctx->phi : nullptr;
     p.uw = elim ? ctx->u : nullptr;
-    p.hist = elim && ctx->extrap ? ctx->hist : nullptr;
-    p.ctl = ctx->ctl;
     CU(launch_micro_prologue(p, ctx->stream));
     return TSF_OK;
 }
@@ -662,9 +697,78 @@ static tsf_status enqueue_elimination_step(tsf_ctx* ctx, double dt, cudaEvent_t*
     mg.coupling_maxit = 1;
     CU(launch_macro_solve(mg, ctx->stream));
     if (ev) CU(cudaEventRecord(ev[2], ctx->stream));
-    CU(launch_commit(ctx->nm, ctx->nmp, ctx->nM, ctx->u, ctx->phi, ctx->v, ctx->extrap ? ctx->ctl : nullptr,
-                     ctx->stream));
+    CU(launch_commit(ctx->nm, ctx->nmp, ctx->nM, ctx->u, ctx->phi, ctx->v, ctx->stream));
     return TSF_OK;
+}
+
+static ElimArgs elim_args(tsf_ctx* ctx, double dt) {
+    ElimArgs a{};
+    a.n1 = ctx->n1;
+    a.nm = ctx->nm;
+    a.nmp = ctx->nmp;
+    a.nM = ctx->nM;
+    a.dt = dt;
+    a.kappa = ctx->kappa;
+    a.M64 = ctx->M64;
+    a.S64 = ctx->S64;
+    a.fv = ctx->has_fv ? ctx->fv : nullptr;
+    a.g = ctx->has_g ? ctx->g : nullptr;
+    a.redge = ctx->redge;
+    a.Rd = ctx->Rd;
+    a.Ru = ctx->Ru;
+    a.phi = ctx->phi;
+    a.mphi = ctx->mphi;
+    a.u = ctx->u;
+    a.v = ctx->v;
+    a.Z = ctx->Z;
+    a.c = ctx->c;
+    a.cpre = ctx->cpre;
+    a.res = ctx->res;
+    a.u_used = ctx->u_used;
+    a.bnorm = ctx->bnorm;
+    a.hist = ctx->hist;
+    a.yhist = tiling_uses_stored_residual(ctx->tiling) ? ctx->yhist : nullptr;
+    a.pnorm = ctx->pnorm;
+    a.mnorm = ctx->mnorm;
+    a.ctl = ctx->ctl;
+    return a;
+}
+
+// One pipelined step by exact elimination (see tsf_elim.cu):
+//   macro prologue, front -> micro solve of z in Z
+//   -> fork: macro solve (this stream) | preparation of the next step (side stream)
+//   -> join -> commit v = z + u phi.
+// ev: optional events around the micro and macro solves.
+static tsf_status enqueue_pipelined_step(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
+    tsf_status st = enqueue_macro_prologue(ctx, dt);
+    if (st) return st;
+    const ElimArgs ea = elim_args(ctx, dt);
+    CU(launch_elim_front(ea, ctx->stream));
+    if (ev) CU(cudaEventRecord(ev[0], ctx->stream));
+    MicroArgs ma = micro_args(ctx, ctx->Z);
+    ma.u = ctx->uzero;
+    CU(launch_micro_solve(ma, ctx->opt.precision, ctx->tiling, ctx->stream));
+    if (ev) CU(cudaEventRecord(ev[1], ctx->stream));
+    CU(cudaEventRecord(ctx->fork_ev, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0));
+    // the one-block macro solve must not wait behind the preparation's blocks
+    CU(launch_elim_pre(ea, ctx->side, ctx->prio_lo));
+    CU(cudaEventRecord(ctx->join_ev, ctx->side));
+    cudaGraphConditionalHandle none{};
+    MacroArgs mg = macro_args(ctx, dt, false, none);
+    mg.gam = ctx->gam_eff;
+    mg.coupling_tol = HUGE_VAL;  // one macro solve ends the step
+    mg.coupling_maxit = 1;
+    CU(launch_macro_solve(mg, ctx->stream, ctx->prio_hi, (size_t)ctx->smem_optin));
+    if (ev) CU(cudaEventRecord(ev[2], ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
+    CU(launch_elim_commit(ea, ctx->stream));
+    return TSF_OK;
+}
+
+// the step of the elimination mode in use
+static tsf_status enqueue_elim(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
+    return ctx->extrap ? enqueue_pipelined_step(ctx, dt, ev) : enqueue_elimination_step(ctx, dt, ev);
 }
 
 static double phi_tol(double cg_tol) { return std::max(1e-3 * cg_tol, 1e-13); }
@@ -705,7 +809,8 @@ static tsf_status compute_phi(tsf_ctx* ctx) {
     if (status)
         return fail(ctx, (tsf_status)status, "solving for the elimination vectors S phi = kappa r failed (status %d)",
                     status);
-    CU(reset_history(ctx));  // past v0 fields belong to the old phi
+    CU(launch_mphi(elim_args(ctx, ctx->ops_dt), ctx->stream));
+    CU(reset_history(ctx));  // past z fields and prepared data belong to the old phi
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->phi_valid = true;
     return TSF_OK;
@@ -790,7 +895,7 @@ static cudaError_t capture_step_into(tsf_ctx* ctx, cudaGraph_t G, double dt, tsf
         *what = "begin capture";
         e = cudaStreamBeginCaptureToGraph(ctx->stream, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        *st = enqueue_elimination_step(ctx, dt, nullptr);
+        *st = enqueue_elim(ctx, dt, nullptr);
         cudaGraph_t endg = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &endg);
         *what = "elimination step";
@@ -850,7 +955,7 @@ static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
     const char* what;
     cudaError_t e = capture_step_into(ctx, ctx->graph, dt, &st, &what);
     if (e != cudaSuccess) return capture_failed(ctx, st, e, what);
-    e = cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0);
+    e = cudaGraphInstantiate(&ctx->gexec, ctx->graph, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "instantiate");
     ctx->graph_valid = true;
     ctx->graph_dt = dt;
@@ -889,7 +994,7 @@ static tsf_status run_plain_steps(tsf_ctx* ctx, double dt, int nsteps) {
         for (int k = 0; k < 4; ++k) CU(cudaEventCreate(&ctx->ev[k]));
     if (eliminating(ctx)) {
         for (int s = 0; s < nsteps; ++s) {
-            tsf_status st = enqueue_elimination_step(ctx, dt, prof ? ctx->ev : nullptr);
+            tsf_status st = enqueue_elim(ctx, dt, prof ? ctx->ev : nullptr);
             if (st) return st;
             if (prof) {
                 float a = 0.f, b = 0.f;
@@ -1257,7 +1362,7 @@ static tsf_status batch_capture(tsf_batch* b, double dt) {
                          cudaGetErrorString(e));
         }
     }
-    e = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+    e = cudaGraphInstantiate(&b->gexec, b->graph, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) {
         batch_drop_graph(b, false);
         cudaGetLastError();

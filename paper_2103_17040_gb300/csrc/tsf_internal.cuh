@@ -37,7 +37,8 @@ struct DevCtl {
     double gamma_bar;                 // preconditioner value of |Gamma| (macro)
     // exact elimination: history of past v0 fields for the warm start
     int hist_level;                   // number of valid past fields (0..2); reset with the state
-    int hist_step;                    // ring position: the current step writes slot hist_step % 3
+    int hist_step;                    // ring position: the current solve's v0 goes to slot hist_step % 3
+    int prep_ok;                      // 1: the next step's right-hand side was prepared (k_elim_pre)
 };
 
 __device__ __forceinline__ void set_status(DevCtl* ctl, int code) {
@@ -116,6 +117,28 @@ __device__ __forceinline__ double block_sum_compensated(double x, double* buf /*
     return s + c;
 }
 
+// y_j = (A x)_j for the symmetric 5-plane stencil A (planes of stride pl) on
+// an n1 x n1 node grid, node j = (p, q), FP64.
+__device__ __forceinline__ double plane_apply(const double* __restrict__ A, size_t pl, const double* __restrict__ x,
+                                              int j, int p, int q, int n1) {
+    double y = A[j] * x[j];
+    const bool e = p + 1 < n1, w = p > 0;
+    if (e) y = fma(A[pl + j], x[j + 1], y);
+    if (w) y = fma(A[pl + j - 1], x[j - 1], y);
+    if (q + 1 < n1) {
+        y = fma(A[2 * pl + j], x[j + n1], y);
+        if (e) y = fma(A[3 * pl + j], x[j + n1 + 1], y);
+        if (w) y = fma(A[4 * pl + j], x[j + n1 - 1], y);
+    }
+    if (q > 0) {
+        y = fma(A[2 * pl + j - n1], x[j - n1], y);
+        if (w) y = fma(A[3 * pl + j - n1 - 1], x[j - n1 - 1], y);
+        if (e) y = fma(A[4 * pl + j - n1 + 1], x[j - n1 + 1], y);
+    }
+    return y;
+}
+
+
 // ---------------------------------------------------------------------------
 // Kernel argument blocks
 // ---------------------------------------------------------------------------
@@ -176,8 +199,6 @@ struct PrologueArgs {
     // warm start v - uw phi of v0, and res = c - S v, u_used = 0
     const double* phi;      // [nM][nmp] S^-1 kappa r
     const double* uw;       // [nM] macro values of the state v
-    double* hist;           // [3][nM][nmp] ring of past v0 fields (nullptr: no extrapolation)
-    const DevCtl* ctl;      // hist_level, hist_step
 };
 
 // One-off set-up of the solve S phi = kappa r with the stored-residual
@@ -236,10 +257,8 @@ cudaError_t launch_instance_sums(int n1, int nm, int nmp, int nM, const double* 
                                  double* gam, double* vol, cudaStream_t s);
 cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s);
 cudaError_t launch_phi_setup(const PhiSetupArgs& a, cudaStream_t s);
-// v_i += u_i phi_i on every micro DoF; with ctl, also advances the warm-start
-// history (hist_step += 1, hist_level up to 2)
-cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double* phi, double* v, DevCtl* ctl,
-                          cudaStream_t s);
+// v_i += u_i phi_i on every micro DoF
+cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double* phi, double* v, cudaStream_t s);
 // out = a - b elementwise
 cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);
 // Micro-solve variants ("tilings"):
@@ -251,7 +270,11 @@ bool tiling_fits(int tiling, int precision, int n1, int smem_optin);
 cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cudaStream_t s);
 bool tiling_uses_stored_residual(int tiling);
 cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s);
-cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s);
+// priority: 0 = the stream's; otherwise a launch priority (lower value = higher
+// priority).  reserve_smem: dynamic shared memory to reserve (at least what
+// the solve needs), so that a large value keeps other kernels' blocks off
+// the macro solve's SM while it runs concurrently with them.
+cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s, int priority = 0, size_t reserve_smem = 0);
 size_t macro_smem_bytes(int N1, int bc, int use_dct);
 cudaError_t launch_vbar(int nm, int nmp, int nM, const double* lm, const double* vol, const double* v,
                         double* vbar, cudaStream_t s);
@@ -259,6 +282,43 @@ cudaError_t launch_flux(int n1, int nm, int nmp, int nM, double kappa, const dou
                         const double* v, const double* redge, const double* g, double* flux, cudaStream_t s);
 cudaError_t configure_micro_kernels(int smem_optin);
 cudaError_t configure_macro_kernels(int smem_optin);
+
+// Pipelined exact elimination (tsf_elim.cu).  A step is
+//   front -> micro solve of z (S z = c, in Z) -> { macro solve ; pre } -> commit
+// where "pre" prepares the next step while the one-block macro solve runs:
+// cpre = M z / dt, the warm start g extrapolated from the last three z, and
+// res = cpre - S g.  Only u enters afterwards: c = cpre + u M phi / dt + src.
+struct ElimArgs {
+    int n1, nm, nmp, nM;
+    double dt, kappa;
+    const double* M64;
+    const double* S64;
+    const double* fv;       // [nM][nmp] or nullptr
+    const double* g;        // [nM][n1] or nullptr (Robin data)
+    const double* redge;
+    const double* Rd;
+    const double* Ru;
+    const double* phi;      // [nM][nmp] S^-1 kappa r
+    double* mphi;           // [nM][nmp] M phi / dt
+    const double* u;        // [nM] committed macro state
+    double* v;              // [nM][nmp] committed micro state
+    double* Z;              // [nM][nmp] unknown of the micro solve (warm start on entry)
+    double* c;              // [nM][nmp] right-hand side
+    double* cpre;           // [nM][nmp] M z / dt of the last solve
+    double* res;            // [nM][nmp] stored residual of Z
+    double* u_used;         // [nM]
+    double* bnorm;          // [nM][3]
+    double* hist;           // [3][nM][nmp] ring of the last solves' z
+    double* yhist;          // [3][nM][nmp] ring of S z = c - (final residual), or nullptr when the
+                            // micro-solve variant does not keep its residual (S g then computed)
+    double* pnorm;          // [nM][3] ||cpre||^2, cpre^T mphi, cpre^T r (written by k_elim_pre)
+    double* mnorm;          // [nM][3] ||mphi||^2, mphi^T r, ||r||^2 (written by k_mphi)
+    DevCtl* ctl;
+};
+cudaError_t launch_elim_front(const ElimArgs& a, cudaStream_t s);
+cudaError_t launch_elim_pre(const ElimArgs& a, cudaStream_t s, int priority = 0);
+cudaError_t launch_elim_commit(const ElimArgs& a, cudaStream_t s);
+cudaError_t launch_mphi(const ElimArgs& a, cudaStream_t s);
 
 // discrete adjoint (tsf_adjoint.cu)
 struct AdjAccArgs {

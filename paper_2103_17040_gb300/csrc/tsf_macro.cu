@@ -25,6 +25,8 @@
 // single thread block; its cost is latency, not bandwidth.
 #include "tsf_internal.cuh"
 
+#include <algorithm>
+
 namespace tsf {
 
 __device__ __forceinline__ bool is_dir_node(int bc, int N, int p, int q) {
@@ -363,10 +365,24 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
     }
 }
 
-cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s) {
-    const size_t sm = macro_smem_bytes(a.N1, a.bc, a.use_dct);
-    k_macro_solve<<<1, kMacroThreads, sm, s>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s, int priority, size_t reserve_smem) {
+    const size_t sm = std::max(macro_smem_bytes(a.N1, a.bc, a.use_dct), reserve_smem);
+    if (priority == 0) {
+        k_macro_solve<<<1, kMacroThreads, sm, s>>>(a);
+        return cudaGetLastError();
+    }
+    // a scheduling priority for the block (kept by graph capture)
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kMacroThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = priority;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_macro_solve, a);
 }
 
 cudaError_t configure_macro_kernels(int smem_optin) {

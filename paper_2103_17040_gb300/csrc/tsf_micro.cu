@@ -940,25 +940,6 @@ cudaError_t configure_micro_kernels(int smem_optin) {
 //   res = c + kappa u r - S v^n                (residual of the warm start v^n)
 //   bnorm = (||c||^2, c^T r, ||r||^2)          (||b(u)|| for any u)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double plane_apply(const double* __restrict__ A, size_t pl, const double* __restrict__ x,
-                                              int j, int p, int q, int n1) {
-    double y = A[j] * x[j];
-    const bool e = p + 1 < n1, w = p > 0;
-    if (e) y = fma(A[pl + j], x[j + 1], y);
-    if (w) y = fma(A[pl + j - 1], x[j - 1], y);
-    if (q + 1 < n1) {
-        y = fma(A[2 * pl + j], x[j + n1], y);
-        if (e) y = fma(A[3 * pl + j], x[j + n1 + 1], y);
-        if (w) y = fma(A[4 * pl + j], x[j + n1 - 1], y);
-    }
-    if (q > 0) {
-        y = fma(A[2 * pl + j - n1], x[j - n1], y);
-        if (w) y = fma(A[3 * pl + j - n1 - 1], x[j - n1 - 1], y);
-        if (e) y = fma(A[4 * pl + j - n1 + 1], x[j - n1 + 1], y);
-    }
-    return y;
-}
-
 __global__ void __launch_bounds__(256) k_micro_prologue(PrologueArgs a) {
     __shared__ double buf[3 * 32];
     const int i = blockIdx.x;
@@ -1000,28 +981,11 @@ __global__ void __launch_bounds__(256) k_micro_prologue(PrologueArgs a) {
         // exact elimination: the unknown is v0 with S v0 = c; its warm start
         // is v^n - u^n phi (= the previous step's v0 when v^n was committed
         // as v0 + u^n phi)
-        // With a history of past v0 fields the warm start is extrapolated in
-        // time: 2 v0^n - v0^{n-1} (one past field) or 3 v0^n - 3 v0^{n-1} +
-        // v0^{n-2} (two), v0^n = v^n - u^n phi being stored for later steps.
         const double* ph = a.phi + (size_t)i * pl;
         double* vw = a.v + (size_t)i * pl;
         const double uw = a.uw[i];
-        const int level = a.hist ? a.ctl->hist_level : 0, st = a.hist ? a.ctl->hist_step : 0;
-        const size_t slot = (size_t)a.nM * pl;
-        double* hc = a.hist ? a.hist + (size_t)(st % 3) * slot + (size_t)i * pl : nullptr;
-        const double* h1 = a.hist ? a.hist + (size_t)((st + 2) % 3) * slot + (size_t)i * pl : nullptr;
-        const double* h2 = a.hist ? a.hist + (size_t)((st + 1) % 3) * slot + (size_t)i * pl : nullptr;
         __syncthreads();  // every thread has read v^n for c
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const double v0 = fma(-uw, ph[j], vw[j]);
-            double g = v0;
-            if (level >= 2)
-                g = fma(3.0, v0 - h1[j], h2[j]);
-            else if (level == 1)
-                g = fma(2.0, v0, -h1[j]);
-            if (hc) hc[j] = v0;
-            vw[j] = g;
-        }
+        for (int j = threadIdx.x; j < nm; j += blockDim.x) vw[j] = fma(-uw, ph[j], vw[j]);
         __syncthreads();
         for (int j = threadIdx.x; j < nm; j += blockDim.x)
             res[j] = c[j] - plane_apply(S, pl, v, j, j % n1, j / n1, n1);
@@ -1067,25 +1031,19 @@ cudaError_t launch_phi_setup(const PhiSetupArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// v_i += u_i phi_i, one thread per (instance, DoF); the first thread moves
-// the warm-start history on (the next step's prologue sees it)
+// v_i += u_i phi_i, one thread per (instance, DoF)
 __global__ void __launch_bounds__(256) k_commit(int nm, int nmp, const double* __restrict__ u,
-                                                const double* __restrict__ phi, double* __restrict__ v, DevCtl* ctl) {
+                                                const double* __restrict__ phi, double* __restrict__ v) {
     const int i = blockIdx.x;  // instances on grid.x (up to 2^31 - 1)
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
-    if (ctl && i == 0 && j == 0) {
-        ctl->hist_step += 1;
-        if (ctl->hist_level < 2) ctl->hist_level += 1;
-    }
     if (j >= nm) return;
     const size_t o = (size_t)i * nmp + j;
     v[o] = fma(u[i], phi[o], v[o]);
 }
 
-cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double* phi, double* v, DevCtl* ctl,
-                          cudaStream_t s) {
+cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double* phi, double* v, cudaStream_t s) {
     dim3 grid(nM, (nm + 255) / 256);
-    k_commit<<<grid, 256, 0, s>>>(nm, nmp, u, phi, v, ctl);
+    k_commit<<<grid, 256, 0, s>>>(nm, nmp, u, phi, v);
     return cudaGetLastError();
 }
 
