@@ -70,14 +70,17 @@ struct tsf_ctx {
     double *phi = nullptr, *beta = nullptr, *gam_eff = nullptr, *uzero = nullptr, *uone = nullptr;
     bool phi_valid = false;
     double* hist = nullptr;      // [3][nM][nmp] ring of the last solves' z (warm-start extrapolation)
-    double *Z = nullptr, *cpre = nullptr, *mphi = nullptr;  // pipelined elimination (tsf_elim.cu)
-    double* yhist = nullptr;     // [3][nM][nmp] ring of S z of the last solves
-    double *pnorm = nullptr, *mnorm = nullptr;  // [nM][3] prepared norms
+    // pipelined elimination (tsf_elim.cu): z = w + u psi
+    double *W = nullptr, *cnext = nullptr, *mphi = nullptr, *psi = nullptr, *mpsi = nullptr;  // [nM][nmp]
+    double* yhist = nullptr;     // [3][nM][nmp] ring of S w of the last solves
+    double *mnorm = nullptr;     // [nM][3] norms of M phi / dt
+    double *u_old = nullptr, *gam_psi = nullptr, *rho_eff = nullptr;  // [nM]
+    bool w_valid = false;        // W holds the solved w of the committed state
     bool extrap = true;          // pipelined elimination with extrapolated warm starts; off while the
                                  // adjoint replays states out of order
     cudaStream_t side = nullptr; // second stream of the pipelined step (prepares the next step)
     int prio_hi = 0, prio_lo = 0; // launch priorities: macro solve first, preparation after
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, mp_ev = nullptr, pre_ev = nullptr;
     int* inst_iters = nullptr;
     DevCtl* ctl = nullptr;
     DevCtl* ctl_host = nullptr;  // pinned
@@ -124,11 +127,12 @@ static tsf_status fail(tsf_ctx* ctx, tsf_status st, const char* fmt, ...) {
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
     } while (0)
 
-// Forget the warm-start history and the prepared next step (after a new
-// state or new operators).
+// Forget the warm-start history and the prepared w (after a new state, new
+// sources or new operators).
 static cudaError_t reset_history(tsf_ctx* ctx) {
+    ctx->w_valid = false;
     cudaError_t e = cudaMemsetAsync(&ctx->ctl->hist_level, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&ctx->ctl->prep_ok, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&ctx->ctl->pushed, 0, sizeof(int), ctx->stream);
     return e;
 }
 
@@ -193,15 +197,19 @@ tsf_status tsf_create(tsf_ctx** out, const tsf_options* opt) {
         }
     }
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&ctx->prio_lo, &ctx->prio_hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, ctx->prio_lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->mp_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->pre_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = configure_micro_kernels(ctx->smem_optin);
     if (e == cudaSuccess) e = configure_macro_kernels(ctx->smem_optin);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->ctl_host, sizeof(DevCtl));
     if (e != cudaSuccess) {
         if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
         if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+        if (ctx->mp_ev) cudaEventDestroy(ctx->mp_ev);
+        if (ctx->pre_ev) cudaEventDestroy(ctx->pre_ev);
         if (ctx->side) cudaStreamDestroy(ctx->side);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
@@ -234,6 +242,8 @@ void tsf_destroy(tsf_ctx* ctx) {
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+    if (ctx->mp_ev) cudaEventDestroy(ctx->mp_ev);
+    if (ctx->pre_ev) cudaEventDestroy(ctx->pre_ev);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
     if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
@@ -322,10 +332,10 @@ static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
     off[k++] = A.take(nM * pl * sizeof(double));                 // phi
     for (int r = 0; r < 4; ++r) off[k++] = A.take(nM * sizeof(double));  // beta gam_eff uzero uone
     off[k++] = A.take(3 * nM * pl * sizeof(double));             // hist
-    for (int r = 0; r < 3; ++r) off[k++] = A.take(nM * pl * sizeof(double));  // Z cpre mphi
+    for (int r = 0; r < 5; ++r) off[k++] = A.take(nM * pl * sizeof(double));  // W cnext mphi psi mpsi
     off[k++] = A.take(3 * nM * pl * sizeof(double));             // yhist
-    off[k++] = A.take(nM * 3 * sizeof(double));                  // pnorm
     off[k++] = A.take(nM * 3 * sizeof(double));                  // mnorm
+    for (int r = 0; r < 3; ++r) off[k++] = A.take(nM * sizeof(double));  // u_old gam_psi rho_eff
 }
 
 static void assign(tsf_ctx* ctx, const size_t* off) {
@@ -363,15 +373,19 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->uzero = (double*)(b + off[k++]);
     ctx->uone = (double*)(b + off[k++]);
     ctx->hist = (double*)(b + off[k++]);
-    ctx->Z = (double*)(b + off[k++]);
-    ctx->cpre = (double*)(b + off[k++]);
+    ctx->W = (double*)(b + off[k++]);
+    ctx->cnext = (double*)(b + off[k++]);
     ctx->mphi = (double*)(b + off[k++]);
+    ctx->psi = (double*)(b + off[k++]);
+    ctx->mpsi = (double*)(b + off[k++]);
     ctx->yhist = (double*)(b + off[k++]);
-    ctx->pnorm = (double*)(b + off[k++]);
     ctx->mnorm = (double*)(b + off[k++]);
+    ctx->u_old = (double*)(b + off[k++]);
+    ctx->gam_psi = (double*)(b + off[k++]);
+    ctx->rho_eff = (double*)(b + off[k++]);
 }
 
-static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5 + 1 + 3 + 1 + 2;
+static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5 + 1 + 5 + 1 + 1 + 3;
 
 tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return TSF_E_ARG;
@@ -401,6 +415,7 @@ static tsf_status init_workspace(tsf_ctx* ctx) {
     ctx->has_ud = !ctx->dir_vals.empty();
     ctx->has_fv = ctx->has_g = ctx->has_fu = false;
     ctx->geom_set = ctx->state_set = ctx->ops_valid = false;
+    ctx->w_valid = false;
     ctx->ws_valid = true;
     invalidate_graph(ctx);
     return TSF_OK;
@@ -558,6 +573,7 @@ tsf_status tsf_set_sources(tsf_ctx* ctx, const double* fv, const double* g, cons
     }
     if (before[0] != ctx->has_fv || before[1] != ctx->has_g || before[2] != ctx->has_fu || before[3] != ctx->has_ud)
         invalidate_graph(ctx);
+    if (before[0] != ctx->has_fv || before[1] != ctx->has_g) CU(reset_history(ctx));  // pipelining on or off
     return TSF_OK;
 }
 
@@ -625,7 +641,7 @@ static MacroArgs macro_args(tsf_ctx* ctx, double dt, bool set_cond, cudaGraphCon
 
 static bool eliminating(const tsf_ctx* ctx) { return ctx->opt.coupling == TSF_COUPLING_ELIMINATION; }
 
-static tsf_status enqueue_macro_prologue(tsf_ctx* ctx, double dt) {
+static tsf_status enqueue_macro_prologue(tsf_ctx* ctx, double dt, bool pipelined = false) {
     MacroPrologueArgs m{};
     m.NM = ctx->NM;
     m.N1 = ctx->N1;
@@ -643,6 +659,11 @@ static tsf_status enqueue_macro_prologue(tsf_ctx* ctx, double dt) {
     m.cH = ctx->cH;
     m.uk = ctx->uk;
     m.ctl = ctx->ctl;
+    if (pipelined) {
+        m.rho_w = ctx->rho;
+        m.gam_psi = ctx->gam_psi;
+        m.rho_eff = ctx->rho_eff;
+    }
     CU(launch_macro_prologue(m, ctx->stream));
     return TSF_OK;
 }
@@ -708,67 +729,90 @@ static ElimArgs elim_args(tsf_ctx* ctx, double dt) {
     a.nmp = ctx->nmp;
     a.nM = ctx->nM;
     a.dt = dt;
-    a.kappa = ctx->kappa;
     a.M64 = ctx->M64;
     a.S64 = ctx->S64;
-    a.fv = ctx->has_fv ? ctx->fv : nullptr;
-    a.g = ctx->has_g ? ctx->g : nullptr;
     a.redge = ctx->redge;
-    a.Rd = ctx->Rd;
-    a.Ru = ctx->Ru;
     a.phi = ctx->phi;
+    a.psi = ctx->psi;
     a.mphi = ctx->mphi;
+    a.mpsi = ctx->mpsi;
     a.u = ctx->u;
+    a.u_old = ctx->u_old;
     a.v = ctx->v;
-    a.Z = ctx->Z;
+    a.W = ctx->W;
     a.c = ctx->c;
-    a.cpre = ctx->cpre;
+    a.cnext = ctx->cnext;
     a.res = ctx->res;
     a.u_used = ctx->u_used;
     a.bnorm = ctx->bnorm;
     a.hist = ctx->hist;
     a.yhist = tiling_uses_stored_residual(ctx->tiling) ? ctx->yhist : nullptr;
-    a.pnorm = ctx->pnorm;
-    a.mnorm = ctx->mnorm;
     a.ctl = ctx->ctl;
     return a;
 }
 
-// One pipelined step by exact elimination (see tsf_elim.cu):
-//   macro prologue, front -> micro solve of z in Z
-//   -> fork: macro solve (this stream) | preparation of the next step (side stream)
-//   -> join -> commit v = z + u phi.
-// ev: optional events around the micro and macro solves.
-static tsf_status enqueue_pipelined_step(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
-    tsf_status st = enqueue_macro_prologue(ctx, dt);
-    if (st) return st;
+// Steps by pipelined elimination (tsf_elim.cu): eliminating, with warm-start
+// history, and without volume or Robin sources (whose next values are not
+// known one step ahead).
+static bool pipelined(const tsf_ctx* ctx) {
+    return eliminating(ctx) && ctx->extrap && !ctx->has_fv && !ctx->has_g;
+}
+
+// The first w from the committed state: k_elim_head and one micro solve.
+static tsf_status enqueue_head(tsf_ctx* ctx, double dt) {
     const ElimArgs ea = elim_args(ctx, dt);
-    CU(launch_elim_front(ea, ctx->stream));
-    if (ev) CU(cudaEventRecord(ev[0], ctx->stream));
-    MicroArgs ma = micro_args(ctx, ctx->Z);
+    CU(launch_elim_head(ea, ctx->stream));
+    MicroArgs ma = micro_args(ctx, ctx->W);
     ma.u = ctx->uzero;
     CU(launch_micro_solve(ma, ctx->opt.precision, ctx->tiling, ctx->stream));
-    if (ev) CU(cudaEventRecord(ev[1], ctx->stream));
+    return TSF_OK;
+}
+
+// One pipelined step (needs the solved w of the committed state):
+//   k_elim_start
+//   -> macro branch (this stream): macro prologue, macro solve, [after pre] commit
+//   -> micro branch (side stream): k_elim_pre, [after the macro prologue] micro solve of the next w
+//   -> join.
+// ev: optional events around the micro solve (ev[0], ev[1], side stream) and
+// the macro solve (ev[2], ev[3], this stream).
+static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
+    const ElimArgs ea = elim_args(ctx, dt);
+    CU(launch_elim_start(ea, ctx->stream));
     CU(cudaEventRecord(ctx->fork_ev, ctx->stream));
     CU(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0));
-    // the one-block macro solve must not wait behind the preparation's blocks
+    // micro branch
     CU(launch_elim_pre(ea, ctx->side, ctx->prio_lo));
+    CU(cudaEventRecord(ctx->pre_ev, ctx->side));
+    // macro branch: its prologue reads r^T w before the next solve rewrites it
+    tsf_status st = enqueue_macro_prologue(ctx, dt, true);
+    if (st) return st;
+    CU(cudaEventRecord(ctx->mp_ev, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->side, ctx->mp_ev, 0));
+    if (ev) CU(cudaEventRecord(ev[0], ctx->side));
+    MicroArgs ma = micro_args(ctx, ctx->W);
+    ma.u = ctx->uzero;
+    CU(launch_micro_solve(ma, ctx->opt.precision, ctx->tiling, ctx->side));
+    if (ev) CU(cudaEventRecord(ev[1], ctx->side));
     CU(cudaEventRecord(ctx->join_ev, ctx->side));
     cudaGraphConditionalHandle none{};
     MacroArgs mg = macro_args(ctx, dt, false, none);
     mg.gam = ctx->gam_eff;
+    mg.rho = ctx->rho_eff;
     mg.coupling_tol = HUGE_VAL;  // one macro solve ends the step
     mg.coupling_maxit = 1;
-    CU(launch_macro_solve(mg, ctx->stream, ctx->prio_hi, (size_t)ctx->smem_optin));
     if (ev) CU(cudaEventRecord(ev[2], ctx->stream));
-    CU(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
+    // high priority and a whole SM: the one-block solve runs beside the micro solve
+    CU(launch_macro_solve(mg, ctx->stream, ctx->prio_hi, (size_t)ctx->smem_optin));
+    if (ev) CU(cudaEventRecord(ev[3], ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->pre_ev, 0));
     CU(launch_elim_commit(ea, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
     return TSF_OK;
 }
 
 // the step of the elimination mode in use
 static tsf_status enqueue_elim(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
-    return ctx->extrap ? enqueue_pipelined_step(ctx, dt, ev) : enqueue_elimination_step(ctx, dt, ev);
+    return pipelined(ctx) ? enqueue_steady(ctx, dt, ev) : enqueue_elimination_step(ctx, dt, ev);
 }
 
 static double phi_tol(double cg_tol) { return std::max(1e-3 * cg_tol, 1e-13); }
@@ -809,8 +853,24 @@ static tsf_status compute_phi(tsf_ctx* ctx) {
     if (status)
         return fail(ctx, (tsf_status)status, "solving for the elimination vectors S phi = kappa r failed (status %d)",
                     status);
-    CU(launch_mphi(elim_args(ctx, ctx->ops_dt), ctx->stream));
-    CU(reset_history(ctx));  // past z fields and prepared data belong to the old phi
+    // psi = S^-1 (M phi / dt) for the pipelined steps, and M psi / dt
+    const ElimArgs ea = elim_args(ctx, ctx->ops_dt);
+    CU(launch_mass_dt(ea, ctx->phi, ctx->mphi, ctx->mnorm, ctx->stream));
+    CU(launch_psi_setup(ea, ctx->psi, ctx->vtmp, ctx->mnorm, ctx->stream));
+    MicroArgs b = micro_args(ctx, ctx->psi);
+    b.c = ctx->vtmp;
+    b.u = ctx->uzero;
+    b.tol = phi_tol(ctx->opt.cg_tol);
+    b.rho = ctx->gam_psi;
+    CU(launch_micro_solve(b, ctx->opt.precision, ctx->tiling, ctx->stream));
+    CU(launch_mass_dt(ea, ctx->psi, ctx->mpsi, nullptr, ctx->stream));
+    CU(cudaMemcpyAsync(&status, &ctx->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(ctx->ctl, &saved, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
+    if (status)
+        return fail(ctx, (tsf_status)status, "solving for the elimination vectors S psi = M phi / dt failed (status %d)",
+                    status);
+    CU(reset_history(ctx));  // past w fields belong to the old phi and psi
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->phi_valid = true;
     return TSF_OK;
@@ -993,14 +1053,15 @@ static tsf_status run_plain_steps(tsf_ctx* ctx, double dt, int nsteps) {
     if (prof && !ctx->ev[0])
         for (int k = 0; k < 4; ++k) CU(cudaEventCreate(&ctx->ev[k]));
     if (eliminating(ctx)) {
+        const bool pipe = pipelined(ctx);
         for (int s = 0; s < nsteps; ++s) {
             tsf_status st = enqueue_elim(ctx, dt, prof ? ctx->ev : nullptr);
             if (st) return st;
             if (prof) {
                 float a = 0.f, b = 0.f;
-                CU(cudaEventSynchronize(ctx->ev[2]));
+                CU(cudaStreamSynchronize(ctx->stream));
                 CU(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
-                CU(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+                CU(cudaEventElapsedTime(&b, ctx->ev[pipe ? 2 : 1], ctx->ev[pipe ? 3 : 2]));
                 ctx->prof_micro_ms += a;
                 ctx->prof_macro_ms += b;
                 ctx->prof_micro_n += 1;
@@ -1045,6 +1106,10 @@ tsf_status tsf_step(tsf_ctx* ctx, double dt, int nsteps) {
     if (nsteps == 0) return TSF_OK;
     tsf_status st = prepare_step(ctx, dt);
     if (st) return st;
+    if (pipelined(ctx) && !ctx->w_valid) {  // the first w of this state
+        if ((st = enqueue_head(ctx, dt))) return st;
+        ctx->w_valid = true;
+    }
     if (ctx->opt.use_graph) {
         if (!ctx->graph_valid || ctx->graph_dt != dt) {
             st = capture_graph(ctx, dt);
@@ -1432,8 +1497,13 @@ tsf_status tsf_batch_step(tsf_batch* b, double dt, int nsteps) {
     }
     if (nsteps == 0) return TSF_OK;
     for (int i = 0; i < n; ++i) {
-        tsf_status st = prepare_step(b->inst[i], dt);
+        tsf_ctx* c = b->inst[i];
+        tsf_status st = prepare_step(c, dt);
         if (st) return inst_fail(b, i, st);
+        if (pipelined(c) && !c->w_valid) {  // the first w of this state
+            if ((st = enqueue_head(c, dt))) return inst_fail(b, i, st);
+            c->w_valid = true;
+        }
     }
     if (!b->use_graph) {
         for (int s = 0; s < nsteps; ++s) {

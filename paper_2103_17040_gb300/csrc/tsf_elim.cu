@@ -1,242 +1,197 @@
-// tsf_elim.cu -- pipelined steps by exact elimination of the coupling.
+// tsf_elim.cu -- steps by exact elimination of the coupling, pipelined across
+// steps.
 //
 // Given u_i the micro solution is affine in u_i (Eq. (17), micro rows):
-//     v_i = z_i + u_i phi_i,   S_i z_i = c_i,   S_i phi_i = kappa r_i,
-// so one micro solve for z and one macro solve for u close a step.  The next
-// step's right-hand side is
-//     c' = M v'/dt + src = M z/dt + u' (M phi/dt) + src,
-// whose only dependence on the new macro values u' is the scalar multiple of
-// the precomputed M phi/dt.  So right after the micro solve, while the
-// one-block macro solve runs, k_elim_pre computes on the other SMs
-//     cpre = M z/dt,   g = warm start of the next z,   res = cpre - S g,
-// and the next step's k_elim_front only adds u' M phi/dt and the sources
-// (elementwise, plus M fv when a volume source is set).
+//     z_i = S_i^-1 c_i,  c = M v/dt,  v' = z + u' phi,  S phi = kappa r,
+// and the fluxes r^T z close one macro solve for u'.  Writing
+//     c_{k+1} = M v^{k+1}/dt = M z_k/dt + u^{k+1} mphi,      mphi = M phi/dt,
+//     z_{k+1} = w_{k+1} + u^{k+1} psi,   S w_{k+1} = M z_k/dt,   S psi = mphi,
+// the micro solve of step k+1 (for w) needs z_k = w_k + u^k psi only, i.e. the
+// macro values of the step before.  So one graph launch per step runs
+//     k_elim_start: u_old = u^k
+//     macro branch: macro prologue (fluxes r^T w_k + u^k r^T psi), macro
+//                   solve for u^{k+1}, k_elim_commit v^{k+1} = w_k + u^k psi +
+//                   u^{k+1} phi
+//     micro branch: k_elim_pre (right-hand side M z_k/dt, warm start and its
+//                   residual), micro solve for w_{k+1}
+// and the one-block macro solve runs beside the micro solve.  At the end of
+// the launch the state (u^{k+1}, v^{k+1}) is committed and w_{k+1} is ready
+// for the next step.  k_elim_head computes the first w from a state:
+//     S w = M v/dt - u mphi   (= c - u mphi, so z = w + u psi).
 //
-// The residual of the warm start needs S g: the solve leaves its residual
-// e = c - S z behind, so S z = c - e is kept in a second ring and S g is the
-// same extrapolation of those (no second stencil product).
-//
-// Warm start: the next z is extrapolated from the last three solves,
-// g = 3 z_n - 3 z_{n-1} + z_{n-2} (quadratic), 2 z_n - z_{n-1} with two, z_n
-// with one; the z's are kept in a ring of three fields.  The first step after
-// a new state (or new operators) has no prepared data and computes
-// everything from the state: c = M v/dt + src, g = v - u phi, res = c - S g.
-//
-// Ring bookkeeping (device counters, so the same kernels serve every graph
-// launch): k_elim_pre pushes z_n into slot hist_step % 3 and reads the
-// hist_level older slots; k_elim_commit reads z_n from that slot; the next
-// k_elim_front (prepared path) advances hist_step and hist_level.
+// Warm start of w: extrapolated from the last three solves (quadratic
+// 3 w_k - 3 w_{k-1} + w_{k-2}, linear with two, w_k with one), kept in a ring.
+// Its residual needs S g: a solve leaves its residual e = c - S w behind, so
+// S w = c - e is kept in a second ring and S g is the same combination (no
+// second stencil product).  Without volume or Robin sources only (those are
+// stepped by the unpipelined elimination).
 #include "tsf_internal.cuh"
 
 namespace tsf {
 
-// M fv + R g at node j = (p, q) of instance i (0 without sources)
-__device__ __forceinline__ double elim_source(const ElimArgs& a, int i, int j, int p, int q, const double* M,
-                                              size_t pl) {
-    double y = 0.0;
-    if (a.fv) y = plane_apply(M, pl, a.fv + (size_t)i * pl, j, p, q, a.n1);
-    if (a.g && p == a.n1 - 1) {
-        const int n1 = a.n1;
-        const double* g = a.g + (size_t)i * n1;
-        const double* Rd = a.Rd + (size_t)i * n1;
-        const double* Ru = a.Ru + (size_t)i * n1;
-        y = fma(Rd[q], g[q], y);
-        if (q + 1 < n1) y = fma(Ru[q], g[q + 1], y);
-        if (q > 0) y = fma(Ru[q - 1], g[q - 1], y);
-    }
-    return y;
-}
-
-// One block per micro problem: the right-hand side, the residual of the warm
-// start in Z, and the norms that scale the tolerance.
-__global__ void __launch_bounds__(256) k_elim_front(ElimArgs a) {
+// One block per micro problem: right-hand side c = M v/dt - u mphi of the
+// first w, warm start W = v - u (phi + psi), residual and norms.
+__global__ void __launch_bounds__(256) k_elim_head(ElimArgs a) {
     __shared__ double buf[3 * 32];
     const int i = blockIdx.x, n1 = a.n1, nm = a.nm;
     const size_t pl = (size_t)a.nmp;
     const double* M = a.M64 + (size_t)i * kPlanes * pl;
     const double* S = a.S64 + (size_t)i * kPlanes * pl;
+    const double* v = a.v + (size_t)i * pl;
+    const double* ph = a.phi + (size_t)i * pl;
+    const double* ps = a.psi + (size_t)i * pl;
+    const double* mp = a.mphi + (size_t)i * pl;
     const double* re = a.redge + (size_t)i * n1;
     double* c = a.c + (size_t)i * pl;
+    double* W = a.W + (size_t)i * pl;
     double* res = a.res + (size_t)i * pl;
-    double* Z = a.Z + (size_t)i * pl;
     const double ui = a.u[i], idt = 1.0 / a.dt;
-    const bool prep = a.ctl->prep_ok != 0;
-    const bool sources = a.fv || a.g;
     double cc = 0.0, cr = 0.0, rr = 0.0;
-    if (prep && !sources) {
-        // c = cpre + u mphi; its norms follow from the prepared ones (the FP64
-        // pipe is the bound of this kernel: two DFMA per node)
-        const double* cp = a.cpre + (size_t)i * pl;
-        const double* mp = a.mphi + (size_t)i * pl;
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const double add = ui * mp[j];
-            c[j] = cp[j] + add;
-            res[j] += add;  // res = cpre - S g + (c - cpre)
+    for (int j = threadIdx.x; j < nm; j += blockDim.x) {
+        const int p = j % n1, q = j / n1;
+        const double cj = fma(plane_apply(M, pl, v, j, p, q, n1), idt, -ui * mp[j]);
+        c[j] = cj;
+        W[j] = fma(-ui, ph[j] + ps[j], v[j]);
+        cc = fma(cj, cj, cc);
+        if (p == n1 - 1) {
+            cr = fma(cj, re[q], cr);
+            rr = fma(re[q], re[q], rr);
         }
-        if (threadIdx.x == 0) {
-            const double* pn = a.pnorm + (size_t)i * 3;
-            const double* mn = a.mnorm + (size_t)i * 3;
-            double* bn = a.bnorm + (size_t)i * 3;
-            bn[0] = fma(ui, fma(ui, mn[0], 2.0 * pn[1]), pn[0]);
-            bn[1] = fma(ui, mn[1], pn[2]);
-            bn[2] = mn[2];
-            a.u_used[i] = 0.0;
-            if (i == 0) {  // the z pushed by the last k_elim_pre becomes history
-                a.ctl->hist_step += 1;
-                if (a.ctl->hist_level < 2) a.ctl->hist_level += 1;
-            }
-        }
-        return;
-    }
-    if (prep) {
-        const double* cp = a.cpre + (size_t)i * pl;
-        const double* mp = a.mphi + (size_t)i * pl;
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const int p = j % n1, q = j / n1;
-            const double add = fma(ui, mp[j], elim_source(a, i, j, p, q, M, pl));
-            const double cj = cp[j] + add;
-            c[j] = cj;
-            res[j] += add;  // res = cpre - S g + (c - cpre)
-            const double rj = p == n1 - 1 ? re[q] : 0.0;
-            cc = fma(cj, cj, cc);
-            cr = fma(cj, rj, cr);
-            rr = fma(rj, rj, rr);
-        }
-    } else {
-        const double* v = a.v + (size_t)i * pl;
-        const double* ph = a.phi + (size_t)i * pl;
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const int p = j % n1, q = j / n1;
-            const double cj = fma(plane_apply(M, pl, v, j, p, q, n1), idt, elim_source(a, i, j, p, q, M, pl));
-            c[j] = cj;
-            Z[j] = fma(-ui, ph[j], v[j]);
-            const double rj = p == n1 - 1 ? re[q] : 0.0;
-            cc = fma(cj, cj, cc);
-            cr = fma(cj, rj, cr);
-            rr = fma(rj, rj, rr);
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) res[j] = c[j] - plane_apply(S, pl, Z, j, j % n1, j / n1, n1);
     }
     double t[3] = {cc, cr, rr};
-    block_allreduce<double, 3>(t, buf);
+    block_allreduce<double, 3>(t, buf);  // (also: every thread has written W)
+    __syncthreads();
+    for (int j = threadIdx.x; j < nm; j += blockDim.x) res[j] = c[j] - plane_apply(S, pl, W, j, j % n1, j / n1, n1);
     if (threadIdx.x == 0) {
         double* bn = a.bnorm + (size_t)i * 3;
         bn[0] = t[0];
         bn[1] = t[1];
         bn[2] = t[2];
         a.u_used[i] = 0.0;
-        if (prep && i == 0) {  // the z pushed by the last k_elim_pre becomes history
-            a.ctl->hist_step += 1;
-            if (a.ctl->hist_level < 2) a.ctl->hist_level += 1;
-        }
     }
 }
 
-// One block per micro problem, right after the micro solve (Z = z_n):
-// cpre = M z/dt, push z into the ring, Z = extrapolated warm start,
-// res = cpre - S Z.
+// u_old = u (the macro state the prepared w belongs to), and the w pushed by
+// the previous step's k_elim_pre becomes history.
+__global__ void __launch_bounds__(256) k_elim_start(ElimArgs a) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < a.nM) a.u_old[k] = a.u[k];
+    if (k == 0 && a.ctl->pushed) {
+        a.ctl->pushed = 0;
+        a.ctl->hist_step += 1;
+        if (a.ctl->hist_level < 2) a.ctl->hist_level += 1;
+    }
+}
+
+// One block per micro problem, after the solve of w_k (in W, with c_k and
+// its residual e_k): c_{k+1} = M (w_k + u^k psi)/dt = M w_k/dt + u^k mpsi,
+// push w_k and S w_k = c_k - e_k, W = extrapolated warm start g,
+// res = c_{k+1} - S g, norms of c_{k+1}.
 __global__ void __launch_bounds__(256) k_elim_pre(ElimArgs a) {
     __shared__ double buf[3 * 32];
     const int i = blockIdx.x, n1 = a.n1, nm = a.nm;
     const size_t pl = (size_t)a.nmp, slot = (size_t)a.nM * pl;
     const double* M = a.M64 + (size_t)i * kPlanes * pl;
     const double* S = a.S64 + (size_t)i * kPlanes * pl;
-    double* Z = a.Z + (size_t)i * pl;
-    double* cp = a.cpre + (size_t)i * pl;
+    const double* mq = a.mpsi + (size_t)i * pl;
+    const double* re = a.redge + (size_t)i * n1;
+    double* W = a.W + (size_t)i * pl;
+    double* c = a.c + (size_t)i * pl;
+    double* cn = a.cnext + (size_t)i * pl;
     double* res = a.res + (size_t)i * pl;
     const int st = a.ctl->hist_step, level = a.ctl->hist_level;
     double* hc = a.hist + (size_t)(st % 3) * slot + (size_t)i * pl;
     const double* h1 = a.hist + (size_t)((st + 2) % 3) * slot + (size_t)i * pl;
     const double* h2 = a.hist + (size_t)((st + 1) % 3) * slot + (size_t)i * pl;
-    const double idt = 1.0 / a.dt;
-    const double* mp = a.mphi + (size_t)i * pl;
-    const double* re = a.redge + (size_t)i * n1;
-    double n0 = 0.0, n1m = 0.0, n2 = 0.0;
+    const double uo = a.u_old[i], idt = 1.0 / a.dt;
+    double cc = 0.0, cr = 0.0, rr = 0.0;
     for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-        const double y = plane_apply(M, pl, Z, j, j % n1, j / n1, n1) * idt;
-        cp[j] = y;
-        n0 = fma(y, y, n0);
-        n1m = fma(y, mp[j], n1m);
-        if (j % n1 == n1 - 1) n2 = fma(y, re[j / n1], n2);
-    }
-    {   // norms of cpre for the next front (also orders every read of z_n at
-        // neighbours before Z is overwritten: the reduction synchronises)
-        double t[3] = {n0, n1m, n2};
-        block_allreduce<double, 3>(t, buf);
-        if (threadIdx.x == 0) {
-            double* pn = a.pnorm + (size_t)i * 3;
-            pn[0] = t[0];
-            pn[1] = t[1];
-            pn[2] = t[2];
+        const int p = j % n1, q = j / n1;
+        const double y = fma(plane_apply(M, pl, W, j, p, q, n1), idt, uo * mq[j]);
+        cn[j] = y;
+        cc = fma(y, y, cc);
+        if (p == n1 - 1) {
+            cr = fma(y, re[q], cr);
+            rr = fma(re[q], re[q], rr);
         }
     }
+    double t[3] = {cc, cr, rr};
+    block_allreduce<double, 3>(t, buf);  // every read of w_k at neighbours is done
     __syncthreads();
     if (a.yhist) {
-        // S z_k = c_k - e_k with e_k the residual the solve left behind, so
-        // S g is the same combination of the stored S z as g of the z: no
-        // second stencil product
-        const double* c = a.c + (size_t)i * pl;
         double* yc = a.yhist + (size_t)(st % 3) * slot + (size_t)i * pl;
         const double* y1 = a.yhist + (size_t)((st + 2) % 3) * slot + (size_t)i * pl;
         const double* y2 = a.yhist + (size_t)((st + 1) % 3) * slot + (size_t)i * pl;
         for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const double z = Z[j], y = c[j] - res[j];
-            double g = z, sg = y;
+            const double w = W[j], y = c[j] - res[j];
+            double g = w, sg = y;
             if (level >= 2) {
-                g = fma(3.0, z - h1[j], h2[j]);
+                g = fma(3.0, w - h1[j], h2[j]);
                 sg = fma(3.0, y - y1[j], y2[j]);
             } else if (level == 1) {
-                g = fma(2.0, z, -h1[j]);
+                g = fma(2.0, w, -h1[j]);
                 sg = fma(2.0, y, -y1[j]);
             }
-            hc[j] = z;
+            hc[j] = w;
             yc[j] = y;
-            Z[j] = g;
-            res[j] = cp[j] - sg;
+            W[j] = g;
+            const double cj = cn[j];
+            res[j] = cj - sg;
+            c[j] = cj;
         }
     } else {
         for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const double z = Z[j];
-            double g = z;
+            const double w = W[j];
+            double g = w;
             if (level >= 2)
-                g = fma(3.0, z - h1[j], h2[j]);
+                g = fma(3.0, w - h1[j], h2[j]);
             else if (level == 1)
-                g = fma(2.0, z, -h1[j]);
-            hc[j] = z;
-            Z[j] = g;
+                g = fma(2.0, w, -h1[j]);
+            hc[j] = w;
+            W[j] = g;
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < nm; j += blockDim.x)
-            res[j] = cp[j] - plane_apply(S, pl, Z, j, j % n1, j / n1, n1);
+        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
+            const double cj = cn[j];
+            res[j] = cj - plane_apply(S, pl, W, j, j % n1, j / n1, n1);
+            c[j] = cj;
+        }
     }
-    if (i == 0 && threadIdx.x == 0) a.ctl->prep_ok = 1;
+    if (threadIdx.x == 0) {
+        double* bn = a.bnorm + (size_t)i * 3;
+        bn[0] = t[0];
+        bn[1] = t[1];
+        bn[2] = t[2];
+        a.u_used[i] = 0.0;
+        if (i == 0) a.ctl->pushed = 1;
+    }
 }
 
-// v = z_n + u phi with z_n from the ring slot the last k_elim_pre wrote.
+// v^{k+1} = w_k + u^k psi + u^{k+1} phi, w_k from the ring slot k_elim_pre
+// wrote.
 __global__ void __launch_bounds__(256) k_elim_commit(ElimArgs a) {
     const int i = blockIdx.x;
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     if (j >= a.nm) return;
     const size_t pl = (size_t)a.nmp, o = (size_t)i * pl + j;
-    const double* z = a.hist + (size_t)(a.ctl->hist_step % 3) * a.nM * pl;
-    a.v[o] = fma(a.u[i], a.phi[o], z[o]);
+    const double* w = a.hist + (size_t)(a.ctl->hist_step % 3) * a.nM * pl;
+    a.v[o] = fma(a.u[i], a.phi[o], fma(a.u_old[i], a.psi[o], w[o]));
 }
 
-// mphi = M phi / dt (once per geometry and dt)
-__global__ void __launch_bounds__(256) k_mphi(ElimArgs a) {
+// out = M x / dt, and ||out||^2, out^T r, ||r||^2 per instance
+__global__ void __launch_bounds__(256) k_mass_dt(ElimArgs a, const double* x, double* out, double* nrm) {
     __shared__ double buf[3 * 32];
     const int i = blockIdx.x, n1 = a.n1;
     const size_t pl = (size_t)a.nmp;
     const double* M = a.M64 + (size_t)i * kPlanes * pl;
-    const double* ph = a.phi + (size_t)i * pl;
+    const double* xi = x + (size_t)i * pl;
     const double* re = a.redge + (size_t)i * n1;
-    double* mp = a.mphi + (size_t)i * pl;
+    double* oi = out + (size_t)i * pl;
     const double idt = 1.0 / a.dt;
     double n0 = 0.0, n1m = 0.0, n2 = 0.0;
     for (int j = threadIdx.x; j < a.nm; j += blockDim.x) {
-        const double y = plane_apply(M, pl, ph, j, j % n1, j / n1, n1) * idt;
-        mp[j] = y;
+        const double y = plane_apply(M, pl, xi, j, j % n1, j / n1, n1) * idt;
+        oi[j] = y;
         n0 = fma(y, y, n0);
         if (j % n1 == n1 - 1) {
             n1m = fma(y, re[j / n1], n1m);
@@ -245,16 +200,35 @@ __global__ void __launch_bounds__(256) k_mphi(ElimArgs a) {
     }
     double t[3] = {n0, n1m, n2};
     block_allreduce<double, 3>(t, buf);
-    if (threadIdx.x == 0) {
-        double* mn = a.mnorm + (size_t)i * 3;
-        mn[0] = t[0];
-        mn[1] = t[1];
-        mn[2] = t[2];
+    if (threadIdx.x == 0 && nrm) {
+        nrm[(size_t)i * 3] = t[0];
+        nrm[(size_t)i * 3 + 1] = t[1];
+        nrm[(size_t)i * 3 + 2] = t[2];
     }
 }
 
-cudaError_t launch_elim_front(const ElimArgs& a, cudaStream_t s) {
-    k_elim_front<<<a.nM, 256, 0, s>>>(a);
+// psi = 0, cz = mphi (right-hand side for the variants that read c),
+// res = mphi, u_used = 0, bnorm = the norms of mphi
+__global__ void __launch_bounds__(256) k_psi_setup(ElimArgs a, double* psi, double* cz, const double* mnorm) {
+    const int i = blockIdx.x;
+    const size_t pl = (size_t)a.nmp;
+    for (int j = threadIdx.x; j < a.nmp; j += blockDim.x) {
+        const size_t o = (size_t)i * pl + j;
+        const double m = j < a.nm ? a.mphi[o] : 0.0;
+        psi[o] = 0.0;
+        cz[o] = m;
+        a.res[o] = m;
+    }
+    if (threadIdx.x < 3) a.bnorm[(size_t)i * 3 + threadIdx.x] = mnorm[(size_t)i * 3 + threadIdx.x];
+    if (threadIdx.x == 0) a.u_used[i] = 0.0;
+}
+
+cudaError_t launch_elim_head(const ElimArgs& a, cudaStream_t s) {
+    k_elim_head<<<a.nM, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_elim_start(const ElimArgs& a, cudaStream_t s) {
+    k_elim_start<<<(a.nM + 255) / 256, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_elim_pre(const ElimArgs& a, cudaStream_t s, int priority) {
@@ -278,8 +252,12 @@ cudaError_t launch_elim_commit(const ElimArgs& a, cudaStream_t s) {
     k_elim_commit<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_mphi(const ElimArgs& a, cudaStream_t s) {
-    k_mphi<<<a.nM, 256, 0, s>>>(a);
+cudaError_t launch_mass_dt(const ElimArgs& a, const double* x, double* out, double* nrm, cudaStream_t s) {
+    k_mass_dt<<<a.nM, 256, 0, s>>>(a, x, out, nrm);
+    return cudaGetLastError();
+}
+cudaError_t launch_psi_setup(const ElimArgs& a, double* psi, double* cz, const double* mnorm, cudaStream_t s) {
+    k_psi_setup<<<a.nM, 256, 0, s>>>(a, psi, cz, mnorm);
     return cudaGetLastError();
 }
 

@@ -37,8 +37,8 @@ struct DevCtl {
     double gamma_bar;                 // preconditioner value of |Gamma| (macro)
     // exact elimination: history of past v0 fields for the warm start
     int hist_level;                   // number of valid past fields (0..2); reset with the state
-    int hist_step;                    // ring position: the current solve's v0 goes to slot hist_step % 3
-    int prep_ok;                      // 1: the next step's right-hand side was prepared (k_elim_pre)
+    int hist_step;                    // ring position: the latest solve's w goes to slot hist_step % 3
+    int pushed;                       // 1: k_elim_pre pushed a w the next k_elim_start must count
 };
 
 __device__ __forceinline__ void set_status(DevCtl* ctl, int code) {
@@ -245,6 +245,10 @@ struct MacroPrologueArgs {
     double* G;              // out: r_i^T g_i (compensated; 0 without g)
     double* cH;             // out
     double* uk;             // out: initial iterate (Dirichlet values applied)
+    // pipelined elimination: rho_eff = rho_w + u gam_psi (fluxes of z = w + u psi)
+    const double* rho_w;    // [nM] r^T w, or nullptr
+    const double* gam_psi;  // [nM] r^T psi
+    double* rho_eff;        // [nM] out
     DevCtl* ctl;
 };
 
@@ -283,42 +287,41 @@ cudaError_t launch_flux(int n1, int nm, int nmp, int nM, double kappa, const dou
 cudaError_t configure_micro_kernels(int smem_optin);
 cudaError_t configure_macro_kernels(int smem_optin);
 
-// Pipelined exact elimination (tsf_elim.cu).  A step is
-//   front -> micro solve of z (S z = c, in Z) -> { macro solve ; pre } -> commit
-// where "pre" prepares the next step while the one-block macro solve runs:
-// cpre = M z / dt, the warm start g extrapolated from the last three z, and
-// res = cpre - S g.  Only u enters afterwards: c = cpre + u M phi / dt + src.
+// Pipelined exact elimination (tsf_elim.cu): the micro unknown of a step is
+// split as z = w + u psi with psi = S^-1 (M phi / dt), so the micro solve for
+// w of step k+1 needs only u^k and runs beside the macro solve of step k.
 struct ElimArgs {
     int n1, nm, nmp, nM;
-    double dt, kappa;
+    double dt;
     const double* M64;
     const double* S64;
-    const double* fv;       // [nM][nmp] or nullptr
-    const double* g;        // [nM][n1] or nullptr (Robin data)
     const double* redge;
-    const double* Rd;
-    const double* Ru;
     const double* phi;      // [nM][nmp] S^-1 kappa r
-    double* mphi;           // [nM][nmp] M phi / dt
+    const double* psi;      // [nM][nmp] S^-1 mphi
+    const double* mphi;     // [nM][nmp] M phi / dt
+    const double* mpsi;     // [nM][nmp] M psi / dt
     const double* u;        // [nM] committed macro state
+    double* u_old;          // [nM] the macro state the prepared w belongs to
     double* v;              // [nM][nmp] committed micro state
-    double* Z;              // [nM][nmp] unknown of the micro solve (warm start on entry)
-    double* c;              // [nM][nmp] right-hand side
-    double* cpre;           // [nM][nmp] M z / dt of the last solve
-    double* res;            // [nM][nmp] stored residual of Z
+    double* W;              // [nM][nmp] unknown of the micro solve (warm start on entry)
+    double* c;              // [nM][nmp] right-hand side of the w solve
+    double* cnext;          // [nM][nmp] scratch: the next right-hand side
+    double* res;            // [nM][nmp] stored residual of W
     double* u_used;         // [nM]
     double* bnorm;          // [nM][3]
-    double* hist;           // [3][nM][nmp] ring of the last solves' z
-    double* yhist;          // [3][nM][nmp] ring of S z = c - (final residual), or nullptr when the
+    double* hist;           // [3][nM][nmp] ring of the last solves' w
+    double* yhist;          // [3][nM][nmp] ring of S w = c - (final residual), or nullptr when the
                             // micro-solve variant does not keep its residual (S g then computed)
-    double* pnorm;          // [nM][3] ||cpre||^2, cpre^T mphi, cpre^T r (written by k_elim_pre)
-    double* mnorm;          // [nM][3] ||mphi||^2, mphi^T r, ||r||^2 (written by k_mphi)
     DevCtl* ctl;
 };
-cudaError_t launch_elim_front(const ElimArgs& a, cudaStream_t s);
+cudaError_t launch_elim_head(const ElimArgs& a, cudaStream_t s);
+cudaError_t launch_elim_start(const ElimArgs& a, cudaStream_t s);
 cudaError_t launch_elim_pre(const ElimArgs& a, cudaStream_t s, int priority = 0);
 cudaError_t launch_elim_commit(const ElimArgs& a, cudaStream_t s);
-cudaError_t launch_mphi(const ElimArgs& a, cudaStream_t s);
+// out = M x / dt with x an [nM][nmp] field (norms of out: ||out||^2, out^T r, ||r||^2 into nrm)
+cudaError_t launch_mass_dt(const ElimArgs& a, const double* x, double* out, double* nrm, cudaStream_t s);
+// set-up of the solve S psi = mphi with the stored-residual protocol
+cudaError_t launch_psi_setup(const ElimArgs& a, double* psi, double* cz, const double* mnorm, cudaStream_t s);
 
 // discrete adjoint (tsf_adjoint.cu)
 struct AdjAccArgs {

@@ -430,6 +430,7 @@ __global__ void k_macro_prologue(MacroPrologueArgs a) {
     double uk = a.u[k];
     if (is_dir_node(a.bc, N, p, q) && a.ud) uk = a.ud[k];
     a.uk[k] = uk;
+    if (a.rho_eff) a.rho_eff[k] = fma(a.u[k], a.gam_psi[k], a.rho_w[k]);  // r^T (w + u psi)
 }
 
 cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s) {
