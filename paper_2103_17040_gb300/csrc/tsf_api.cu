@@ -747,8 +747,22 @@ static ElimArgs elim_args(tsf_ctx* ctx, double dt) {
     a.bnorm = ctx->bnorm;
     a.hist = ctx->hist;
     a.yhist = tiling_uses_stored_residual(ctx->tiling) ? ctx->yhist : nullptr;
+    a.mw_ready = tiling_uses_stored_residual(ctx->tiling) ? 1 : 0;
     a.ctl = ctx->ctl;
     return a;
+}
+
+// The micro solve of w: u = 0 in the right-hand side; the strip kernels also
+// leave M w / dt in cnext for k_elim_pre.
+static MicroArgs w_solve_args(tsf_ctx* ctx, double dt) {
+    MicroArgs ma = micro_args(ctx, ctx->W);
+    ma.u = ctx->uzero;
+    if (tiling_uses_stored_residual(ctx->tiling)) {
+        ma.M64 = ctx->M64;
+        ma.mw = ctx->cnext;
+        ma.idt = 1.0 / dt;
+    }
+    return ma;
 }
 
 // Steps by pipelined elimination (tsf_elim.cu): eliminating, with warm-start
@@ -762,9 +776,7 @@ static bool pipelined(const tsf_ctx* ctx) {
 static tsf_status enqueue_head(tsf_ctx* ctx, double dt) {
     const ElimArgs ea = elim_args(ctx, dt);
     CU(launch_elim_head(ea, ctx->stream));
-    MicroArgs ma = micro_args(ctx, ctx->W);
-    ma.u = ctx->uzero;
-    CU(launch_micro_solve(ma, ctx->opt.precision, ctx->tiling, ctx->stream));
+    CU(launch_micro_solve(w_solve_args(ctx, dt), ctx->opt.precision, ctx->tiling, ctx->stream));
     return TSF_OK;
 }
 
@@ -789,9 +801,7 @@ static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
     CU(cudaEventRecord(ctx->mp_ev, ctx->stream));
     CU(cudaStreamWaitEvent(ctx->side, ctx->mp_ev, 0));
     if (ev) CU(cudaEventRecord(ev[0], ctx->side));
-    MicroArgs ma = micro_args(ctx, ctx->W);
-    ma.u = ctx->uzero;
-    CU(launch_micro_solve(ma, ctx->opt.precision, ctx->tiling, ctx->side));
+    CU(launch_micro_solve(w_solve_args(ctx, dt), ctx->opt.precision, ctx->tiling, ctx->side));
     if (ev) CU(cudaEventRecord(ev[1], ctx->side));
     CU(cudaEventRecord(ctx->join_ev, ctx->side));
     cudaGraphConditionalHandle none{};

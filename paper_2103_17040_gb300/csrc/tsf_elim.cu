@@ -21,6 +21,9 @@
 //
 // Warm start of w: extrapolated from the last three solves (quadratic
 // 3 w_k - 3 w_{k-1} + w_{k-2}, linear with two, w_k with one), kept in a ring.
+// The column-strip micro kernels compute M w / dt of their solution in an
+// epilogue (FP64 work that overlaps the other blocks' FP32 iterations), so
+// k_elim_pre is then elementwise apart from its norms.
 // Its residual needs S g: a solve leaves its residual e = c - S w behind, so
 // S w = c - e is kept in a second ring and S g is the same combination (no
 // second stencil product).  Without volume or Robin sources only (those are
@@ -107,7 +110,9 @@ __global__ void __launch_bounds__(256) k_elim_pre(ElimArgs a) {
     double cc = 0.0, cr = 0.0, rr = 0.0;
     for (int j = threadIdx.x; j < nm; j += blockDim.x) {
         const int p = j % n1, q = j / n1;
-        const double y = fma(plane_apply(M, pl, W, j, p, q, n1), idt, uo * mq[j]);
+        // M w_k / dt from the micro solve's epilogue, or computed here
+        const double mwj = a.mw_ready ? cn[j] : plane_apply(M, pl, W, j, p, q, n1) * idt;
+        const double y = fma(uo, mq[j], mwj);
         cn[j] = y;
         cc = fma(y, y, cc);
         if (p == n1 - 1) {

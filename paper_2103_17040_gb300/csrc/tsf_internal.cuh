@@ -177,6 +177,10 @@ struct MicroArgs {
     double* res;            // [nM][nmp] FP64 residual b(u_used) - S v of the current iterate
     double* u_used;         // [nM] macro value the stored residual belongs to
     const double* bnorm;    // [nM][3] ||c||^2, c^T r, ||r||^2 (so ||b(u)||^2 is a quadratic in u)
+    // column-strip kernels, optional epilogue: mw = M v / dt of the solution (FP64)
+    const double* M64;
+    double* mw;             // [nM][nmp] or nullptr
+    double idt;
 };
 
 struct PrologueArgs {
@@ -312,6 +316,7 @@ struct ElimArgs {
     double* hist;           // [3][nM][nmp] ring of the last solves' w
     double* yhist;          // [3][nM][nmp] ring of S w = c - (final residual), or nullptr when the
                             // micro-solve variant does not keep its residual (S g then computed)
+    int mw_ready;           // 1: the micro solve left M w / dt in cnext (strip kernels' epilogue)
     DevCtl* ctl;
 };
 cudaError_t launch_elim_head(const ElimArgs& a, cudaStream_t s);

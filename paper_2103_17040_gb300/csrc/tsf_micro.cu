@@ -812,6 +812,19 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
     for (int k = 0; k < R; ++k)
         if (valid[k] && (solved || (edge && kdu != 0.0))) res[p + n1 * (q0 + k)] = r64[k];
     __syncthreads();
+    // optional epilogue: M v / dt of the solution in FP64 (the next step's
+    // right-hand side of the pipelined elimination; the FP64 work overlaps
+    // the FP32 iterations of the other blocks on the SM)
+    if (a.mw) {
+        const double* Mi = a.M64 + (size_t)i * kPlanes * pl;
+        double* mw = a.mw + (size_t)i * pl;
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (valid[k]) {
+                const int q = q0 + k, j = p + n1 * q;
+                mw[j] = plane_apply(Mi, pl, v, j, p, q, n1) * a.idt;
+            }
+    }
     // flux integral rho_i = r_i^T v_i over the Robin-edge nodes, one warp,
     // compensated (TwoSum) FP64
     if (tid < 32) {
