@@ -49,9 +49,7 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # change the DRAM traffic): partitioned, averaged over the four coupling
 # iterations of a step (micro_strip_c2_64x64_32x32.md);  Keyed by (workload,
 # precision, strip kernel, coupling); entries are removed when the kernel changes.
-MICRO_TRAFFIC = {("c2", "mixed", True, "partitioned"): 322.3e6,
-                 # elimination: one full solve per launch (step_elimination_c2_64x64_32x32.md)
-                 ("c2", "mixed", True, "elimination"): 410.9e6}
+MICRO_TRAFFIC = {("c2", "mixed", True, "partitioned"): 322.3e6}
 
 
 def parse():
@@ -350,33 +348,50 @@ def run_gb300(args):
 
 
 def run_e2e(torch, T, w, args, stream):
-    """Each step: pinned host -> device state upload, one step, macro field and
-    micro averages back to pinned host memory."""
+    """End to end through the public API: every step uploads that step's
+    input -- the macro source term (zero for this workload) -- from pinned
+    host memory, takes one step and reads the macro field and the micro
+    averages back into pinned host memory.  Beside it, the same with the
+    whole state (u, v) uploaded every step, which restarts the solver's
+    history each step."""
     P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling])
     P.step(w.dt, 2)
     P.synchronize()
+    fu_h = torch.zeros(w.nM, dtype=torch.float64).pin_memory()
+    u_out = torch.empty(w.nM, dtype=torch.float64).pin_memory()
+    vbar_out = torch.empty(w.nM, dtype=torch.float64).pin_memory()
+    fu_np, uo_np, vo_np = fu_h.numpy(), u_out.numpy(), vbar_out.numpy()
+    k = max(3, min(args.steps, 20))
+
+    def run(upload):
+        P.reset_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            upload()
+            P.step(w.dt, 1)
+            P.u(uo_np)
+            P.vbar(vo_np)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, P.stats()
+
+    P.set_sources(fu=fu_np)
+    P.step(w.dt, 1)
+    el, st = run(lambda: P.set_sources(fu=fu_np))
+    out = {"value": st["dof_cg_iters"] / el, "unit": "DOF-iter/s", "steps": k, "ms_per_step": 1e3 * el / k,
+           "steps_per_s": k / el, "h2d_bytes_per_step": 8 * w.nM, "d2h_bytes_per_step": 8 * 2 * w.nM,
+           "inputs": "macro source term per step (pinned host -> device), macro field and averages back"}
+    P.set_sources()
     u_h = torch.empty(w.nM, dtype=torch.float64).pin_memory()
     v_h = torch.empty(w.nM * w.nm, dtype=torch.float64).pin_memory()
-    vbar_h = np.empty(w.nM)
-    u_out = np.empty(w.nM)
     u_h.copy_(torch.from_numpy(P.u()))
     v_h.copy_(torch.from_numpy(P.v().ravel()))
     u_np, v_np = u_h.numpy(), v_h.numpy()
-    P.reset_stats()
-    k = max(3, min(args.steps, 20))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(k):
-        P.set_state(u_np, v_np)
-        P.step(w.dt, 1)
-        P.u(u_out)
-        P.vbar(vbar_h)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    st = P.stats()
+    el2, st2 = run(lambda: P.set_state(u_np, v_np))
+    out["state_roundtrip"] = {"value": st2["dof_cg_iters"] / el2, "ms_per_step": 1e3 * el2 / k,
+                              "h2d_bytes_per_step": 8 * (w.nM + w.nM * w.nm), "d2h_bytes_per_step": 8 * 2 * w.nM}
     P.close()
-    return {"value": st["dof_cg_iters"] / dt, "unit": "DOF-iter/s", "steps": k, "ms_per_step": 1e3 * dt / k,
-            "h2d_bytes_per_step": 8 * (w.nM + w.nM * w.nm), "d2h_bytes_per_step": 8 * 2 * w.nM}
+    return out
 
 
 def run_cpu_baseline(T, w, args, stream):
@@ -620,16 +635,27 @@ def run_c4(args):
     else:
         ms_max, dof_iters = ms, float(st["dof_cg_iters"])
 
-    # the same problems one after another, each its own graph per step
-    seq_ms = 0.0
-    ks = max(1, min(K, 5))
+    # the same problems one after another, each its own graph per step: a
+    # second, identical batch advanced through the same steps one problem at
+    # a time (the solves get cheaper as the march settles, so both are timed
+    # over the same step range)
+    B2 = build()
+    for _ in range(Wm):
+        for k in range(len(ws)):
+            B2[k].step(dt, 1)
+    torch.cuda.synchronize()
     for k in range(len(ws)):
-        P = B[k]
-        e0.record(stream)
-        P.step(dt, ks)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        seq_ms += e0.elapsed_time(e1)
+        B2[k].reset_stats()
+    e0.record(stream)
+    for _ in range(K):
+        for k in range(len(ws)):
+            B2[k].step(dt, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    seq_iters = sum(B2[k].stats()["dof_cg_iters"] for k in range(len(ws)))
+    B2.close()
+    ks = K
 
     # per-kernel timing of the micro solves (plain launches, one problem at a time)
     bytes_total, micro_ms, launches = 0.0, 0.0, 0
@@ -663,6 +689,7 @@ def run_c4(args):
                    "l2": "working set > L2, no flush"},
         "batch_steps_per_s": world * K / (ms_max / 1e3),
         "sequential_ms_per_step": seq_ms / ks, "batch_speedup_vs_sequential": (seq_ms / ks) / (ms / K),
+        "sequential_dof_cg_iters_per_step": seq_iters / ks, "batch_dof_cg_iters_per_step": st["dof_cg_iters"] / K,
         "coupling_iters_per_problem_step": st["coupling_iters_total"] / (K * len(ws)),
         "tilings": tilings, "coupling": args.coupling,
         "gpu_launches": (5 * K * len(ws) if args.coupling == "elimination"

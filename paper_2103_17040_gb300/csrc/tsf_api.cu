@@ -811,8 +811,8 @@ static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
     mg.coupling_tol = HUGE_VAL;  // one macro solve ends the step
     mg.coupling_maxit = 1;
     if (ev) CU(cudaEventRecord(ev[2], ctx->stream));
-    // high priority and a whole SM: the one-block solve runs beside the micro solve
-    CU(launch_macro_solve(mg, ctx->stream, ctx->prio_hi, (size_t)ctx->smem_optin));
+    // high priority: the one-block solve is scheduled beside the micro solve
+    CU(launch_macro_solve(mg, ctx->stream, ctx->prio_hi));
     if (ev) CU(cudaEventRecord(ev[3], ctx->stream));
     CU(cudaStreamWaitEvent(ctx->stream, ctx->pre_ev, 0));
     CU(launch_elim_commit(ea, ctx->stream));
@@ -961,7 +961,7 @@ static tsf_status capture_failed(tsf_ctx* ctx, tsf_status st, cudaError_t e, con
 static cudaError_t capture_step_into(tsf_ctx* ctx, cudaGraph_t G, double dt, tsf_status* st, const char** what) {
     *st = TSF_OK;
     cudaError_t e;
-    if (eliminating(ctx)) {  // a straight sequence of kernels, no coupling loop
+    if (eliminating(ctx)) {  // the eliminated step: no coupling loop
         *what = "begin capture";
         e = cudaStreamBeginCaptureToGraph(ctx->stream, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
