@@ -49,7 +49,10 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # change the DRAM traffic): partitioned, averaged over the four coupling
 # iterations of a step (micro_strip_c2_64x64_32x32.md);  Keyed by (workload,
 # precision, strip kernel, coupling); entries are removed when the kernel changes.
-MICRO_TRAFFIC = {("c2", "mixed", True, "partitioned"): 322.3e6}
+MICRO_TRAFFIC = {("c2", "mixed", True, "partitioned"): 322.3e6,
+                 # pipelined elimination: one solve of the next w per launch, with the
+                 # M w / dt epilogue (step_pipelined_c2_64x64_32x32.md, k_micro_strip<3>)
+                 ("c2", "mixed", True, "elimination"): 632.3e6}
 
 
 def parse():
