@@ -338,3 +338,56 @@ def test_elimination_history_is_reset_by_set_state():
     A.step(0.01, 4)
     B.step(0.01, 4)
     assert np.array_equal(A.u(), B.u()) and np.array_equal(A.v(), B.v())
+
+
+@pytest.mark.parametrize("coupling", [0, 1])
+def test_largest_micro_mesh_matches_oracle(coupling):
+    """64x64 micro cells (4225 DoFs, the largest micro mesh) in mixed precision:
+    only the tall-strip and 8-nodes-per-thread variants fit; two steps against
+    the oracle."""
+    NM, Nm = 2, 64
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_SHEAR_BUMP, nM, seed=31)
+    P, R = _pair(Nm, NM, W.FAMILY_SHEAR_BUMP, prm, D=(1.0, 0.0, 0.1), precision=1, coupling=coupling)
+    u0, v0 = W.random_state(nM, nm, seed=32)
+    P.set_state(u0, v0)
+    R.set_state(u0, v0)
+    P.step(0.005, 2)
+    P.synchronize()
+    R.step(0.005, 2, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13)
+    assert P.stats()["tiling"] in (3, 7, 8, 9)
+    assert rel(P.u(), R.u) < MIXED_TOL
+    assert rel(P.v(), R.v) < MIXED_TOL
+
+
+def test_many_micro_problems_sampled():
+    """A 600x600 macro mesh (361201 micro problems of 3x3 cells: grids far past
+    65535 blocks in one dimension) in both couplings: sampled problems against
+    the oracle of a small mesh with the same parameters at those nodes, and
+    mass balance over everything."""
+    T = _T()
+    NM, Nm = 600, 3
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    a = np.full(nM, 0.08)
+    for coupling in (0, 1):
+        P = T.TwoScale(Nm, NM, precision=0, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13, coupling=coupling)
+        P.set_deformation(W.FAMILY_BUMP, a)
+        P.set_state(np.ones(nM), None)
+        _, vol = P.geometry()
+        x1, x2 = W.macro_coords(NM)
+        mH = 0.25 * np.where((x1 == 0) | (x1 == 1), 1.0, 2.0) * np.where((x2 == 0) | (x2 == 1), 1.0, 2.0) / NM ** 2
+        m0 = mH @ P.u() + np.sum(mH * vol * P.vbar())
+        P.step(0.005, 2)
+        P.synchronize()
+        m1 = mH @ P.u() + np.sum(mH * vol * P.vbar())
+        assert abs(m1 - m0) < 1e-11 * abs(m0)
+        # uniform data and u0 = 1: every micro problem sees the same u, so all
+        # micro fields equal the one of a 1x1 macro mesh with the same data
+        R = oracle.Problem(Nm, 1, 0, W.FAMILY_BUMP, np.full(4, 0.08))
+        R.set_state(np.ones(4), None)
+        R.step(0.005, 2, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13)
+        V = P.v()
+        for i in (0, 1, nM // 2, nM - 1):
+            assert np.max(np.abs(V[i] - R.v[0])) < 1e-10
+        assert np.max(np.abs(P.u() - R.u[0])) < 1e-10
+        P.close()
