@@ -208,6 +208,20 @@ tsf_status tsf_get_micro_field(tsf_ctx *ctx, double *v_out, int on_device);
 tsf_status tsf_get_flux(tsf_ctx *ctx, double *flux_out, int on_device);
 tsf_status tsf_get_geometry(tsf_ctx *ctx, double *gamma_out, double *vol_out, int on_device);
 
+/* Push-forward of the micro fields for visualisation (Sec. 3.5: every micro
+ * solution is mapped from the reference cell Z to its physical cell Y_x and
+ * translated to its macroscopic location, scaled so that the cells can be
+ * told apart).  Micro node j of the micro problem at macro node i (reference
+ * point yhat_j = (p, q)/Nm, macro point x_i on [0,1]^2) goes to
+ *     X = x_i + scale (chi(x_i, yhat_j) - (1/2, 1/2)),
+ * chi the deformation map of tsf_set_deformation (shift of the affine family
+ * included).  out[(i nm + j) 3 + {0, 1, 2}] = (X1, X2, v_i(yhat_j)): nM x nm
+ * x 3 floats (FP32, for pictures), host (on_device = 0) or device.  scale > 0
+ * (for instance 0.8 / NM).  With a host buffer the call allocates and frees a
+ * device buffer of the same size.  Synchronises the stream.  Errors:
+ * TSF_E_ARG, TSF_E_STATE (no deformation), TSF_E_OOM, TSF_E_CUDA. */
+tsf_status tsf_get_pushforward(tsf_ctx *ctx, float scale, float *out, int on_device);
+
 tsf_status tsf_get_stats(tsf_ctx *ctx, tsf_stats *out);
 tsf_status tsf_reset_stats(tsf_ctx *ctx);
 

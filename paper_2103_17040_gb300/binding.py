@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "TSF_OK", 1: "TSF_E_ARG", 2: "TSF_E_STATE", 3: "TSF_E_BAD_JAC
 EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micro_mesh", "tsf_set_macro_mesh",
            "tsf_set_physics", "tsf_set_deformation", "tsf_set_state", "tsf_set_sources", "tsf_step",
            "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux",
-           "tsf_get_geometry", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
+           "tsf_get_geometry", "tsf_get_pushforward", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
            "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u",
            "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_synchronize",
            "tsf_batch_get_stats", "tsf_batch_reset_stats", "tsf_batch_last_error", "tsf_batch_destroy"]
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     for f in ("tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux"):
         getattr(L, f).argtypes = [vp, vp, i]
     L.tsf_get_geometry.argtypes = [vp, vp, vp, i]
+    L.tsf_get_pushforward.argtypes = [vp, ctypes.c_float, vp, i]
     L.tsf_get_stats.argtypes = [vp, ctypes.POINTER(tsf_stats)]
     L.tsf_reset_stats.argtypes = [vp]
     L.tsf_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -261,6 +262,25 @@ def tsf_get_geometry(ctx, nM):
     v = np.empty(nM)
     _check(ctx, _lib.tsf_get_geometry(ctx, g.ctypes.data, v.ctypes.data, 0))
     return g, v
+
+
+def tsf_get_pushforward(ctx, nM, nm, scale, out=None):
+    """(X1, X2, v) of every micro node at its macroscopic location: [nM * nm * 3]
+    float32 (a NumPy array, or a float32 CUDA tensor given as out)."""
+    n = nM * nm * 3
+    if out is None:
+        out = np.empty(n, dtype=np.float32)
+    if _is_cuda_tensor(out):
+        import torch
+        if out.dtype != torch.float32 or out.numel() != n or not out.is_contiguous():
+            raise ValueError("output tensor must be contiguous float32 with the right size")
+        p, dev = out.data_ptr(), 1
+    else:
+        if out.dtype != np.float32 or out.size != n or not out.flags.c_contiguous:
+            raise ValueError("output array must be contiguous float32 with the right size")
+        p, dev = out.ctypes.data, 0
+    _check(ctx, _lib.tsf_get_pushforward(ctx, float(scale), p, dev))
+    return out
 
 
 def tsf_get_stats(ctx) -> dict:
@@ -467,6 +487,12 @@ class TwoScale:
 
     def geometry(self):
         return tsf_get_geometry(self.ctx, self.nM)
+
+    def pushforward(self, scale=None, out=None):
+        """Micro fields at their macroscopic locations, [nM, nm, 3] = (X1, X2, v);
+        scale defaults to 0.8 of the macro mesh width."""
+        a = tsf_get_pushforward(self.ctx, self.nM, self.nm, 0.8 / self.NM if scale is None else scale, out)
+        return a.reshape(self.nM, self.nm, 3) if isinstance(a, np.ndarray) else a
 
     def stats(self):
         return tsf_get_stats(self.ctx)

@@ -70,6 +70,7 @@ struct tsf_ctx {
     double *phi = nullptr, *beta = nullptr, *gam_eff = nullptr, *uzero = nullptr, *uone = nullptr;
     bool phi_valid = false;
     double* hist = nullptr;      // [3][nM][nmp] ring of the last solves' z (warm-start extrapolation)
+    float* map32 = nullptr;      // [nM][8] FP32 copy of the deformation maps (push-forward)
     // pipelined elimination (tsf_elim.cu): z = w + u psi
     double *W = nullptr, *cnext = nullptr, *mphi = nullptr, *psi = nullptr, *mpsi = nullptr;  // [nM][nmp]
     double* yhist = nullptr;     // [3][nM][nmp] ring of S w of the last solves
@@ -335,6 +336,7 @@ static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
     for (int r = 0; r < 5; ++r) off[k++] = A.take(nM * pl * sizeof(double));  // W cnext mphi psi mpsi
     off[k++] = A.take(3 * nM * pl * sizeof(double));             // yhist
     off[k++] = A.take(nM * 3 * sizeof(double));                  // mnorm
+    off[k++] = A.take(nM * 8 * sizeof(float));                   // map32
     for (int r = 0; r < 3; ++r) off[k++] = A.take(nM * sizeof(double));  // u_old gam_psi rho_eff
 }
 
@@ -380,12 +382,13 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->mpsi = (double*)(b + off[k++]);
     ctx->yhist = (double*)(b + off[k++]);
     ctx->mnorm = (double*)(b + off[k++]);
+    ctx->map32 = (float*)(b + off[k++]);
     ctx->u_old = (double*)(b + off[k++]);
     ctx->gam_psi = (double*)(b + off[k++]);
     ctx->rho_eff = (double*)(b + off[k++]);
 }
 
-static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5 + 1 + 5 + 1 + 1 + 3;
+static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5 + 1 + 5 + 1 + 1 + 3 + 1;
 
 tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return TSF_E_ARG;
@@ -517,7 +520,7 @@ tsf_status tsf_set_deformation(tsf_ctx* ctx, int family, int nparam, const doubl
         st = copy_in(ctx, ctx->vtmp, params, (size_t)ctx->nM * nparam, params_on_device);
         if (st) return st;
     }
-    CU(launch_expand_params(family, nparam, ctx->vtmp, ctx->prm5, ctx->nM, ctx->stream));
+    CU(launch_expand_params(family, nparam, ctx->vtmp, ctx->prm5, ctx->map32, ctx->nM, ctx->stream));
     CU(cudaMemsetAsync(&ctx->ctl->geom_error, 0, sizeof(int), ctx->stream));
     st = build_operators(ctx, 1.0);
     if (st) return st;
@@ -1329,6 +1332,29 @@ tsf_status tsf_get_geometry(tsf_ctx* ctx, double* gamma_out, double* vol_out, in
     tsf_status st = TSF_OK;
     if (gamma_out && (st = copy_out(ctx, gamma_out, ctx->gam, ctx->nM, on_device))) return st;
     if (vol_out && (st = copy_out(ctx, vol_out, ctx->vol, ctx->nM, on_device))) return st;
+    return TSF_OK;
+}
+
+tsf_status tsf_get_pushforward(tsf_ctx* ctx, float scale, float* out, int on_device) {
+    if (!ctx || !out) return TSF_E_ARG;
+    if (!(scale > 0.0f) || !std::isfinite(scale)) return fail(ctx, TSF_E_ARG, "scale must be positive");
+    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
+    const size_t n = (size_t)ctx->nM * ctx->nm * 3;
+    float* dst = out;
+    if (!on_device) {
+        cudaError_t e = cudaMalloc((void**)&dst, n * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, TSF_E_OOM, "cudaMalloc of %zu bytes for the push-forward failed", n * sizeof(float));
+        }
+    }
+    cudaError_t e = launch_pushforward(ctx->Nm, ctx->n1, ctx->nm, ctx->nmp, ctx->NM, ctx->nM, ctx->map32, ctx->v,
+                                       scale, dst, ctx->stream);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (!on_device) cudaFree(dst);
+    if (e != cudaSuccess) return fail(ctx, TSF_E_CUDA, "push-forward: %s", cudaGetErrorString(e));
     return TSF_OK;
 }
 

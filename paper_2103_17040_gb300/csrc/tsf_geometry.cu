@@ -19,24 +19,68 @@
 namespace tsf {
 
 __global__ void k_expand_params(int family, int nparam, const double* __restrict__ in, double* __restrict__ prm5,
-                                int nM) {
+                                float* __restrict__ map32, int nM) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nM) return;
     const double* p = in + (size_t)i * nparam;
-    double A11 = 1.0, A12 = 0.0, A21 = 0.0, A22 = 1.0, b = 0.0;
+    double A11 = 1.0, A12 = 0.0, A21 = 0.0, A22 = 1.0, b = 0.0, c1 = 0.0, c2 = 0.0;
     switch (family) {
         case 1: b = p[0]; break;                                           // bump (a)
         case 2: A12 = p[0]; b = p[1]; break;                               // shear + bump (s, b)
-        case 3: A11 = p[0]; A12 = p[1]; A21 = p[2]; A22 = p[3]; break;     // affine (A, c): c drops out of F
+        case 3:                                                            // affine (A, c): c drops out of F
+            A11 = p[0]; A12 = p[1]; A21 = p[2]; A22 = p[3]; c1 = p[4]; c2 = p[5];
+            break;
         case 4: A11 = p[0]; A12 = p[1]; A21 = p[2]; A22 = p[3]; b = p[4]; break;
         default: break;                                                    // identity
     }
     double* o = prm5 + (size_t)i * 5;
     o[0] = A11; o[1] = A12; o[2] = A21; o[3] = A22; o[4] = b;
+    float* m = map32 + (size_t)i * 8;  // the whole map in FP32 for the push-forward
+    m[0] = (float)A11; m[1] = (float)A12; m[2] = (float)A21; m[3] = (float)A22;
+    m[4] = (float)b; m[5] = (float)c1; m[6] = (float)c2; m[7] = 0.f;
 }
 
-cudaError_t launch_expand_params(int family, int nparam, const double* in, double* prm5, int nM, cudaStream_t s) {
-    k_expand_params<<<(nM + 127) / 128, 128, 0, s>>>(family, nparam, in, prm5, nM);
+cudaError_t launch_expand_params(int family, int nparam, const double* in, double* prm5, float* map32, int nM,
+                                 cudaStream_t s) {
+    k_expand_params<<<(nM + 127) / 128, 128, 0, s>>>(family, nparam, in, prm5, map32, nM);
+    return cudaGetLastError();
+}
+
+// Push-forward for visualisation (Sec. 3.5): micro node j of instance i,
+// reference point yhat_j, goes to
+//     X = x_i + scale (chi(x_i, yhat_j) - (1/2, 1/2)),
+// chi = A yhat + b (sin pi y1 sin pi y2, 0) + c; out[(i nm + j) 3 + {0,1,2}]
+// = (X1, X2, v_i(yhat_j)) in FP32 (a picture needs no more, and GB300's FP64
+// rate would make this streaming kernel compute-bound).  One thread per
+// (instance, node); sin(pi k/Nm) of the n1 grid lines from a table.
+__global__ void __launch_bounds__(256) k_pushforward(int n1, int nm, int nmp, int NM, float H, float h,
+                                                     const float* __restrict__ map32, const double* __restrict__ v,
+                                                     float scale, float* __restrict__ out) {
+    __shared__ float sinpi_tab[65];  // n1 <= 65
+    for (int k = threadIdx.x; k < n1; k += blockDim.x) sinpi_tab[k] = sinpif((float)k * h);
+    __syncthreads();
+    const int i = blockIdx.x;
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    if (j >= nm) return;
+    const int N1 = NM + 1;
+    const float x1 = (float)(i % N1) * H, x2 = (float)(i / N1) * H;
+    const int pj = j % n1, qj = j / n1;
+    const float y1 = (float)pj * h, y2 = (float)qj * h;
+    const float4 m0 = *reinterpret_cast<const float4*>(map32 + (size_t)i * 8);
+    const float4 m1 = *reinterpret_cast<const float4*>(map32 + (size_t)i * 8 + 4);
+    const float s12 = sinpi_tab[pj] * sinpi_tab[qj];
+    const float ch1 = fmaf(m1.x, s12, fmaf(m0.x, y1, fmaf(m0.y, y2, m1.y)));
+    const float ch2 = fmaf(m0.z, y1, fmaf(m0.w, y2, m1.z));
+    float* o = out + ((size_t)i * nm + j) * 3;
+    o[0] = fmaf(scale, ch1 - 0.5f, x1);
+    o[1] = fmaf(scale, ch2 - 0.5f, x2);
+    o[2] = (float)v[(size_t)i * nmp + j];
+}
+
+cudaError_t launch_pushforward(int Nm, int n1, int nm, int nmp, int NM, int nM, const float* map32, const double* v,
+                               float scale, float* out, cudaStream_t s) {
+    dim3 grid(nM, (nm + 255) / 256);
+    k_pushforward<<<grid, 256, 0, s>>>(n1, nm, nmp, NM, 1.0f / NM, 1.0f / Nm, map32, v, scale, out);
     return cudaGetLastError();
 }
 

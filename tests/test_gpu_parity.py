@@ -391,3 +391,31 @@ def test_many_micro_problems_sampled():
             assert np.max(np.abs(V[i] - R.v[0])) < 1e-10
         assert np.max(np.abs(P.u() - R.u[0])) < 1e-10
         P.close()
+
+
+@pytest.mark.parametrize("family", [0, 1, 2, 3, 4])
+def test_pushforward_matches_oracle_map(family):
+    """Push-forward for visualisation: every micro node at
+    x_i + scale (chi(x_i, yhat_j) - 1/2) with its value, against the
+    oracle's chi."""
+    T = _T()
+    NM, Nm = 3, 5
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(family, nM, seed=40 + family)
+    P = T.TwoScale(Nm, NM, precision=0)
+    P.set_deformation(family, prm)
+    P.set_state(*W.random_state(nM, nm, seed=41))
+    P.step(0.01, 1)
+    scale = 0.7 / NM
+    out = P.pushforward(scale)
+    y1, y2 = W.micro_coords(Nm)
+    x1, x2 = W.macro_coords(NM)
+    # FP32 output: positions to a few FP32 ulps of the unit square, values rounded
+    for i in range(nM):
+        ch, _ = oracle.chi_many(family, prm[i] if prm.shape[1] else [], y1, y2)
+        ch = ch.reshape(-1, 2)
+        assert np.max(np.abs(out[i, :, 0] - (x1[i] + scale * (ch[:, 0] - 0.5)))) < 1e-6
+        assert np.max(np.abs(out[i, :, 1] - (x2[i] + scale * (ch[:, 1] - 0.5)))) < 1e-6
+    assert np.array_equal(out[:, :, 2], P.v().astype(np.float32))
+    with pytest.raises(T.TsfError):
+        P.pushforward(-1.0)
