@@ -44,19 +44,22 @@ def _q1_eval(N, nodal, s, t, A, B):
     return val, ds, dt
 
 
-def macro_errors(NM, uh, u_fn, grad_fn):
+def macro_errors(NM, uh, u_fn, grad_fn, x0=0.0, L=1.0):
+    """errors of a Q1 field on the macro mesh of [x0, x0 + L]^2"""
     s, t, A, B, w = _cell_points(NM)
-    H = 1.0 / NM
-    x1, x2 = (A + s) * H, (B + t) * H
+    H = L / NM
+    x1, x2 = x0 + (A + s) * H, x0 + (B + t) * H
     val, d1, d2 = _q1_eval(NM, np.asarray(uh), s, t, A, B)
+    d1, d2 = d1 / L, d2 / L
     g1, g2 = grad_fn(x1, x2)
     e2 = np.sum(w * H * H * (u_fn(x1, x2) - val) ** 2)
     h2 = np.sum(w * H * H * ((g1 - d1) ** 2 + (g2 - d2) ** 2))
     return float(np.sqrt(e2)), float(np.sqrt(h2))
 
 
-def micro_errors(NM, Nm, family, params, vh, mH, v_fn, grad_fn):
-    """v_fn(x1, x2, y1, y2), grad_fn(...) -> (dv/dy1, dv/dy2) in physical coordinates."""
+def micro_errors(NM, Nm, family, params, vh, mH, v_fn, grad_fn, x0=0.0, L=1.0):
+    """v_fn(x1, x2, y1, y2), grad_fn(...) -> (dv/dy1, dv/dy2) in physical coordinates;
+    macro nodes on [x0, x0 + L]^2."""
     s, t, A, B, w = _cell_points(Nm)
     h = 1.0 / Nm
     yh1, yh2 = (A + s) * h, (B + t) * h
@@ -66,7 +69,7 @@ def micro_errors(NM, Nm, family, params, vh, mH, v_fn, grad_fn):
     e2 = 0.0
     h2 = 0.0
     for i in range(vh.shape[0]):
-        x1, x2 = (i % n1) / NM, (i // n1) / NM
+        x1, x2 = x0 + (i % n1) * (L / NM), x0 + (i // n1) * (L / NM)
         y, F = chi_many(family, params[i], yh1, yh2)
         J = F[:, 0, 0] * F[:, 1, 1] - F[:, 0, 1] * F[:, 1, 0]
         val, ds, dt = _q1_eval(Nm, vh[i], s, t, A, B)
