@@ -213,6 +213,10 @@ class ThreeField:
 
     def solve(self, dt=None, prev=None, **sources):
         """(u [nM], w [nM], v [nM][nm])"""
+        if not dt and not self.dir.any():
+            # the constant equilibrium state spans the null space (Sec. 2.2 asks
+            # for a non-empty Dirichlet boundary)
+            raise ValueError("the stationary system needs at least one Dirichlet edge")
         A = self.matrix(dt)
         X = spla.spsolve(A, self.rhs(dt=dt, prev=prev, **sources))
         nM, nm = self.nM, self.nm

@@ -210,3 +210,15 @@ def test_manufactured_convergence_rates():
     assert abs(p_macro - 2) < 0.06 and abs(p_micro - 2) < 0.06, rates
     assert abs(q_macro - 1) < 0.06 and abs(q_micro - 1) < 0.06, rates
     assert np.all(E[1:] < E[:-1])
+
+
+def test_stationary_system_without_dirichlet_edge_is_rejected():
+    """Sec. 2.2 asks for a Dirichlet part: without one the constant equilibrium
+    (u, kappa_1/kappa_2 u, kappa_1 kappa_4/(kappa_2 kappa_3) u) is a null vector."""
+    wl = T3.case_a(3, 3)
+    P = ThreeField(wl.Nm, wl.NM, wl.family, wl.params, kappa=wl.kappa, dir_mask=0)
+    k1, k2, k3, k4 = wl.kappa
+    null = np.concatenate([np.ones(P.nM), np.full(P.nM * P.nm, k1 / k2), np.full(P.nM, k1 * k4 / (k2 * k3))])
+    assert np.abs(P.matrix() @ null).max() < 1e-13
+    with pytest.raises(ValueError):
+        P.solve()
