@@ -208,7 +208,7 @@ tsf_status tsf_get_micro_field(tsf_ctx *ctx, double *v_out, int on_device);
 tsf_status tsf_get_flux(tsf_ctx *ctx, double *flux_out, int on_device);
 tsf_status tsf_get_geometry(tsf_ctx *ctx, double *gamma_out, double *vol_out, int on_device);
 
-/* Push-forward of the micro fields for visualisation (Sec. 3.5: every micro
+/* Push-forward of the micro fields for visualisation (Sec. 3.6: every micro
  * solution is mapped from the reference cell Z to its physical cell Y_x and
  * translated to its macroscopic location, scaled so that the cells can be
  * told apart).  Micro node j of the micro problem at macro node i (reference

@@ -8,4 +8,4 @@ source, and the macro solve that closes the coupling iteration.  The C ABI is
 declared in ``include/tsfem.h``; :mod:`.binding` mirrors it in Python.
 """
 from .binding import *  # noqa: F401,F403
-from .binding import TwoScale, TsfError, load_library, LIB_PATH, EXPORTS  # noqa: F401
+from .binding import TwoScale, ThreeField, TsfError, load_library, LIB_PATH, EXPORTS, EXPORTS3  # noqa: F401

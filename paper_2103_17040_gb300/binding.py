@@ -1,4 +1,4 @@
-"""ctypes binding of ``libtsfem`` (include/tsfem.h), argument marshalling only.
+"""ctypes binding of ``libtsfem`` (include/tsfem.h, include/tsfem3.h), argument marshalling only.
 
 Every C entry point has a Python function of the same name.  Array arguments
 may be NumPy arrays (host memory) or CUDA ``torch.Tensor`` s (device memory,
@@ -34,6 +34,10 @@ EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micr
            "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u",
            "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_synchronize",
            "tsf_batch_get_stats", "tsf_batch_reset_stats", "tsf_batch_last_error", "tsf_batch_destroy"]
+# every symbol include/tsfem3.h declares (the stationary three-field system)
+EXPORTS3 = ["tsf3_create", "tsf3_set_meshes", "tsf3_set_physics", "tsf3_set_deformation", "tsf3_set_sources",
+            "tsf3_solve", "tsf3_get_fields", "tsf3_get_stats", "tsf3_last_error", "tsf3_destroy"]
+TSF3_EDGE_BOTTOM, TSF3_EDGE_RIGHT, TSF3_EDGE_TOP, TSF3_EDGE_LEFT = 1, 2, 4, 8
 TSF_NOALLOC_MAX_NM = 128
 TSF_BATCH_MAX = 4096
 
@@ -54,6 +58,16 @@ class tsf_stats(ctypes.Structure):
                 ("tiling", ctypes.c_int), ("coupling_change", ctypes.c_double),
                 ("micro_launches", ctypes.c_int64), ("macro_launches", ctypes.c_int64),
                 ("micro_kernel_ms", ctypes.c_double), ("macro_kernel_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class tsf3_stats(ctypes.Structure):
+    _fields_ = [("inner_iters", ctypes.c_int64), ("dof_cg_iters", ctypes.c_int64), ("refine_sweeps", ctypes.c_int64),
+                ("micro_solves", ctypes.c_int64), ("macro_iters", ctypes.c_int64), ("status", ctypes.c_int),
+                ("tiling", ctypes.c_int), ("micro_ms", ctypes.c_double), ("macro_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -116,10 +130,22 @@ def load_library(path: str = LIB_PATH):
     L.tsf_batch_last_error.restype = ctypes.c_char_p
     L.tsf_batch_destroy.argtypes = [vp]
     L.tsf_batch_destroy.restype = None
-    for f in EXPORTS:
+    L.tsf3_create.argtypes = [pp, ctypes.POINTER(tsf_options)]
+    L.tsf3_set_meshes.argtypes = [vp, i, i, d, d, i]
+    L.tsf3_set_physics.argtypes = [vp, vp, d, vp]
+    L.tsf3_set_deformation.argtypes = [vp, i, i, vp, i]
+    L.tsf3_set_sources.argtypes = [vp] + [vp] * 9 + [i]
+    L.tsf3_solve.argtypes = [vp]
+    L.tsf3_get_fields.argtypes = [vp, vp, vp, vp, vp, i]
+    L.tsf3_get_stats.argtypes = [vp, ctypes.POINTER(tsf3_stats)]
+    L.tsf3_last_error.argtypes = [vp]
+    L.tsf3_last_error.restype = ctypes.c_char_p
+    L.tsf3_destroy.argtypes = [vp]
+    L.tsf3_destroy.restype = None
+    for f in EXPORTS + EXPORTS3:
         fn = getattr(L, f)
         if f not in ("tsf_default_options", "tsf_last_error", "tsf_destroy", "tsf_batch_last_error",
-                     "tsf_batch_destroy"):
+                     "tsf_batch_destroy", "tsf3_last_error", "tsf3_destroy"):
             fn.restype = ctypes.c_int
     _lib = L
     return L
@@ -398,6 +424,76 @@ def tsf_macro_solve_noalloc(NM, bc, dt, macro_diff, kappa, gam, cH, rho, u0, u_o
 
 
 # ---------------------------------------------------------------------------
+# stationary three-field system (include/tsfem3.h)
+# ---------------------------------------------------------------------------
+def _check3(ctx, status):
+    if status != TSF_OK:
+        msg = _lib.tsf3_last_error(ctx).decode() if ctx else ""
+        raise TsfError(status, msg)
+
+
+def tsf3_create(opt: tsf_options | None = None) -> int:
+    L = load_library()
+    out = ctypes.c_void_p()
+    st = L.tsf3_create(ctypes.byref(out), ctypes.byref(opt) if opt is not None else None)
+    if st != TSF_OK:
+        raise TsfError(st, "tsf3_create failed")
+    return out.value
+
+
+def tsf3_set_meshes(ctx, Nm, NM, x0=0.0, L=1.0, dir_mask=TSF3_EDGE_LEFT):
+    _check3(ctx, _lib.tsf3_set_meshes(ctx, int(Nm), int(NM), float(x0), float(L), int(dir_mask)))
+
+
+def tsf3_set_physics(ctx, D=(1.0, 0.0, 1.0), Dw=1.0, kappa=(1.0, 1.0, 1.0, 1.0)):
+    Da = (ctypes.c_double * 3)(*[float(x) for x in D])
+    ka = (ctypes.c_double * 4)(*[float(x) for x in kappa])
+    _check3(ctx, _lib.tsf3_set_physics(ctx, Da, float(Dw), ka))
+
+
+def tsf3_set_deformation(ctx, family, nparam, params):
+    p, dev, keep = _ptr_in(params) if nparam else (None, 0, None)
+    _check3(ctx, _lib.tsf3_set_deformation(ctx, int(family), int(nparam), p, dev))
+
+
+def tsf3_set_sources(ctx, fu=None, fw=None, ud=None, gu=None, gw=None, fv=None, gI=None, gO=None, gN=None):
+    args = [_ptr_in(a) for a in (fu, fw, ud, gu, gw, fv, gI, gO, gN)]
+    devs = {dev for (ptr, dev, _) in args if ptr is not None}
+    if len(devs) > 1:
+        raise ValueError("sources must all be host arrays or all CUDA tensors")
+    _check3(ctx, _lib.tsf3_set_sources(ctx, *[ptr for (ptr, _, _) in args], devs.pop() if devs else 0))
+
+
+def tsf3_solve(ctx):
+    _check3(ctx, _lib.tsf3_solve(ctx))
+
+
+def tsf3_get_fields(ctx, nM, nm, u=None, w=None, v=None, vbar=None):
+    """(u [nM], w [nM], v [nM*nm], vbar [nM]); outputs None -> new host arrays."""
+    outs = [_out(a, n) for a, n in ((u, nM), (w, nM), (v, nM * nm), (vbar, nM))]
+    devs = {dev for (_, dev, _) in outs}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be host arrays or all CUDA tensors")
+    _check3(ctx, _lib.tsf3_get_fields(ctx, *[ptr for (ptr, _, _) in outs], devs.pop()))
+    return tuple(a for (_, _, a) in outs)
+
+
+def tsf3_get_stats(ctx) -> dict:
+    s = tsf3_stats()
+    _check3(ctx, _lib.tsf3_get_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def tsf3_last_error(ctx) -> str:
+    return load_library().tsf3_last_error(ctx).decode()
+
+
+def tsf3_destroy(ctx):
+    if ctx:
+        load_library().tsf3_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
 # convenience wrapper (still marshalling only)
 # ---------------------------------------------------------------------------
 def _make_options(precision, stream, opts):
@@ -555,3 +651,47 @@ class TwoScaleBatch:
             self.close()
         except Exception:
             pass
+
+
+class ThreeField:
+    """The stationary three-field system (u, v, w; include/tsfem3.h) on the
+    current CUDA device: Nm x Nm micro cells, NM x NM macro cells on
+    [x0, x0 + L]^2, u Dirichlet on the edges of ``dir_mask`` (TSF3_EDGE_*)."""
+
+    def __init__(self, Nm, NM, x0=0.0, L=1.0, dir_mask=TSF3_EDGE_LEFT, precision=TSF_MIXED, stream=None, **opts):
+        self.ctx = tsf3_create(_make_options(precision, stream, opts))
+        self.Nm, self.NM = int(Nm), int(NM)
+        self.nm, self.nM = (self.Nm + 1) ** 2, (self.NM + 1) ** 2
+        tsf3_set_meshes(self.ctx, self.Nm, self.NM, x0, L, dir_mask)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            tsf3_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_physics(self, D=(1.0, 0.0, 1.0), Dw=1.0, kappa=(1.0, 1.0, 1.0, 1.0)):
+        tsf3_set_physics(self.ctx, D, Dw, kappa)
+
+    def set_deformation(self, family, params):
+        nparam = {0: 0, 1: 1, 2: 2, 3: 6, 4: 5}[int(family)]
+        tsf3_set_deformation(self.ctx, family, nparam, params)
+
+    def set_sources(self, fu=None, fw=None, ud=None, gu=None, gw=None, fv=None, gI=None, gO=None, gN=None):
+        tsf3_set_sources(self.ctx, fu, fw, ud, gu, gw, fv, gI, gO, gN)
+
+    def solve(self):
+        tsf3_solve(self.ctx)
+
+    def fields(self):
+        """(u [nM], w [nM], v [nM, nm], vbar [nM]) as host arrays"""
+        u, w, v, vbar = tsf3_get_fields(self.ctx, self.nM, self.nm)
+        return u, w, v.reshape(self.nM, self.nm), vbar
+
+    def stats(self):
+        return tsf3_get_stats(self.ctx)

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtsfem.so")
-SOURCES = ["tsf_api.cu", "tsf_geometry.cu", "tsf_micro.cu", "tsf_macro.cu", "tsf_noalloc.cu", "tsf_adjoint.cu", "tsf_elim.cu"]
+SOURCES = ["tsf_api.cu", "tsf_geometry.cu", "tsf_micro.cu", "tsf_macro.cu", "tsf_noalloc.cu", "tsf_adjoint.cu",
+           "tsf_elim.cu", "tsf3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -33,7 +34,7 @@ def nvcc() -> str:
 
 
 def _newest_input() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "tsfem.h"), __file__]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, h) for h in ("tsfem.h", "tsfem3.h")] + [__file__]
     return max(os.path.getmtime(f) for f in files)
 
 

@@ -14,7 +14,7 @@
 //     chi(yhat) = A yhat + b (sin pi y1 sin pi y2, 0),
 //     F = A + b pi [[cos pi y1 sin pi y2, sin pi y1 cos pi y2], [0, 0]],
 // with parameters (A11, A12, A21, A22, b).
-#include "tsf_internal.cuh"
+#include "tsf_geom.cuh"
 
 namespace tsf {
 
@@ -46,7 +46,7 @@ cudaError_t launch_expand_params(int family, int nparam, const double* in, doubl
     return cudaGetLastError();
 }
 
-// Push-forward for visualisation (Sec. 3.5): micro node j of instance i,
+// Push-forward for visualisation (Sec. 3.6): micro node j of instance i,
 // reference point yhat_j, goes to
 //     X = x_i + scale (chi(x_i, yhat_j) - (1/2, 1/2)),
 // chi = A yhat + b (sin pi y1 sin pi y2, 0) + c; out[(i nm + j) 3 + {0,1,2}]
@@ -84,19 +84,6 @@ cudaError_t launch_pushforward(int Nm, int n1, int nm, int nmp, int NM, int nM, 
     return cudaGetLastError();
 }
 
-struct Deform {
-    double A11, A12, A21, A22, bpi;
-};
-
-// F at reference point (y1, y2) given sin/cos of pi*y1, pi*y2.
-__device__ __forceinline__ void jacobian(const Deform& d, double s1, double c1, double s2, double c2, double& F11,
-                                         double& F12, double& F21, double& F22) {
-    F11 = fma(d.bpi, c1 * s2, d.A11);
-    F12 = fma(d.bpi, s1 * c2, d.A12);
-    F21 = d.A21;
-    F22 = d.A22;
-}
-
 // One thread per (micro node j, instance i): the five stored couplings of
 // node j in M and in S = M/dt + A + kappa R, summed over the (up to four)
 // cells around the node with 2x2 Gauss points; on Robin-edge nodes also the
@@ -120,98 +107,15 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
     }
     const int N = a.Nm, n1 = a.n1;
     const int p = j % n1, q = j / n1;
-    const double h = 1.0 / N;
-    const double* pr = a.prm5 + (size_t)i * 5;
-    Deform d{pr[0], pr[1], pr[2], pr[3], pr[4] * 3.14159265358979323846};
-    const double D11 = a.D11, D12 = a.D12, D22 = a.D22;
-
-    // 2-point Gauss abscissae on [0,1]
-    const double g0 = 0.5 - 0.28867513459481288225, g1 = 0.5 + 0.28867513459481288225;
-
-    double m[kPlanes] = {0, 0, 0, 0, 0};
-    double k[kPlanes] = {0, 0, 0, 0, 0};
-    double lump = 0.0;
-    bool bad = false;
-
-    for (int cb = 0; cb < 2; ++cb) {
-        const int b = q - 1 + cb;
-        if (b < 0 || b >= N) continue;
-        for (int ca = 0; ca < 2; ++ca) {
-            const int ac = p - 1 + ca;
-            if (ac < 0 || ac >= N) continue;
-            // local index of node j in this cell
-            const int lx = p - ac, ly = q - b, la = lx + 2 * ly;
-            for (int qt = 0; qt < 2; ++qt) {
-                const double t = qt ? g1 : g0;
-                double s2, c2;
-                sincospi((b + t) * h, &s2, &c2);
-                for (int qs = 0; qs < 2; ++qs) {
-                    const double s = qs ? g1 : g0;
-                    double s1, c1;
-                    sincospi((ac + s) * h, &s1, &c1);
-                    double F11, F12, F21, F22;
-                    jacobian(d, s1, c1, s2, c2, F11, F12, F21, F22);
-                    const double J = F11 * F22 - F12 * F21;
-                    if (!(J > 0.0)) bad = true;
-                    // C = J F^-1 D F^-T = G D G^T / J with G = adj(F) = J F^-1
-                    const double G11 = F22, G12 = -F12, G21 = -F21, G22 = F11;
-                    const double GD11 = G11 * D11 + G12 * D12, GD12 = G11 * D12 + G12 * D22;
-                    const double GD21 = G21 * D11 + G22 * D12, GD22 = G21 * D12 + G22 * D22;
-                    const double iJ = 1.0 / J;
-                    const double C11 = (GD11 * G11 + GD12 * G12) * iJ;
-                    const double C12 = (GD11 * G21 + GD12 * G22) * iJ;
-                    const double C22 = (GD21 * G21 + GD22 * G22) * iJ;
-                    // bilinear shape functions of the cell at (s, t)
-                    const double phi[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
-                    const double dsv[4] = {-(1 - t), (1 - t), -t, t};
-                    const double dtv[4] = {-(1 - s), -s, (1 - s), s};
-                    const double wm = 0.25 * h * h * J;
-                    const double gs = C11 * dsv[la] + C12 * dtv[la];
-                    const double gt = C12 * dsv[la] + C22 * dtv[la];
-                    for (int lb = 0; lb < 4; ++lb) {
-                        const double me = wm * phi[la] * phi[lb];
-                        lump += me;
-                        const int dp = (lb & 1) - lx, dq = (lb >> 1) - ly;
-                        int plane = -1;
-                        if (dp == 0 && dq == 0) plane = 0;
-                        else if (dp == 1 && dq == 0) plane = 1;
-                        else if (dp == 0 && dq == 1) plane = 2;
-                        else if (dp == 1 && dq == 1) plane = 3;
-                        else if (dp == -1 && dq == 1) plane = 4;
-                        if (plane < 0) continue;
-                        m[plane] += me;
-                        k[plane] += 0.25 * (gs * dsv[lb] + gt * dtv[lb]);
-                    }
-                }
-            }
-        }
-    }
+    const Deform d = load_deform(a.prm5, i);
+    double m[kPlanes], k[kPlanes], lump;
+    bool bad;
+    node_couplings(d, a.D11, a.D12, a.D22, p, q, N, m, k, lump, bad);
 
     // Robin edge yhat_1 = 1: R = int s eta eta with s = |cof(F) e1| = sqrt(F22^2 + F12^2)
     double Rd = 0.0, Ru = 0.0, Rdn = 0.0;
     if (p == N) {
-        double s1, c1;
-        sincospi(1.0, &s1, &c1);
-        for (int seg = 0; seg < 2; ++seg) {
-            const int b = q - 1 + seg;  // segment [b, b+1]
-            if (b < 0 || b >= N) continue;
-            for (int qt = 0; qt < 2; ++qt) {
-                const double t = qt ? g1 : g0;
-                double s2, c2;
-                sincospi((b + t) * h, &s2, &c2);
-                double F11, F12, F21, F22;
-                jacobian(d, s1, c1, s2, c2, F11, F12, F21, F22);
-                const double sg = sqrt(F22 * F22 + F12 * F12);
-                const double w = 0.5 * h * sg;
-                if (seg == 0) {  // node is the upper end (phi = t)
-                    Rd += w * t * t;
-                    Rdn += w * t * (1 - t);
-                } else {         // node is the lower end (phi = 1 - t)
-                    Rd += w * (1 - t) * (1 - t);
-                    Ru += w * (1 - t) * t;
-                }
-            }
-        }
+        edge_node_mass(d, kEdgeRight, q, N, Rd, Ru, Rdn);
         const size_t e = (size_t)i * n1 + q;
         a.Rd[e] = Rd;
         a.Ru[e] = Ru;

@@ -1,6 +1,6 @@
 """Legacy-VTK file of pushed-forward micro fields (host post-processing).
 
-The paper renders its two-scale solutions with ParaView (Sec. 3.5).  Without a
+The paper renders its two-scale solutions with ParaView (Sec. 3.6).  Without a
 graphics stack here, the library computes the push-forward on the GPU
 (``TwoScale.pushforward``: every micro node at its physical, translated and
 scaled position with its value) and this module writes that buffer as a VTK
