@@ -52,6 +52,8 @@ extern "C" {
 
 typedef struct tsf3_ctx tsf3_ctx;
 
+enum { TSF3_TILING_DIRECT = 10 };
+
 /* Dirichlet edges of u (bit set = Dirichlet), also the order of the per-edge data */
 enum { TSF3_EDGE_BOTTOM = 1, TSF3_EDGE_RIGHT = 2, TSF3_EDGE_TOP = 4, TSF3_EDGE_LEFT = 8 };
 
@@ -62,15 +64,22 @@ typedef struct {
     int64_t micro_solves;    /* micro problems solved (3 per node with a new geometry, else 1) */
     int64_t macro_iters;     /* CG iterations of the coupled macro solve */
     int status;              /* device status of the last solve (tsf_status) */
-    int tiling;              /* micro-solve variant in use (as tsf_stats.tiling) */
+    int tiling;              /* micro-solve variant in use (0..9 as tsf_stats.tiling, or TSF3_TILING_DIRECT) */
     double micro_ms;         /* device time of the micro solves of the last tsf3_solve */
     double macro_ms;         /* device time of the macro solve */
     double total_ms;         /* device time of the whole last tsf3_solve */
 } tsf3_stats;
 
 /* Uses from tsf_options: precision, cg_tol (micro relative residual),
- * inner_tol, cg_maxit, max_sweeps, macro_tol, macro_maxit, tiling (-1 =
- * autotune on the first solve), cuda_stream (NULL = own stream). */
+ * inner_tol, cg_maxit, max_sweeps, macro_tol, macro_maxit, tiling,
+ * cuda_stream (NULL = own stream).  tiling: 0..9 the iterative micro-solve
+ * variants of tsf_stats.tiling; TSF3_TILING_DIRECT (mixed precision only): a
+ * banded Cholesky factor of every micro operator in FP32, kept while the
+ * geometry and physics stay the same, with FP64 iterative refinement to
+ * cg_tol (at most max(max_sweeps, 30) sweeps); -1: the direct solve in
+ * mixed precision when its factor (nM nm (Nm+3) 4 bytes) fits in half the
+ * free device memory, else the fastest iterative variant, timed on the first
+ * solve. */
 tsf_status tsf3_create(tsf3_ctx** out, const tsf_options* opt);
 
 /* Nm x Nm micro cells (1..64), NM x NM macro cells (1..256) on

@@ -38,6 +38,7 @@ EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micr
 EXPORTS3 = ["tsf3_create", "tsf3_set_meshes", "tsf3_set_physics", "tsf3_set_deformation", "tsf3_set_sources",
             "tsf3_solve", "tsf3_get_fields", "tsf3_get_stats", "tsf3_last_error", "tsf3_destroy"]
 TSF3_EDGE_BOTTOM, TSF3_EDGE_RIGHT, TSF3_EDGE_TOP, TSF3_EDGE_LEFT = 1, 2, 4, 8
+TSF3_TILING_DIRECT = 10
 TSF_NOALLOC_MAX_NM = 128
 TSF_BATCH_MAX = 4096
 

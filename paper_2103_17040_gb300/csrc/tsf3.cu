@@ -21,9 +21,12 @@
 // solution.
 //
 // Kernels: geometry with four edges (k3_geometry), right-hand sides and the
-// stored-residual set-up of the micro solves (k3_setup), the batched micro
-// solves of tsf_micro.cu, edge moments and macro coefficients (k3_moments),
-// the coupled macro PCG in one thread block (k3_macro), and the commit.
+// stored-residual set-up of the micro solves (k3_setup), the micro solves
+// (the iterative kernels of tsf_micro.cu, or the direct banded-Cholesky
+// solves of tsf_band.cu: S does not change between the three right-hand
+// sides and the re-solves), edge moments and macro coefficients
+// (k3_moments), the coupled macro PCG in one thread block (k3_macro), and the
+// commit.
 #include "tsfem3.h"
 #include "tsf_geom.cuh"
 
@@ -515,6 +518,13 @@ struct tsf3_ctx {
     DevCtl* ctl = nullptr;
     bool geom_valid = false, phi_valid = false, solved = false;
     int tiling = -1;
+    // direct micro solves (tiling kTilingDirect): the FP32 band factor is kept while S stays the same
+    float* Lband = nullptr;
+    float* yband[3] = {nullptr, nullptr, nullptr};
+    int* done[3] = {nullptr, nullptr, nullptr};
+    int* open_count = nullptr;
+    int* flag = nullptr;
+    bool factor_valid = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     tsf3_stats stats{};
     std::string err;
@@ -544,7 +554,9 @@ static void free_all(tsf3_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (void* p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
-    ctx->geom_valid = ctx->phi_valid = ctx->solved = false;
+    ctx->geom_valid = ctx->phi_valid = ctx->solved = ctx->factor_valid = false;
+    ctx->Lband = nullptr;
+    for (int t = 0; t < 3; ++t) ctx->yband[t] = nullptr;
     ctx->has_fu = ctx->has_fw = ctx->has_ud = ctx->has_gu = ctx->has_gw = false;
     ctx->has_fv = ctx->has_gI = ctx->has_gO = ctx->has_gN = false;
 }
@@ -568,7 +580,7 @@ tsf_status tsf3_create(tsf3_ctx** out, const tsf_options* opt) {
     tsf_default_options(&o);
     if (opt) o = *opt;
     if ((o.precision != TSF_FP64 && o.precision != TSF_MIXED) || !(o.cg_tol > 0.0) || !(o.macro_tol > 0.0) ||
-        o.cg_maxit < 1 || o.macro_maxit < 1 || o.tiling < -1 || o.tiling >= kNumTilings)
+        o.cg_maxit < 1 || o.macro_maxit < 1 || o.tiling < -1 || o.tiling > kTilingDirect)
         return TSF_E_ARG;
     tsf3_ctx* ctx = new (std::nothrow) tsf3_ctx();
     if (!ctx) return TSF_E_OOM;
@@ -679,6 +691,9 @@ tsf_status tsf3_set_meshes(tsf3_ctx* ctx, int Nm, int NM, double x0, double L, i
     CU3(dalloc(ctx, &ctx->mp, 2 * nM));
     CU3(dalloc(ctx, &ctx->mq, 2 * nM));
     CU3(dalloc(ctx, &ctx->pinv, 3 * nM));
+    for (int t = 0; t < 3; ++t) CU3(dalloc(ctx, &ctx->done[t], nM));
+    CU3(dalloc(ctx, &ctx->open_count, 1));
+    CU3(dalloc(ctx, &ctx->flag, 1));
     CU3(cudaMemsetAsync(ctx->zero, 0, nM * sizeof(double), ctx->stream));
     CU3(cudaMemsetAsync(ctx->fv, 0, F * sizeof(double), ctx->stream));
     CU3(cudaMemsetAsync(ctx->eRd, 0, E * sizeof(double), ctx->stream));
@@ -698,7 +713,7 @@ tsf_status tsf3_set_physics(tsf3_ctx* ctx, const double D[3], double Dw, const d
     for (int k = 0; k < 3; ++k) ctx->D[k] = D[k];
     for (int k = 0; k < 4; ++k) ctx->kap[k] = kappa[k];
     ctx->Dw = Dw;
-    ctx->geom_valid = ctx->phi_valid = false;
+    ctx->geom_valid = ctx->phi_valid = ctx->factor_valid = false;
     return TSF_OK;
 }
 
@@ -715,7 +730,7 @@ tsf_status tsf3_set_deformation(tsf3_ctx* ctx, int family, int nparam, const dou
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     ctx->family = family;
     ctx->nparam = nparam;
-    ctx->geom_valid = ctx->phi_valid = false;
+    ctx->geom_valid = ctx->phi_valid = ctx->factor_valid = false;
     CU3(cudaStreamSynchronize(ctx->stream));
     return TSF_OK;
 }
@@ -843,8 +858,26 @@ static tsf_status build_geometry(tsf3_ctx* ctx) {
 
 // Micro-solve variant: fixed by the options, or the fastest of the variants
 // that fit, timed on the phi_I solve of the actual problem.
+static size_t band_bytes(const tsf3_ctx* ctx) {
+    return (size_t)ctx->nM * ctx->nm * (ctx->n1 + 2) * sizeof(float) + 3 * (size_t)ctx->nM * ctx->nmp * sizeof(float);
+}
+
 static tsf_status choose_tiling(tsf3_ctx* ctx) {
     const int prec = ctx->opt.precision;
+    if (ctx->opt.tiling == kTilingDirect) {
+        if (prec != TSF_MIXED)
+            return fail3(ctx, TSF_E_ARG, "the direct micro solve (tiling %d) is a mixed-precision method", kTilingDirect);
+        ctx->tiling = kTilingDirect;
+        return TSF_OK;
+    }
+    if (ctx->opt.tiling < 0 && prec == TSF_MIXED) {
+        size_t free_b = 0, total_b = 0;
+        CU3(cudaMemGetInfo(&free_b, &total_b));
+        if (band_bytes(ctx) <= free_b / 2) {
+            ctx->tiling = kTilingDirect;
+            return TSF_OK;
+        }
+    }
     if (ctx->opt.tiling >= 0) {
         if (!tiling_fits(ctx->opt.tiling, prec, ctx->n1, ctx->smem_optin))
             return fail3(ctx, TSF_E_ARG, "tiling %d does not fit this micro mesh / precision", ctx->opt.tiling);
@@ -878,6 +911,83 @@ static tsf_status choose_tiling(tsf3_ctx* ctx) {
     return TSF_OK;
 }
 
+// FP32 band factor of every S_i (once per geometry and physics), then
+// refinement sweeps on the nsolve right-hand sides set up by k3_setup:
+// x += L^-T L^-1 r, r = c - S x (FP64), until every problem meets the tolerance.
+static tsf_status direct_solves(tsf3_ctx* ctx, int nsolve) {
+    if (!ctx->factor_valid) {
+        if (!ctx->Lband) {
+            CU3(dalloc(ctx, &ctx->Lband, (size_t)ctx->nM * ctx->nm * (ctx->n1 + 2)));
+            for (int t = 0; t < 3; ++t) CU3(dalloc(ctx, &ctx->yband[t], (size_t)ctx->nM * ctx->nmp));
+        }
+        CU3(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
+        BandArgs f{};
+        f.n1 = ctx->n1;
+        f.nm = ctx->nm;
+        f.nmp = ctx->nmp;
+        f.nM = ctx->nM;
+        f.S32 = ctx->S32;
+        f.L = ctx->Lband;
+        f.flag = ctx->flag;
+        CU3(launch_band_factor(f, ctx->stream));
+        int bad = 0;
+        CU3(cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CU3(cudaStreamSynchronize(ctx->stream));
+        if (bad) return fail3(ctx, TSF_E_BREAKDOWN, "non-positive pivot in the FP32 band factor of a micro operator");
+        ctx->factor_valid = true;
+    }
+    BandSolveArgs b{};
+    b.n1 = ctx->n1;
+    b.nm = ctx->nm;
+    b.nmp = ctx->nmp;
+    b.nM = ctx->nM;
+    b.L = ctx->Lband;
+    BandResidualArgs r{};
+    r.n1 = ctx->n1;
+    r.nm = ctx->nm;
+    r.nmp = ctx->nmp;
+    r.nM = ctx->nM;
+    r.nrhs = nsolve;
+    r.tol = ctx->opt.cg_tol;
+    r.S64 = ctx->S64;
+    r.open_count = ctx->open_count;
+    r.ctl = ctx->ctl;
+    for (int t = 0; t < 3; ++t) {
+        b.r[t] = ctx->res[t];
+        b.x[t] = ctx->x[t];
+        b.y[t] = ctx->yband[t];
+        b.done[t] = ctx->done[t];
+        r.c[t] = ctx->c[t];
+        r.x[t] = ctx->x[t];
+        r.r[t] = ctx->res[t];
+        r.bnorm[t] = ctx->bnorm[t];
+        r.done[t] = ctx->done[t];
+    }
+    for (int t = 0; t < nsolve; ++t) CU3(cudaMemsetAsync(ctx->done[t], 0, ctx->nM * sizeof(int), ctx->stream));
+    const int max_sweeps = std::max(ctx->opt.max_sweeps, 30);
+    int open = 1;
+    for (int sweep = 0; sweep < max_sweeps && open; ++sweep) {
+        CU3(launch_band_solve(b, nsolve, ctx->stream));
+        CU3(cudaMemsetAsync(ctx->open_count, 0, sizeof(int), ctx->stream));
+        CU3(launch_band_residual(r, ctx->stream));
+        CU3(cudaMemcpyAsync(&open, ctx->open_count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CU3(cudaStreamSynchronize(ctx->stream));
+    }
+    const unsigned long long solved = (unsigned long long)nsolve * ctx->nM;
+    DevCtl* c = ctx->ctl;
+    // count the solved problems like the iterative kernels do
+    unsigned long long ms = 0;
+    CU3(cudaMemcpyAsync(&ms, &c->micro_solves, sizeof ms, cudaMemcpyDeviceToHost, ctx->stream));
+    CU3(cudaStreamSynchronize(ctx->stream));
+    ms += solved;
+    CU3(cudaMemcpyAsync(&c->micro_solves, &ms, sizeof ms, cudaMemcpyHostToDevice, ctx->stream));
+    if (open) {
+        const int st = (int)TSF_E_NOT_CONVERGED;
+        CU3(cudaMemcpyAsync(&c->status, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return TSF_OK;
+}
+
 tsf_status tsf3_solve(tsf3_ctx* ctx) {
     if (!ctx) return TSF_E_ARG;
     if (!ctx->nM) return fail3(ctx, TSF_E_STATE, "set the meshes first");
@@ -892,7 +1002,11 @@ tsf_status tsf3_solve(tsf3_ctx* ctx) {
     const int nsolve = ctx->phi_valid ? 1 : 3;
     CU3(cudaEventRecord(ctx->ev[0], ctx->stream));
     CU3(enqueue_setup(ctx, nsolve));
-    for (int t = 0; t < nsolve; ++t) CU3(launch_micro_solve(micro3_args(ctx, t), prec, ctx->tiling, ctx->stream));
+    if (ctx->tiling == kTilingDirect) {
+        if ((st = direct_solves(ctx, nsolve))) return st;
+    } else {
+        for (int t = 0; t < nsolve; ++t) CU3(launch_micro_solve(micro3_args(ctx, t), prec, ctx->tiling, ctx->stream));
+    }
     CU3(cudaEventRecord(ctx->ev[1], ctx->stream));
     Moments3Args mo{};
     mo.n1 = ctx->n1;

@@ -278,6 +278,8 @@ cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cud
 //   4..6  column strips of R = 3, 5, 7 nodes with register stencils, mixed only
 //   7..9  column strips of R = 9, 11, 13 nodes with the stencil in shared memory, mixed only
 constexpr int kNumTilings = 10;
+// the three-field system's direct micro solve (banded Cholesky, tsf_band.cu)
+constexpr int kTilingDirect = 10;
 bool tiling_fits(int tiling, int precision, int n1, int smem_optin);
 cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cudaStream_t s);
 bool tiling_uses_stored_residual(int tiling);
@@ -331,6 +333,40 @@ cudaError_t launch_elim_commit(const ElimArgs& a, cudaStream_t s);
 cudaError_t launch_mass_dt(const ElimArgs& a, const double* x, double* out, double* nrm, cudaStream_t s);
 // set-up of the solve S psi = mphi with the stored-residual protocol
 cudaError_t launch_psi_setup(const ElimArgs& a, double* psi, double* cz, const double* mnorm, cudaStream_t s);
+
+// Direct micro solves (tsf_band.cu): FP32 banded Cholesky factor of every
+// micro operator, column k of instance i at L + (i nm + k)(n1 + 2):
+// [1 / L_kk, L_{k+1,k}, ..., L_{k+n1+1,k}].
+struct BandArgs {
+    int n1, nm, nmp, nM;
+    const float* S32;
+    float* L;               // [nM][nm][n1 + 2]
+    int* flag;              // set to 1 on a non-positive pivot
+};
+struct BandSolveArgs {      // x_t += L^-T L^-1 r_t for the right-hand sides not done
+    int n1, nm, nmp, nM;
+    const float* L;
+    const double* r[3];     // [nM][nmp] residuals
+    double* x[3];           // [nM][nmp] solutions, updated
+    float* y[3];            // [nM][nmp] scratch
+    const int* done[3];     // [nM] 1 = converged
+};
+struct BandResidualArgs {   // r_t = c_t - S x_t, done_t = ||r_t|| <= tol ||c_t||
+    int n1, nm, nmp, nM, nrhs;
+    double tol;
+    const double* S64;
+    const double* c[3];
+    const double* x[3];
+    double* r[3];
+    const double* bnorm[3]; // [nM][3], ||c||^2 first
+    int* done[3];
+    int* open_count;        // += right-hand sides still open after this residual
+    DevCtl* ctl;
+};
+size_t band_factor_smem(int n1);
+cudaError_t launch_band_factor(const BandArgs& a, cudaStream_t s);
+cudaError_t launch_band_solve(const BandSolveArgs& a, int nrhs, cudaStream_t s);
+cudaError_t launch_band_residual(const BandResidualArgs& a, cudaStream_t s);
 
 // discrete adjoint (tsf_adjoint.cu)
 struct AdjAccArgs {

@@ -91,15 +91,16 @@ def test_parity_with_the_monolithic_oracle(T, case, precision):
 
 
 def test_every_micro_solve_variant(T):
+    """The ten iterative variants and the direct banded-Cholesky solve."""
     wl = _random_case(3, 20, 5)      # every variant of each precision fits a 21 x 21 micro grid
     _, u0, w0, v0 = _oracle(wl)
     ran = 0
     for precision in (0, 1):
-        for tiling in range(10):
+        for tiling in range(T.TSF3_TILING_DIRECT + 1):
             try:
                 P = _gpu(T, wl, precision, tiling=tiling)
             except T.TsfError as e:
-                assert e.status == T.TSF_E_ARG   # variant does not fit (strips are mixed only)
+                assert e.status == T.TSF_E_ARG   # strips and the direct solve are mixed only
                 continue
             u, w, v, _ = P.fields()
             tol = 1e-10 if precision == 0 else 1e-8
@@ -107,7 +108,7 @@ def test_every_micro_solve_variant(T):
             assert P.stats()["tiling"] == tiling
             ran += 1
             P.close()
-    assert ran == 14   # 4 FP64 + 10 mixed
+    assert ran == 15   # 4 FP64 + 10 mixed + the direct solve
 
 
 @pytest.mark.parametrize("case", [T3.case_a, T3.case_b])
@@ -161,6 +162,17 @@ def test_manufactured_convergence_on_the_gpu(T):
     rates = np.log(E[:-1] / E[1:]) / np.log(2.0)
     assert np.all(np.abs(rates[:, 0] - 2) < 0.06) and np.all(np.abs(rates[:, 2] - 2) < 0.06), rates
     assert np.all(np.abs(rates[:, 1] - 1) < 0.06) and np.all(np.abs(rates[:, 3] - 1) < 0.06), rates
+
+
+@pytest.mark.parametrize("Nm", [1, 2, 30, 64])
+def test_direct_solve_is_the_default_in_mixed_precision(T, Nm):
+    """Band widths 4 .. 67 (one, two and three band slots per lane)."""
+    wl = _random_case(2, Nm, 10 + Nm)
+    _, u0, w0, v0 = _oracle(wl)
+    P = _gpu(T, wl, 1)
+    u, w, v, _ = P.fields()
+    assert P.stats()["tiling"] == T.TSF3_TILING_DIRECT
+    assert _rel(u, u0) < 1e-8 and _rel(w, w0) < 1e-8 and _rel(v, v0) < 1e-8
 
 
 def test_new_sources_reuse_the_elimination_vectors(T):
