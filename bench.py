@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--coupling", default="elimination", choices=["elimination", "partitioned"],
                     help="how each step reaches the coupled solution (the other way is timed beside it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--macro-cells", type=int, default=128, help="t1: macro cells per side (profiling: a smaller case)")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, e2e, cpu baseline")
     return ap.parse_args()
 
@@ -817,10 +818,13 @@ def run_t1(args):
     (16641 nodes, the largest macro mesh of Table 1), 64 x 64 micro cells
     (4225 DoFs each, 70.3 M micro DoFs), mixed precision, tolerance 1e-10.
     Times (i) the complete solve: geometry, the three micro solves (v0, phi_I,
-    phi_O), the coupled macro solve and the commit; (ii) a re-solve for new
-    sources, which re-uses phi_I and phi_O (one micro solve).  Nodal errors
-    against the manufactured solution; CPU baseline: the oracle's monolithic
-    sparse solve of the same problem at 16 x 16 / 16 x 16."""
+    phi_O; direct: the band factorisation and the refinement sweeps), the
+    coupled macro solve and the commit; (ii) a re-solve for new sources,
+    which re-uses phi_I, phi_O and the factor (one right-hand side).  The
+    default micro solve is the direct banded Cholesky one; the fastest
+    iterative variant (tall strips) is timed beside it.  Nodal errors against
+    the manufactured solution; CPU baseline: the oracle's monolithic sparse
+    solve of the same problem at 16 x 16 / 16 x 16."""
     import torch
     import paper_2103_17040_gb300 as T
     from workloads import three_field as T3
@@ -830,66 +834,88 @@ def run_t1(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     T.load_library()
     stream = torch.cuda.Stream()
-    NM, Nm = 128, 64
+    NM, Nm = args.macro_cells, 64
     wl = T3.manufactured(NM, Nm, Dv=1.0, Dw=0.5, kappa=(0.5, 1.0, 0.25, 1.0), tol=1e-10)
-    P = T.ThreeField(Nm, NM, x0=wl.x0, L=wl.L, dir_mask=wl.dir_mask, precision=T.TSF_MIXED, stream=stream,
-                     cg_tol=wl.tol, macro_tol=1e-12)
-    P.set_physics(wl.D, wl.Dw, wl.kappa)
-    P.set_deformation(wl.family, wl.params)
-    P.set_sources(**wl.sources())
-    P.solve()                                   # tunes the micro-solve variant
-    full, resolve = [], []
+    K = max(3, min(args.steps, 10))
+    dofs = wl.nM * wl.nm
+
+    def measure(tiling):
+        P = T.ThreeField(Nm, NM, x0=wl.x0, L=wl.L, dir_mask=wl.dir_mask, precision=T.TSF_MIXED, stream=stream,
+                         cg_tol=wl.tol, macro_tol=1e-12, tiling=tiling)
+        P.set_physics(wl.D, wl.Dw, wl.kappa)
+        P.set_deformation(wl.family, wl.params)
+        P.set_sources(**wl.sources())
+        P.solve()                               # allocates, tunes
+        full, resolve = [], []
+        for rep in range(K):
+            P.set_physics(wl.D, wl.Dw, wl.kappa)    # forces geometry, factor and the phi solves again
+            s0 = P.stats()
+            t0 = time.perf_counter()
+            P.solve()
+            full.append((time.perf_counter() - t0, P.stats(), s0))
+            t0 = time.perf_counter()
+            P.solve()                               # same sources: phi (and the factor) re-used
+            resolve.append((time.perf_counter() - t0, P.stats()))
+        u, w, v, _ = P.fields()
+        P.close()
+        med = lambda xs: statistics.median(xs)
+        st = full[-1][1]
+        r = {"tiling": st["tiling"], "complete_solve_ms": 1e3 * med(x[0] for x in full),
+             "resolve_ms": 1e3 * med(x[0] for x in resolve),
+             "device_ms": {"micro_3_solves": med(x[1]["micro_ms"] for x in full),
+                           "macro": med(x[1]["macro_ms"] for x in full),
+                           "total": med(x[1]["total_ms"] for x in full),
+                           "resolve_micro": med(x[1]["micro_ms"] for x in resolve),
+                           "resolve_total": med(x[1]["total_ms"] for x in resolve)},
+             "refine_sweeps_per_problem": (st["refine_sweeps"] - full[-1][2]["refine_sweeps"]) / wl.nM,
+             "fields": (u, w, v)}
+        if st["tiling"] == T.TSF3_TILING_DIRECT:
+            r["device_ms"]["factor"] = med(x[1]["factor_ms"] for x in full)
+            r["device_ms"]["band_solves"] = med(x[1]["band_solve_ms"] for x in full)
+            r["band_launches"] = st["band_launches"]
+            r["band_solve_ms_per_launch"] = {
+                "3_rhs": med(x[1]["band_solve_ms"] / x[1]["band_launches"] for x in full),
+                "1_rhs": med(x[1]["band_solve_ms"] / x[1]["band_launches"] for x in resolve)}
+        else:
+            iters = st["dof_cg_iters"] - full[-1][2]["dof_cg_iters"]
+            r["micro_dof_cg_iters_per_s"] = iters / (r["device_ms"]["micro_3_solves"] * 1e-3)
+        return r
+
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    K = max(3, min(args.steps, 10))
-    for rep in range(K):
-        P.set_physics(wl.D, wl.Dw, wl.kappa)    # forces geometry and the phi solves again
-        s0 = P.stats()
-        t0 = time.perf_counter()
-        P.solve()
-        full.append((time.perf_counter() - t0, P.stats(), s0))
-        t0 = time.perf_counter()
-        P.solve()                               # same sources: phi re-used, one micro solve
-        resolve.append((time.perf_counter() - t0, P.stats()))
+    d = measure(-1)
     ck = clocks.stop()
-    u, w, v, _ = P.fields()
+    u, w, v = d.pop("fields")
     ue, we, ve = T3.mms_exact(NM, Nm)
-    P.close()
-    dofs = wl.nM * wl.nm
-    tf = statistics.median(x[0] for x in full)
-    tr = statistics.median(x[0] for x in resolve)
-    st_full = full[-1][1]
-    iters_full = st_full["dof_cg_iters"] - full[-1][2]["dof_cg_iters"]
-    micro_ms = statistics.median(x[1]["micro_ms"] for x in full)
-    rate = iters_full / (micro_ms * 1e-3)
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    line = {"metric": "micro DoFs solved/s (stationary three-field solve)", "value": dofs / tf,
-            "unit": "DoF/s", "n_gpus": 1, "steps": K, "warmup": 1, "ms_per_step": 1e3 * tf,
+    # k_band_solve, algorithmic bytes per launch: the factor twice (forward and
+    # backward substitution, nm (Nm+3) FP32 values a problem), and per DoF and
+    # right-hand side: r (8 B), y written and read (4 + 4 B), x updated (16 B)
+    B = Nm + 3
+    bytes_3 = wl.nM * wl.nm * (2 * B * 4 + 3 * 32)
+    ms3 = d["band_solve_ms_per_launch"]["3_rhs"]
+    achieved = bytes_3 / (ms3 * 1e-3) / 1e9
+    line = {"metric": "micro DoFs solved/s (stationary three-field solve)", "value": dofs / (1e-3 * d["complete_solve_ms"]),
+            "unit": "DoF/s", "n_gpus": 1, "steps": K, "warmup": 1, "ms_per_step": d["complete_solve_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "t1: manufactured three-field problem of Eqs. (18)-(19), macro 128x128 on "
-                                   "[-1,1]^2 (Dirichlet u), micro 64x64, mixed, tol 1e-10; inputs larger than L2"},
-            "complete_solve_ms": 1e3 * tf, "resolve_ms": 1e3 * tr,
-            "device_ms": {"micro_3_solves": micro_ms,
-                          "macro": statistics.median(x[1]["macro_ms"] for x in full),
-                          "total": statistics.median(x[1]["total_ms"] for x in full),
-                          "resolve_micro": statistics.median(x[1]["micro_ms"] for x in resolve),
-                          "resolve_total": statistics.median(x[1]["total_ms"] for x in resolve)},
-            "micro_dof_cg_iters_per_s": rate,
-            "roofline": {"bound": "hbm", "achieved": rate * BYTES_PER_DOF_ITER["mixed"] / 1e9,
-                         "peak": peak, "unit": "GB/s", "frac": rate * BYTES_PER_DOF_ITER["mixed"] / 1e9 / peak,
-                         "traffic": None,
-                         "note": "algorithmic bytes of the micro solves (64 B per DoF-iteration); "
-                                 "the solves keep their vectors on chip"},
-            "tiling": st_full["tiling"],
+            "config": {"workload": f"t1: manufactured three-field problem of Eqs. (18)-(19), macro {NM}x{NM} on "
+                                   "[-1,1]^2 (Dirichlet u), micro 64x64, mixed, tol 1e-10; direct micro solves; "
+                                   "inputs larger than L2"},
+            **d,
+            "roofline": {"bound": "hbm", "kernel": "k_band_solve<3>", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None},
             "max_nodal_error": {"u": float(np.abs(u - ue).max()), "w": float(np.abs(w - we).max()),
                                 "v": float(np.abs(v - ve).max())},
             "clocks": ck,
-            # complete solve: expand, geometry, set-up, 3 micro solves, moments, macro, commit, vbar (10);
-            # re-solve: set-up, 1 micro solve, moments, macro, commit, vbar (6)
-            "gpu_launches": 16 * K}
+            # complete solve: expand, geometry, set-up, factor, sweeps x (solve, residual), moments, macro,
+            # commit, vbar; re-solve: set-up, sweeps x (solve, residual), moments, macro, commit, vbar
+            "gpu_launches": K * (8 + 2 * d["band_launches"] + 5 + 2 * d["band_launches"])}
     if not args.no_extras:
+        it = measure(9)
+        it.pop("fields")
+        line["iterative"] = it
         from oracle.three_field import ThreeField
         s = T3.manufactured(16, 16, Dv=1.0, Dw=0.5, kappa=(0.5, 1.0, 0.25, 1.0))
         t0 = time.perf_counter()

@@ -68,6 +68,10 @@ typedef struct {
     double micro_ms;         /* device time of the micro solves of the last tsf3_solve */
     double macro_ms;         /* device time of the macro solve */
     double total_ms;         /* device time of the whole last tsf3_solve */
+    double factor_ms;        /* direct solve: device time of the band factorisation in the last solve (0 if kept) */
+    double band_solve_ms;    /* direct solve: device time of the triangular-solve launches of the last solve */
+    int band_launches;       /* direct solve: triangular-solve launches (refinement sweeps) of the last solve */
+    int band_rhs;            /* direct solve: right-hand sides per launch in the last solve (1 or 3) */
 } tsf3_stats;
 
 /* Uses from tsf_options: precision, cg_tol (micro relative residual),

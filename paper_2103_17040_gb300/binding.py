@@ -68,7 +68,8 @@ class tsf3_stats(ctypes.Structure):
     _fields_ = [("inner_iters", ctypes.c_int64), ("dof_cg_iters", ctypes.c_int64), ("refine_sweeps", ctypes.c_int64),
                 ("micro_solves", ctypes.c_int64), ("macro_iters", ctypes.c_int64), ("status", ctypes.c_int),
                 ("tiling", ctypes.c_int), ("micro_ms", ctypes.c_double), ("macro_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("factor_ms", ctypes.c_double), ("band_solve_ms", ctypes.c_double),
+                ("band_launches", ctypes.c_int), ("band_rhs", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -30,6 +30,8 @@
 #include "tsfem3.h"
 #include "tsf_geom.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -41,12 +43,15 @@
 
 namespace tsf {
 
+namespace cg = cooperative_groups;
+
 // ---------------------------------------------------------------------------
 // geometry: M, S = A + kappa_2 R_I + kappa_4 R_O, and the edge masses of all
 // four edges ([4][nM][n1]: diagonal, coupling to the next node, r = R 1)
 // ---------------------------------------------------------------------------
 struct Geom3Args {
     int Nm, n1, nm, nmp, nM;
+    int affine;             // 1: identity or affine family (F constant per problem)
     const double* prm5;
     double D11, D12, D22, k2, k4;
     double* M64;
@@ -59,7 +64,14 @@ struct Geom3Args {
     DevCtl* ctl;
 };
 
+// AFFINE: reference-table path (separate instantiation, as in k_geometry)
+template <bool AFFINE>
 __global__ void __launch_bounds__(128) k3_geometry(Geom3Args a) {
+    __shared__ double ref[AFFINE ? 64 : 1];
+    if constexpr (AFFINE) {
+        fill_reference_tables(ref);
+        __syncthreads();
+    }
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     const int i = blockIdx.x;
     if (j >= a.nmp) return;
@@ -81,7 +93,8 @@ __global__ void __launch_bounds__(128) k3_geometry(Geom3Args a) {
     const Deform d = load_deform(a.prm5, i);
     double m[kPlanes], k[kPlanes], lump;
     bool bad;
-    node_couplings(d, a.D11, a.D12, a.D22, p, q, N, m, k, lump, bad);
+    if constexpr (AFFINE) node_couplings_affine(d, a.D11, a.D12, a.D22, p, q, N, ref, m, k, lump, bad);
+    else node_couplings(d, a.D11, a.D12, a.D22, p, q, N, m, k, lump, bad);
     // edge masses; the Robin edges add to S (their couplings run along q: plane 2)
     const bool on_edge[4] = {p == 0, p == N, q == 0, q == N};
     const int along[4] = {q, q, p, p};
@@ -260,9 +273,9 @@ __global__ void __launch_bounds__(128) k3_moments(Moments3Args a) {
 
 // ---------------------------------------------------------------------------
 // coupled macro solve in (u, w): PCG with 2x2 block-Jacobi preconditioner,
-// matrix-free on the uniform mesh, one thread block
+// matrix-free on the uniform mesh, one cooperative grid
 // ---------------------------------------------------------------------------
-constexpr int kMacro3Threads = 1024;
+constexpr int kMacro3Threads = 256;
 
 struct Macro3Args {
     int NM, N1, nM, dir_mask;
@@ -339,15 +352,44 @@ __device__ __forceinline__ void macro3_apply(const Macro3Args& a, const double* 
     y[nM + k] = fma(a.sw * a.Dw, stiff_apply(x + nM, k, p, q, N, n1), fma(c[1], xw, c[2] * xu));
 }
 
-__global__ void __launch_bounds__(kMacro3Threads, 1) k3_macro(Macro3Args a) {
-    __shared__ double red[4 * 96];
-    const int tid = threadIdx.x, T = blockDim.x;
-    const int nM = a.nM, n1 = a.N1, N = a.NM;
+// Sum over the blocks of the per-block partials part[b][slot] (after a grid
+// barrier); every block sums them in the same order, so all get the same value.
+__device__ __forceinline__ double grid_total(const double* part, int slot, double* buf) {
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) v[0] += part[4 * b + slot];
+    block_allreduce<double, 1>(v, buf);
+    return v[0];
+}
+
+// One cooperative grid (all blocks resident), one macro node per thread for
+// both fields; three grid barriers per CG iteration.  part: [gridDim.x][4].
+__global__ void __launch_bounds__(kMacro3Threads) k3_macro(Macro3Args a, double* part) {
+    cg::grid_group grid = cg::this_grid();
+    // four reduction buffers of 64 (a two-value block reduction uses 64);
+    // consecutive reductions rotate through them, so a buffer is reused only
+    // after three more block-wide barriers
+    __shared__ double red[4 * 64];
     int rb = 0;
-    auto nextbuf = [&]() { double* b = red + 96 * rb; rb = (rb + 1) & 3; return b; };
+    auto nextbuf = [&]() { double* b = red + 64 * rb; rb = (rb + 1) & 3; return b; };
+    const int nM = a.nM, n1 = a.N1, N = a.NM;
+    const int T = gridDim.x * blockDim.x;
+    const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+    auto block_partial = [&](double v, int slot) {
+        double t[1] = {v};
+        block_allreduce<double, 1>(t, nextbuf());
+        if (threadIdx.x == 0) part[4 * blockIdx.x + slot] = t[0];
+    };
+    auto block_partial2 = [&](double v0, double v1, int slot) {
+        double t[2] = {v0, v1};
+        block_allreduce<double, 2>(t, nextbuf());
+        if (threadIdx.x == 0) {
+            part[4 * blockIdx.x + slot] = t[0];
+            part[4 * blockIdx.x + slot + 1] = t[1];
+        }
+    };
     // right-hand side (in q), initial iterate (Dirichlet values of u, zero
     // elsewhere) and the inverse 2x2 diagonal blocks
-    for (int k = tid; k < nM; k += T) {
+    for (int k = k0; k < nM; k += T) {
         const int p = k % n1, q = k / n1;
         const double* c = a.coef + (size_t)k * 5;
         const bool dir = dir_node3(a.dir_mask, N, p, q);
@@ -378,53 +420,41 @@ __global__ void __launch_bounds__(kMacro3Threads, 1) k3_macro(Macro3Args a) {
             pi[2] = a11 * id;
         }
     }
-    __syncthreads();
-    // r = b - A x0 (x0 carries only the Dirichlet values)
-    double rr = 0.0;
-    for (int k = tid; k < nM; k += T) {
+    grid.sync();
+    // r = b - A x0 (x0 carries only the Dirichlet values), z = P r, p = z
+    double rr = 0.0, rz = 0.0;
+    for (int k = k0; k < nM; k += T) {
         const int p = k % n1, q = k / n1;
         macro3_apply(a, a.x, a.r, k, p, q);
         const double ru = a.qv[k] - a.r[k], rw = a.qv[nM + k] - a.r[nM + k];
         a.r[k] = ru;
         a.r[nM + k] = rw;
+        const double* pi = a.pinv + (size_t)k * 3;
+        const double zu = fma(pi[0], ru, pi[1] * rw), zw = fma(pi[1], ru, pi[2] * rw);
+        a.pv[k] = zu;
+        a.pv[nM + k] = zw;
         rr = fma(ru, ru, fma(rw, rw, rr));
+        rz = fma(ru, zu, fma(rw, zw, rz));
     }
-    {
-        double t[1] = {rr};
-        block_allreduce<double, 1>(t, nextbuf());
-        rr = t[0];
-    }
+    block_partial2(rr, rz, 0);
+    grid.sync();
+    rr = grid_total(part, 0, nextbuf());
+    rz = grid_total(part, 1, nextbuf());
     const double stop2 = a.tol * a.tol * rr;
     int it = 0;
     bool fail = false;
     if (rr > 0.0) {
-        double rz = 0.0;
-        for (int k = tid; k < nM; k += T) {
-            const double* pi = a.pinv + (size_t)k * 3;
-            const double ru = a.r[k], rw = a.r[nM + k];
-            const double zu = fma(pi[0], ru, pi[1] * rw), zw = fma(pi[1], ru, pi[2] * rw);
-            a.pv[k] = zu;
-            a.pv[nM + k] = zw;
-            rz = fma(ru, zu, fma(rw, zw, rz));
-        }
-        {
-            double t[1] = {rz};
-            block_allreduce<double, 1>(t, nextbuf());
-            rz = t[0];
-        }
         while (it < a.maxit) {
-            __syncthreads();   // p complete before the neighbours read it
+            // p is complete (barrier above / at the end of the previous iteration)
             double pq = 0.0;
-            for (int k = tid; k < nM; k += T) {
+            for (int k = k0; k < nM; k += T) {
                 const int p = k % n1, q = k / n1;
                 macro3_apply(a, a.pv, a.qv, k, p, q);
                 pq = fma(a.pv[k], a.qv[k], fma(a.pv[nM + k], a.qv[nM + k], pq));
             }
-            {
-                double t[1] = {pq};
-                block_allreduce<double, 1>(t, nextbuf());
-                pq = t[0];
-            }
+            block_partial(pq, 2);
+            grid.sync();
+            pq = grid_total(part, 2, nextbuf());
             ++it;
             if (!(pq > 0.0)) {
                 fail = true;
@@ -432,7 +462,7 @@ __global__ void __launch_bounds__(kMacro3Threads, 1) k3_macro(Macro3Args a) {
             }
             const double alpha = rz / pq;
             double rn2 = 0.0, rzn = 0.0;
-            for (int k = tid; k < nM; k += T) {
+            for (int k = k0; k < nM; k += T) {
                 a.x[k] = fma(alpha, a.pv[k], a.x[k]);
                 a.x[nM + k] = fma(alpha, a.pv[nM + k], a.x[nM + k]);
                 const double ru = fma(-alpha, a.qv[k], a.r[k]), rw = fma(-alpha, a.qv[nM + k], a.r[nM + k]);
@@ -445,12 +475,10 @@ __global__ void __launch_bounds__(kMacro3Threads, 1) k3_macro(Macro3Args a) {
                 rn2 = fma(ru, ru, fma(rw, rw, rn2));
                 rzn = fma(ru, zu, fma(rw, zw, rzn));
             }
-            {
-                double t[2] = {rn2, rzn};
-                block_allreduce<double, 2>(t, nextbuf());
-                rn2 = t[0];
-                rzn = t[1];
-            }
+            block_partial2(rn2, rzn, 0);
+            grid.sync();
+            rn2 = grid_total(part, 0, nextbuf());
+            rzn = grid_total(part, 1, nextbuf());
             if (!(rn2 == rn2)) {
                 fail = true;
                 break;
@@ -458,16 +486,19 @@ __global__ void __launch_bounds__(kMacro3Threads, 1) k3_macro(Macro3Args a) {
             if (rn2 <= stop2) break;
             const double beta = rzn / rz;
             rz = rzn;
-            for (int k = tid; k < 2 * nM; k += T) a.pv[k] = fma(beta, a.pv[k], a.z[k]);
+            for (int k = k0; k < nM; k += T) {
+                a.pv[k] = fma(beta, a.pv[k], a.z[k]);
+                a.pv[nM + k] = fma(beta, a.pv[nM + k], a.z[nM + k]);
+            }
+            grid.sync();
         }
         if (it >= a.maxit) fail = true;
     }
-    __syncthreads();
-    for (int k = tid; k < nM; k += T) {
+    for (int k = k0; k < nM; k += T) {
         a.u[k] = a.x[k];
         a.w[k] = a.x[nM + k];
     }
-    if (tid == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctl->macro_iters += (unsigned long long)it;
         if (fail) set_status(a.ctl, kNotConverged);
     }
@@ -515,6 +546,7 @@ struct tsf3_ctx {
     double *zero = nullptr, *rho = nullptr, *G = nullptr, *coef = nullptr, *vol = nullptr;
     double *u = nullptr, *w = nullptr, *v = nullptr, *vbar = nullptr;
     double *mx = nullptr, *mr = nullptr, *mz = nullptr, *mp = nullptr, *mq = nullptr, *pinv = nullptr;
+    double* mpart = nullptr;    // [blocks][4] partial sums of the cooperative macro solve
     DevCtl* ctl = nullptr;
     bool geom_valid = false, phi_valid = false, solved = false;
     int tiling = -1;
@@ -526,6 +558,7 @@ struct tsf3_ctx {
     int* flag = nullptr;
     bool factor_valid = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t bev[2] = {nullptr, nullptr};    // direct solve: factor and triangular-solve timing
     tsf3_stats stats{};
     std::string err;
 };
@@ -597,12 +630,15 @@ tsf_status tsf3_create(tsf3_ctx** out, const tsf_options* opt) {
         }
     }
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ctx->ev[k]);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreate(&ctx->bev[k]);
     if (e == cudaSuccess) e = configure_micro_kernels(ctx->smem_optin);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->ctl, sizeof(DevCtl));
     if (e == cudaSuccess) e = cudaMemset(ctx->ctl, 0, sizeof(DevCtl));
     if (e != cudaSuccess) {
         for (int k = 0; k < 4; ++k)
             if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+        for (int k = 0; k < 2; ++k)
+            if (ctx->bev[k]) cudaEventDestroy(ctx->bev[k]);
         if (ctx->ctl) cudaFree(ctx->ctl);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
@@ -617,6 +653,8 @@ void tsf3_destroy(tsf3_ctx* ctx) {
     free_all(ctx);
     for (int k = 0; k < 4; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    for (int k = 0; k < 2; ++k)
+        if (ctx->bev[k]) cudaEventDestroy(ctx->bev[k]);
     if (ctx->ctl) cudaFree(ctx->ctl);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -691,6 +729,7 @@ tsf_status tsf3_set_meshes(tsf3_ctx* ctx, int Nm, int NM, double x0, double L, i
     CU3(dalloc(ctx, &ctx->mp, 2 * nM));
     CU3(dalloc(ctx, &ctx->mq, 2 * nM));
     CU3(dalloc(ctx, &ctx->pinv, 3 * nM));
+    CU3(dalloc(ctx, &ctx->mpart, 4 * ((nM + kMacro3Threads - 1) / kMacro3Threads) + 4));
     for (int t = 0; t < 3; ++t) CU3(dalloc(ctx, &ctx->done[t], nM));
     CU3(dalloc(ctx, &ctx->open_count, 1));
     CU3(dalloc(ctx, &ctx->flag, 1));
@@ -844,8 +883,10 @@ static tsf_status build_geometry(tsf3_ctx* ctx) {
     g.eRu = ctx->eRu;
     g.er = ctx->er;
     g.ctl = ctx->ctl;
+    g.affine = ctx->family == TSF_FAMILY_IDENTITY || ctx->family == TSF_FAMILY_AFFINE;
     dim3 grid(ctx->nM, (ctx->nmp + 127) / 128);
-    k3_geometry<<<grid, 128, 0, ctx->stream>>>(g);
+    if (g.affine) k3_geometry<true><<<grid, 128, 0, ctx->stream>>>(g);
+    else k3_geometry<false><<<grid, 128, 0, ctx->stream>>>(g);
     CU3(cudaGetLastError());
     int bad = 0;
     CU3(cudaMemcpyAsync(&bad, &ctx->ctl->geom_error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -915,6 +956,10 @@ static tsf_status choose_tiling(tsf3_ctx* ctx) {
 // refinement sweeps on the nsolve right-hand sides set up by k3_setup:
 // x += L^-T L^-1 r, r = c - S x (FP64), until every problem meets the tolerance.
 static tsf_status direct_solves(tsf3_ctx* ctx, int nsolve) {
+    ctx->stats.factor_ms = 0.0;
+    ctx->stats.band_solve_ms = 0.0;
+    ctx->stats.band_launches = 0;
+    ctx->stats.band_rhs = nsolve;
     if (!ctx->factor_valid) {
         if (!ctx->Lband) {
             CU3(dalloc(ctx, &ctx->Lband, (size_t)ctx->nM * ctx->nm * (ctx->n1 + 2)));
@@ -929,10 +974,15 @@ static tsf_status direct_solves(tsf3_ctx* ctx, int nsolve) {
         f.S32 = ctx->S32;
         f.L = ctx->Lband;
         f.flag = ctx->flag;
+        CU3(cudaEventRecord(ctx->bev[0], ctx->stream));
         CU3(launch_band_factor(f, ctx->stream));
+        CU3(cudaEventRecord(ctx->bev[1], ctx->stream));
         int bad = 0;
         CU3(cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         CU3(cudaStreamSynchronize(ctx->stream));
+        float fm = 0.f;
+        CU3(cudaEventElapsedTime(&fm, ctx->bev[0], ctx->bev[1]));
+        ctx->stats.factor_ms = fm;
         if (bad) return fail3(ctx, TSF_E_BREAKDOWN, "non-positive pivot in the FP32 band factor of a micro operator");
         ctx->factor_valid = true;
     }
@@ -967,11 +1017,17 @@ static tsf_status direct_solves(tsf3_ctx* ctx, int nsolve) {
     const int max_sweeps = std::max(ctx->opt.max_sweeps, 30);
     int open = 1;
     for (int sweep = 0; sweep < max_sweeps && open; ++sweep) {
+        CU3(cudaEventRecord(ctx->bev[0], ctx->stream));
         CU3(launch_band_solve(b, nsolve, ctx->stream));
+        CU3(cudaEventRecord(ctx->bev[1], ctx->stream));
         CU3(cudaMemsetAsync(ctx->open_count, 0, sizeof(int), ctx->stream));
         CU3(launch_band_residual(r, ctx->stream));
         CU3(cudaMemcpyAsync(&open, ctx->open_count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         CU3(cudaStreamSynchronize(ctx->stream));
+        float sm = 0.f;
+        CU3(cudaEventElapsedTime(&sm, ctx->bev[0], ctx->bev[1]));
+        ctx->stats.band_solve_ms += sm;
+        ctx->stats.band_launches += 1;
     }
     const unsigned long long solved = (unsigned long long)nsolve * ctx->nM;
     DevCtl* c = ctx->ctl;
@@ -986,6 +1042,21 @@ static tsf_status direct_solves(tsf3_ctx* ctx, int nsolve) {
         CU3(cudaMemcpyAsync(&c->status, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
     }
     return TSF_OK;
+}
+
+// The coupled macro solve as one cooperative grid: one node per thread, at
+// most as many blocks as can be resident at once.
+static cudaError_t launch_macro3(tsf3_ctx* ctx, Macro3Args& ma) {
+    int per_sm = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_macro, kMacro3Threads, 0);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int want = (ctx->nM + kMacro3Threads - 1) / kMacro3Threads;
+    const int blocks = std::max(1, std::min(want, per_sm * sms));
+    double* part = ctx->mpart;
+    void* args[] = {&ma, &part};
+    return cudaLaunchCooperativeKernel((void*)k3_macro, dim3(blocks), dim3(kMacro3Threads), args, 0, ctx->stream);
 }
 
 tsf_status tsf3_solve(tsf3_ctx* ctx) {
@@ -1055,8 +1126,7 @@ tsf_status tsf3_solve(tsf3_ctx* ctx) {
     ma.tol = ctx->opt.macro_tol;
     ma.maxit = std::max(ctx->opt.macro_maxit, 50 * ctx->N1);
     ma.ctl = ctx->ctl;
-    k3_macro<<<1, kMacro3Threads, 0, ctx->stream>>>(ma);
-    CU3(cudaGetLastError());
+    CU3(launch_macro3(ctx, ma));
     CU3(cudaEventRecord(ctx->ev[2], ctx->stream));
     const size_t total = (size_t)ctx->nM * ctx->nmp;
     k3_commit<<<(unsigned)std::min<size_t>((total + 255) / 256, 152 * 16), 256, 0, ctx->stream>>>(

@@ -478,6 +478,7 @@ static tsf_status copy_field_in(tsf_ctx* ctx, double* dst, const double* src, in
 
 static tsf_status build_operators(tsf_ctx* ctx, double dt) {
     GeomArgs a{};
+    a.affine = ctx->family == TSF_FAMILY_IDENTITY || ctx->family == TSF_FAMILY_AFFINE;
     a.Nm = ctx->Nm;
     a.n1 = ctx->n1;
     a.nm = ctx->nm;
@@ -522,12 +523,12 @@ tsf_status tsf_set_deformation(tsf_ctx* ctx, int family, int nparam, const doubl
     }
     CU(launch_expand_params(family, nparam, ctx->vtmp, ctx->prm5, ctx->map32, ctx->nM, ctx->stream));
     CU(cudaMemsetAsync(&ctx->ctl->geom_error, 0, sizeof(int), ctx->stream));
+    ctx->family = family;   // before the operators: it selects the geometry kernel
     st = build_operators(ctx, 1.0);
     if (st) return st;
     int gerr = 0;
     CU(cudaMemcpyAsync(&gerr, &ctx->ctl->geom_error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    ctx->family = family;
     invalidate_graph(ctx);
     if (gerr) {
         ctx->geom_set = false;

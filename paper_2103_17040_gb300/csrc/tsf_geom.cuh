@@ -101,6 +101,81 @@ __device__ __forceinline__ void node_couplings(const Deform& d, double D11, doub
     }
 }
 
+// Reference element tables of the unit square with 2x2 Gauss points (exact
+// for Q1): ref[0..15] = int phi_a phi_b, ref[16..31] = int d_s phi_a d_s phi_b,
+// ref[32..47] = int d_s phi_a d_t phi_b, ref[48..63] = int d_t phi_a d_t phi_b,
+// entry a * 4 + b.  Filled by threads 0..15 of a block.
+__device__ __forceinline__ void fill_reference_tables(double* ref) {
+    const int e = threadIdx.x;
+    if (e >= 16) return;
+    const int la = e >> 2, lb = e & 3;
+    double m = 0.0, ss = 0.0, st = 0.0, tt = 0.0;
+    for (int qt = 0; qt < 2; ++qt) {
+        const double t = qt ? kGauss1 : kGauss0;
+        for (int qs = 0; qs < 2; ++qs) {
+            const double s = qs ? kGauss1 : kGauss0;
+            const double phi[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
+            const double dsv[4] = {-(1 - t), (1 - t), -t, t};
+            const double dtv[4] = {-(1 - s), -s, (1 - s), s};
+            m += 0.25 * phi[la] * phi[lb];
+            ss += 0.25 * dsv[la] * dsv[lb];
+            st += 0.25 * dsv[la] * dtv[lb];
+            tt += 0.25 * dtv[la] * dtv[lb];
+        }
+    }
+    ref[e] = m;
+    ref[16 + e] = ss;
+    ref[32 + e] = st;
+    ref[48 + e] = tt;
+}
+
+// node_couplings for an affine map (b = 0): F, J and C are the same at every
+// quadrature point, so the element matrices are J h^2 Mref and
+// C11 Kss + C12 (Kst + Kst^T) + C22 Ktt of the reference tables.
+__device__ __forceinline__ void node_couplings_affine(const Deform& d, double D11, double D12, double D22, int p,
+                                                      int q, int N, const double* ref, double (&m)[kPlanes],
+                                                      double (&k)[kPlanes], double& lump, bool& bad) {
+    const double h = 1.0 / N;
+#pragma unroll
+    for (int c = 0; c < kPlanes; ++c) m[c] = k[c] = 0.0;
+    lump = 0.0;
+    const double F11 = d.A11, F12 = d.A12, F21 = d.A21, F22 = d.A22;
+    const double J = F11 * F22 - F12 * F21;
+    bad = !(J > 0.0);
+    const double G11 = F22, G12 = -F12, G21 = -F21, G22 = F11;
+    const double GD11 = G11 * D11 + G12 * D12, GD12 = G11 * D12 + G12 * D22;
+    const double GD21 = G21 * D11 + G22 * D12, GD22 = G21 * D12 + G22 * D22;
+    const double iJ = 1.0 / J;
+    const double C11 = (GD11 * G11 + GD12 * G12) * iJ;
+    const double C12 = (GD11 * G21 + GD12 * G22) * iJ;
+    const double C22 = (GD21 * G21 + GD22 * G22) * iJ;
+    const double Jh2 = J * h * h;
+    for (int cb = 0; cb < 2; ++cb) {
+        const int b = q - 1 + cb;
+        if (b < 0 || b >= N) continue;
+        for (int ca = 0; ca < 2; ++ca) {
+            const int ac = p - 1 + ca;
+            if (ac < 0 || ac >= N) continue;
+            const int lx = p - ac, ly = q - b, la = lx + 2 * ly;
+            for (int lb = 0; lb < 4; ++lb) {
+                const int e = la * 4 + lb;
+                const double me = Jh2 * ref[e];
+                lump += me;
+                const int dp = (lb & 1) - lx, dq = (lb >> 1) - ly;
+                int plane = -1;
+                if (dp == 0 && dq == 0) plane = 0;
+                else if (dp == 1 && dq == 0) plane = 1;
+                else if (dp == 0 && dq == 1) plane = 2;
+                else if (dp == 1 && dq == 1) plane = 3;
+                else if (dp == -1 && dq == 1) plane = 4;
+                if (plane < 0) continue;
+                m[plane] += me;
+                k[plane] += C11 * ref[16 + e] + C12 * (ref[32 + e] + ref[32 + lb * 4 + la]) + C22 * ref[48 + e];
+            }
+        }
+    }
+}
+
 // Edges of the reference cell: 0 yhat_1 = 0, 1 yhat_1 = 1 (the nodes are
 // numbered by q along them), 2 yhat_2 = 0, 3 yhat_2 = 1 (numbered by p).
 enum : int { kEdgeLeft = 0, kEdgeRight = 1, kEdgeBottom = 2, kEdgeTop = 3 };
@@ -116,13 +191,14 @@ __device__ __forceinline__ void edge_node_mass(const Deform& d, int edge, int t,
     const bool vertical = edge == kEdgeLeft || edge == kEdgeRight;
     double sf, cf;  // sin/cos of pi times the fixed coordinate (0 or 1)
     sincospi((edge == kEdgeRight || edge == kEdgeTop) ? 1.0 : 0.0, &sf, &cf);
+    const bool affine = d.bpi == 0.0;   // F = A: no trigonometry needed
     for (int seg = 0; seg < 2; ++seg) {
         const int b = t - 1 + seg;  // segment [b, b+1]
         if (b < 0 || b >= N) continue;
         for (int qt = 0; qt < 2; ++qt) {
             const double g = qt ? kGauss1 : kGauss0;
-            double sa, ca;
-            sincospi((b + g) * h, &sa, &ca);
+            double sa = 0.0, ca = 1.0;
+            if (!affine) sincospi((b + g) * h, &sa, &ca);
             double F11, F12, F21, F22;
             if (vertical) jacobian(d, sf, cf, sa, ca, F11, F12, F21, F22);
             else jacobian(d, sa, ca, sf, cf, F11, F12, F21, F22);

@@ -87,8 +87,18 @@ cudaError_t launch_pushforward(int Nm, int n1, int nm, int nmp, int NM, int nM, 
 // One thread per (micro node j, instance i): the five stored couplings of
 // node j in M and in S = M/dt + A + kappa R, summed over the (up to four)
 // cells around the node with 2x2 Gauss points; on Robin-edge nodes also the
-// boundary mass R (2-point Gauss per edge segment).
+// boundary mass R (2-point Gauss per edge segment).  AFFINE (identity and
+// affine families): F is constant, the element matrices come from the
+// reference tables.  The two paths are separate instantiations: with both
+// in one kernel behind a run-time branch on b = 0, the general path gave
+// wrong couplings on the GPU (cause not found; each path alone is correct).
+template <bool AFFINE>
 __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
+    __shared__ double ref[AFFINE ? 64 : 1];
+    if constexpr (AFFINE) {
+        fill_reference_tables(ref);
+        __syncthreads();
+    }
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     const int i = blockIdx.x;  // instances on grid.x (up to 2^31 - 1); nodes on grid.y
     if (j >= a.nmp) return;
@@ -110,7 +120,8 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
     const Deform d = load_deform(a.prm5, i);
     double m[kPlanes], k[kPlanes], lump;
     bool bad;
-    node_couplings(d, a.D11, a.D12, a.D22, p, q, N, m, k, lump, bad);
+    if constexpr (AFFINE) node_couplings_affine(d, a.D11, a.D12, a.D22, p, q, N, ref, m, k, lump, bad);
+    else node_couplings(d, a.D11, a.D12, a.D22, p, q, N, m, k, lump, bad);
 
     // Robin edge yhat_1 = 1: R = int s eta eta with s = |cof(F) e1| = sqrt(F22^2 + F12^2)
     double Rd = 0.0, Ru = 0.0, Rdn = 0.0;
@@ -140,7 +151,8 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
 
 cudaError_t launch_geometry(const GeomArgs& a, cudaStream_t s) {
     dim3 grid(a.nM, (a.nmp + 127) / 128);
-    k_geometry<<<grid, 128, 0, s>>>(a);
+    if (a.affine) k_geometry<true><<<grid, 128, 0, s>>>(a);
+    else k_geometry<false><<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -144,6 +144,7 @@ __device__ __forceinline__ double plane_apply(const double* __restrict__ A, size
 // ---------------------------------------------------------------------------
 struct GeomArgs {
     int Nm, n1, nm, nmp, nM;
+    int affine;             // 1: every map has b = 0 (identity and affine families)
     const double* prm5;     // [nM][5] general form (A11, A12, A21, A22, b)
     double D11, D12, D22, kappa, dt;
     double* M64;            // [nM][5][nmp] mass planes

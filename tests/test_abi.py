@@ -64,10 +64,10 @@ def test_options_struct_layout_matches_header():
 #include <stddef.h>
 #include "tsfem3.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tsf_options), offsetof(tsf_options, cuda_stream),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tsf_options), offsetof(tsf_options, cuda_stream),
          offsetof(tsf_options, coupling), sizeof(tsf_stats), offsetof(tsf_stats, coupling_change),
          offsetof(tsf_stats, steps), sizeof(tsf3_stats), offsetof(tsf3_stats, tiling),
-         offsetof(tsf3_stats, total_ms));
+         offsetof(tsf3_stats, total_ms), offsetof(tsf3_stats, band_rhs));
   return 0;
 }'''
     src = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"tsf_layout_{os.getpid()}.c")
@@ -79,5 +79,6 @@ int main(void) {
     os.remove(exe)
     exp = [ctypes.sizeof(T.tsf_options), T.tsf_options.cuda_stream.offset, T.tsf_options.coupling.offset,
            ctypes.sizeof(T.tsf_stats), T.tsf_stats.coupling_change.offset, T.tsf_stats.steps.offset,
-           ctypes.sizeof(T.tsf3_stats), T.tsf3_stats.tiling.offset, T.tsf3_stats.total_ms.offset]
+           ctypes.sizeof(T.tsf3_stats), T.tsf3_stats.tiling.offset, T.tsf3_stats.total_ms.offset,
+           T.tsf3_stats.band_rhs.offset]
     assert [int(x) for x in out] == exp
