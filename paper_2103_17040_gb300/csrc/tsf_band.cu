@@ -13,7 +13,7 @@
 // k_band_factor: one block per micro problem, right-looking band Cholesky on
 // a B x B sliding window of the trailing matrix in shared memory (circular
 // row/column slots); a finished column leaves the window, the next row of S
-// (its five stored couplings) enters it.
+// (its five stored couplings, staged ahead with cp.async) enters it.
 // k_band_solve: one warp per micro problem: forward substitution with the
 // pending right-hand side values spread over the lanes (3 slots a lane),
 // backward substitution as one warp dot product per column.
@@ -23,12 +23,28 @@
 
 namespace tsf {
 
-constexpr int kBandFactorThreads = 256;
+constexpr int kBandFactorThreads = 128;  // four warps per micro problem
+
+// Staging of the stencil values of the rows that enter the window: chunk c
+// (steps 32c .. 32c+31) brings rows j = B + 32c .. B + 32c + 31, whose
+// couplings sit at node indices lo = j0 - n1 - 1 .. j0 + 31: n1 + 33 values
+// per plane, two chunks in flight (cp.async, loaded one chunk ahead).
+__host__ __device__ __forceinline__ int band_stage_len(int n1) { return n1 + 33; }
 
 size_t band_factor_smem(int n1) {
-    const int B = n1 + 2, bw = B - 1;
-    return (size_t)B * B * sizeof(float) + (size_t)B * sizeof(float) + (size_t)bw * (bw + 1) / 2 * sizeof(uint16_t);
+    const int B = n1 + 2;
+    size_t b = (size_t)B * B * sizeof(float) + (size_t)B * sizeof(float);
+    b = (b + 15) & ~(size_t)15;
+    return b + 2 * (size_t)kPlanes * band_stage_len(n1) * sizeof(float);
 }
+
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 4 : 0;                        // 0: zero-fill, nothing read
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // S coupling of node g = (p, q) to node h <= g (both in [0, nm)), FP32
 // stencil planes.  The four lower neighbours are stored at h: W = E(h),
@@ -46,38 +62,72 @@ __device__ __forceinline__ float band_entry(const float* S, size_t pl, int n1, i
     return v;
 }
 
+// band_entry on staged plane values: st = one chunk's [kPlanes][len] values
+// starting at node index lo
+__device__ __forceinline__ float band_entry_staged(const float* st, int len, int lo, int n1, int g, int h) {
+    const int d = g - h;
+    const int p = g % n1;
+    if (d == 0) return st[g - lo];
+    float v = 0.f;
+    if (d == 1 && p > 0) v = st[len + h - lo];                     // west: E(h)
+    if (d == n1 - 1 && p + 1 < n1) v = st[4 * len + h - lo];       // south-east: NW(h)
+    if (d == n1) v = st[2 * len + h - lo];                         // south: N(h)
+    if (d == n1 + 1 && p > 0) v = st[3 * len + h - lo];            // south-west: NE(h)
+    return v;
+}
+
+// kBandFactorWarps warps per micro problem.  Lane l of every warp owns the
+// window columns s = l+1 + 32 g (g < NG = ceil((n1 + 1) / 32)); warp w walks
+// its contiguous share of the rows: the lanes of a warp touch the same row
+// at the same time (col[t] is a broadcast) and consecutive columns.
+template <int NG>
 __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n1 = a.n1, nm = a.nm, B = n1 + 2, bw = B - 1;
     float* W = reinterpret_cast<float*>(smem);        // [B][B], row = slot of the larger index
     float* col = W + B * B;                           // [B]
-    uint16_t* pairs = reinterpret_cast<uint16_t*>(col + B);
-    const int npairs = bw * (bw + 1) / 2;
-    const int i = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+    size_t off = (size_t)B * B * sizeof(float) + (size_t)B * sizeof(float);
+    off = (off + 15) & ~(size_t)15;
+    const int slen = band_stage_len(n1);
+    float* stage = reinterpret_cast<float*>(smem + off);   // [2][kPlanes][slen]
+    const int i = blockIdx.x, tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = T >> 5;
     const size_t pl = (size_t)a.nmp;
     const float* S = a.S32 + (size_t)i * kPlanes * pl;
     float* L = a.L + (size_t)i * nm * B;
-    // (t, s) pairs of the rank-1 update, 1 <= s <= t <= bw
-    for (int idx = tid; idx < npairs; idx += T) {
-        int t = (int)((sqrtf(8.f * idx + 1.f) - 1.f) * 0.5f);
-        while ((t + 1) * (t + 2) / 2 <= idx) ++t;
-        while (t * (t + 1) / 2 > idx) --t;
-        const int s = idx - t * (t + 1) / 2;          // 0 <= s <= t
-        pairs[idx] = (uint16_t)(((t + 1) << 8) | (s + 1));
-    }
+    // this warp's rows t in [t0, t1) of 1 .. bw
+    const int per = (bw + nw - 1) / nw;
+    const int t0 = 1 + warp * per, t1 = min(bw + 1, t0 + per);
+    // chunk c of entering rows into stage buffer c & 1
+    auto issue_chunk = [&](int c) {
+        const int lo = B + 32 * c - n1 - 1;
+        float* st = stage + (c & 1) * kPlanes * slen;
+        for (int e = tid; e < kPlanes * slen; e += T) {
+            const int plane = e / slen, idx = lo + e % slen;
+            const bool ok = idx >= 0 && idx < nm;
+            cp_async4(st + e, S + plane * pl + (ok ? idx : 0), ok);
+        }
+        cp_async_commit();
+    };
+    issue_chunk(0);
     // initial window: rows 0..bw
     for (int e = tid; e < B * B; e += T) {
         const int g = e / B, h = e % B;
         W[e] = (g < nm && h <= g) ? band_entry(S, pl, n1, g, h) : 0.f;
     }
-    __syncthreads();
     bool bad = false;
     for (int k = 0; k < nm; ++k) {
         const int base = k % B;
+        if ((k & 31) == 0) {
+            // the chunk of this step's entering rows is complete; fetch the next one
+            cp_async_wait_all();
+            __syncthreads();
+            issue_chunk((k >> 5) + 1);
+        }
         // finished column k
         if (tid < B) {
             const float d = W[base * B + base];
-            const float r = 1.0f / sqrtf(d);
+            const float r = rsqrtf(d);
             if (!(d > 0.f)) bad = true;
             const int t = tid;
             float v;
@@ -93,27 +143,71 @@ __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) 
             L[(size_t)k * B + t] = v;
         }
         __syncthreads();
-        // rank-1 update of the trailing window, and the entering row j = k + B
-        for (int idx = tid; idx < npairs; idx += T) {
-            const int pr = pairs[idx];
-            const int t = pr >> 8, s = pr & 0xff;
-            if (k + t >= nm) continue;
-            int rt = base + t, cs = base + s;
-            rt -= rt >= B ? B : 0;
-            cs -= cs >= B ? B : 0;
-            W[rt * B + cs] = fmaf(-col[t], col[s], W[rt * B + cs]);
-        }
-        const int j = k + B;
-        if (j < nm) {
-            for (int o = tid; o < B; o += T) {
-                const int h = k + 1 + o;              // columns k+1 .. j of the new row
-                int sh = base + 1 + o;
-                sh -= sh >= B ? B : 0;
-                W[base * B + sh] = band_entry(S, pl, n1, j, h);
+        // rank-1 update of the whole trailing square (rows and columns t, s =
+        // 1 .. bw).  Only its lower half (row index >= column index) is ever
+        // read; the upper half holds finite leftovers and is rewritten when a
+        // row slot is reused, so the update needs no predicate.  A column
+        // beyond bw is replaced by the retired slot with a zero multiplier.
+        if (t0 < t1) {
+            float cv[NG];
+            float* Wc[NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const int sc = 1 + 32 * g + lane;
+                const bool mine = sc <= bw;
+                int cs = base + sc;
+                cs -= cs >= B ? B : 0;
+                cv[g] = mine ? col[sc] : 0.f;
+                Wc[g] = W + (mine ? cs : base);
             }
+            const float* ct = col + t0;
+            auto rows = [&](int r0, int r1) {
+                int r = r0;
+                for (; r + 4 <= r1; r += 4) {
+                    float c[4], w[4][NG];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        c[u] = ct[u];
+#pragma unroll
+                        for (int g = 0; g < NG; ++g) w[u][g] = Wc[g][(r + u) * B];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int g = 0; g < NG; ++g) Wc[g][(r + u) * B] = fmaf(-c[u], cv[g], w[u][g]);
+                    ct += 4;
+                }
+                for (; r < r1; ++r) {
+                    const float c = *ct++;
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) Wc[g][r * B] = fmaf(-c, cv[g], Wc[g][r * B]);
+                }
+            };
+            // rows t0 .. t1-1 occupy the slots base+t0 .. (mod B)
+            int r0 = base + t0;
+            r0 -= r0 >= B ? B : 0;
+            const int len = t1 - t0;
+            if (r0 + len <= B) {
+                rows(r0, r0 + len);
+            } else {
+                rows(r0, B);
+                rows(0, r0 + len - B);
+            }
+        }
+        // the entering row j = k + B takes the retired slot
+        const int jr = k + B;
+        if (jr < nm && tid < B) {
+            const float* st = stage + ((k >> 5) & 1) * kPlanes * slen;
+            const int lo = B + 32 * (k >> 5) - n1 - 1;
+            const int o = tid;
+            const int h = k + 1 + o;                  // columns k+1 .. j of the new row
+            int sh = base + 1 + o;
+            sh -= sh >= B ? B : 0;
+            W[base * B + sh] = band_entry_staged(st, slen, lo, n1, jr, h);
         }
         __syncthreads();
     }
+    cp_async_wait_all();
     if (bad) atomicOr(a.flag, 1);
 }
 
@@ -126,8 +220,10 @@ __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) 
 // factor and is meant to run at HBM speed).
 constexpr int kBandAhead = 4;
 
+constexpr int kBandSolveThreads = 64;   // two problems per block: fine-grained balance over the SMs
+
 template <int NR>
-__global__ void __launch_bounds__(256) k_band_solve(BandSolveArgs a) {
+__global__ void __launch_bounds__(kBandSolveThreads) k_band_solve(BandSolveArgs a) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= a.nM) return;
@@ -167,9 +263,18 @@ __global__ void __launch_bounds__(256) k_band_solve(BandSolveArgs a) {
         p1[t] = (has1 && lane + 32 < nm) ? (float)r[lane + 32] : 0.f;
         p2[t] = (has2 && lane + 64 < nm) ? (float)r[lane + 64] : 0.f;
     }
-    float ybuf[NR], ent[NR];
+    float ybuf[NR], ent[NR], ent_next[NR];
+    // entering values r[k' + 1 + bw] of the 32 steps k' = c0 .. c0 + 31 (lane l: step c0 + l)
+    auto load_ent = [&](int c0, float (&dst)[NR]) {
 #pragma unroll
-    for (int t = 0; t < NR; ++t) ybuf[t] = ent[t] = 0.f;
+        for (int t = 0; t < NR; ++t) {
+            const int e = c0 + lane + 1 + bw;
+            dst[t] = e < nm ? (float)a.r[t][base + e] : 0.f;
+        }
+    };
+#pragma unroll
+    for (int t = 0; t < NR; ++t) ybuf[t] = 0.f;
+    load_ent(0, ent_next);
 #pragma unroll
     for (int u = 0; u < kBandAhead; ++u) load_col(u, qa[u], qb[u], qc[u]);
     for (int kb = 0; kb < nm; kb += kBandAhead) {
@@ -178,12 +283,10 @@ __global__ void __launch_bounds__(256) k_band_solve(BandSolveArgs a) {
             const int k = kb + u;
             if (k >= nm) break;
             if ((k & 31) == 0) {
-                // entering values r[k' + 1 + bw] of the 32 steps k' = k .. k + 31 (lane l: step k + l)
+                // this chunk's entering values were fetched one chunk ahead
 #pragma unroll
-                for (int t = 0; t < NR; ++t) {
-                    const int e = k + lane + 1 + bw;
-                    ent[t] = e < nm ? (float)a.r[t][base + e] : 0.f;
-                }
+                for (int t = 0; t < NR; ++t) ent[t] = ent_next[t];
+                load_ent(k + 32, ent_next);
             }
             const float c0 = qa[u], c1 = qb[u], c2 = qc[u];
             load_col(k + kBandAhead, qa[u], qb[u], qc[u]);
@@ -225,9 +328,15 @@ __global__ void __launch_bounds__(256) k_band_solve(BandSolveArgs a) {
     __syncwarp();
 
     // ---- backward: L^T x = y; X[m] = x_{k+m}, m = lane, lane+32, lane+64 (X[0] unused)
-    float x0[NR], x1[NR], x2[NR], yc[NR], xbuf[NR];
+    float x0[NR], x1[NR], x2[NR], yc[NR], ynext[NR], xbuf[NR];
+    // y of the 32-step chunk [k0, k0 + 31] (lane l: index k0 + l), fetched one chunk ahead
+    auto load_y = [&](int k0, float (&dst)[NR]) {
+#pragma unroll
+        for (int t = 0; t < NR; ++t) dst[t] = (k0 >= 0 && k0 + lane < nm) ? y[t][k0 + lane] : 0.f;
+    };
 #pragma unroll
     for (int t = 0; t < NR; ++t) x0[t] = x1[t] = x2[t] = yc[t] = xbuf[t] = 0.f;
+    load_y((nm - 1) & ~31, ynext);
 #pragma unroll
     for (int u = 0; u < kBandAhead; ++u) load_col(nm - 1 - u, qa[u], qb[u], qc[u]);
     for (int kb = nm - 1; kb >= 0; kb -= kBandAhead) {
@@ -236,9 +345,9 @@ __global__ void __launch_bounds__(256) k_band_solve(BandSolveArgs a) {
             const int k = kb - u;
             if (k < 0) break;
             if (k == nm - 1 || (k & 31) == 31) {
-                const int k0 = k & ~31;
 #pragma unroll
-                for (int t = 0; t < NR; ++t) yc[t] = (k0 + lane <= k) ? y[t][k0 + lane] : 0.f;
+                for (int t = 0; t < NR; ++t) yc[t] = ynext[t];
+                load_y((k & ~31) - 32, ynext);
             }
             const float c0 = qa[u], c1 = qb[u], c2 = qc[u];
             load_col(k - kBandAhead, qa[u], qb[u], qc[u]);
@@ -314,18 +423,35 @@ __global__ void __launch_bounds__(256) k_band_residual(BandResidualArgs a) {
 
 cudaError_t launch_band_factor(const BandArgs& a, cudaStream_t s) {
     const size_t sm = band_factor_smem(a.n1);
-    cudaError_t e = cudaFuncSetAttribute(k_band_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int ng = (a.n1 + 1 + 31) / 32;          // column groups of the half-bandwidth n1 + 1
+    cudaError_t e = cudaSuccess;
+    switch (ng) {
+        case 1:
+            e = cudaFuncSetAttribute(k_band_factor<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) k_band_factor<1><<<a.nM, kBandFactorThreads, sm, s>>>(a);
+            break;
+        case 2:
+            e = cudaFuncSetAttribute(k_band_factor<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) k_band_factor<2><<<a.nM, kBandFactorThreads, sm, s>>>(a);
+            break;
+        case 3:
+            e = cudaFuncSetAttribute(k_band_factor<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) k_band_factor<3><<<a.nM, kBandFactorThreads, sm, s>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess) return e;
-    k_band_factor<<<a.nM, kBandFactorThreads, sm, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_band_solve(const BandSolveArgs& a, int nrhs, cudaStream_t s) {
-    const unsigned grid = (unsigned)((a.nM + 7) / 8);
+    const int per_block = kBandSolveThreads / 32;
+    const unsigned grid = (unsigned)((a.nM + per_block - 1) / per_block);
     switch (nrhs) {
-        case 1: k_band_solve<1><<<grid, 256, 0, s>>>(a); break;
-        case 2: k_band_solve<2><<<grid, 256, 0, s>>>(a); break;
-        case 3: k_band_solve<3><<<grid, 256, 0, s>>>(a); break;
+        case 1: k_band_solve<1><<<grid, kBandSolveThreads, 0, s>>>(a); break;
+        case 2: k_band_solve<2><<<grid, kBandSolveThreads, 0, s>>>(a); break;
+        case 3: k_band_solve<3><<<grid, kBandSolveThreads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
