@@ -10,10 +10,11 @@
 // (zero below the matrix).  Both triangular solves read whole columns, so
 // every solve streams the factor contiguously.
 //
-// k_band_factor: one block per micro problem, right-looking band Cholesky on
-// a B x B sliding window of the trailing matrix in shared memory (circular
-// row/column slots); a finished column leaves the window, the next row of S
-// (its five stored couplings, staged ahead with cp.async) enters it.
+// k_band_factor: one block per micro problem, right-looking band Cholesky in
+// panels of four columns on a sliding window of the trailing matrix in shared
+// memory (circular row/column slots); finished columns leave the window, the
+// next rows of S (their five stored couplings, staged ahead with cp.async)
+// enter it.
 // k_band_solve: one warp per micro problem: forward substitution with the
 // pending right-hand side values spread over the lanes (3 slots a lane),
 // backward substitution as one warp dot product per column.
@@ -26,14 +27,15 @@ namespace tsf {
 constexpr int kBandFactorThreads = 128;  // four warps per micro problem
 
 // Staging of the stencil values of the rows that enter the window: chunk c
-// (steps 32c .. 32c+31) brings rows j = B + 32c .. B + 32c + 31, whose
-// couplings sit at node indices lo = j0 - n1 - 1 .. j0 + 31: n1 + 33 values
-// per plane, two chunks in flight (cp.async, loaded one chunk ahead).
+// (columns 32c .. 32c+31) brings rows j = BW + 32c .. BW + 32c + 31 (BW the
+// window size), whose couplings sit at node indices lo = j0 - n1 - 1 ..
+// j0 + 31: n1 + 33 values per plane, two chunks in flight (cp.async, loaded
+// one chunk ahead).
 __host__ __device__ __forceinline__ int band_stage_len(int n1) { return n1 + 33; }
 
 size_t band_factor_smem(int n1) {
-    const int B = n1 + 2;
-    size_t b = (size_t)B * B * sizeof(float) + (size_t)B * sizeof(float);
+    const int BW = n1 + 2 + 3;   // window of the panel factorisation (panel of 4 columns)
+    size_t b = (size_t)BW * 16 + (size_t)BW * BW * sizeof(float) + (size_t)BW * sizeof(float);
     b = (b + 15) & ~(size_t)15;
     return b + 2 * (size_t)kPlanes * band_stage_len(n1) * sizeof(float);
 }
@@ -76,31 +78,44 @@ __device__ __forceinline__ float band_entry_staged(const float* st, int len, int
     return v;
 }
 
-// kBandFactorWarps warps per micro problem.  Lane l of every warp owns the
-// window columns s = l+1 + 32 g (g < NG = ceil((n1 + 1) / 32)); warp w walks
-// its contiguous share of the rows: the lanes of a warp touch the same row
-// at the same time (col[t] is a broadcast) and consecutive columns.
+// One block of kBandFactorThreads per micro problem, panels of kBandPanel
+// columns.  The window holds BW = B + kBandPanel - 1 consecutive rows in
+// circular slots (slot(g) = g mod BW), lower half valid.  Per panel: the
+// kBandPanel columns are finished one after the other (each first takes the
+// updates of the earlier columns of the panel), then ONE rank-kBandPanel
+// update of the trailing square, then the kBandPanel rows that follow the
+// window enter it.  In the rank update lane l of every warp owns the columns
+// s = l + 32 g (g < NG) of the trailing square and walks its warp's share of
+// the rows; a row's kBandPanel factor values are one broadcast float4, so a
+// window element is loaded and stored once per kBandPanel columns.  The upper
+// half of the square is updated as well (it is never read, and holds finite
+// values), so the update needs no predicate.
+constexpr int kBandPanel = 4;
+
 template <int NG>
 __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n1 = a.n1, nm = a.nm, B = n1 + 2, bw = B - 1;
-    float* W = reinterpret_cast<float*>(smem);        // [B][B], row = slot of the larger index
-    float* col = W + B * B;                           // [B]
-    size_t off = (size_t)B * B * sizeof(float) + (size_t)B * sizeof(float);
+    const int BW = B + kBandPanel - 1;
+    float4* Lp = reinterpret_cast<float4*>(smem);                 // [BW] panel columns by row slot
+    float* W = reinterpret_cast<float*>(Lp + BW);                 // [BW][BW]
+    float* wcol = W + BW * BW;                                    // [BW]
+    size_t off = (size_t)BW * sizeof(float4) + (size_t)BW * BW * sizeof(float) + (size_t)BW * sizeof(float);
     off = (off + 15) & ~(size_t)15;
     const int slen = band_stage_len(n1);
-    float* stage = reinterpret_cast<float*>(smem + off);   // [2][kPlanes][slen]
+    float* stage = reinterpret_cast<float*>(smem + off);         // [2][kPlanes][slen]
     const int i = blockIdx.x, tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int nw = T >> 5;
     const size_t pl = (size_t)a.nmp;
     const float* S = a.S32 + (size_t)i * kPlanes * pl;
     float* L = a.L + (size_t)i * nm * B;
-    // this warp's rows t in [t0, t1) of 1 .. bw
+    // this warp's rows q in [q0, q1) of the trailing square (q = 0 .. bw-1)
     const int per = (bw + nw - 1) / nw;
-    const int t0 = 1 + warp * per, t1 = min(bw + 1, t0 + per);
-    // chunk c of entering rows into stage buffer c & 1
+    const int q0 = warp * per, q1 = min(bw, q0 + per);
+    auto slot = [&](int g) { return g % BW; };
+    // chunk c of entering rows (j = BW + 32c .. BW + 32c + 31) into stage buffer c & 1
     auto issue_chunk = [&](int c) {
-        const int lo = B + 32 * c - n1 - 1;
+        const int lo = BW + 32 * c - n1 - 1;
         float* st = stage + (c & 1) * kPlanes * slen;
         for (int e = tid; e < kPlanes * slen; e += T) {
             const int plane = e / slen, idx = lo + e % slen;
@@ -110,100 +125,121 @@ __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) 
         cp_async_commit();
     };
     issue_chunk(0);
-    // initial window: rows 0..bw
-    for (int e = tid; e < B * B; e += T) {
-        const int g = e / B, h = e % B;
-        W[e] = (g < nm && h <= g) ? band_entry(S, pl, n1, g, h) : 0.f;
+    // initial window: rows 0..BW-1
+    for (int e = tid; e < BW * BW; e += T) {
+        const int g = e / BW, h = e % BW;
+        W[e] = (g < nm && h <= g && g - h <= bw) ? band_entry(S, pl, n1, g, h) : 0.f;
     }
     bool bad = false;
-    for (int k = 0; k < nm; ++k) {
-        const int base = k % B;
+    auto wrap = [&](int x) { return x >= BW ? x - BW : x; };     // x < 2 BW
+    for (int k = 0; k < nm; k += kBandPanel) {
         if ((k & 31) == 0) {
-            // the chunk of this step's entering rows is complete; fetch the next one
+            // the chunk of this panel's entering rows is complete; fetch the next one
             cp_async_wait_all();
             __syncthreads();
             issue_chunk((k >> 5) + 1);
         }
-        // finished column k
-        if (tid < B) {
-            const float d = W[base * B + base];
-            const float r = rsqrtf(d);
-            if (!(d > 0.f)) bad = true;
-            const int t = tid;
-            float v;
-            if (t == 0) {
-                v = r;
-                col[0] = 0.f;
-            } else {
-                int st = base + t;
-                st -= st >= B ? B : 0;
-                v = (k + t < nm) ? W[st * B + base] * r : 0.f;
-                col[t] = v;
+        const int sk0 = k % BW;                                   // slot of row k
+        // ---- warp 0 finishes the panel's columns, one after the other
+        if (warp == 0) {
+            for (int e = lane; e < BW; e += 32) Lp[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp();
+            for (int c = 0; c < kBandPanel; ++c) {
+                const int kc = k + c;
+                if (kc >= nm) break;
+                const int sk = wrap(sk0 + c);
+                const float4 lk = Lp[sk];
+                const float lkc[4] = {lk.x, lk.y, lk.z, lk.w};
+                float wv[3];
+                int sgv[3];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int t = lane + 32 * u, g = kc + t;
+                    const int sg = wrap(sk + t < 2 * BW ? sk + t : sk + t - BW);
+                    sgv[u] = sg;
+                    float w = 0.f;
+                    if (t < BW - c && t <= bw && g < nm) {
+                        const float4 lg = Lp[sg];
+                        const float lgc[4] = {lg.x, lg.y, lg.z, lg.w};
+                        w = W[sg * BW + sk];
+#pragma unroll
+                        for (int cp = 0; cp < kBandPanel; ++cp)
+                            if (cp < c) w = fmaf(-lgc[cp], lkc[cp], w);
+                    }
+                    wv[u] = w;
+                }
+                const float d = __shfl_sync(0xffffffffu, wv[0], 0);
+                const float r = rsqrtf(d);
+                if (!(d > 0.f)) bad = true;
+                __syncwarp();                                     // every lane has read Lp
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int t = lane + 32 * u, g = kc + t;
+                    if (t < BW - c) {
+                        const float v = (t <= bw && g < nm) ? wv[u] * r : 0.f;
+                        reinterpret_cast<float*>(&Lp[sgv[u]])[c] = v;
+                        if (t == 0) L[(size_t)kc * B] = r;
+                        else if (t <= bw) L[(size_t)kc * B + t] = v;
+                    }
+                }
+                __syncwarp();
             }
-            L[(size_t)k * B + t] = v;
         }
         __syncthreads();
-        // rank-1 update of the whole trailing square (rows and columns t, s =
-        // 1 .. bw).  Only its lower half (row index >= column index) is ever
-        // read; the upper half holds finite leftovers and is rewritten when a
-        // row slot is reused, so the update needs no predicate.  A column
-        // beyond bw is replaced by the retired slot with a zero multiplier.
-        if (t0 < t1) {
-            float cv[NG];
+        // ---- rank-kBandPanel update of the trailing square, rows/columns k+P .. k+BW-1
+        {
+            const int base = wrap(sk0 + kBandPanel);
+            float4 cv[NG];
             float* Wc[NG];
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                const int sc = 1 + 32 * g + lane;
-                const bool mine = sc <= bw;
-                int cs = base + sc;
-                cs -= cs >= B ? B : 0;
-                cv[g] = mine ? col[sc] : 0.f;
-                Wc[g] = W + (mine ? cs : base);
+            for (int gi = 0; gi < NG; ++gi) {
+                const int s = 32 * gi + lane;
+                const bool mine = s < bw;
+                const int cs = mine ? wrap(base + s) : sk0;      // sk0: a retired row, zero multiplier
+                cv[gi] = mine ? Lp[cs] : make_float4(0.f, 0.f, 0.f, 0.f);
+                Wc[gi] = W + cs;
             }
-            const float* ct = col + t0;
             auto rows = [&](int r0, int r1) {
-                int r = r0;
-                for (; r + 4 <= r1; r += 4) {
-                    float c[4], w[4][NG];
+                for (int rr = r0; rr < r1; ++rr) {
+                    const float4 lr = Lp[rr];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        c[u] = ct[u];
-#pragma unroll
-                        for (int g = 0; g < NG; ++g) w[u][g] = Wc[g][(r + u) * B];
+                    for (int gi = 0; gi < NG; ++gi) {
+                        float w = Wc[gi][rr * BW];
+                        w = fmaf(-lr.x, cv[gi].x, w);
+                        w = fmaf(-lr.y, cv[gi].y, w);
+                        w = fmaf(-lr.z, cv[gi].z, w);
+                        w = fmaf(-lr.w, cv[gi].w, w);
+                        Wc[gi][rr * BW] = w;
                     }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int g = 0; g < NG; ++g) Wc[g][(r + u) * B] = fmaf(-c[u], cv[g], w[u][g]);
-                    ct += 4;
-                }
-                for (; r < r1; ++r) {
-                    const float c = *ct++;
-#pragma unroll
-                    for (int g = 0; g < NG; ++g) Wc[g][r * B] = fmaf(-c, cv[g], Wc[g][r * B]);
                 }
             };
-            // rows t0 .. t1-1 occupy the slots base+t0 .. (mod B)
-            int r0 = base + t0;
-            r0 -= r0 >= B ? B : 0;
-            const int len = t1 - t0;
-            if (r0 + len <= B) {
-                rows(r0, r0 + len);
-            } else {
-                rows(r0, B);
-                rows(0, r0 + len - B);
+            if (q0 < q1) {
+                const int r0 = wrap(base + q0);
+                const int len = q1 - q0;
+                if (r0 + len <= BW) {
+                    rows(r0, r0 + len);
+                } else {
+                    rows(r0, BW);
+                    rows(0, r0 + len - BW);
+                }
             }
         }
-        // the entering row j = k + B takes the retired slot
-        const int jr = k + B;
-        if (jr < nm && tid < B) {
+        // ---- meanwhile the rows j = k + BW + m take the retired slots of the
+        // panel rows (rows the update does not touch; it only passes through
+        // their columns with zero multipliers)
+        if (tid < BW) {
             const float* st = stage + ((k >> 5) & 1) * kPlanes * slen;
-            const int lo = B + 32 * (k >> 5) - n1 - 1;
-            const int o = tid;
-            const int h = k + 1 + o;                  // columns k+1 .. j of the new row
-            int sh = base + 1 + o;
-            sh -= sh >= B ? B : 0;
-            W[base * B + sh] = band_entry_staged(st, slen, lo, n1, jr, h);
+            const int lo = BW + 32 * (k >> 5) - n1 - 1;
+#pragma unroll
+            for (int m = 0; m < kBandPanel; ++m) {
+                const int j = k + BW + m;
+                if (j < nm) {
+                    const int h = k + m + 1 + tid;               // columns j-BW+1 .. j of the new row
+                    int sh = sk0 + m + 1 + tid;
+                    sh = sh >= 2 * BW ? sh - 2 * BW : (sh >= BW ? sh - BW : sh);
+                    W[wrap(sk0 + m) * BW + sh] = band_entry_staged(st, slen, lo, n1, j, h);
+                }
+            }
         }
         __syncthreads();
     }
