@@ -33,9 +33,12 @@ constexpr int kBandFactorThreads = 128;  // four warps per micro problem
 // one chunk ahead).
 __host__ __device__ __forceinline__ int band_stage_len(int n1) { return n1 + 33; }
 
+constexpr int kBandPanel = 4;                // columns per panel of the factorisation
+constexpr int kPanelVec = kBandPanel / 4;    // float4 per row of panel values
+
 size_t band_factor_smem(int n1) {
-    const int BW = n1 + 2 + 3;   // window of the panel factorisation (panel of 4 columns)
-    size_t b = (size_t)BW * 16 + (size_t)BW * BW * sizeof(float) + (size_t)BW * sizeof(float);
+    const int BW = n1 + 2 + kBandPanel - 1;  // window of the panel factorisation
+    size_t b = (size_t)BW * kPanelVec * sizeof(float4) + (size_t)BW * BW * sizeof(float);
     b = (b + 15) & ~(size_t)15;
     return b + 2 * (size_t)kPlanes * band_stage_len(n1) * sizeof(float);
 }
@@ -86,21 +89,19 @@ __device__ __forceinline__ float band_entry_staged(const float* st, int len, int
 // update of the trailing square, then the kBandPanel rows that follow the
 // window enter it.  In the rank update lane l of every warp owns the columns
 // s = l + 32 g (g < NG) of the trailing square and walks its warp's share of
-// the rows; a row's kBandPanel factor values are one broadcast float4, so a
-// window element is loaded and stored once per kBandPanel columns.  The upper
+// the rows; a row's kBandPanel factor values are kPanelVec broadcast float4,
+// so a window element is loaded and stored once per kBandPanel columns.  The upper
 // half of the square is updated as well (it is never read, and holds finite
 // values), so the update needs no predicate.
-constexpr int kBandPanel = 4;
 
 template <int NG>
 __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n1 = a.n1, nm = a.nm, B = n1 + 2, bw = B - 1;
     const int BW = B + kBandPanel - 1;
-    float4* Lp = reinterpret_cast<float4*>(smem);                 // [BW] panel columns by row slot
-    float* W = reinterpret_cast<float*>(Lp + BW);                 // [BW][BW]
-    float* wcol = W + BW * BW;                                    // [BW]
-    size_t off = (size_t)BW * sizeof(float4) + (size_t)BW * BW * sizeof(float) + (size_t)BW * sizeof(float);
+    float4* Lp = reinterpret_cast<float4*>(smem);                 // [BW][kPanelVec] panel columns by row slot
+    float* W = reinterpret_cast<float*>(Lp + BW * kPanelVec);     // [BW][BW]
+    size_t off = (size_t)BW * kPanelVec * sizeof(float4) + (size_t)BW * BW * sizeof(float);
     off = (off + 15) & ~(size_t)15;
     const int slen = band_stage_len(n1);
     float* stage = reinterpret_cast<float*>(smem + off);         // [2][kPlanes][slen]
@@ -142,14 +143,13 @@ __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) 
         const int sk0 = k % BW;                                   // slot of row k
         // ---- warp 0 finishes the panel's columns, one after the other
         if (warp == 0) {
-            for (int e = lane; e < BW; e += 32) Lp[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e = lane; e < BW * kPanelVec; e += 32) Lp[e] = make_float4(0.f, 0.f, 0.f, 0.f);
             __syncwarp();
             for (int c = 0; c < kBandPanel; ++c) {
                 const int kc = k + c;
                 if (kc >= nm) break;
                 const int sk = wrap(sk0 + c);
-                const float4 lk = Lp[sk];
-                const float lkc[4] = {lk.x, lk.y, lk.z, lk.w};
+                const float* lkc = reinterpret_cast<const float*>(&Lp[sk * kPanelVec]);
                 float wv[3];
                 int sgv[3];
 #pragma unroll
@@ -159,8 +159,7 @@ __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) 
                     sgv[u] = sg;
                     float w = 0.f;
                     if (t < BW - c && t <= bw && g < nm) {
-                        const float4 lg = Lp[sg];
-                        const float lgc[4] = {lg.x, lg.y, lg.z, lg.w};
+                        const float* lgc = reinterpret_cast<const float*>(&Lp[sg * kPanelVec]);
                         w = W[sg * BW + sk];
 #pragma unroll
                         for (int cp = 0; cp < kBandPanel; ++cp)
@@ -177,7 +176,7 @@ __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) 
                     const int t = lane + 32 * u, g = kc + t;
                     if (t < BW - c) {
                         const float v = (t <= bw && g < nm) ? wv[u] * r : 0.f;
-                        reinterpret_cast<float*>(&Lp[sgv[u]])[c] = v;
+                        reinterpret_cast<float*>(&Lp[sgv[u] * kPanelVec])[c] = v;
                         if (t == 0) L[(size_t)kc * B] = r;
                         else if (t <= bw) L[(size_t)kc * B + t] = v;
                     }
@@ -189,26 +188,33 @@ __global__ void __launch_bounds__(kBandFactorThreads) k_band_factor(BandArgs a) 
         // ---- rank-kBandPanel update of the trailing square, rows/columns k+P .. k+BW-1
         {
             const int base = wrap(sk0 + kBandPanel);
-            float4 cv[NG];
+            float4 cv[NG][kPanelVec];
             float* Wc[NG];
 #pragma unroll
             for (int gi = 0; gi < NG; ++gi) {
                 const int s = 32 * gi + lane;
                 const bool mine = s < bw;
                 const int cs = mine ? wrap(base + s) : sk0;      // sk0: a retired row, zero multiplier
-                cv[gi] = mine ? Lp[cs] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < kPanelVec; ++h)
+                    cv[gi][h] = mine ? Lp[cs * kPanelVec + h] : make_float4(0.f, 0.f, 0.f, 0.f);
                 Wc[gi] = W + cs;
             }
             auto rows = [&](int r0, int r1) {
                 for (int rr = r0; rr < r1; ++rr) {
-                    const float4 lr = Lp[rr];
+                    float4 lr[kPanelVec];
+#pragma unroll
+                    for (int h = 0; h < kPanelVec; ++h) lr[h] = Lp[rr * kPanelVec + h];
 #pragma unroll
                     for (int gi = 0; gi < NG; ++gi) {
                         float w = Wc[gi][rr * BW];
-                        w = fmaf(-lr.x, cv[gi].x, w);
-                        w = fmaf(-lr.y, cv[gi].y, w);
-                        w = fmaf(-lr.z, cv[gi].z, w);
-                        w = fmaf(-lr.w, cv[gi].w, w);
+#pragma unroll
+                        for (int h = 0; h < kPanelVec; ++h) {
+                            w = fmaf(-lr[h].x, cv[gi][h].x, w);
+                            w = fmaf(-lr[h].y, cv[gi][h].y, w);
+                            w = fmaf(-lr[h].z, cv[gi][h].z, w);
+                            w = fmaf(-lr[h].w, cv[gi][h].w, w);
+                        }
                         Wc[gi][rr * BW] = w;
                     }
                 }
@@ -258,25 +264,30 @@ constexpr int kBandAhead = 4;
 
 constexpr int kBandSolveThreads = 64;   // two problems per block: fine-grained balance over the SMs
 
+// NR right-hand sides per warp, one pass over the factor for all of them
+// (one warp per right-hand side reads the factor NR times and was slower).
 template <int NR>
 __global__ void __launch_bounds__(kBandSolveThreads) k_band_solve(BandSolveArgs a) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= a.nM) return;
+    const int n1 = a.n1, nm = a.nm, B = n1 + 2, bw = B - 1;
+    const size_t pl = (size_t)a.nmp, base = (size_t)i * pl;
+    const double* rp[NR];
+    double* xp[NR];
+    float* y[NR];
     bool open[NR];
     bool any = false;
 #pragma unroll
     for (int t = 0; t < NR; ++t) {
+        rp[t] = a.r[t] + base;
+        xp[t] = a.x[t] + base;
+        y[t] = a.y[t] + base;
         open[t] = !a.done[t][i];
         any = any || open[t];
     }
     if (!any) return;
-    const int n1 = a.n1, nm = a.nm, B = n1 + 2, bw = B - 1;
-    const size_t pl = (size_t)a.nmp, base = (size_t)i * pl;
     const float* L = a.L + (size_t)i * nm * B;
-    float* y[NR];
-#pragma unroll
-    for (int t = 0; t < NR; ++t) y[t] = a.y[t] + base;
     const bool has1 = lane + 32 <= bw, has2 = lane + 64 <= bw;
     auto load_col = [&](int k, float& c0, float& c1, float& c2) {
         if (k < 0 || k >= nm) {
@@ -294,7 +305,7 @@ __global__ void __launch_bounds__(kBandSolveThreads) k_band_solve(BandSolveArgs 
     float p0[NR], p1[NR], p2[NR];
 #pragma unroll
     for (int t = 0; t < NR; ++t) {
-        const double* r = a.r[t] + base;
+        const double* r = rp[t];
         p0[t] = (lane <= bw && lane < nm) ? (float)r[lane] : 0.f;
         p1[t] = (has1 && lane + 32 < nm) ? (float)r[lane + 32] : 0.f;
         p2[t] = (has2 && lane + 64 < nm) ? (float)r[lane + 64] : 0.f;
@@ -305,7 +316,7 @@ __global__ void __launch_bounds__(kBandSolveThreads) k_band_solve(BandSolveArgs 
 #pragma unroll
         for (int t = 0; t < NR; ++t) {
             const int e = c0 + lane + 1 + bw;
-            dst[t] = e < nm ? (float)a.r[t][base + e] : 0.f;
+            dst[t] = e < nm ? (float)rp[t][e] : 0.f;
         }
     };
 #pragma unroll
@@ -415,7 +426,7 @@ __global__ void __launch_bounds__(kBandSolveThreads) k_band_solve(BandSolveArgs 
 #pragma unroll
                 for (int t = 0; t < NR; ++t) {
                     const int g = k + lane;
-                    if (open[t] && g < nm) a.x[t][base + g] += (double)xbuf[t];
+                    if (open[t] && g < nm) xp[t][g] += (double)xbuf[t];
                 }
             }
         }
