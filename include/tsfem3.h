@@ -122,6 +122,12 @@ tsf_status tsf3_solve(tsf3_ctx* ctx);
  * vbar [nM] (micro averages 1^T M_i v_i / |Y_x_i|). */
 tsf_status tsf3_get_fields(tsf3_ctx* ctx, double* u, double* w, double* v, double* vbar, int on_device);
 
+/* Push-forward of the micro fields for visualisation (Sec. 3.6): micro node j
+ * of node i at X = x_i + scale (chi(x_i, yhat_j) - chi(x_i, (1/2, 1/2))), each
+ * cell centred on its macro node; out = [nM][nm][3] FP32 (X1, X2, v).  The
+ * same buffer layout as tsf_get_pushforward; TSF_E_STATE before a solve. */
+tsf_status tsf3_get_pushforward(tsf3_ctx* ctx, float scale, float* out, int on_device);
+
 tsf_status tsf3_get_stats(tsf3_ctx* ctx, tsf3_stats* out);
 const char* tsf3_last_error(const tsf3_ctx* ctx);
 void tsf3_destroy(tsf3_ctx* ctx);

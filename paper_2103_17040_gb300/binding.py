@@ -36,7 +36,8 @@ EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micr
            "tsf_batch_get_stats", "tsf_batch_reset_stats", "tsf_batch_last_error", "tsf_batch_destroy"]
 # every symbol include/tsfem3.h declares (the stationary three-field system)
 EXPORTS3 = ["tsf3_create", "tsf3_set_meshes", "tsf3_set_physics", "tsf3_set_deformation", "tsf3_set_sources",
-            "tsf3_solve", "tsf3_get_fields", "tsf3_get_stats", "tsf3_last_error", "tsf3_destroy"]
+            "tsf3_solve", "tsf3_get_fields", "tsf3_get_pushforward", "tsf3_get_stats", "tsf3_last_error",
+            "tsf3_destroy"]
 TSF3_EDGE_BOTTOM, TSF3_EDGE_RIGHT, TSF3_EDGE_TOP, TSF3_EDGE_LEFT = 1, 2, 4, 8
 TSF3_TILING_DIRECT = 10
 TSF_NOALLOC_MAX_NM = 128
@@ -139,6 +140,7 @@ def load_library(path: str = LIB_PATH):
     L.tsf3_set_sources.argtypes = [vp] + [vp] * 9 + [i]
     L.tsf3_solve.argtypes = [vp]
     L.tsf3_get_fields.argtypes = [vp, vp, vp, vp, vp, i]
+    L.tsf3_get_pushforward.argtypes = [vp, ctypes.c_float, vp, i]
     L.tsf3_get_stats.argtypes = [vp, ctypes.POINTER(tsf3_stats)]
     L.tsf3_last_error.argtypes = [vp]
     L.tsf3_last_error.restype = ctypes.c_char_p
@@ -480,6 +482,23 @@ def tsf3_get_fields(ctx, nM, nm, u=None, w=None, v=None, vbar=None):
     return tuple(a for (_, _, a) in outs)
 
 
+def tsf3_get_pushforward(ctx, nM, nm, scale, out=None):
+    """[nM * nm * 3] FP32 (X1, X2, v); out None -> new host array."""
+    n = nM * nm * 3
+    if out is None:
+        out = np.empty(n, dtype=np.float32)
+    if _is_cuda_tensor(out):
+        import torch
+        if out.dtype != torch.float32 or out.numel() != n or not out.is_contiguous():
+            raise ValueError("output tensor must be contiguous float32 with nM*nm*3 values")
+        _check3(ctx, _lib.tsf3_get_pushforward(ctx, float(scale), out.data_ptr(), 1))
+        return out
+    if out.dtype != np.float32 or out.size != n or not out.flags.c_contiguous:
+        raise ValueError("output array must be contiguous float32 with nM*nm*3 values")
+    _check3(ctx, _lib.tsf3_get_pushforward(ctx, float(scale), out.ctypes.data, 0))
+    return out
+
+
 def tsf3_get_stats(ctx) -> dict:
     s = tsf3_stats()
     _check3(ctx, _lib.tsf3_get_stats(ctx, ctypes.byref(s)))
@@ -694,6 +713,12 @@ class ThreeField:
         """(u [nM], w [nM], v [nM, nm], vbar [nM]) as host arrays"""
         u, w, v, vbar = tsf3_get_fields(self.ctx, self.nM, self.nm)
         return u, w, v.reshape(self.nM, self.nm), vbar
+
+    def pushforward(self, scale, out=None):
+        """Micro fields at their macroscopic locations, [nM, nm, 3] = (X1, X2, v),
+        each cell scaled by ``scale`` and centred on its macro node."""
+        a = tsf3_get_pushforward(self.ctx, self.nM, self.nm, scale, out)
+        return a.reshape(self.nM, self.nm, 3) if isinstance(a, np.ndarray) else a
 
     def stats(self):
         return tsf3_get_stats(self.ctx)

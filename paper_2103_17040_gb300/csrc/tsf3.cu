@@ -1176,6 +1176,29 @@ tsf_status tsf3_get_fields(tsf3_ctx* ctx, double* u, double* w, double* v, doubl
     return TSF_OK;
 }
 
+tsf_status tsf3_get_pushforward(tsf3_ctx* ctx, float scale, float* out, int on_device) {
+    if (!ctx || !out) return TSF_E_ARG;
+    if (!(scale > 0.0f) || !std::isfinite(scale)) return fail3(ctx, TSF_E_ARG, "scale must be positive");
+    if (!ctx->solved) return fail3(ctx, TSF_E_STATE, "no solution yet");
+    const size_t n = (size_t)ctx->nM * ctx->nm * 3;
+    float* dst = out;
+    if (!on_device) {
+        cudaError_t e = cudaMalloc((void**)&dst, n * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail3(ctx, TSF_E_OOM, "cudaMalloc of %zu bytes for the push-forward failed", n * sizeof(float));
+        }
+    }
+    cudaError_t e = launch_pushforward(ctx->Nm, ctx->n1, ctx->nm, ctx->nmp, ctx->NM, ctx->nM, ctx->map32, ctx->v,
+                                       (float)ctx->x0, (float)(ctx->L / ctx->NM), scale, 1, dst, ctx->stream);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (!on_device) cudaFree(dst);
+    if (e != cudaSuccess) return fail3(ctx, TSF_E_CUDA, "push-forward: %s", cudaGetErrorString(e));
+    return TSF_OK;
+}
+
 tsf_status tsf3_get_stats(tsf3_ctx* ctx, tsf3_stats* out) {
     if (!ctx || !out) return TSF_E_ARG;
     *out = ctx->stats;

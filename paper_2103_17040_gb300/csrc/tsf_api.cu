@@ -1350,7 +1350,7 @@ tsf_status tsf_get_pushforward(tsf_ctx* ctx, float scale, float* out, int on_dev
         }
     }
     cudaError_t e = launch_pushforward(ctx->Nm, ctx->n1, ctx->nm, ctx->nmp, ctx->NM, ctx->nM, ctx->map32, ctx->v,
-                                       scale, dst, ctx->stream);
+                                       0.0f, 1.0f / ctx->NM, scale, 0, dst, ctx->stream);
     if (e == cudaSuccess && !on_device)
         e = cudaMemcpyAsync(out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

@@ -48,14 +48,17 @@ cudaError_t launch_expand_params(int family, int nparam, const double* in, doubl
 
 // Push-forward for visualisation (Sec. 3.6): micro node j of instance i,
 // reference point yhat_j, goes to
-//     X = x_i + scale (chi(x_i, yhat_j) - (1/2, 1/2)),
-// chi = A yhat + b (sin pi y1 sin pi y2, 0) + c; out[(i nm + j) 3 + {0,1,2}]
-// = (X1, X2, v_i(yhat_j)) in FP32 (a picture needs no more, and GB300's FP64
+//     X = x_i + scale (chi(x_i, yhat_j) - centre),
+// chi = A yhat + b (sin pi y1 sin pi y2, 0) + c, x_i = x0 + H (p, q);
+// centre = (1/2, 1/2) (centre_mode 0: cells around the reference cell
+// [0,1]^2), or chi(x_i, (1/2, 1/2)) (centre_mode 1: each cell centred on its
+// own image of the reference centre).  out[(i nm + j) 3 + {0,1,2}] =
+// (X1, X2, v_i(yhat_j)) in FP32 (a picture needs no more, and GB300's FP64
 // rate would make this streaming kernel compute-bound).  One thread per
 // (instance, node); sin(pi k/Nm) of the n1 grid lines from a table.
-__global__ void __launch_bounds__(256) k_pushforward(int n1, int nm, int nmp, int NM, float H, float h,
+__global__ void __launch_bounds__(256) k_pushforward(int n1, int nm, int nmp, int NM, float x0, float H, float h,
                                                      const float* __restrict__ map32, const double* __restrict__ v,
-                                                     float scale, float* __restrict__ out) {
+                                                     float scale, int centre_mode, float* __restrict__ out) {
     __shared__ float sinpi_tab[65];  // n1 <= 65
     for (int k = threadIdx.x; k < n1; k += blockDim.x) sinpi_tab[k] = sinpif((float)k * h);
     __syncthreads();
@@ -63,7 +66,7 @@ __global__ void __launch_bounds__(256) k_pushforward(int n1, int nm, int nmp, in
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     if (j >= nm) return;
     const int N1 = NM + 1;
-    const float x1 = (float)(i % N1) * H, x2 = (float)(i / N1) * H;
+    const float x1 = fmaf((float)(i % N1), H, x0), x2 = fmaf((float)(i / N1), H, x0);
     const int pj = j % n1, qj = j / n1;
     const float y1 = (float)pj * h, y2 = (float)qj * h;
     const float4 m0 = *reinterpret_cast<const float4*>(map32 + (size_t)i * 8);
@@ -71,16 +74,21 @@ __global__ void __launch_bounds__(256) k_pushforward(int n1, int nm, int nmp, in
     const float s12 = sinpi_tab[pj] * sinpi_tab[qj];
     const float ch1 = fmaf(m1.x, s12, fmaf(m0.x, y1, fmaf(m0.y, y2, m1.y)));
     const float ch2 = fmaf(m0.z, y1, fmaf(m0.w, y2, m1.z));
+    float c1 = 0.5f, c2 = 0.5f;
+    if (centre_mode == 1) {   // chi(1/2, 1/2): sin(pi/2)^2 = 1
+        c1 = m1.x + fmaf(m0.x, 0.5f, fmaf(m0.y, 0.5f, m1.y));
+        c2 = fmaf(m0.z, 0.5f, fmaf(m0.w, 0.5f, m1.z));
+    }
     float* o = out + ((size_t)i * nm + j) * 3;
-    o[0] = fmaf(scale, ch1 - 0.5f, x1);
-    o[1] = fmaf(scale, ch2 - 0.5f, x2);
+    o[0] = fmaf(scale, ch1 - c1, x1);
+    o[1] = fmaf(scale, ch2 - c2, x2);
     o[2] = (float)v[(size_t)i * nmp + j];
 }
 
 cudaError_t launch_pushforward(int Nm, int n1, int nm, int nmp, int NM, int nM, const float* map32, const double* v,
-                               float scale, float* out, cudaStream_t s) {
+                               float x0, float H, float scale, int centre_mode, float* out, cudaStream_t s) {
     dim3 grid(nM, (nm + 255) / 256);
-    k_pushforward<<<grid, 256, 0, s>>>(n1, nm, nmp, NM, 1.0f / NM, 1.0f / Nm, map32, v, scale, out);
+    k_pushforward<<<grid, 256, 0, s>>>(n1, nm, nmp, NM, x0, H, 1.0f / Nm, map32, v, scale, centre_mode, out);
     return cudaGetLastError();
 }
 

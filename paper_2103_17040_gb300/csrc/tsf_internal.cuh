@@ -263,8 +263,9 @@ struct MacroPrologueArgs {
 // map32: [nM][8] FP32 copy of the whole map (A11, A12, A21, A22, b, c1, c2, 0) for the push-forward
 cudaError_t launch_expand_params(int family, int nparam, const double* in, double* prm5, float* map32, int nM,
                                  cudaStream_t s);
+// x_i = x0 + H (p, q); centre_mode 0: X = x_i + scale (chi - 1/2), 1: X = x_i + scale (chi - chi(1/2, 1/2))
 cudaError_t launch_pushforward(int Nm, int n1, int nm, int nmp, int NM, int nM, const float* map32, const double* v,
-                               float scale, float* out, cudaStream_t s);
+                               float x0, float H, float scale, int centre_mode, float* out, cudaStream_t s);
 cudaError_t launch_geometry(const GeomArgs& a, cudaStream_t s);
 cudaError_t launch_instance_sums(int n1, int nm, int nmp, int nM, const double* lm, const double* redge,
                                  double* gam, double* vol, cudaStream_t s);

@@ -212,3 +212,24 @@ def test_error_statuses(T):
         T.ThreeField(3, 2, dir_mask=0)       # no Dirichlet edge: singular
     assert e.value.status == T.TSF_E_ARG
     P.close()
+
+
+def test_pushforward_centres_every_cell_on_its_node(T):
+    """Sec. 3.6 push-forward of the three-field micro fields: X = x_i + scale
+    (chi(x_i, yhat) - chi(x_i, (1/2, 1/2))), against the oracle's chi (FP32)."""
+    from oracle import chi_many
+    wl = T3.case_b(4, 6, sink=True)
+    P = _gpu(T, wl, 1)
+    _, _, v, _ = P.fields()
+    scale = 0.1
+    xyv = P.pushforward(scale)
+    assert xyv.shape == (wl.nM, wl.nm, 3) and xyv.dtype == np.float32
+    X0, X1 = T3.macro_nodes(wl.NM, wl.x0, wl.L)
+    yh = np.arange(wl.Nm + 1) / wl.Nm
+    Y1, Y2 = np.meshgrid(yh, yh, indexing="xy")
+    for i in range(wl.nM):
+        y, _ = chi_many(wl.family, wl.params[i], Y1.ravel(), Y2.ravel())
+        c, _ = chi_many(wl.family, wl.params[i], [0.5], [0.5])
+        X = np.stack([X0[i], X1[i]]) + scale * (y - c[0])
+        assert np.abs(xyv[i, :, :2] - X).max() < 1e-5
+        assert np.allclose(xyv[i, :, 2], v[i], rtol=1e-6, atol=1e-6)
