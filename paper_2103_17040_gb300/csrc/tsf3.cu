@@ -687,57 +687,73 @@ tsf_status tsf3_set_meshes(tsf3_ctx* ctx, int Nm, int NM, double x0, double L, i
     ctx->nparam = 0;
     ctx->tiling = -1;
     const size_t nM = ctx->nM, F = nM * ctx->nmp, E = 4 * nM * ctx->n1;
-    CU3(dalloc(ctx, &ctx->params, nM * 6));
-    CU3(dalloc(ctx, &ctx->prm5, nM * 5));
-    CU3(dalloc(ctx, &ctx->map32, nM * 8));
-    CU3(dalloc(ctx, &ctx->M64, F * kPlanes));
-    CU3(dalloc(ctx, &ctx->S64, F * kPlanes));
-    CU3(dalloc(ctx, &ctx->S32, F * kPlanes));
-    CU3(dalloc(ctx, &ctx->lm, F));
-    CU3(dalloc(ctx, &ctx->eRd, E));
-    CU3(dalloc(ctx, &ctx->eRu, E));
-    CU3(dalloc(ctx, &ctx->er, E));
-    CU3(dalloc(ctx, &ctx->fu, nM));
-    CU3(dalloc(ctx, &ctx->fw, nM));
-    CU3(dalloc(ctx, &ctx->ud, nM));
-    CU3(dalloc(ctx, &ctx->gu, 4 * (size_t)ctx->N1));
-    CU3(dalloc(ctx, &ctx->gw, 4 * (size_t)ctx->N1));
-    CU3(dalloc(ctx, &ctx->fv, F));
-    CU3(dalloc(ctx, &ctx->gI, nM * ctx->n1));
-    CU3(dalloc(ctx, &ctx->gO, nM * ctx->n1));
-    CU3(dalloc(ctx, &ctx->gN, 2 * nM * ctx->n1));
+    // a failed allocation leaves no half-built context behind: everything is
+    // released and the meshes must be set again
+    cudaError_t err = cudaSuccess;
+#define AL(call)                            \
+    do {                                    \
+        if (err == cudaSuccess) err = (call); \
+    } while (0)
+    AL(dalloc(ctx, &ctx->params, nM * 6));
+    AL(dalloc(ctx, &ctx->prm5, nM * 5));
+    AL(dalloc(ctx, &ctx->map32, nM * 8));
+    AL(dalloc(ctx, &ctx->M64, F * kPlanes));
+    AL(dalloc(ctx, &ctx->S64, F * kPlanes));
+    AL(dalloc(ctx, &ctx->S32, F * kPlanes));
+    AL(dalloc(ctx, &ctx->lm, F));
+    AL(dalloc(ctx, &ctx->eRd, E));
+    AL(dalloc(ctx, &ctx->eRu, E));
+    AL(dalloc(ctx, &ctx->er, E));
+    AL(dalloc(ctx, &ctx->fu, nM));
+    AL(dalloc(ctx, &ctx->fw, nM));
+    AL(dalloc(ctx, &ctx->ud, nM));
+    AL(dalloc(ctx, &ctx->gu, 4 * (size_t)ctx->N1));
+    AL(dalloc(ctx, &ctx->gw, 4 * (size_t)ctx->N1));
+    AL(dalloc(ctx, &ctx->fv, F));
+    AL(dalloc(ctx, &ctx->gI, nM * ctx->n1));
+    AL(dalloc(ctx, &ctx->gO, nM * ctx->n1));
+    AL(dalloc(ctx, &ctx->gN, 2 * nM * ctx->n1));
     for (int t = 0; t < 3; ++t) {
-        CU3(dalloc(ctx, &ctx->c[t], F));
-        CU3(dalloc(ctx, &ctx->x[t], F));
-        CU3(dalloc(ctx, &ctx->res[t], F));
-        CU3(dalloc(ctx, &ctx->uu[t], nM));
-        CU3(dalloc(ctx, &ctx->bnorm[t], 3 * nM));
+        AL(dalloc(ctx, &ctx->c[t], F));
+        AL(dalloc(ctx, &ctx->x[t], F));
+        AL(dalloc(ctx, &ctx->res[t], F));
+        AL(dalloc(ctx, &ctx->uu[t], nM));
+        AL(dalloc(ctx, &ctx->bnorm[t], 3 * nM));
     }
-    CU3(dalloc(ctx, &ctx->iters, nM));
-    CU3(dalloc(ctx, &ctx->zero, nM));
-    CU3(dalloc(ctx, &ctx->rho, nM));
-    CU3(dalloc(ctx, &ctx->G, 2 * nM));
-    CU3(dalloc(ctx, &ctx->coef, 5 * nM));
-    CU3(dalloc(ctx, &ctx->vol, nM));
-    CU3(dalloc(ctx, &ctx->u, nM));
-    CU3(dalloc(ctx, &ctx->w, nM));
-    CU3(dalloc(ctx, &ctx->v, F));
-    CU3(dalloc(ctx, &ctx->vbar, nM));
-    CU3(dalloc(ctx, &ctx->mx, 2 * nM));
-    CU3(dalloc(ctx, &ctx->mr, 2 * nM));
-    CU3(dalloc(ctx, &ctx->mz, 2 * nM));
-    CU3(dalloc(ctx, &ctx->mp, 2 * nM));
-    CU3(dalloc(ctx, &ctx->mq, 2 * nM));
-    CU3(dalloc(ctx, &ctx->pinv, 3 * nM));
-    CU3(dalloc(ctx, &ctx->mpart, 4 * ((nM + kMacro3Threads - 1) / kMacro3Threads) + 4));
-    for (int t = 0; t < 3; ++t) CU3(dalloc(ctx, &ctx->done[t], nM));
-    CU3(dalloc(ctx, &ctx->open_count, 1));
-    CU3(dalloc(ctx, &ctx->flag, 1));
-    CU3(cudaMemsetAsync(ctx->zero, 0, nM * sizeof(double), ctx->stream));
-    CU3(cudaMemsetAsync(ctx->fv, 0, F * sizeof(double), ctx->stream));
-    CU3(cudaMemsetAsync(ctx->eRd, 0, E * sizeof(double), ctx->stream));
-    CU3(cudaMemsetAsync(ctx->eRu, 0, E * sizeof(double), ctx->stream));
-    CU3(cudaMemsetAsync(ctx->er, 0, E * sizeof(double), ctx->stream));
+    AL(dalloc(ctx, &ctx->iters, nM));
+    AL(dalloc(ctx, &ctx->zero, nM));
+    AL(dalloc(ctx, &ctx->rho, nM));
+    AL(dalloc(ctx, &ctx->G, 2 * nM));
+    AL(dalloc(ctx, &ctx->coef, 5 * nM));
+    AL(dalloc(ctx, &ctx->vol, nM));
+    AL(dalloc(ctx, &ctx->u, nM));
+    AL(dalloc(ctx, &ctx->w, nM));
+    AL(dalloc(ctx, &ctx->v, F));
+    AL(dalloc(ctx, &ctx->vbar, nM));
+    AL(dalloc(ctx, &ctx->mx, 2 * nM));
+    AL(dalloc(ctx, &ctx->mr, 2 * nM));
+    AL(dalloc(ctx, &ctx->mz, 2 * nM));
+    AL(dalloc(ctx, &ctx->mp, 2 * nM));
+    AL(dalloc(ctx, &ctx->mq, 2 * nM));
+    AL(dalloc(ctx, &ctx->pinv, 3 * nM));
+    AL(dalloc(ctx, &ctx->mpart, 4 * ((nM + kMacro3Threads - 1) / kMacro3Threads) + 4));
+    for (int t = 0; t < 3; ++t) AL(dalloc(ctx, &ctx->done[t], nM));
+    AL(dalloc(ctx, &ctx->open_count, 1));
+    AL(dalloc(ctx, &ctx->flag, 1));
+    AL(cudaMemsetAsync(ctx->zero, 0, nM * sizeof(double), ctx->stream));
+    AL(cudaMemsetAsync(ctx->fv, 0, F * sizeof(double), ctx->stream));
+    AL(cudaMemsetAsync(ctx->eRd, 0, E * sizeof(double), ctx->stream));
+    AL(cudaMemsetAsync(ctx->eRu, 0, E * sizeof(double), ctx->stream));
+    AL(cudaMemsetAsync(ctx->er, 0, E * sizeof(double), ctx->stream));
+#undef AL
+    if (err != cudaSuccess) {
+        free_all(ctx);
+        ctx->nM = 0;
+        cudaGetLastError();
+        return fail3(ctx, err == cudaErrorMemoryAllocation ? TSF_E_OOM : TSF_E_CUDA,
+                     "allocating the three-field state (%d x %d macro, %d x %d micro): %s", NM, NM, Nm, Nm,
+                     cudaGetErrorString(err));
+    }
     return TSF_OK;
 }
 
@@ -961,10 +977,10 @@ static tsf_status direct_solves(tsf3_ctx* ctx, int nsolve) {
     ctx->stats.band_launches = 0;
     ctx->stats.band_rhs = nsolve;
     if (!ctx->factor_valid) {
-        if (!ctx->Lband) {
-            CU3(dalloc(ctx, &ctx->Lband, (size_t)ctx->nM * ctx->nm * (ctx->n1 + 2)));
-            for (int t = 0; t < 3; ++t) CU3(dalloc(ctx, &ctx->yband[t], (size_t)ctx->nM * ctx->nmp));
-        }
+        // allocated on first use; whatever a failed attempt left out is allocated next time
+        if (!ctx->Lband) CU3(dalloc(ctx, &ctx->Lband, (size_t)ctx->nM * ctx->nm * (ctx->n1 + 2)));
+        for (int t = 0; t < 3; ++t)
+            if (!ctx->yband[t]) CU3(dalloc(ctx, &ctx->yband[t], (size_t)ctx->nM * ctx->nmp));
         CU3(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
         BandArgs f{};
         f.n1 = ctx->n1;
