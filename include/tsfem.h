@@ -208,6 +208,16 @@ tsf_status tsf_get_micro_field(tsf_ctx *ctx, double *v_out, int on_device);
 tsf_status tsf_get_flux(tsf_ctx *ctx, double *flux_out, int on_device);
 tsf_status tsf_get_geometry(tsf_ctx *ctx, double *gamma_out, double *vol_out, int on_device);
 
+/* Asynchronous variants of tsf_get_macro and tsf_get_micro_averages for
+ * streaming results out while the next steps run: the copy is enqueued on
+ * the context's stream behind the work already there, and the call returns
+ * without synchronising.  The destination holds the values once the stream
+ * reaches the copy (after tsf_synchronize, or an event recorded behind it);
+ * a host destination must be page-locked memory for the copy to be
+ * asynchronous and must stay valid until then. */
+tsf_status tsf_get_macro_async(tsf_ctx *ctx, double *u_out, int on_device);
+tsf_status tsf_get_micro_averages_async(tsf_ctx *ctx, double *vbar_out, int on_device);
+
 /* Push-forward of the micro fields for visualisation (Sec. 3.6: every micro
  * solution is mapped from the reference cell Z to its physical cell Y_x and
  * translated to its macroscopic location, scaled so that the cells can be

@@ -29,8 +29,8 @@ STATUS_NAMES = {0: "TSF_OK", 1: "TSF_E_ARG", 2: "TSF_E_STATE", 3: "TSF_E_BAD_JAC
 # every symbol include/tsfem.h declares
 EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micro_mesh", "tsf_set_macro_mesh",
            "tsf_set_physics", "tsf_set_deformation", "tsf_set_state", "tsf_set_sources", "tsf_step",
-           "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux",
-           "tsf_get_geometry", "tsf_get_pushforward", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
+           "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_macro_async",
+           "tsf_get_micro_averages_async", "tsf_get_micro_field", "tsf_get_flux", "tsf_get_geometry", "tsf_get_pushforward", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
            "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u",
            "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_synchronize",
            "tsf_batch_get_stats", "tsf_batch_reset_stats", "tsf_batch_last_error", "tsf_batch_destroy"]
@@ -108,7 +108,8 @@ def load_library(path: str = LIB_PATH):
     L.tsf_set_sources.argtypes = [vp, vp, vp, vp, vp, i]
     L.tsf_step.argtypes = [vp, d, i]
     L.tsf_synchronize.argtypes = [vp]
-    for f in ("tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux"):
+    for f in ("tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux",
+              "tsf_get_macro_async", "tsf_get_micro_averages_async"):
         getattr(L, f).argtypes = [vp, vp, i]
     L.tsf_get_geometry.argtypes = [vp, vp, vp, i]
     L.tsf_get_pushforward.argtypes = [vp, ctypes.c_float, vp, i]
@@ -277,6 +278,21 @@ def tsf_get_macro(ctx, nM, out=None):
 
 def tsf_get_micro_averages(ctx, nM, out=None):
     return _getter("tsf_get_micro_averages", ctx, nM, out)
+
+
+def tsf_get_macro_async(ctx, nM, out):
+    """Enqueue the copy of u into out (page-locked host array or CUDA tensor of nM
+    doubles) without synchronising; out holds u once the stream reaches the copy."""
+    ptr, dev, _ = _out(out, nM)
+    _check(ctx, _lib.tsf_get_macro_async(ctx, ptr, dev))
+    return out
+
+
+def tsf_get_micro_averages_async(ctx, nM, out):
+    """As tsf_get_macro_async, for the micro averages."""
+    ptr, dev, _ = _out(out, nM)
+    _check(ctx, _lib.tsf_get_micro_averages_async(ctx, ptr, dev))
+    return out
 
 
 def tsf_get_micro_field(ctx, n, out=None):
@@ -598,6 +614,15 @@ class TwoScale:
 
     def vbar(self, out=None):
         return tsf_get_micro_averages(self.ctx, self.nM, out)
+
+    def u_async(self, out):
+        """Queue a copy of u into ``out`` (page-locked host array or CUDA tensor of
+        nM doubles); valid after ``synchronize()``."""
+        return tsf_get_macro_async(self.ctx, self.nM, out)
+
+    def vbar_async(self, out):
+        """Queue the micro averages into ``out`` (as ``u_async``)."""
+        return tsf_get_micro_averages_async(self.ctx, self.nM, out)
 
     def flux(self, out=None):
         return tsf_get_flux(self.ctx, self.nM, out)

@@ -1299,6 +1299,14 @@ tsf_status tsf_get_macro(tsf_ctx* ctx, double* u_out, int on_device) {
     return copy_out(ctx, u_out, ctx->u, ctx->nM, on_device);
 }
 
+tsf_status tsf_get_macro_async(tsf_ctx* ctx, double* u_out, int on_device) {
+    if (!ctx || !u_out) return TSF_E_ARG;
+    if (!ctx->ws_valid) return fail(ctx, TSF_E_STATE, "no state");
+    CU(cudaMemcpyAsync(u_out, ctx->u, ctx->nM * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    return TSF_OK;
+}
+
 tsf_status tsf_get_micro_field(tsf_ctx* ctx, double* v_out, int on_device) {
     if (!ctx || !v_out) return TSF_E_ARG;
     if (!ctx->ws_valid) return fail(ctx, TSF_E_STATE, "no state");
@@ -1313,6 +1321,17 @@ tsf_status tsf_get_micro_averages(tsf_ctx* ctx, double* vbar_out, int on_device)
     if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
     CU(launch_vbar(ctx->nm, ctx->nmp, ctx->nM, ctx->lm, ctx->vol, ctx->v, ctx->out, ctx->stream));
     return copy_out(ctx, vbar_out, ctx->out, ctx->nM, on_device);
+}
+
+// The averages go through the context's scratch vector; the next kernel that
+// writes it is later on the same stream, so the queued copy reads this step's.
+tsf_status tsf_get_micro_averages_async(tsf_ctx* ctx, double* vbar_out, int on_device) {
+    if (!ctx || !vbar_out) return TSF_E_ARG;
+    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
+    CU(launch_vbar(ctx->nm, ctx->nmp, ctx->nM, ctx->lm, ctx->vol, ctx->v, ctx->out, ctx->stream));
+    CU(cudaMemcpyAsync(vbar_out, ctx->out, ctx->nM * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    return TSF_OK;
 }
 
 tsf_status tsf_get_flux(tsf_ctx* ctx, double* flux_out, int on_device) {

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_elim_start(ElimArgs a) {
 // push w_k and S w_k = c_k - e_k, W = extrapolated warm start g,
 // res = c_{k+1} - S g, norms of c_{k+1}.
 __global__ void __launch_bounds__(256) k_elim_pre(ElimArgs a) {
-    __shared__ double buf[3 * 32];
+    __shared__ float buf[3 * 32];
     const int i = blockIdx.x, n1 = a.n1, nm = a.nm;
     const size_t pl = (size_t)a.nmp, slot = (size_t)a.nM * pl;
     const double* M = a.M64 + (size_t)i * kPlanes * pl;
@@ -107,22 +107,45 @@ __global__ void __launch_bounds__(256) k_elim_pre(ElimArgs a) {
     const double* h1 = a.hist + (size_t)((st + 2) % 3) * slot + (size_t)i * pl;
     const double* h2 = a.hist + (size_t)((st + 1) % 3) * slot + (size_t)i * pl;
     const double uo = a.u_old[i], idt = 1.0 / a.dt;
-    double cc = 0.0, cr = 0.0, rr = 0.0;
+    // The norms only set the reference ||b|| of the next solve's stopping test
+    // (u = 0 there, so only ||c||^2 counts): FP32 is ample, and GB300's FP64
+    // rate would make an FP64 block reduction a sizeable part of this kernel.
+    float cc = 0.f, cr = 0.f, rr = 0.f;
     for (int j = threadIdx.x; j < nm; j += blockDim.x) {
         const int p = j % n1, q = j / n1;
         // M w_k / dt from the micro solve's epilogue, or computed here
         const double mwj = a.mw_ready ? cn[j] : plane_apply(M, pl, W, j, p, q, n1) * idt;
         const double y = fma(uo, mq[j], mwj);
         cn[j] = y;
-        cc = fma(y, y, cc);
+        const float yf = (float)y;
+        cc = fmaf(yf, yf, cc);
         if (p == n1 - 1) {
-            cr = fma(y, re[q], cr);
-            rr = fma(re[q], re[q], rr);
+            const float rf = (float)re[q];
+            cr = fmaf(yf, rf, cr);
+            rr = fmaf(rf, rf, rr);
         }
     }
-    double t[3] = {cc, cr, rr};
-    block_allreduce<double, 3>(t, buf);  // every read of w_k at neighbours is done
+    float tf[3] = {cc, cr, rr};
+    block_allreduce<float, 3>(tf, buf);  // every read of w_k at neighbours is done
     __syncthreads();
+    double t[3] = {tf[0], tf[1], tf[2]};
+    if (!(tf[0] >= 1e-30f && tf[0] <= 1e30f && tf[2] <= 1e30f)) {
+        // FP32 range exceeded (or c = 0): the same norms in FP64 from the
+        // stored c_{k+1}.  The branch is uniform across the block.
+        __shared__ double dbuf[3 * 32];
+        t[0] = t[1] = t[2] = 0.0;
+        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
+            const double y = cn[j];
+            t[0] = fma(y, y, t[0]);
+            if (j % n1 == n1 - 1) {
+                const double r = re[j / n1];
+                t[1] = fma(y, r, t[1]);
+                t[2] = fma(r, r, t[2]);
+            }
+        }
+        block_allreduce<double, 3>(t, dbuf);
+        __syncthreads();
+    }
     if (a.yhist) {
         double* yc = a.yhist + (size_t)(st % 3) * slot + (size_t)i * pl;
         const double* y1 = a.yhist + (size_t)((st + 2) % 3) * slot + (size_t)i * pl;

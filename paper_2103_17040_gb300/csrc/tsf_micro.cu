@@ -1075,21 +1075,27 @@ cudaError_t launch_micro_prologue(const PrologueArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// vbar_i = 1^T M_i v_i / vol_i = lm_i^T v_i / vol_i (M_i symmetric)
-__global__ void __launch_bounds__(256) k_vbar(int nm, int nmp, const double* __restrict__ lm,
+// vbar_i = 1^T M_i v_i / vol_i = lm_i^T v_i / vol_i (M_i symmetric).  One
+// warp per instance, plain FP64 sums in a fixed order (a block-wide or
+// compensated reduction per instance costs more FP64 issue than the whole sum
+// on GB300).
+__global__ void __launch_bounds__(256) k_vbar(int nm, int nmp, int nM, const double* __restrict__ lm,
                                               const double* __restrict__ vol, const double* __restrict__ v,
                                               double* vbar) {
-    __shared__ double buf[64];
-    const int i = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= nM) return;
+    const size_t base = (size_t)i * nmp;
     double s = 0.0;
-    for (int j = threadIdx.x; j < nm; j += blockDim.x) s = fma(lm[(size_t)i * nmp + j], v[(size_t)i * nmp + j], s);
-    const double t = block_sum_compensated(s, buf);
-    if (threadIdx.x == 0) vbar[i] = t / vol[i];
+    for (int j = lane; j < nm; j += 32) s = fma(lm[base + j], v[base + j], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) vbar[i] = s / vol[i];
 }
 
 cudaError_t launch_vbar(int nm, int nmp, int nM, const double* lm, const double* vol, const double* v, double* vbar,
                         cudaStream_t s) {
-    k_vbar<<<nM, 256, 0, s>>>(nm, nmp, lm, vol, v, vbar);
+    k_vbar<<<(nM + 7) / 8, 256, 0, s>>>(nm, nmp, nM, lm, vol, v, vbar);
     return cudaGetLastError();
 }
 

@@ -419,3 +419,33 @@ def test_pushforward_matches_oracle_map(family):
     assert np.array_equal(out[:, :, 2], P.v().astype(np.float32))
     with pytest.raises(T.TsfError):
         P.pushforward(-1.0)
+
+
+def test_async_getters_match_the_synchronous_ones():
+    """tsf_get_macro_async / tsf_get_micro_averages_async queue their copies
+    behind the steps; after synchronize() they hold what the synchronous
+    getters return (pinned host arrays and CUDA tensors)."""
+    import torch
+    T = _T()
+    Nm, NM = 8, 6
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    P = T.TwoScale(Nm, NM, precision=1, coupling=1)
+    P.set_deformation(W.FAMILY_BUMP, W.random_params(1, nM, seed=3))
+    P.set_state(*W.random_state(nM, nm, seed=4))
+    uh = torch.empty(nM, dtype=torch.float64).pin_memory().numpy()
+    vh = torch.empty(nM, dtype=torch.float64).pin_memory().numpy()
+    ud = torch.empty(nM, dtype=torch.float64, device="cuda")
+    vd = torch.empty(nM, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        P.step(0.01, 1)
+        P.u_async(uh)
+        P.vbar_async(vh)
+        P.u_async(ud)
+        P.vbar_async(vd)
+    P.synchronize()
+    u, vbar = P.u(), P.vbar()
+    assert np.array_equal(uh, u) and np.array_equal(vh, vbar)
+    assert np.array_equal(ud.cpu().numpy(), u) and np.array_equal(vd.cpu().numpy(), vbar)
+    with pytest.raises(ValueError):
+        P.u_async(np.empty(nM + 1))
+    P.close()
