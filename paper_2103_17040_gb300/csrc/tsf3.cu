@@ -57,6 +57,7 @@ struct Geom3Args {
     double* M64;
     double* S64;
     float* S32;
+    float* S32lo;
     double* lm;
     double* eRd;
     double* eRu;
@@ -79,11 +80,13 @@ __global__ void __launch_bounds__(128) k3_geometry(Geom3Args a) {
     double* M64 = a.M64 + (size_t)i * kPlanes * pl;
     double* S64 = a.S64 + (size_t)i * kPlanes * pl;
     float* S32 = a.S32 + (size_t)i * kPlanes * pl;
+    float* S32lo = a.S32lo + (size_t)i * kPlanes * pl;
     if (j >= a.nm) {
         for (int k = 0; k < kPlanes; ++k) {
             M64[k * pl + j] = 0.0;
             S64[k * pl + j] = 0.0;
             S32[k * pl + j] = 0.0f;
+            S32lo[k * pl + j] = 0.0f;
         }
         a.lm[(size_t)i * pl + j] = 0.0;
         return;
@@ -117,7 +120,9 @@ __global__ void __launch_bounds__(128) k3_geometry(Geom3Args a) {
     for (int c = 0; c < kPlanes; ++c) {
         M64[c * pl + j] = m[c];
         S64[c * pl + j] = k[c];
-        S32[c * pl + j] = (float)k[c];
+        const float hi = (float)k[c];
+        S32[c * pl + j] = hi;
+        S32lo[c * pl + j] = (float)(k[c] - (double)hi);
     }
     a.lm[(size_t)i * pl + j] = lump;
     if (bad) atomicOr(&a.ctl->geom_error, 1);
@@ -535,7 +540,7 @@ struct tsf3_ctx {
     double *params = nullptr, *prm5 = nullptr;
     float* map32 = nullptr;
     double *M64 = nullptr, *S64 = nullptr, *lm = nullptr;
-    float* S32 = nullptr;
+    float *S32 = nullptr, *S32lo = nullptr;
     double *eRd = nullptr, *eRu = nullptr, *er = nullptr;
     double *fu = nullptr, *fw = nullptr, *ud = nullptr, *gu = nullptr, *gw = nullptr;
     double *fv = nullptr, *gI = nullptr, *gO = nullptr, *gN = nullptr;
@@ -700,6 +705,7 @@ tsf_status tsf3_set_meshes(tsf3_ctx* ctx, int Nm, int NM, double x0, double L, i
     AL(dalloc(ctx, &ctx->M64, F * kPlanes));
     AL(dalloc(ctx, &ctx->S64, F * kPlanes));
     AL(dalloc(ctx, &ctx->S32, F * kPlanes));
+    AL(dalloc(ctx, &ctx->S32lo, F * kPlanes));
     AL(dalloc(ctx, &ctx->lm, F));
     AL(dalloc(ctx, &ctx->eRd, E));
     AL(dalloc(ctx, &ctx->eRu, E));
@@ -828,6 +834,7 @@ static MicroArgs micro3_args(tsf3_ctx* ctx, int t) {
     a.W = ctx->n1 + 2;
     a.nM = ctx->nM;
     a.S32 = ctx->S32;
+    a.S32lo = ctx->S32lo;
     a.S64 = ctx->S64;
     a.c = ctx->c[t];
     a.v = ctx->x[t];
@@ -894,6 +901,7 @@ static tsf_status build_geometry(tsf3_ctx* ctx) {
     g.M64 = ctx->M64;
     g.S64 = ctx->S64;
     g.S32 = ctx->S32;
+    g.S32lo = ctx->S32lo;
     g.lm = ctx->lm;
     g.eRd = ctx->eRd;
     g.eRu = ctx->eRu;

@@ -59,7 +59,7 @@ struct tsf_ctx {
     // device arrays
     double *prm5 = nullptr, *M64 = nullptr, *S64 = nullptr, *lm = nullptr, *redge = nullptr, *Rd = nullptr,
            *Ru = nullptr, *gam = nullptr, *vol = nullptr;
-    float* S32 = nullptr;
+    float *S32 = nullptr, *S32lo = nullptr;
     double *v = nullptr, *c = nullptr, *vtmp = nullptr, *fv = nullptr, *g = nullptr, *G = nullptr;
     double *u = nullptr, *uk = nullptr, *cH = nullptr, *fu = nullptr, *ud = nullptr, *rho = nullptr,
            *out = nullptr;
@@ -310,6 +310,7 @@ static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
     off[k++] = A.take(nM * kPlanes * pl * sizeof(double));       // M64
     off[k++] = A.take(nM * kPlanes * pl * sizeof(double));       // S64
     off[k++] = A.take(nM * kPlanes * pl * sizeof(float));        // S32
+    off[k++] = A.take(nM * kPlanes * pl * sizeof(float));        // S32lo
     off[k++] = A.take(nM * pl * sizeof(double));                 // lm
     off[k++] = A.take(nM * n1 * sizeof(double));                 // redge
     off[k++] = A.take(nM * n1 * sizeof(double));                 // Rd
@@ -347,6 +348,7 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->M64 = (double*)(b + off[k++]);
     ctx->S64 = (double*)(b + off[k++]);
     ctx->S32 = (float*)(b + off[k++]);
+    ctx->S32lo = (float*)(b + off[k++]);
     ctx->lm = (double*)(b + off[k++]);
     ctx->redge = (double*)(b + off[k++]);
     ctx->Rd = (double*)(b + off[k++]);
@@ -388,7 +390,7 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->rho_eff = (double*)(b + off[k++]);
 }
 
-static constexpr int kNumBuffers = 16 + 13 + 5 + 2 + 5 + 1 + 5 + 1 + 1 + 3 + 1;
+static constexpr int kNumBuffers = 17 + 13 + 5 + 2 + 5 + 1 + 5 + 1 + 1 + 3 + 1;
 
 tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return TSF_E_ARG;
@@ -493,6 +495,7 @@ static tsf_status build_operators(tsf_ctx* ctx, double dt) {
     a.M64 = ctx->M64;
     a.S64 = ctx->S64;
     a.S32 = ctx->S32;
+    a.S32lo = ctx->S32lo;
     a.lm = ctx->lm;
     a.redge = ctx->redge;
     a.Rd = ctx->Rd;
@@ -592,6 +595,7 @@ static MicroArgs micro_args(tsf_ctx* ctx, double* v) {
     a.W = ctx->n1 + 2;
     a.nM = ctx->nM;
     a.S32 = ctx->S32;
+    a.S32lo = ctx->S32lo;
     a.S64 = ctx->S64;
     a.c = ctx->c;
     a.v = v;

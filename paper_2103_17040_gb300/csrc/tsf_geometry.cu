@@ -114,11 +114,13 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
     double* M64 = a.M64 + (size_t)i * kPlanes * pl;
     double* S64 = a.S64 + (size_t)i * kPlanes * pl;
     float* S32 = a.S32 + (size_t)i * kPlanes * pl;
+    float* S32lo = a.S32lo + (size_t)i * kPlanes * pl;
     if (j >= a.nm) {  // padding of the planes: zero couplings
         for (int k = 0; k < kPlanes; ++k) {
             M64[k * pl + j] = 0.0;
             S64[k * pl + j] = 0.0;
             S32[k * pl + j] = 0.0f;
+            S32lo[k * pl + j] = 0.0f;
         }
         a.lm[(size_t)i * pl + j] = 0.0;
         return;
@@ -151,7 +153,9 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
     for (int c = 0; c < kPlanes; ++c) {
         M64[c * pl + j] = m[c];
         S64[c * pl + j] = sv[c];
-        S32[c * pl + j] = (float)sv[c];
+        const float hi = (float)sv[c];
+        S32[c * pl + j] = hi;
+        S32lo[c * pl + j] = (float)(sv[c] - (double)hi);  // the difference is exact in FP64
     }
     a.lm[(size_t)i * pl + j] = lump;
     if (bad) atomicOr(&a.ctl->geom_error, 1);

@@ -150,6 +150,7 @@ struct GeomArgs {
     double* M64;            // [nM][5][nmp] mass planes
     double* S64;            // [nM][5][nmp] M/dt + A + kappa R planes
     float* S32;             // [nM][5][nmp] S64 rounded to FP32
+    float* S32lo;           // [nM][5][nmp] S64 - S32 rounded to FP32
     double* lm;             // [nM][nmp]    row sums of M (lumped mass)
     double* redge;          // [nM][n1]     r = R 1 on the Robin edge nodes
     double* Rd;             // [nM][n1]     diagonal of R on the edge
@@ -161,6 +162,8 @@ struct MicroArgs {
     int n1, nm, nmp, W;     // W = n1 + 2: width of the zero-haloed shared-memory grid
     int nM;
     const float* S32;
+    const float* S32lo;     // [nM][5][nmp] S64 - S32 rounded to FP32: S32 + S32lo carries S64 to
+                            // about 2^-48 (the residual update of the column-strip kernels)
     const double* S64;
     const double* c;        // [nM][nmp] right-hand side without the u term
     double* v;              // [nM][nmp] in: initial guess, out: solution

@@ -388,7 +388,12 @@ static cudaError_t launch_smem(const MicroArgs& a, cudaStream_t s) {
 // the current iterate is kept in global memory (written by the step prologue
 // and by every solve), so a solve starts from
 //     r = res + kappa (u_i - u_used_i) r_i          (only Robin-edge nodes change)
-// and after each FP32 correction d updates it in FP64 as r -= S64 d, v += d.
+// and after each FP32 correction d updates it as r -= S d, v += d.  The
+// products S d are formed in compensated FP32 from S = S32 + S32lo (S64 to
+// about 2^-48; d is exact in FP32) and subtracted from the FP64 residual:
+// the stored residual stays within about 1e-12 ||b|| of b - S64 v, while
+// FP64 instructions (a small fraction of GB300's FP32 rate) are 7 per node
+// instead of about 20.
 // A micro problem whose residual already meets the tolerance returns before
 // staging anything.  ||b(u)||^2 = ||c||^2 + 2 kappa u c^T r + kappa^2 u^2 ||r||^2
 // comes from three per-instance scalars of the prologue.  Convergence tests
@@ -639,6 +644,23 @@ __device__ int strip_cg(const CS& c, const bool (&valid)[R], float (&x)[R], floa
     return it;
 }
 
+// Accumulate (hi + lo) x into the unevaluated float pair (s, c) for an FP32
+// x: hi x = p + e exactly (TwoProduct with an FMA), s + p = t + err exactly
+// (Knuth's TwoSum), and the small parts go to c.  For the nine terms of a
+// stencil row the pair carries the FP64 product sum to about 2^-44 of the
+// largest partial sum, without the FP64 pipe (a warp-wide FP64 instruction
+// costs as much issue as 64 FP32 ones on this part).  The round-to-nearest
+// intrinsics keep the compiler from contracting the error-free steps.
+__device__ __forceinline__ void df_add_prod(float& s, float& c, float hi, float lo, float x) {
+    const float p = __fmul_rn(hi, x);
+    const float e = fmaf(hi, x, -p);
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, fmaf(lo, x, e)));
+}
+
 template <int R, bool SC>
 __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -739,7 +761,8 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
         }
         __syncthreads();
         const SmemCouplings cs{cA, cB, p + n1 * q0, n1};
-        const double* S64 = a.S64 + (size_t)i * kPlanes * pl;
+        const float* Sh = S;                                   // S64 = Sh + Sl to about 2^-48
+        const float* Sl = a.S32lo + (size_t)i * kPlanes * pl;
         for (;;) {
             if (sweeps >= a.max_sweeps || inner >= a.maxit) {
                 flag = kNotConverged;
@@ -762,7 +785,9 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
                 inner += strip_cg<R>(c, valid, y, r, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 64, &flag);
             if (flag == kNaN) break;
             flag = 0;
-            // v += d and r -= S64 d in FP64 (d is exact in FP64)
+            // v += d and r -= S d with S = S32 + S32lo (S64 to about 2^-48)
+            // and the FP32 correction d: the products and their sum in
+            // compensated FP32, one FP64 subtraction from the stored residual
             float d[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) d[k] = sc[k] * y[k];
@@ -776,19 +801,19 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
                 if (!valid[k]) continue;
                 const int q = q0 + k, j = p + n1 * q;
                 const bool w = p > 0, e = p + 1 < n1, sd = q > 0;
-                // FP32 values converted as they are used (exact in FP64)
-                const double up = (double)((k + 1 < R) ? d[k + 1] : h.xp);
-                const double dn = (double)((k > 0) ? d[k - 1] : h.xm);
-                double yv = S64[j] * (double)d[k];
-                yv = fma(S64[pl + j], (double)h.Rt[k + 1], yv);
-                if (w) yv = fma(S64[pl + j - 1], (double)h.L[k + 1], yv);
-                yv = fma(S64[2 * pl + j], up, yv);
-                if (sd) yv = fma(S64[2 * pl + j - n1], dn, yv);
-                yv = fma(S64[3 * pl + j], (double)h.Rt[k + 2], yv);
-                yv = fma(S64[4 * pl + j], (double)h.L[k + 2], yv);
-                if (e && sd) yv = fma(S64[4 * pl + j - n1 + 1], (double)h.Rt[k], yv);
-                if (w && sd) yv = fma(S64[3 * pl + j - n1 - 1], (double)h.L[k], yv);
-                r64[k] = res[j] - yv;
+                const float up = (k + 1 < R) ? d[k + 1] : h.xp;
+                const float dn = (k > 0) ? d[k - 1] : h.xm;
+                float ys = 0.f, yc = 0.f;
+                df_add_prod(ys, yc, Sh[j], Sl[j], d[k]);
+                df_add_prod(ys, yc, Sh[pl + j], Sl[pl + j], h.Rt[k + 1]);
+                if (w) df_add_prod(ys, yc, Sh[pl + j - 1], Sl[pl + j - 1], h.L[k + 1]);
+                df_add_prod(ys, yc, Sh[2 * pl + j], Sl[2 * pl + j], up);
+                if (sd) df_add_prod(ys, yc, Sh[2 * pl + j - n1], Sl[2 * pl + j - n1], dn);
+                df_add_prod(ys, yc, Sh[3 * pl + j], Sl[3 * pl + j], h.Rt[k + 2]);
+                df_add_prod(ys, yc, Sh[4 * pl + j], Sl[4 * pl + j], h.L[k + 2]);
+                if (e && sd) df_add_prod(ys, yc, Sh[4 * pl + j - n1 + 1], Sl[4 * pl + j - n1 + 1], h.Rt[k]);
+                if (w && sd) df_add_prod(ys, yc, Sh[3 * pl + j - n1 - 1], Sl[3 * pl + j - n1 - 1], h.L[k]);
+                r64[k] = res[j] - ((double)ys + (double)yc);
                 const float rf = (float)r64[k];
                 rr = fmaf(rf, rf, rr);
                 v[j] += (double)d[k];
