@@ -45,14 +45,21 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
                 "k_micro_strip<3>", "k_micro_strip<5>", "k_micro_strip<7>",
                 "k_micro_strip_tall<9>", "k_micro_strip_tall<11>", "k_micro_strip_tall<13>"]
 # DRAM bytes (read + write) per micro-solve launch from the ncu captures
-# summarised under profiles/ (column-strip kernel; the strip height does not
-# change the DRAM traffic): partitioned, averaged over the four coupling
-# iterations of a step (micro_strip_c2_64x64_32x32.md);  Keyed by (workload,
-# precision, strip kernel, coupling); entries are removed when the kernel changes.
-MICRO_TRAFFIC = {("c2", "mixed", True, "partitioned"): 322.3e6,
-                 # pipelined elimination: one solve of the next w per launch, with the
-                 # M w / dt epilogue (step_pipelined_c2_64x64_32x32.md, k_micro_strip<3>)
-                 ("c2", "mixed", True, "elimination"): 632.3e6}
+# summarised under profiles/ (column-strip kernels, residual update from the
+# split FP32 stencil planes); keyed by (workload, precision, short strip
+# kernel, coupling); entries are removed when the kernel changes.
+MICRO_TRAFFIC = {
+    # partitioned: averaged over the four coupling iterations of a step
+    # (micro_strip_c2_64x64_32x32.md, k_micro_strip<3>)
+    ("c2", "mixed", True, "partitioned"): 247.9e6,
+    # pipelined elimination: one solve of the next w per launch, with the
+    # M w / dt epilogue (step_pipelined_c2_64x64_32x32.md, k_micro_strip<3>)
+    ("c2", "mixed", True, "elimination"): 538.1e6,
+    # 128x128/64x64, tall strips: captured on 32x32 macro cells (1089 of the
+    # 16641 problems, 538.3 MB a launch) and scaled by the problem count
+    # (micro_strip_tall_c3_128x128_64x64.md, k_micro_strip_tall<13>)
+    ("c3", "mixed", False, "elimination"): 8.225e9,
+}
 
 
 def parse():
@@ -65,17 +72,23 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "t1"],
                     help="t1: the stationary three-field system (manufactured solution, 128x128 / 64x64)")
     ap.add_argument("--fd-dirs", type=int, default=20, help="c5: finite-difference directions per family")
+    ap.add_argument("--tiling", type=int, default=-1,
+                    help="micro-kernel variant of the main timed problem (-1: the library's autotuner; a fixed "
+                         "variant keeps a profiled run on the kernel the plain run chose)")
     ap.add_argument("--coupling", default="elimination", choices=["elimination", "partitioned"],
                     help="how each step reaches the coupled solution (the other way is timed beside it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
-    ap.add_argument("--macro-cells", type=int, default=128, help="t1: macro cells per side (profiling: a smaller case)")
+    ap.add_argument("--macro-cells", type=int, default=None,
+                    help="macro cells per side of a smaller case for profiling (c3 and t1; default: the full size)")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, e2e, cpu baseline")
     return ap.parse_args()
 
 
-def workload(name, seed=0):
+def workload(name, seed=0, macro_cells=None):
     import workloads as W
-    return W.c2(seed=seed) if name == "c2" else W.c3(seed=seed)
+    if name == "c2":
+        return W.c2(seed=seed)
+    return W.c3(seed=seed) if macro_cells is None else W.c3(NM=macro_cells, seed=seed)
 
 
 class Clocks:
@@ -238,13 +251,13 @@ def run_gb300(args):
     # events on it bracket exactly the library's work
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    w = workload(args.workload, seed=rank)
+    w = workload(args.workload, seed=rank, macro_cells=args.macro_cells)
     nm, nM = w.nm, w.nM
     K, Wm = args.steps, args.warmup
 
     # ---- main timed region (graph-launched steps, inputs resident) ----
     other = "partitioned" if args.coupling == "elimination" else "elimination"
-    P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling])
+    P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling], tiling=args.tiling)
     P.step(w.dt, Wm)
     P.synchronize()
     P.reset_stats()
@@ -319,7 +332,8 @@ def run_gb300(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     line["roofline"] = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": MICRO_TRAFFIC.get((args.workload, args.precision, st["tiling"] in (4, 5, 6), args.coupling)),
+        "traffic": None if args.macro_cells else
+                   MICRO_TRAFFIC.get((args.workload, args.precision, st["tiling"] in (4, 5, 6), args.coupling)),
         # measured DRAM bytes (ncu, committed summary) per launch / launch time / peak: the
         # resident kernel keeps its CG state on chip, so this is far below frac
         "dram_frac": None,
@@ -863,7 +877,7 @@ def run_t1(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     T.load_library()
     stream = torch.cuda.Stream()
-    NM, Nm = args.macro_cells, 64
+    NM, Nm = args.macro_cells or 128, 64
     wl = T3.manufactured(NM, Nm, Dv=1.0, Dw=0.5, kappa=(0.5, 1.0, 0.25, 1.0), tol=1e-10)
     K = max(3, min(args.steps, 10))
     dofs = wl.nM * wl.nm

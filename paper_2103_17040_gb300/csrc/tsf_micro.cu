@@ -115,6 +115,10 @@ __device__ int pcg_smem(const TI* cf, TI* pp, int W, int W2, const int (&sidx)[K
             break;
         }
         const TI alpha = rz / pq;
+        if (!isfinite(alpha)) {  // pq lost to underflow: end this solve like a breakdown
+            *flag = kBreakdown;
+            break;
+        }
         TI rzn = TI(0), rr = TI(0);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -307,20 +311,26 @@ __global__ void __launch_bounds__(MaxThreads<K>::value) k_micro_solve(MicroArgs 
                     flag = kNotConverged;
                     break;
                 }
+                // The FP32 correction is solved for the unit-norm residual
+                // r / ||r|| (the FP32 values keep their range however small
+                // the residual is) and scaled back in FP64; the inner solve
+                // goes inner_tol below it, but no further than half of what
+                // the outer tolerance still needs.
+                const double rn = sqrt(rr), rs = 1.0 / rn;
                 TI d[K], r[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     d[k] = TI(0);
-                    r[k] = (TI)r64[k];
+                    r[k] = (TI)(r64[k] * rs);
                 }
-                const TI stop32 = (TI)(a.inner_tol * a.inner_tol * rr);
+                const TI stop32 = (TI)fmax(a.inner_tol * a.inner_tol, 0.25 * stop2 / rr);
                 inner += pcg_smem<TI, K>(cf, pp, W, W2, sidx, valid, dinv, d, r, stop32, a.maxit - inner, redA,
                                          redB, &flag);
                 if (flag == kNaN) break;
                 flag = 0;  // an FP32 breakdown only ends this inner solve; the FP64 residual decides
 #pragma unroll
                 for (int k = 0; k < K; ++k)
-                    if (valid[k]) vi[JJ(k)] += (double)d[k];
+                    if (valid[k]) vi[JJ(k)] = fma(rn, (double)d[k], vi[JJ(k)]);
                 __syncthreads();
             }
         }

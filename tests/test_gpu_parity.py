@@ -190,6 +190,30 @@ def test_all_tilings_agree(precision):
         assert rel(r, res[0]) < 1e-9
 
 
+@pytest.mark.parametrize("tiling", [1, 2, 3])
+def test_per_problem_variants_under_pipelined_elimination(tiling):
+    """The one-block-per-problem variants under the pipelined elimination at
+    the benchmark tolerance (1e-8), 40x40 micro cells, shear+bump maps and
+    D = diag(1, 0.1): the extrapolated warm starts leave residuals close to
+    the target, so the FP32 correction works on small values (the case that
+    ended in a non-finite CG step before the correction was solved for the
+    unit-norm residual).  Three steps against the oracle."""
+    NM, Nm = 3, 40
+    nM = (NM + 1) ** 2
+    prm = W.random_params(W.FAMILY_SHEAR_BUMP, nM, seed=31)
+    P, R = _pair(Nm, NM, W.FAMILY_SHEAR_BUMP, prm, D=(1.0, 0.0, 0.1), precision=1, coupling=1, tiling=tiling,
+                 cg_tol=1e-8, coupling_tol=1e-12)
+    u0 = np.ones(nM)
+    P.set_state(u0, None)
+    R.set_state(u0, None)
+    P.step(0.005, 3)
+    P.synchronize()
+    R.step(0.005, 3, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13)
+    assert P.stats()["tiling"] == tiling
+    assert rel(P.u(), R.u) < MIXED_TOL
+    assert rel(P.v(), R.v) < MIXED_TOL
+
+
 @pytest.mark.parametrize("coupling", [0, 1])
 def test_mass_balance_on_gpu(coupling):
     NM, Nm = 6, 10
