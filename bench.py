@@ -48,18 +48,7 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # summarised under profiles/ (column-strip kernels, residual update from the
 # split FP32 stencil planes); keyed by (workload, precision, short strip
 # kernel, coupling); entries are removed when the kernel changes.
-MICRO_TRAFFIC = {
-    # partitioned: averaged over the four coupling iterations of a step
-    # (micro_strip_c2_64x64_32x32.md, k_micro_strip<3>)
-    ("c2", "mixed", True, "partitioned"): 247.9e6,
-    # pipelined elimination: one solve of the next w per launch, with the
-    # M w / dt epilogue (step_pipelined_c2_64x64_32x32.md, k_micro_strip<3>)
-    ("c2", "mixed", True, "elimination"): 538.1e6,
-    # 128x128/64x64, tall strips: captured on 32x32 macro cells (1089 of the
-    # 16641 problems, 538.3 MB a launch) and scaled by the problem count
-    # (micro_strip_tall_c3_128x128_64x64.md, k_micro_strip_tall<13>)
-    ("c3", "mixed", False, "elimination"): 8.225e9,
-}
+MICRO_TRAFFIC = {}
 
 
 def parse():
@@ -269,8 +258,12 @@ def run_gb300(args):
     st = P.stats()
     value, ms_max, dof_iters = whole_job_rate(float(st["dof_cg_iters"]), ms, world, "cuda")
     steps_per_s = world * K / (ms_max / 1e3)
-    # partitioned: 2 prologues + (micro, macro) per coupling iteration; elimination: 5 kernels per step
-    launches = 5 * K if args.coupling == "elimination" else 2 * K + 2 * st["coupling_iters_total"]
+    # partitioned: 2 prologues + (micro, macro) per coupling iteration; pipelined elimination: start,
+    # macro prologue, micro solve, macro solve, commit (+ k_elim_pre with the one-block-per-problem variants)
+    if args.coupling == "elimination":
+        launches = (5 if st["tiling"] >= 4 else 6) * K
+    else:
+        launches = 2 * K + 2 * st["coupling_iters_total"]
 
     line = {
         "metric": "micro DOF-CG-iters/s",

@@ -756,19 +756,28 @@ static ElimArgs elim_args(tsf_ctx* ctx, double dt) {
     a.hist = ctx->hist;
     a.yhist = tiling_uses_stored_residual(ctx->tiling) ? ctx->yhist : nullptr;
     a.mw_ready = tiling_uses_stored_residual(ctx->tiling) ? 1 : 0;
+    a.commit_off = tiling_uses_stored_residual(ctx->tiling) ? 2 : 0;
     a.ctl = ctx->ctl;
     return a;
 }
 
-// The micro solve of w: u = 0 in the right-hand side; the strip kernels also
-// leave M w / dt in cnext for k_elim_pre.
-static MicroArgs w_solve_args(tsf_ctx* ctx, double dt) {
+// The micro solve of w: u = 0 in the right-hand side.  The strip kernels run
+// it pipelined (MicroArgs::pipe): they add u_old M psi / dt to the right-hand
+// side and residual the previous solve left (zeros for the first w, whose
+// right-hand side k_elim_head writes whole) and prepare the next step in
+// their epilogue, in place of k_elim_pre.
+static MicroArgs w_solve_args(tsf_ctx* ctx, double dt, bool head = false) {
     MicroArgs ma = micro_args(ctx, ctx->W);
     ma.u = ctx->uzero;
     if (tiling_uses_stored_residual(ctx->tiling)) {
         ma.M64 = ctx->M64;
         ma.mw = ctx->cnext;
         ma.idt = 1.0 / dt;
+        ma.pipe = 1;
+        ma.mq = ctx->mpsi;
+        ma.u_old = head ? ctx->uzero : ctx->u_old;
+        ma.hist = ctx->hist;
+        ma.yhist = ctx->yhist;
     }
     return ma;
 }
@@ -784,14 +793,15 @@ static bool pipelined(const tsf_ctx* ctx) {
 static tsf_status enqueue_head(tsf_ctx* ctx, double dt) {
     const ElimArgs ea = elim_args(ctx, dt);
     CU(launch_elim_head(ea, ctx->stream));
-    CU(launch_micro_solve(w_solve_args(ctx, dt), ctx->opt.precision, ctx->tiling, ctx->stream));
+    CU(launch_micro_solve(w_solve_args(ctx, dt, true), ctx->opt.precision, ctx->tiling, ctx->stream));
     return TSF_OK;
 }
 
 // One pipelined step (needs the solved w of the committed state):
 //   k_elim_start
 //   -> macro branch (this stream): macro prologue, macro solve, [after pre] commit
-//   -> micro branch (side stream): k_elim_pre, [after the macro prologue] micro solve of the next w
+//   -> micro branch (side stream): k_elim_pre (not with the strip kernels),
+//      [after the macro prologue] micro solve of the next w
 //   -> join.
 // ev: optional events around the micro solve (ev[0], ev[1], side stream) and
 // the macro solve (ev[2], ev[3], this stream).
@@ -800,9 +810,12 @@ static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
     CU(launch_elim_start(ea, ctx->stream));
     CU(cudaEventRecord(ctx->fork_ev, ctx->stream));
     CU(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0));
-    // micro branch
-    CU(launch_elim_pre(ea, ctx->side, ctx->prio_lo));
-    CU(cudaEventRecord(ctx->pre_ev, ctx->side));
+    // micro branch (the strip kernels do k_elim_pre's work in the previous solve's epilogue)
+    const bool fused = tiling_uses_stored_residual(ctx->tiling);
+    if (!fused) {
+        CU(launch_elim_pre(ea, ctx->side, ctx->prio_lo));
+        CU(cudaEventRecord(ctx->pre_ev, ctx->side));
+    }
     // macro branch: its prologue reads r^T w before the next solve rewrites it
     tsf_status st = enqueue_macro_prologue(ctx, dt, true);
     if (st) return st;
@@ -822,7 +835,7 @@ static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
     // high priority: the one-block solve is scheduled beside the micro solve
     CU(launch_macro_solve(mg, ctx->stream, ctx->prio_hi));
     if (ev) CU(cudaEventRecord(ev[3], ctx->stream));
-    CU(cudaStreamWaitEvent(ctx->stream, ctx->pre_ev, 0));
+    if (!fused) CU(cudaStreamWaitEvent(ctx->stream, ctx->pre_ev, 0));
     CU(launch_elim_commit(ea, ctx->stream));
     CU(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
     return TSF_OK;

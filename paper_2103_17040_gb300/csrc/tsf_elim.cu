@@ -21,19 +21,26 @@
 //
 // Warm start of w: extrapolated from the last three solves (quadratic
 // 3 w_k - 3 w_{k-1} + w_{k-2}, linear with two, w_k with one), kept in a ring.
-// The column-strip micro kernels compute M w / dt of their solution in an
-// epilogue (FP64 work that overlaps the other blocks' FP32 iterations), so
-// k_elim_pre is then elementwise apart from its norms.
 // Its residual needs S g: a solve leaves its residual e = c - S w behind, so
 // S w = c - e is kept in a second ring and S g is the same combination (no
 // second stencil product).  Without volume or Robin sources only (those are
 // stepped by the unpipelined elimination).
+//
+// The column-strip micro kernels do k_elim_pre's work themselves, so their
+// step has no k_elim_pre: the solve of w_k ends by computing M w_k / dt,
+// pushing w_k and S w_k, and leaving the warm start g and the u-independent
+// part M w_k / dt - S g of the next residual; the next solve adds
+// u^k M psi / dt to both its right-hand side and that residual.  The push
+// then happens one step earlier, so the commit finds w_k at ring slot
+// hist_step + 2 instead of hist_step (ElimArgs::commit_off).  k_elim_pre
+// remains for the one-block-per-problem variants, which keep no residual.
 #include "tsf_internal.cuh"
 
 namespace tsf {
 
 // One block per micro problem: right-hand side c = M v/dt - u mphi of the
-// first w, warm start W = v - u (phi + psi), residual and norms.
+// first w (also into cnext, where the pipelined strip solve reads it with
+// u_old = 0), warm start W = v - u (phi + psi), residual and norms.
 __global__ void __launch_bounds__(256) k_elim_head(ElimArgs a) {
     __shared__ double buf[3 * 32];
     const int i = blockIdx.x, n1 = a.n1, nm = a.nm;
@@ -54,6 +61,7 @@ __global__ void __launch_bounds__(256) k_elim_head(ElimArgs a) {
         const int p = j % n1, q = j / n1;
         const double cj = fma(plane_apply(M, pl, v, j, p, q, n1), idt, -ui * mp[j]);
         c[j] = cj;
+        a.cnext[(size_t)i * pl + j] = cj;
         W[j] = fma(-ui, ph[j] + ps[j], v[j]);
         cc = fma(cj, cj, cc);
         if (p == n1 - 1) {
@@ -195,14 +203,14 @@ __global__ void __launch_bounds__(256) k_elim_pre(ElimArgs a) {
     }
 }
 
-// v^{k+1} = w_k + u^k psi + u^{k+1} phi, w_k from the ring slot k_elim_pre
-// wrote.
+// v^{k+1} = w_k + u^k psi + u^{k+1} phi, w_k from its ring slot (pushed by
+// k_elim_pre in this step, or by the previous step's strip-solve epilogue).
 __global__ void __launch_bounds__(256) k_elim_commit(ElimArgs a) {
     const int i = blockIdx.x;
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     if (j >= a.nm) return;
     const size_t pl = (size_t)a.nmp, o = (size_t)i * pl + j;
-    const double* w = a.hist + (size_t)(a.ctl->hist_step % 3) * a.nM * pl;
+    const double* w = a.hist + (size_t)((a.ctl->hist_step + a.commit_off) % 3) * a.nM * pl;
     a.v[o] = fma(a.u[i], a.phi[o], fma(a.u_old[i], a.psi[o], w[o]));
 }
 

@@ -185,6 +185,17 @@ struct MicroArgs {
     const double* M64;
     double* mw;             // [nM][nmp] or nullptr
     double idt;
+    // column-strip kernels, pipelined elimination (pipe = 1): the solve of w
+    // takes its right-hand side as c = mw + u_old mq (mw as the previous
+    // solve's epilogue left it) and its residual as res + u_old mq; its
+    // epilogue pushes w and S w = c - e into the rings at slot hist_step,
+    // leaves the extrapolated warm start in v, the u-independent part
+    // M w / dt - S g of the next residual in res and M w / dt in mw.
+    int pipe;
+    const double* mq;       // [nM][nmp] M psi / dt
+    const double* u_old;    // [nM] macro values of the right-hand side (zeros for the first w)
+    double* hist;           // [3][nM][nmp] ring of w
+    double* yhist;          // [3][nM][nmp] ring of S w
 };
 
 struct PrologueArgs {
@@ -328,6 +339,8 @@ struct ElimArgs {
     double* yhist;          // [3][nM][nmp] ring of S w = c - (final residual), or nullptr when the
                             // micro-solve variant does not keep its residual (S g then computed)
     int mw_ready;           // 1: the micro solve left M w / dt in cnext (strip kernels' epilogue)
+    int commit_off;         // ring slot of w_k for the commit: (hist_step + commit_off) mod 3 (0: pushed
+                            // by k_elim_pre in this step; 2: pushed by the previous solve's epilogue)
     DevCtl* ctl;
 };
 cudaError_t launch_elim_head(const ElimArgs& a, cudaStream_t s);

@@ -701,23 +701,54 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
     const double ui = a.u[i];
     const double kdu = a.kappa * (ui - a.u_used[i]);
     const bool edge = p == n1 - 1;
+    // pipelined elimination: right-hand side c = mw + u_old mq, residual res + u_old mq
+    const bool pipe = a.pipe != 0;
+    const double uo = pipe ? a.u_old[i] : 0.0;
+    const double* mqi = pipe ? a.mq + (size_t)i * pl : nullptr;
+    double* mwi = pipe ? a.mw + (size_t)i * pl : nullptr;
     double r64[R];
-    float rr = 0.f;
+    float rr = 0.f, cc = 0.f;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         double r = 0.0;
         if (valid[k]) {
-            const int q = q0 + k;
-            r = res[p + n1 * q];
+            const int q = q0 + k, j = p + n1 * q;
+            r = res[j];
             if (edge) r = fma(kdu, re[q], r);
+            if (pipe) {
+                const double m = mqi[j];
+                r = fma(uo, m, r);
+                const float cf = (float)fma(uo, m, mwi[j]);
+                cc = fmaf(cf, cf, cc);
+            }
         }
         r64[k] = r;
         rr = fmaf((float)r, (float)r, rr);
     }
-    const double* bn = a.bnorm + (size_t)i * 3;
-    const double ku = a.kappa * ui;
-    const double bn2 = fma(ku * ku, bn[2], fma(2.0 * ku, bn[1], bn[0]));
-    {
+    double bn2;
+    if (pipe) {
+        // ||c||^2 only sets the stopping-test reference: FP32, with an FP64
+        // recomputation when the FP32 sum leaves [1e-30, 1e30]
+        float t[2] = {rr, cc};
+        block_allreduce<float, 2>(t, red + 128);
+        rr = t[0];
+        bn2 = (double)t[1];
+        if (!(bn2 >= 1e-30 && bn2 <= 1e30)) {  // uniform across the block
+            double c2[1] = {0.0};
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                if (valid[k]) {
+                    const int j = p + n1 * (q0 + k);
+                    const double c = fma(uo, mqi[j], mwi[j]);
+                    c2[0] = fma(c, c, c2[0]);
+                }
+            block_allreduce<double, 1>(c2, reinterpret_cast<double*>(red));
+            bn2 = c2[0];
+        }
+    } else {
+        const double* bn = a.bnorm + (size_t)i * 3;
+        const double ku = a.kappa * ui;
+        bn2 = fma(ku * ku, bn[2], fma(2.0 * ku, bn[1], bn[0]));
         float t[1] = {rr};
         block_allreduce<float, 1>(t, red + 128);
         rr = t[0];
@@ -842,15 +873,54 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
         }
     }
     // store the residual of the new iterate (only Robin-edge values change
-    // when no correction was needed)
+    // when no correction was needed); the pipelined epilogue stores its own
+    if (!pipe) {
 #pragma unroll
-    for (int k = 0; k < R; ++k)
-        if (valid[k] && (solved || (edge && kdu != 0.0))) res[p + n1 * (q0 + k)] = r64[k];
+        for (int k = 0; k < R; ++k)
+            if (valid[k] && (solved || (edge && kdu != 0.0))) res[p + n1 * (q0 + k)] = r64[k];
+    }
     __syncthreads();
+    // pipelined elimination, first half of the epilogue (w = v is final):
+    // M w / dt, S w = c - e, push w and S w into the rings at slot hist_step,
+    // and the extrapolated warm start g with S g from the same combination
+    // (quadratic with two older solves, linear with one)
+    double gv[R], sgv[R], mwn[R];
+    if (pipe) {
+        const int st = a.ctl->hist_step, level = a.ctl->hist_level;
+        const size_t slot = (size_t)a.nM * pl, io = (size_t)i * pl;
+        const double* Mi = a.M64 + (size_t)i * kPlanes * pl;
+        double* hc = a.hist + (size_t)(st % 3) * slot + io;
+        const double* h1 = a.hist + (size_t)((st + 2) % 3) * slot + io;
+        const double* h2 = a.hist + (size_t)((st + 1) % 3) * slot + io;
+        double* yc = a.yhist + (size_t)(st % 3) * slot + io;
+        const double* y1 = a.yhist + (size_t)((st + 2) % 3) * slot + io;
+        const double* y2 = a.yhist + (size_t)((st + 1) % 3) * slot + io;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            gv[k] = sgv[k] = mwn[k] = 0.0;
+            if (!valid[k]) continue;
+            const int q = q0 + k, j = p + n1 * q;
+            const double w = v[j];
+            mwn[k] = plane_apply(Mi, pl, v, j, p, q, n1) * a.idt;
+            const double sw = fma(uo, mqi[j], mwi[j]) - r64[k];
+            double g = w, sg = sw;
+            if (level >= 2) {
+                g = fma(3.0, w - h1[j], h2[j]);
+                sg = fma(3.0, sw - y1[j], y2[j]);
+            } else if (level == 1) {
+                g = fma(2.0, w, -h1[j]);
+                sg = fma(2.0, sw, -y1[j]);
+            }
+            hc[j] = w;
+            yc[j] = sw;
+            gv[k] = g;
+            sgv[k] = sg;
+        }
+    }
     // optional epilogue: M v / dt of the solution in FP64 (the next step's
     // right-hand side of the pipelined elimination; the FP64 work overlaps
     // the FP32 iterations of the other blocks on the SM)
-    if (a.mw) {
+    if (a.mw && !pipe) {
         const double* Mi = a.M64 + (size_t)i * kPlanes * pl;
         double* mw = a.mw + (size_t)i * pl;
 #pragma unroll
@@ -890,6 +960,21 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
             atomicMax(&a.ctl->max_inner, inner);
             if (flag) set_status(a.ctl, flag);
         }
+    }
+    // pipelined elimination, second half: once every read of w (neighbours,
+    // flux) is done, v becomes the warm start of the next solve, res the
+    // u-independent part M w / dt - S g of its residual, mw = M w / dt
+    if (pipe) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (valid[k]) {
+                const int j = p + n1 * (q0 + k);
+                v[j] = gv[k];
+                res[j] = mwn[k] - sgv[k];
+                mwi[j] = mwn[k];
+            }
+        if (i == 0 && tid == 0) a.ctl->pushed = 1;
     }
 }
 
