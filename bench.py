@@ -45,10 +45,21 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
                 "k_micro_strip<3>", "k_micro_strip<5>", "k_micro_strip<7>",
                 "k_micro_strip_tall<9>", "k_micro_strip_tall<11>", "k_micro_strip_tall<13>"]
 # DRAM bytes (read + write) per micro-solve launch from the ncu captures
-# summarised under profiles/ (column-strip kernels, residual update from the
-# split FP32 stencil planes); keyed by (workload, precision, short strip
-# kernel, coupling); entries are removed when the kernel changes.
-MICRO_TRAFFIC = {}
+# summarised under profiles/ (column-strip kernels with the compensated FP32
+# residual update and the pipelined epilogue); keyed by (workload, precision,
+# short strip kernel, coupling); entries are removed when the kernel changes.
+MICRO_TRAFFIC = {
+    # partitioned: averaged over the four coupling iterations of a step
+    # (micro_strip_c2_64x64_32x32.md, k_micro_strip<3>)
+    ("c2", "mixed", True, "partitioned"): 249.7e6,
+    # pipelined elimination: one solve of the next w per launch, with the
+    # epilogue that prepares the following step (step_pipelined_c2_64x64_32x32.md)
+    ("c2", "mixed", True, "elimination"): 850.7e6,
+    # 128x128/64x64, tall strips: captured on 32x32 macro cells (1089 of the
+    # 16641 problems, 898.7 MB a steady launch) and scaled by the problem count
+    # (micro_strip_tall_c3_128x128_64x64.md, k_micro_strip_tall<13>)
+    ("c3", "mixed", False, "elimination"): 13.73e9,
+}
 
 
 def parse():
