@@ -957,6 +957,13 @@ static tsf_status autotune(tsf_ctx* ctx, double dt) {
     CU(cudaMemcpyAsync(ctx->ctl, &saved, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     if (best_t < 0) return fail(ctx, TSF_E_ARG, "no micro-solve variant fits this mesh");
+    // The variants are timed without the pipelined elimination's epilogue,
+    // whose serial per-thread work grows with the strip height: on 32x32
+    // micro cells the short strips R = 3 and R = 5 solve within 1 % of each
+    // other, but with the epilogue R = 3 takes 0.62 ms and R = 5 0.76 ms a
+    // launch.  Eliminating, the lowest short strip is taken when it fits.
+    if (eliminating(ctx) && (best_t == 5 || best_t == 6) && tiling_fits(4, prec, ctx->n1, ctx->smem_optin))
+        best_t = 4;
     ctx->tiling = best_t;
     ctx->tiling_prec = prec;
     return TSF_OK;

@@ -671,7 +671,7 @@ __device__ __forceinline__ void df_add_prod(float& s, float& c, float hi, float 
     c = __fadd_rn(c, __fadd_rn(err, fmaf(lo, x, e)));
 }
 
-template <int R, bool SC>
+template <int R, bool SC, bool PIPE>
 __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n1 = a.n1, Wd = strip_stride(n1, R);
@@ -701,29 +701,33 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
     const double ui = a.u[i];
     const double kdu = a.kappa * (ui - a.u_used[i]);
     const bool edge = p == n1 - 1;
-    // pipelined elimination: right-hand side c = mw + u_old mq, residual res + u_old mq
-    const bool pipe = a.pipe != 0;
-    const double uo = pipe ? a.u_old[i] : 0.0;
-    const double* mqi = pipe ? a.mq + (size_t)i * pl : nullptr;
-    double* mwi = pipe ? a.mw + (size_t)i * pl : nullptr;
+    // pipelined elimination: right-hand side c = mw + u_old mq, residual
+    // res + u_old mq (u_old and the pointers are derived again in the
+    // epilogue, so that nothing of this stays live through the CG loop)
+    constexpr bool pipe = PIPE;
     double r64[R];
     float rr = 0.f, cc = 0.f;
+    {
+        const double uo = pipe ? a.u_old[i] : 0.0;
+        const double* mqi = a.mq + (size_t)i * pl;
+        const double* mwi = a.mw + (size_t)i * pl;
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        double r = 0.0;
-        if (valid[k]) {
-            const int q = q0 + k, j = p + n1 * q;
-            r = res[j];
-            if (edge) r = fma(kdu, re[q], r);
-            if (pipe) {
-                const double m = mqi[j];
-                r = fma(uo, m, r);
-                const float cf = (float)fma(uo, m, mwi[j]);
-                cc = fmaf(cf, cf, cc);
+        for (int k = 0; k < R; ++k) {
+            double r = 0.0;
+            if (valid[k]) {
+                const int q = q0 + k, j = p + n1 * q;
+                r = res[j];
+                if (edge) r = fma(kdu, re[q], r);
+                if (pipe) {
+                    const double m = mqi[j];
+                    r = fma(uo, m, r);
+                    const float cf = (float)fma(uo, m, mwi[j]);
+                    cc = fmaf(cf, cf, cc);
+                }
             }
+            r64[k] = r;
+            rr = fmaf((float)r, (float)r, rr);
         }
-        r64[k] = r;
-        rr = fmaf((float)r, (float)r, rr);
     }
     double bn2;
     if (pipe) {
@@ -734,6 +738,9 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
         rr = t[0];
         bn2 = (double)t[1];
         if (!(bn2 >= 1e-30 && bn2 <= 1e30)) {  // uniform across the block
+            const double uo = a.u_old[i];
+            const double* mqi = a.mq + (size_t)i * pl;
+            const double* mwi = a.mw + (size_t)i * pl;
             double c2[1] = {0.0};
 #pragma unroll
             for (int k = 0; k < R; ++k)
@@ -882,11 +889,16 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
     __syncthreads();
     // pipelined elimination, first half of the epilogue (w = v is final):
     // M w / dt, S w = c - e, push w and S w into the rings at slot hist_step,
-    // and the extrapolated warm start g with S g from the same combination
-    // (quadratic with two older solves, linear with one)
-    double gv[R], sgv[R], mwn[R];
+    // the extrapolated warm start g with S g from the same combination
+    // (quadratic with two older solves, linear with one), and the next
+    // residual's u-independent part M w / dt - S g.  Only v is read at
+    // neighbours, so everything but g is stored at once.
+    double gv[R];
     if (pipe) {
         const int st = a.ctl->hist_step, level = a.ctl->hist_level;
+        const double uo = a.u_old[i];
+        const double* mqi = a.mq + (size_t)i * pl;
+        double* mwi = a.mw + (size_t)i * pl;
         const size_t slot = (size_t)a.nM * pl, io = (size_t)i * pl;
         const double* Mi = a.M64 + (size_t)i * kPlanes * pl;
         double* hc = a.hist + (size_t)(st % 3) * slot + io;
@@ -897,11 +909,11 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
         const double* y2 = a.yhist + (size_t)((st + 1) % 3) * slot + io;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            gv[k] = sgv[k] = mwn[k] = 0.0;
+            gv[k] = 0.0;
             if (!valid[k]) continue;
             const int q = q0 + k, j = p + n1 * q;
             const double w = v[j];
-            mwn[k] = plane_apply(Mi, pl, v, j, p, q, n1) * a.idt;
+            const double mwn = plane_apply(Mi, pl, v, j, p, q, n1) * a.idt;
             const double sw = fma(uo, mqi[j], mwi[j]) - r64[k];
             double g = w, sg = sw;
             if (level >= 2) {
@@ -913,8 +925,9 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
             }
             hc[j] = w;
             yc[j] = sw;
+            mwi[j] = mwn;
+            res[j] = mwn - sg;
             gv[k] = g;
-            sgv[k] = sg;
         }
     }
     // optional epilogue: M v / dt of the solution in FP64 (the next step's
@@ -962,42 +975,42 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
         }
     }
     // pipelined elimination, second half: once every read of w (neighbours,
-    // flux) is done, v becomes the warm start of the next solve, res the
-    // u-independent part M w / dt - S g of its residual, mw = M w / dt
+    // flux) is done, v becomes the warm start of the next solve
     if (pipe) {
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < R; ++k)
-            if (valid[k]) {
-                const int j = p + n1 * (q0 + k);
-                v[j] = gv[k];
-                res[j] = mwn[k] - sgv[k];
-                mwi[j] = mwn[k];
-            }
+            if (valid[k]) v[p + n1 * (q0 + k)] = gv[k];
         if (i == 0 && tid == 0) a.ctl->pushed = 1;
     }
 }
 
 // Short strips (couplings in registers) and tall strips (couplings in shared
-// memory, register budget capped so that several blocks share an SM).
-template <int R>
+// memory, register budget capped so that several blocks share an SM).  PIPE:
+// the pipelined-elimination instantiation (MicroArgs::pipe), separate so that
+// its prologue and epilogue cost the other solves no registers.
+template <int R, bool PIPE>
 __global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::value) k_micro_strip(MicroArgs a) {
-    micro_strip_body<R, false>(a);
+    micro_strip_body<R, false, PIPE>(a);
 }
 constexpr int kTallStripRegs = 160;
-template <int R>
+template <int R, bool PIPE>
 __global__ void __maxnreg__(kTallStripRegs) k_micro_strip_tall(MicroArgs a) {
-    micro_strip_body<R, true>(a);
+    micro_strip_body<R, true, PIPE>(a);
 }
 
 template <int R, bool SC>
 static cudaError_t launch_strip(const MicroArgs& a, cudaStream_t s) {
     const int T = strip_threads(a.n1, R);
     if (T > StripMaxThreads<R>::value) return cudaErrorInvalidConfiguration;
-    if constexpr (SC)
-        k_micro_strip_tall<R><<<a.nM, T, strip_smem_bytes(a.n1, R, SC), s>>>(a);
-    else
-        k_micro_strip<R><<<a.nM, T, strip_smem_bytes(a.n1, R, SC), s>>>(a);
+    const size_t sm = strip_smem_bytes(a.n1, R, SC);
+    if constexpr (SC) {
+        if (a.pipe) k_micro_strip_tall<R, true><<<a.nM, T, sm, s>>>(a);
+        else k_micro_strip_tall<R, false><<<a.nM, T, sm, s>>>(a);
+    } else {
+        if (a.pipe) k_micro_strip<R, true><<<a.nM, T, sm, s>>>(a);
+        else k_micro_strip<R, false><<<a.nM, T, sm, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -1056,14 +1069,17 @@ cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cu
 cudaError_t configure_micro_kernels(int smem_optin) {
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaSuccess;
-    const void* fns[14] = {(const void*)k_micro_solve<double, false, 1>, (const void*)k_micro_solve<double, false, 2>,
+    const void* fns[20] = {(const void*)k_micro_solve<double, false, 1>, (const void*)k_micro_solve<double, false, 2>,
                            (const void*)k_micro_solve<double, false, 4>, (const void*)k_micro_solve<double, false, 8>,
                            (const void*)k_micro_solve<float, true, 1>,   (const void*)k_micro_solve<float, true, 2>,
                            (const void*)k_micro_solve<float, true, 4>,   (const void*)k_micro_solve<float, true, 8>,
-                           (const void*)k_micro_strip<3>,                (const void*)k_micro_strip<5>,
-                           (const void*)k_micro_strip<7>,                (const void*)k_micro_strip_tall<9>,
-                           (const void*)k_micro_strip_tall<11>,          (const void*)k_micro_strip_tall<13>};
-    for (int k = 0; k < 14 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
+                           (const void*)k_micro_strip<3, false>,         (const void*)k_micro_strip<5, false>,
+                           (const void*)k_micro_strip<7, false>,         (const void*)k_micro_strip_tall<9, false>,
+                           (const void*)k_micro_strip_tall<11, false>,   (const void*)k_micro_strip_tall<13, false>,
+                           (const void*)k_micro_strip<3, true>,          (const void*)k_micro_strip<5, true>,
+                           (const void*)k_micro_strip<7, true>,          (const void*)k_micro_strip_tall<9, true>,
+                           (const void*)k_micro_strip_tall<11, true>,    (const void*)k_micro_strip_tall<13, true>};
+    for (int k = 0; k < 20 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
     return e;
 }
 
