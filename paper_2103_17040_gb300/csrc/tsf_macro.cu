@@ -221,27 +221,28 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
         a.x[k] = a.uk[k];
     }
     __syncthreads();
-    // stopping norms in FP32 (they only decide when to stop; vectors, operator
-    // and CG coefficients stay FP64)
-    float bn2 = 0.f, rr = 0.f;
+    // stopping norms in FP64 like everything else here: FP32 sums of squares
+    // would underflow for data scaled below about 1e-19 and stop the solve
+    // before it starts
+    double bn2 = 0.0, rr = 0.0;
     for (int k = tid; k < nM; k += T) {
         const int p = k % n1, q = k / n1;
         const double b = a.q[k];
         const double res = is_dir_node(a.bc, N, p, q) ? 0.0 : b - macro_apply(a, mc, a.x, k, p, q);
         a.r[k] = res;
-        bn2 = fmaf((float)b, (float)b, bn2);
-        rr = fmaf((float)res, (float)res, rr);
+        bn2 = fma(b, b, bn2);
+        rr = fma(res, res, rr);
     }
     {
-        float t[2] = {bn2, rr};
-        block_allreduce<float, 2>(t, reinterpret_cast<float*>(nextbuf()));
+        double t[2] = {bn2, rr};
+        block_allreduce<double, 2>(t, nextbuf());
         bn2 = t[0];
         rr = t[1];
     }
-    const float stop2 = (float)(a.tol * a.tol) * bn2;
+    const double stop2 = a.tol * a.tol * bn2;
     int it = 0;
     bool fail = false;
-    if (rr > stop2 && bn2 > 0.f) {
+    if (rr > stop2 && bn2 > 0.0) {
         // z = P r, p = z
         if (a.use_dct) {
             dct_precond(a, d, a.r, a.z);
@@ -278,17 +279,17 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
                 break;
             }
             const double alpha = rz / pq;
-            rr = 0.f;
+            rr = 0.0;
             for (int k = tid; k < nM; k += T) {
                 a.x[k] = fma(alpha, a.p[k], a.x[k]);
                 const double rn = fma(-alpha, a.q[k], a.r[k]);
                 a.r[k] = rn;
                 a.zo[k] = a.z[k];
-                rr = fmaf((float)rn, (float)rn, rr);
+                rr = fma(rn, rn, rr);
             }
             {
-                float t[1] = {rr};
-                block_allreduce<float, 1>(t, reinterpret_cast<float*>(nextbuf()));
+                double t[1] = {rr};
+                block_allreduce<double, 1>(t, nextbuf());
                 rr = t[0];
             }
             if (!(rr == rr)) {
@@ -322,21 +323,22 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
         if (!fail && rr > stop2) fail = true;
     }
 
-    // coupling control: relative change of the macro iterate
-    float dn2 = 0.f, un2 = 0.f;
+    // coupling control: relative change of the macro iterate (FP64 sums, for
+    // the same reason)
+    double dn2 = 0.0, un2 = 0.0;
     for (int k = tid; k < nM; k += T) {
         const double xn = a.x[k];
-        const float dd = (float)(xn - a.uk[k]);
-        dn2 = fmaf(dd, dd, dn2);
-        un2 = fmaf((float)xn, (float)xn, un2);
+        const double dd = xn - a.uk[k];
+        dn2 = fma(dd, dd, dn2);
+        un2 = fma(xn, xn, un2);
     }
     {
-        float t[2] = {dn2, un2};
-        block_allreduce<float, 2>(t, reinterpret_cast<float*>(nextbuf()));
+        double t[2] = {dn2, un2};
+        block_allreduce<double, 2>(t, nextbuf());
         dn2 = t[0];
         un2 = t[1];
     }
-    const double change = un2 > 0.f ? sqrt((double)dn2 / (double)un2) : sqrt((double)dn2);
+    const double change = un2 > 0.0 ? sqrt(dn2 / un2) : sqrt(dn2);
     const int iter = my_iter + 1;
     const bool converged = change <= a.coupling_tol;
     const bool last = converged || iter >= a.coupling_maxit || !(change == change);

@@ -771,6 +771,12 @@ __device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
             if (valid[k]) v[p + n1 * (q0 + k)] = 0.0;
         }
         solved = true;
+    } else if (!flag && !(stop2 >= 1.17549435e-38f && bn2 <= 1e37)) {
+        // the stopping test and the residual norms are FP32: outside the
+        // range where tol^2 ||b||^2 is a normal FP32 number (and ||r||^2 cannot
+        // overflow) an underflowed ||r||^2 would read as converged, so the
+        // solve reports non-convergence instead (FP64 precision has no limit)
+        flag = kNotConverged;
     } else if (!flag && rr > stop2) {
         solved = true;
         // zero the plane (halo and padding stay zero); scaled couplings into

@@ -215,6 +215,37 @@ def test_per_problem_variants_under_pipelined_elimination(tiling):
 
 
 @pytest.mark.parametrize("coupling", [0, 1])
+def test_fp32_range_of_the_strip_kernels(coupling):
+    """Data scaled by 1e-25: tol^2 ||b||^2 is below the FP32 normal range, so
+    the strip kernels (FP32 stopping test) must report non-convergence
+    instead of returning an unsolved iterate; the per-problem variant
+    (correction solved for the unit-norm residual) and the FP64 path solve
+    the scaled problem, and their results scale back to the unscaled one."""
+    T = _T()
+    NM, Nm = 3, 10
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_SHEAR_BUMP, nM, seed=41)
+    u0, v0 = W.random_state(nM, nm, seed=42)
+    out = {}
+    for key, scale, prec, tiling in (("ref", 1.0, 0, -1), ("fp64", 1e-25, 0, -1), ("mixed_k", 1e-25, 1, 1),
+                                     ("strip", 1e-25, 1, 4)):
+        P = T.TwoScale(Nm, NM, precision=prec, tiling=tiling, coupling=coupling, cg_tol=1e-10, coupling_tol=1e-12)
+        P.set_physics((1.0, 0.0, 0.1), 1.0, 1.0)
+        P.set_deformation(W.FAMILY_SHEAR_BUMP, prm)
+        P.set_state(scale * u0, scale * v0)
+        try:
+            P.step(0.01, 2)
+            P.synchronize()
+            out[key] = (P.u() / scale, P.v() / scale)
+        except T.TsfError as e:
+            out[key] = e.status
+        P.close()
+    assert out["strip"] == T.TSF_E_NOT_CONVERGED
+    for key in ("fp64", "mixed_k"):
+        assert rel(out[key][0], out["ref"][0]) < 1e-7 and rel(out[key][1], out["ref"][1]) < 1e-7, key
+
+
+@pytest.mark.parametrize("coupling", [0, 1])
 def test_mass_balance_on_gpu(coupling):
     NM, Nm = 6, 10
     nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
