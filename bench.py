@@ -54,9 +54,9 @@ MICRO_TRAFFIC = {
     ("c2", "mixed", True, "partitioned"): 247.9e6,
     # pipelined elimination: one solve of the next w per launch, with the
     # epilogue that prepares the following step (step_pipelined_c2_64x64_32x32.md)
-    ("c2", "mixed", True, "elimination"): 846.6e6,
+    ("c2", "mixed", True, "elimination"): 847.2e6,
     # 128x128/64x64, tall strips: captured on 32x32 macro cells (1089 of the
-    # 16641 problems, 895.6 MB a steady launch) and scaled by the problem count
+    # 16641 problems, 896.2 MB a steady launch) and scaled by the problem count
     # (micro_strip_tall_c3_128x128_64x64.md, k_micro_strip_tall<13>)
     ("c3", "mixed", False, "elimination"): 13.69e9,
 }
