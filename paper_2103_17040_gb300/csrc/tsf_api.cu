@@ -754,8 +754,6 @@ static ElimArgs elim_args(tsf_ctx* ctx, double dt) {
     a.u_used = ctx->u_used;
     a.bnorm = ctx->bnorm;
     a.hist = ctx->hist;
-    a.yhist = tiling_uses_stored_residual(ctx->tiling) ? ctx->yhist : nullptr;
-    a.mw_ready = tiling_uses_stored_residual(ctx->tiling) ? 1 : 0;
     a.commit_off = tiling_uses_stored_residual(ctx->tiling) ? 2 : 0;
     a.ctl = ctx->ctl;
     return a;

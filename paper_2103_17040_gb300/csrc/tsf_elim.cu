@@ -12,8 +12,8 @@
 //     macro branch: macro prologue (fluxes r^T w_k + u^k r^T psi), macro
 //                   solve for u^{k+1}, k_elim_commit v^{k+1} = w_k + u^k psi +
 //                   u^{k+1} phi
-//     micro branch: k_elim_pre (right-hand side M z_k/dt, warm start and its
-//                   residual), micro solve for w_{k+1}
+//     micro branch: k_elim_pre (right-hand side M z_k/dt, warm start), micro
+//                   solve for w_{k+1}
 // and the one-block macro solve runs beside the micro solve.  At the end of
 // the launch the state (u^{k+1}, v^{k+1}) is committed and w_{k+1} is ready
 // for the next step.  k_elim_head computes the first w from a state:
@@ -21,19 +21,20 @@
 //
 // Warm start of w: extrapolated from the last three solves (quadratic
 // 3 w_k - 3 w_{k-1} + w_{k-2}, linear with two, w_k with one), kept in a ring.
-// Its residual needs S g: a solve leaves its residual e = c - S w behind, so
-// S w = c - e is kept in a second ring and S g is the same combination (no
-// second stencil product).  Without volume or Robin sources only (those are
-// stepped by the unpipelined elimination).
+// Without volume or Robin sources only (those are stepped by the unpipelined
+// elimination).
 //
-// The column-strip micro kernels do k_elim_pre's work themselves, so their
-// step has no k_elim_pre: the solve of w_k ends by computing M w_k / dt,
-// pushing w_k and S w_k, and leaving the warm start g and the u-independent
-// part M w_k / dt - S g of the next residual; the next solve adds
-// u^k M psi / dt to both its right-hand side and that residual.  The push
-// then happens one step earlier, so the commit finds w_k at ring slot
-// hist_step + 2 instead of hist_step (ElimArgs::commit_off).  k_elim_pre
-// remains for the one-block-per-problem variants, which keep no residual.
+// The column-strip micro kernels, which keep their FP64 residual between
+// solves, do k_elim_pre's work themselves, so their step has no k_elim_pre:
+// the solve of w_k ends by computing M w_k / dt, pushing w_k, and leaving the
+// warm start g and the u-independent part M w_k / dt - S g of the next
+// residual; the next solve adds u^k M psi / dt to both its right-hand side
+// and that residual.  S g needs no second stencil product: the solve leaves
+// its residual e = c - S w, so S w = c - e is kept in a second ring and S g
+// is the same combination of it.  The push then happens one step earlier, so
+// the commit finds w_k at ring slot hist_step + 2 instead of hist_step
+// (ElimArgs::commit_off).  k_elim_pre remains for the one-block-per-problem
+// variants, which form their residual from scratch.
 #include "tsf_internal.cuh"
 
 namespace tsf {
@@ -94,113 +95,37 @@ __global__ void __launch_bounds__(256) k_elim_start(ElimArgs a) {
     }
 }
 
-// One block per micro problem, after the solve of w_k (in W, with c_k and
-// its residual e_k): c_{k+1} = M (w_k + u^k psi)/dt = M w_k/dt + u^k mpsi,
-// push w_k and S w_k = c_k - e_k, W = extrapolated warm start g,
-// res = c_{k+1} - S g, norms of c_{k+1}.
+// One block per micro problem, after the solve of w_k (in W) by a
+// one-block-per-problem variant, which forms its residual and ||b|| itself:
+// c_{k+1} = M (w_k + u^k psi)/dt = M w_k/dt + u^k mpsi, w_k pushed into the
+// ring, W = the extrapolated warm start.  (The strip kernels do this in their
+// pipelined epilogue, with the stored residual.)
 __global__ void __launch_bounds__(256) k_elim_pre(ElimArgs a) {
-    __shared__ float buf[3 * 32];
     const int i = blockIdx.x, n1 = a.n1, nm = a.nm;
     const size_t pl = (size_t)a.nmp, slot = (size_t)a.nM * pl;
     const double* M = a.M64 + (size_t)i * kPlanes * pl;
-    const double* S = a.S64 + (size_t)i * kPlanes * pl;
     const double* mq = a.mpsi + (size_t)i * pl;
-    const double* re = a.redge + (size_t)i * n1;
     double* W = a.W + (size_t)i * pl;
     double* c = a.c + (size_t)i * pl;
-    double* cn = a.cnext + (size_t)i * pl;
-    double* res = a.res + (size_t)i * pl;
     const int st = a.ctl->hist_step, level = a.ctl->hist_level;
     double* hc = a.hist + (size_t)(st % 3) * slot + (size_t)i * pl;
     const double* h1 = a.hist + (size_t)((st + 2) % 3) * slot + (size_t)i * pl;
     const double* h2 = a.hist + (size_t)((st + 1) % 3) * slot + (size_t)i * pl;
     const double uo = a.u_old[i], idt = 1.0 / a.dt;
-    // The norms only set the reference ||b|| of the next solve's stopping test
-    // (u = 0 there, so only ||c||^2 counts): FP32 is ample, and GB300's FP64
-    // rate would make an FP64 block reduction a sizeable part of this kernel.
-    float cc = 0.f, cr = 0.f, rr = 0.f;
+    for (int j = threadIdx.x; j < nm; j += blockDim.x)
+        c[j] = fma(uo, mq[j], plane_apply(M, pl, W, j, j % n1, j / n1, n1) * idt);
+    __syncthreads();  // every read of w_k at neighbours is done
     for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-        const int p = j % n1, q = j / n1;
-        // M w_k / dt from the micro solve's epilogue, or computed here
-        const double mwj = a.mw_ready ? cn[j] : plane_apply(M, pl, W, j, p, q, n1) * idt;
-        const double y = fma(uo, mq[j], mwj);
-        cn[j] = y;
-        const float yf = (float)y;
-        cc = fmaf(yf, yf, cc);
-        if (p == n1 - 1) {
-            const float rf = (float)re[q];
-            cr = fmaf(yf, rf, cr);
-            rr = fmaf(rf, rf, rr);
-        }
+        const double w = W[j];
+        double g = w;
+        if (level >= 2)
+            g = fma(3.0, w - h1[j], h2[j]);
+        else if (level == 1)
+            g = fma(2.0, w, -h1[j]);
+        hc[j] = w;
+        W[j] = g;
     }
-    float tf[3] = {cc, cr, rr};
-    block_allreduce<float, 3>(tf, buf);  // every read of w_k at neighbours is done
-    __syncthreads();
-    double t[3] = {tf[0], tf[1], tf[2]};
-    if (!(tf[0] >= 1e-30f && tf[0] <= 1e30f && tf[2] <= 1e30f)) {
-        // FP32 range exceeded (or c = 0): the same norms in FP64 from the
-        // stored c_{k+1}.  The branch is uniform across the block.
-        __shared__ double dbuf[3 * 32];
-        t[0] = t[1] = t[2] = 0.0;
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const double y = cn[j];
-            t[0] = fma(y, y, t[0]);
-            if (j % n1 == n1 - 1) {
-                const double r = re[j / n1];
-                t[1] = fma(y, r, t[1]);
-                t[2] = fma(r, r, t[2]);
-            }
-        }
-        block_allreduce<double, 3>(t, dbuf);
-        __syncthreads();
-    }
-    if (a.yhist) {
-        double* yc = a.yhist + (size_t)(st % 3) * slot + (size_t)i * pl;
-        const double* y1 = a.yhist + (size_t)((st + 2) % 3) * slot + (size_t)i * pl;
-        const double* y2 = a.yhist + (size_t)((st + 1) % 3) * slot + (size_t)i * pl;
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const double w = W[j], y = c[j] - res[j];
-            double g = w, sg = y;
-            if (level >= 2) {
-                g = fma(3.0, w - h1[j], h2[j]);
-                sg = fma(3.0, y - y1[j], y2[j]);
-            } else if (level == 1) {
-                g = fma(2.0, w, -h1[j]);
-                sg = fma(2.0, y, -y1[j]);
-            }
-            hc[j] = w;
-            yc[j] = y;
-            W[j] = g;
-            const double cj = cn[j];
-            res[j] = cj - sg;
-            c[j] = cj;
-        }
-    } else {
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const double w = W[j];
-            double g = w;
-            if (level >= 2)
-                g = fma(3.0, w - h1[j], h2[j]);
-            else if (level == 1)
-                g = fma(2.0, w, -h1[j]);
-            hc[j] = w;
-            W[j] = g;
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < nm; j += blockDim.x) {
-            const double cj = cn[j];
-            res[j] = cj - plane_apply(S, pl, W, j, j % n1, j / n1, n1);
-            c[j] = cj;
-        }
-    }
-    if (threadIdx.x == 0) {
-        double* bn = a.bnorm + (size_t)i * 3;
-        bn[0] = t[0];
-        bn[1] = t[1];
-        bn[2] = t[2];
-        a.u_used[i] = 0.0;
-        if (i == 0) a.ctl->pushed = 1;
-    }
+    if (i == 0 && threadIdx.x == 0) a.ctl->pushed = 1;
 }
 
 // v^{k+1} = w_k + u^k psi + u^{k+1} phi, w_k from its ring slot (pushed by

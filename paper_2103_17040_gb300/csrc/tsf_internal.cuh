@@ -336,9 +336,6 @@ struct ElimArgs {
     double* u_used;         // [nM]
     double* bnorm;          // [nM][3]
     double* hist;           // [3][nM][nmp] ring of the last solves' w
-    double* yhist;          // [3][nM][nmp] ring of S w = c - (final residual), or nullptr when the
-                            // micro-solve variant does not keep its residual (S g then computed)
-    int mw_ready;           // 1: the micro solve left M w / dt in cnext (strip kernels' epilogue)
     int commit_off;         // ring slot of w_k for the commit: (hist_step + commit_off) mod 3 (0: pushed
                             // by k_elim_pre in this step; 2: pushed by the previous solve's epilogue)
     DevCtl* ctl;
