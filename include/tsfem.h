@@ -71,7 +71,12 @@ typedef enum tsf_status {
 /* arithmetic of the micro solves */
 enum {
     TSF_FP64 = 0,  /* Jacobi-PCG in FP64 */
-    TSF_MIXED = 1  /* FP32 Jacobi-PCG inner solves, FP64 residual and iterative refinement */
+    TSF_MIXED = 1  /* FP32 Jacobi-PCG inner solves, FP64 residual and iterative refinement.
+                      The column-strip variants test convergence with FP32 norms: where
+                      cg_tol^2 ||b||^2 is not a normal FP32 number or ||b||^2 > 1e37 (b the
+                      right-hand side of one micro problem) they report TSF_E_NOT_CONVERGED
+                      rather than return an unsolved iterate; rescale such data or use
+                      TSF_FP64 */
 };
 
 /* deformation families chi(x_i, .) : Z -> Y_{x_i} (Sec. 2, Eqs. (2)-(3)) and their
