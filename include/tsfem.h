@@ -211,6 +211,13 @@ tsf_status tsf_get_macro(tsf_ctx *ctx, double *u_out, int on_device);
 tsf_status tsf_get_micro_averages(tsf_ctx *ctx, double *vbar_out, int on_device);
 tsf_status tsf_get_micro_field(tsf_ctx *ctx, double *v_out, int on_device);
 tsf_status tsf_get_flux(tsf_ctx *ctx, double *flux_out, int on_device);
+/* Coupling moments rho_i = r_i^T v_i of the current micro fields (the Robin
+ * boundary integral of v_i that enters the macro equation, Eq. (17) and
+ * Sec. 3.3), rho_out[nM], summed with compensated (TwoSum) FP64 arithmetic.
+ * tsf_get_flux returns kappa (|Gam_i| u_i - rho_i) + G_i from the same sum;
+ * rho itself does not cancel, so it is the quantity to compare at tight
+ * tolerances.  Synchronises the stream.  Errors: TSF_E_ARG, TSF_E_STATE. */
+tsf_status tsf_get_rho(tsf_ctx *ctx, double *rho_out, int on_device);
 tsf_status tsf_get_geometry(tsf_ctx *ctx, double *gamma_out, double *vol_out, int on_device);
 
 /* Asynchronous variants of tsf_get_macro and tsf_get_micro_averages for
@@ -322,9 +329,8 @@ void tsf_batch_destroy(tsf_batch *b);
  * Macro solve that allocates no device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc when they
  * need a solve -- for example an application that gives all device memory to
- * its own pool allocator at start-up, a latency-critical loop in which a
- * device-synchronising allocation is not acceptable, or code that must not
- * touch the allocator while a stream is being captured.
+ * its own pool allocator at start-up, or a latency-critical loop in which a
+ * device-synchronising allocation is not acceptable.
  *
  * It runs the macro-solve kernel of tsf_step once, on caller-owned device
  * arrays, solving on the NM x NM macro mesh
@@ -343,12 +349,12 @@ void tsf_batch_destroy(tsf_batch *b);
  * device array of the library, sized for TSF_NOALLOC_MAX_NM (about 0.8 MB);
  * every GPU that loads the library holds it until the process exits.  The
  * first call on a device looks up that array's device address and sets the
- * kernel's shared-memory limit, so make the first call on each device before
- * any stream capture.  All calls on a device share the array (it keeps the
- * last call's contents; the call clears what must start from zero): calls
- * that overlap on the GPU, e.g. on two streams at once, race and must not be
- * issued.  The call returns after the solve has finished (it waits for
- * cuda_stream).  Errors: TSF_E_ARG (NM outside 1..TSF_NOALLOC_MAX_NM, bad
+ * kernel's shared-memory limit (and keeps both for the later calls).  All
+ * calls on a device share the array (it keeps the last call's contents; the
+ * call clears what must start from zero): calls that overlap on the GPU, e.g.
+ * on two streams at once, race and must not be issued.  The call blocks: it
+ * reads the solve's status back and waits for cuda_stream before returning,
+ * so it must not be issued on a stream that is being captured.  Errors: TSF_E_ARG (NM outside 1..TSF_NOALLOC_MAX_NM, bad
  * scalar, NULL array), TSF_E_CUDA (runtime failure), TSF_E_NOT_CONVERGED or
  * TSF_E_NAN from the solve; there is no context, so tsf_last_error does not
  * apply.

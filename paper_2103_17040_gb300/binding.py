@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "TSF_OK", 1: "TSF_E_ARG", 2: "TSF_E_STATE", 3: "TSF_E_BAD_JAC
 EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micro_mesh", "tsf_set_macro_mesh",
            "tsf_set_physics", "tsf_set_deformation", "tsf_set_state", "tsf_set_sources", "tsf_step",
            "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_macro_async",
-           "tsf_get_micro_averages_async", "tsf_get_micro_field", "tsf_get_flux", "tsf_get_geometry", "tsf_get_pushforward", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
+           "tsf_get_micro_averages_async", "tsf_get_micro_field", "tsf_get_flux", "tsf_get_rho", "tsf_get_geometry", "tsf_get_pushforward", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
            "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u",
            "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_synchronize",
            "tsf_batch_get_stats", "tsf_batch_reset_stats", "tsf_batch_last_error", "tsf_batch_destroy"]
@@ -108,7 +108,7 @@ def load_library(path: str = LIB_PATH):
     L.tsf_set_sources.argtypes = [vp, vp, vp, vp, vp, i]
     L.tsf_step.argtypes = [vp, d, i]
     L.tsf_synchronize.argtypes = [vp]
-    for f in ("tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux",
+    for f in ("tsf_get_macro", "tsf_get_micro_averages", "tsf_get_micro_field", "tsf_get_flux", "tsf_get_rho",
               "tsf_get_macro_async", "tsf_get_micro_averages_async"):
         getattr(L, f).argtypes = [vp, vp, i]
     L.tsf_get_geometry.argtypes = [vp, vp, vp, i]
@@ -303,6 +303,10 @@ def tsf_get_flux(ctx, nM, out=None):
     return _getter("tsf_get_flux", ctx, nM, out)
 
 
+def tsf_get_rho(ctx, nM, out=None):
+    return _getter("tsf_get_rho", ctx, nM, out)
+
+
 def tsf_get_geometry(ctx, nM):
     g = np.empty(nM)
     v = np.empty(nM)
@@ -425,15 +429,29 @@ def tsf_macro_solve_noalloc(NM, bc, dt, macro_diff, kappa, gam, cH, rho, u0, u_o
     All arrays are CUDA tensors of (NM+1)^2 float64 values; the library uses a
     fixed scratch array of its own instead of allocating.  Returns the PCG
     iteration count; a non-OK status raises TsfError (there is no context, so
-    the message is the status name only)."""
+    the message is the status name only).
+
+    The call runs on the current CUDA device, so every tensor must live on
+    that device (a pointer into another GPU's memory is not reachable from the
+    kernel).  stream: a torch.cuda.Stream or a raw cudaStream_t handle; None
+    means torch's current stream, so the solve is ordered after the work that
+    produced the inputs.  The call waits for the solve to finish before it
+    returns."""
+    import torch
     L = load_library()
     arrs = (gam, cH, rho, u0, u_out)
     n = (int(NM) + 1) ** 2
+    dev = torch.cuda.current_device()
     for a in arrs:
         if not (_is_cuda_tensor(a) and a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()
                 and a.numel() == n):
             raise ValueError(f"expected contiguous float64 CUDA tensors of {n} values")
-    s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        if a.device.index != dev:
+            raise ValueError(f"tensor on cuda:{a.device.index}, but the current device is cuda:{dev}")
+    if stream is None:
+        s = torch.cuda.current_stream().cuda_stream
+    else:
+        s = stream if isinstance(stream, int) else stream.cuda_stream
     it = ctypes.c_int(0)
     st = L.tsf_macro_solve_noalloc(int(NM), int(bc), float(dt), float(macro_diff), float(kappa),
                                    *[a.data_ptr() for a in arrs], float(tol), int(maxit), s or None,
@@ -626,6 +644,10 @@ class TwoScale:
 
     def flux(self, out=None):
         return tsf_get_flux(self.ctx, self.nM, out)
+
+    def rho(self, out=None):
+        """coupling moments r_i^T v_i (compensated FP64 sums)"""
+        return tsf_get_rho(self.ctx, self.nM, out)
 
     def geometry(self):
         return tsf_get_geometry(self.ctx, self.nM)

@@ -1364,8 +1364,20 @@ tsf_status tsf_get_flux(tsf_ctx* ctx, double* flux_out, int on_device) {
         if (st) return st;
     }
     CU(launch_flux(ctx->n1, ctx->nm, ctx->nmp, ctx->nM, ctx->kappa, ctx->gam, ctx->u, ctx->v, ctx->redge,
-                   ctx->has_g ? ctx->g : nullptr, ctx->out, ctx->stream));
+                   ctx->has_g ? ctx->g : nullptr, ctx->out, nullptr, ctx->stream));
     return copy_out(ctx, flux_out, ctx->out, ctx->nM, on_device);
+}
+
+tsf_status tsf_get_rho(tsf_ctx* ctx, double* rho_out, int on_device) {
+    if (!ctx || !rho_out) return TSF_E_ARG;
+    if (!ctx->ws_valid || !ctx->geom_set) return fail(ctx, TSF_E_STATE, "set meshes and deformation first");
+    if (!ctx->ops_valid) {
+        tsf_status st = build_operators(ctx, ctx->ops_dt > 0 ? ctx->ops_dt : 1.0);
+        if (st) return st;
+    }
+    CU(launch_flux(ctx->n1, ctx->nm, ctx->nmp, ctx->nM, ctx->kappa, ctx->gam, ctx->u, ctx->v, ctx->redge, nullptr,
+                   nullptr, ctx->out, ctx->stream));
+    return copy_out(ctx, rho_out, ctx->out, ctx->nM, on_device);
 }
 
 tsf_status tsf_get_geometry(tsf_ctx* ctx, double* gamma_out, double* vol_out, int on_device) {

@@ -308,8 +308,10 @@ cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s, int priority 
 size_t macro_smem_bytes(int N1, int bc, int use_dct);
 cudaError_t launch_vbar(int nm, int nmp, int nM, const double* lm, const double* vol, const double* v,
                         double* vbar, cudaStream_t s);
+// flux_i = kappa (|Gam_i| u_i - rho_i) + r_i^T g_i and rho_i = r_i^T v_i (compensated); either output may be null
 cudaError_t launch_flux(int n1, int nm, int nmp, int nM, double kappa, const double* gam, const double* u,
-                        const double* v, const double* redge, const double* g, double* flux, cudaStream_t s);
+                        const double* v, const double* redge, const double* g, double* flux, double* rho,
+                        cudaStream_t s);
 cudaError_t configure_micro_kernels(int smem_optin);
 cudaError_t configure_macro_kernels(int smem_optin);
 

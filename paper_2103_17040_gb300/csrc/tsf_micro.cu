@@ -1241,24 +1241,52 @@ cudaError_t launch_vbar(int nm, int nmp, int nM, const double* lm, const double*
     return cudaGetLastError();
 }
 
-// F_i = kappa (|Gamma_i| u_i - r_i^T v_i) + r_i^T g_i   (one thread per instance)
-__global__ void k_flux(int n1, int nm, int nmp, int nM, double kappa, const double* __restrict__ gam,
-                       const double* __restrict__ u, const double* __restrict__ v,
-                       const double* __restrict__ redge, const double* __restrict__ g, double* flux) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// rho_i = r_i^T v_i over the Robin-edge nodes (the coupling moment of Eq. (17)
+// that feeds the macro source) and F_i = kappa (|Gamma_i| u_i - rho_i) + r_i^T g_i.
+// One warp per instance; both sums are compensated (TwoSum along the lanes,
+// then a TwoSum butterfly), in a fixed order.  flux and rho may each be null.
+__global__ void __launch_bounds__(256) k_flux(int n1, int nmp, int nM, double kappa, const double* __restrict__ gam,
+                                              const double* __restrict__ u, const double* __restrict__ v,
+                                              const double* __restrict__ redge, const double* __restrict__ g,
+                                              double* flux, double* rho_out) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= nM) return;
-    double rho = 0.0, G = 0.0;
-    for (int q = 0; q < n1; ++q) {
+    double s = 0.0, c = 0.0, sg = 0.0, cg = 0.0;
+    for (int q = lane; q < n1; q += 32) {
         const double r = redge[(size_t)i * n1 + q];
-        rho = fma(r, v[(size_t)i * nmp + (n1 - 1) + (size_t)n1 * q], rho);
-        if (g) G = fma(r, g[(size_t)i * n1 + q], G);
+        double t, e;
+        two_sum(s, r * v[(size_t)i * nmp + (n1 - 1) + (size_t)n1 * q], t, e);
+        s = t;
+        c += e;
+        if (g) {
+            two_sum(sg, r * g[(size_t)i * n1 + q], t, e);
+            sg = t;
+            cg += e;
+        }
     }
-    flux[i] = kappa * (gam[i] * u[i] - rho) + G;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double t, e;
+        two_sum(s, __shfl_xor_sync(0xffffffffu, s, o), t, e);
+        s = t;
+        c += __shfl_xor_sync(0xffffffffu, c, o) + e;
+        two_sum(sg, __shfl_xor_sync(0xffffffffu, sg, o), t, e);
+        sg = t;
+        cg += __shfl_xor_sync(0xffffffffu, cg, o) + e;
+    }
+    if (lane == 0) {
+        const double rho = s + c;
+        if (rho_out) rho_out[i] = rho;
+        if (flux) flux[i] = kappa * (gam[i] * u[i] - rho) + (sg + cg);
+    }
 }
 
 cudaError_t launch_flux(int n1, int nm, int nmp, int nM, double kappa, const double* gam, const double* u,
-                        const double* v, const double* redge, const double* g, double* flux, cudaStream_t s) {
-    k_flux<<<(nM + 127) / 128, 128, 0, s>>>(n1, nm, nmp, nM, kappa, gam, u, v, redge, g, flux);
+                        const double* v, const double* redge, const double* g, double* flux, double* rho,
+                        cudaStream_t s) {
+    (void)nm;
+    k_flux<<<(nM + 7) / 8, 256, 0, s>>>(n1, nmp, nM, kappa, gam, u, v, redge, g, flux, rho);
     return cudaGetLastError();
 }
 

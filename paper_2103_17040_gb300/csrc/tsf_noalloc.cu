@@ -3,14 +3,15 @@
 //
 // Some programs cannot call cudaMalloc at the point where they need a solve:
 // a host application that hands all device memory to its own pool at start-up
-// (so a library allocation would fail or fragment the pool), code running in a
-// latency-critical loop (cudaMalloc may synchronise the whole device), or code
-// that must not touch the allocator while a stream is being captured.  For
-// them this file offers tsf_macro_solve_noalloc: the same macro-solve kernel
-// the coupled step uses, but its scratch vectors and control block live in a
-// fixed file-scope device array instead of a workspace.  The array is part of
-// the loaded library, so every GPU that loads the library holds it (about
-// 0.8 MB) until the process exits.
+// (so a library allocation would fail or fragment the pool), or code running
+// in a latency-critical loop (cudaMalloc may synchronise the whole device).
+// For them this file offers tsf_macro_solve_noalloc: the same macro-solve
+// kernel the coupled step uses, but its scratch vectors and control block live
+// in a fixed file-scope device array instead of a workspace.  The array is
+// part of the loaded library, so every GPU that loads the library holds it
+// (about 0.8 MB) until the process exits.  The call reads its status back and
+// waits for the stream, so it must not be issued on a stream that is being
+// captured into a CUDA graph.
 #include "tsfem.h"
 #include "tsf_internal.cuh"
 
@@ -30,6 +31,7 @@ constexpr size_t kScratchDoubles = 6 * kNoAllocMaxNodes + kCtlDoubles;
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double* g_scratch_addr[kMaxDevices] = {nullptr};  // device address of the array, per device
+int g_smem_optin[kMaxDevices] = {0};                // opt-in shared memory per block, per device
 bool g_setup_done[kMaxDevices] = {false};
 
 }  // namespace
@@ -39,11 +41,14 @@ bool g_setup_done[kMaxDevices] = {false};
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 // Once per device, with that device current: the array's device address and
-// the kernel's shared-memory limit.  Returns the address or nullptr.
-static double* noalloc_setup(int dev, cudaError_t* err) {
+// the kernel's shared-memory limit (*optin receives the device's opt-in
+// shared memory per block, kept for the later calls).  Returns the address or
+// nullptr.
+static double* noalloc_setup(int dev, int* optin_out, cudaError_t* err) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (g_setup_done[dev]) {
         *err = cudaSuccess;
+        *optin_out = g_smem_optin[dev];
         return g_scratch_addr[dev];
     }
     void* ptr = nullptr;
@@ -54,7 +59,9 @@ static double* noalloc_setup(int dev, cudaError_t* err) {
     *err = e;
     if (e != cudaSuccess) return nullptr;
     g_scratch_addr[dev] = static_cast<double*>(ptr);
+    g_smem_optin[dev] = optin;
     g_setup_done[dev] = true;
+    *optin_out = optin;
     return g_scratch_addr[dev];
 }
 
@@ -69,7 +76,8 @@ extern "C" tsf_status tsf_macro_solve_noalloc(int NM, int bc, double dt, double 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TSF_E_CUDA;
     cudaError_t e;
-    double* scratch = noalloc_setup(dev, &e);
+    int optin = 0;
+    double* scratch = noalloc_setup(dev, &optin, &e);
     if (!scratch) return TSF_E_CUDA;
     const int N1 = NM + 1, nM = N1 * N1;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -106,8 +114,6 @@ extern "C" tsf_status tsf_macro_solve_noalloc(int NM, int bc, double dt, double 
     a.maxit = maxit;
     a.coupling_tol = HUGE_VAL;  // one pass: the solve itself is the whole job
     a.coupling_maxit = 1;
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     a.use_dct = macro_smem_bytes(N1, bc, 1) <= (size_t)optin ? 1 : 0;
     a.set_cond = 0;
     a.ctl = ctl;

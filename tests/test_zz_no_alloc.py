@@ -84,6 +84,35 @@ def test_noalloc_macro_solve_matches_step():
     assert np.array_equal(out.cpu().numpy(), u1)
 
 
+def test_noalloc_at_its_size_limit():
+    """NM = TSF_NOALLOC_MAX_NM (the largest mesh the fixed scratch array
+    holds; the fast-diagonalisation preconditioner then takes about 207 KB of
+    shared memory) with the Neumann and the Dirichlet boundary, one call after
+    the other, against the macro solve inside tsf_step."""
+    import torch
+    import paper_2103_17040_gb300 as T
+    T.load_library()
+    NM = T.TSF_NOALLOC_MAX_NM
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
+    for n, (bc, fam, kappa, Du, dt) in enumerate(((T.TSF_BC_NEUMANN, W.FAMILY_BUMP, 1.0, 1.0, 0.01),
+                                                  (T.TSF_BC_DIRICHLET, W.FAMILY_SHEAR_BUMP, 0.7, 1.1, 0.005))):
+        prm = W.random_params(fam, (NM + 1) ** 2, seed=60 + n)
+        gam, cH, rho, u0, u_ref = _reference_step(T, NM, 2, bc, fam, prm, kappa, Du, dt, seed=70 + n)
+        args = [dev(a) for a in (gam, cH, rho, u0)]
+        out = torch.empty_like(args[3])
+        T.tsf_macro_solve_noalloc(NM, bc, dt, Du, kappa, *args, out, tol=1e-13, maxit=500)
+        assert _rel(out.cpu().numpy(), u_ref) < TOL, (bc, _rel(out.cpu().numpy(), u_ref))
+
+
+def test_noalloc_rejects_tensors_on_another_device():
+    import torch
+    import paper_2103_17040_gb300 as T
+    T.load_library()
+    z = torch.zeros(9, dtype=torch.float64)   # host tensor: not on the current CUDA device
+    with pytest.raises(ValueError):
+        T.tsf_macro_solve_noalloc(2, 0, 0.01, 1.0, 1.0, z, z, z, z, z)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
     import paper_2103_17040_gb300 as T
