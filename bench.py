@@ -44,24 +44,16 @@ BYTES_PER_DOF_SWEEP = 64
 KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_micro_solve<8>",
                 "k_micro_strip<3>", "k_micro_strip<5>", "k_micro_strip<7>",
                 "k_micro_strip_tall<9>", "k_micro_strip_tall<11>", "k_micro_strip_tall<13>"]
-# DRAM bytes (read + write) per micro-solve launch from the ncu captures
-# summarised under profiles/ (column-strip kernels with the compensated FP32
-# residual update and the pipelined epilogue); keyed by (workload, precision,
-# short strip kernel, coupling); entries are removed when the kernel changes.
-MICRO_TRAFFIC = {
-    # partitioned: averaged over the four coupling iterations of a step
-    # (micro_strip_c2_64x64_32x32.md, k_micro_strip<3>)
-    ("c2", "mixed", True, "partitioned"): 247.9e6,
-    # pipelined elimination: one solve of the next w per launch, with the
-    # epilogue that prepares the following step (step_pipelined_c2_64x64_32x32.md)
-    ("c2", "mixed", True, "elimination"): 847.2e6,
-    # 128x128/64x64, tall strips: captured on 32x32 macro cells (1089 of the
-    # 16641 problems, 896.2 MB a steady launch) and scaled by the problem count
-    # (micro_strip_tall_c3_128x128_64x64.md, k_micro_strip_tall<13>)
-    ("c3", "mixed", False, "elimination"): 13.69e9,
-}
-
-
+# Source revision of the column-strip kernels that the ncu counters below were
+# taken on.  A kernel change gets a new revision, so counters of an older
+# kernel no longer match and read as null.
+KERNEL_REV = "ff1"
+# Per-launch ncu counters of the micro-solve kernel (the same bench command,
+# captured after a plain run): DRAM bytes (read + write) and executed warp
+# instructions, keyed by (workload, precision, tiling, coupling, revision).
+MICRO_COUNTERS = {}
+# warp instructions one SM can issue per clock (four schedulers)
+ISSUE_PER_SM_CLK = 4
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,7 +259,7 @@ def run_gb300(args):
     clocks = clk.stop()
     P.synchronize()
     st = P.stats()
-    value, ms_max, dof_iters = whole_job_rate(float(st["dof_cg_iters"]), ms, world, "cuda")
+    dof_rate, ms_max, dof_iters = whole_job_rate(float(st["dof_cg_iters"]), ms, world, "cuda")
     steps_per_s = world * K / (ms_max / 1e3)
     # partitioned: 2 prologues + (micro, macro) per coupling iteration; pipelined elimination: start,
     # macro prologue, micro solve, macro solve, commit (+ k_elim_pre with the one-block-per-problem variants)
@@ -277,9 +269,9 @@ def run_gb300(args):
         launches = 2 * K + 2 * st["coupling_iters_total"]
 
     line = {
-        "metric": "micro DOF-CG-iters/s",
-        "value": value,
-        "unit": "DOF-iter/s",
+        "metric": "two-scale steps/s",
+        "value": steps_per_s,
+        "unit": "steps/s",
         "n_gpus": world,
         "steps": K,
         "warmup": Wm,
@@ -295,8 +287,8 @@ def run_gb300(args):
                    "macro_mesh": w.NM, "micro_mesh": w.Nm, "micro_dofs": nM * nm, "dt": w.dt, "tol": w.tol,
                    "coupling_tol": w.coupling_tol, "precision": args.precision, "coupling": args.coupling,
                    "replicas": world,
-                   "l2": "working set > L2 (stencils + vectors ~0.6 GB), no flush"},
-        "steps_per_s": steps_per_s,
+                   "l2": "working set > L2 (operators + vectors over 1 GB), no flush"},
+        "dof_cg_iters_per_s": dof_rate,
         "coupling_iters_per_step": st["coupling_iters_total"] / K,
         "inner_iters_per_solve": st["inner_iters"] / max(st["micro_solves"], 1),
         "refine_sweeps_per_solve": st["refine_sweeps"] / max(st["micro_solves"], 1),
@@ -327,28 +319,8 @@ def run_gb300(args):
     P.step(w.dt, min(K, 10))
     P.synchronize()
     sp = P.stats()
-    micro_ms = sp["micro_kernel_ms"] / max(sp["micro_launches"], 1)
-    bytes_launch = (BYTES_PER_DOF_ITER[args.precision] * sp["dof_cg_iters"] +
-                    (BYTES_PER_DOF_SWEEP * sp["refine_sweeps"] * nm if args.precision == "mixed" else 0)) \
-        / max(sp["micro_launches"], 1)
-    achieved = bytes_launch / (micro_ms / 1e3) / 1e9
-    peaks = measured_peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
-    line["roofline"] = {
-        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": None if args.macro_cells else
-                   MICRO_TRAFFIC.get((args.workload, args.precision, st["tiling"] in (4, 5, 6), args.coupling)),
-        # measured DRAM bytes (ncu, committed summary) per launch / launch time / peak: the
-        # resident kernel keeps its CG state on chip, so this is far below frac
-        "dram_frac": None,
-        "kernel": KERNEL_NAMES[st["tiling"]], "bytes_per_launch": bytes_launch,
-        "avg_launch_ms": micro_ms, "launches_timed": sp["micro_launches"],
-        "macro_kernel_share": sp["macro_kernel_ms"] / max(sp["macro_kernel_ms"] + sp["micro_kernel_ms"], 1e-30),
-        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
-    }
-    tr = line["roofline"]["traffic"]
-    if tr:
-        line["roofline"]["dram_frac"] = tr / (micro_ms / 1e3) / 1e9 / peak
+    line["roofline"] = micro_roofline(args.workload if not args.macro_cells else None, args.precision, args.coupling,
+                                      sp, nm, clocks)
 
     # ---- push-forward of the micro fields for visualisation (device buffer) ----
     xyv = torch.empty(nM * nm * 3, dtype=torch.float32, device="cuda")
@@ -377,19 +349,64 @@ def run_gb300(args):
             k64 = max(2, min(K, 10))
             ms64 = timed_steps(torch, Q, w, k64, lambda: None)
             s64 = Q.stats()
-            line["fp64_path"] = {"value": s64["dof_cg_iters"] / (ms64 / 1e3), "unit": "DOF-iter/s",
+            line["fp64_path"] = {"value": k64 / (ms64 / 1e3), "unit": "steps/s",
+                                 "dof_cg_iters_per_s": s64["dof_cg_iters"] / (ms64 / 1e3),
                                  "ms_per_step": ms64 / k64, "steps": k64,
                                  "speedup_mixed_vs_fp64_per_step": (ms64 / k64) / (ms_max / K)}
             Q.close()
         # ---- end to end through the public API with host buffers ----
         line["e2e"] = run_e2e(torch, T, w, args, stream, float(st["dof_cg_iters"]))
-        # ---- CPU baseline: the oracle on this host's cores + error of the GPU path ----
+        # ---- CPU baseline: the oracle on this host's cores; errors against the tight oracle ----
         if world == 1:
-            line["cpu_baseline"], line["error_vs_oracle"] = run_cpu_baseline(T, w, args, stream)
+            line["cpu_baseline"] = run_cpu_baseline(T, w, args, stream)
+            line["error_vs_tight_oracle"] = run_tight_errors(T, w, args, stream)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def micro_roofline(workload_key, precision, coupling, sp, nm, clocks):
+    """Roofline entry of the micro-solve kernel from its CUDA-event launch time
+    (plain launches, profiled by the library) and, where an ncu capture of the
+    same kernel revision exists, its measured DRAM bytes and instructions.
+
+    * frac: algorithmic bytes (64 B per FP32 DoF-iteration of the inner CG and
+      64 B per DoF and refinement sweep; 128 B per FP64 DoF-iteration) per
+      launch / launch time / HBM peak.  The CG state stays on chip, so this is
+      an algorithmic-equivalent rate that can exceed 1, not an HBM fraction.
+    * dram_frac: the measured DRAM bytes per launch / launch time / HBM peak.
+    * onchip: the issue-rate roofline -- executed warp instructions per launch
+      over the time the SMs would need at four instructions per clock each --
+      the bound of a kernel limited by instruction issue and latency rather
+      than by memory."""
+    micro_ms = sp["micro_kernel_ms"] / max(sp["micro_launches"], 1)
+    bytes_launch = (BYTES_PER_DOF_ITER[precision] * sp["dof_cg_iters"] +
+                    (BYTES_PER_DOF_SWEEP * sp["refine_sweeps"] * nm if precision == "mixed" else 0)) \
+        / max(sp["micro_launches"], 1)
+    achieved = bytes_launch / (micro_ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    ctr = MICRO_COUNTERS.get((workload_key, precision, sp["tiling"], coupling, KERNEL_REV)) if workload_key else None
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "frac_kind": "algorithmic-equivalent (streaming accounting; the CG state stays on chip)",
+           "traffic": ctr["dram_bytes"] if ctr else None,
+           "dram_frac": (ctr["dram_bytes"] / (micro_ms / 1e3) / 1e9 / peak) if ctr else None,
+           "kernel": KERNEL_NAMES[sp["tiling"]], "kernel_rev": KERNEL_REV, "bytes_per_launch": bytes_launch,
+           "avg_launch_ms": micro_ms, "launches_timed": sp["micro_launches"],
+           "macro_kernel_share": sp["macro_kernel_ms"] / max(sp["macro_kernel_ms"] + sp["micro_kernel_ms"], 1e-30),
+           "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s"}
+    if ctr:
+        import torch
+        nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = clocks.get("sm_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
+        ipeak = ISSUE_PER_SM_CLK * nsm * mhz * 1e6
+        ach = ctr["warp_insts"] / (micro_ms / 1e3)
+        out["onchip"] = {"bound": "issue", "achieved": ach, "peak": ipeak, "unit": "warp-inst/s",
+                         "frac": ach / ipeak, "warp_insts_per_launch": ctr["warp_insts"],
+                         "note": f"{ISSUE_PER_SM_CLK} warp instructions per clock per SM at {mhz:.0f} MHz, "
+                                 f"{nsm} SMs; instructions from ncu (smsp__inst_executed.sum)"}
+    return out
 
 
 def run_e2e(torch, T, w, args, stream, dof_iters_device):
@@ -441,8 +458,8 @@ def run_e2e(torch, T, w, args, stream, dof_iters_device):
     if not (np.array_equal(uo_np, P.u()) and np.array_equal(vo_np, P.vbar())):
         raise RuntimeError("asynchronous reads differ from the state")
     P.close()
-    out = {"value": st["dof_cg_iters"] / el, "unit": "DOF-iter/s", "steps": k, "warmup": Wm,
-           "ms_per_step": 1e3 * el / k, "steps_per_s": k / el,
+    out = {"value": k / el, "unit": "steps/s", "steps": k, "warmup": Wm,
+           "ms_per_step": 1e3 * el / k, "dof_cg_iters_per_s": st["dof_cg_iters"] / el,
            "h2d_bytes_per_step": 8 * w.nM, "d2h_bytes_per_step": 8 * 2 * w.nM,
            "inner_iters_per_solve": ips(st),
            "dof_iters_vs_device_loop": st["dof_cg_iters"] / max(dof_iters_device, 1.0),
@@ -451,7 +468,7 @@ def run_e2e(torch, T, w, args, stream, dof_iters_device):
     P = fresh()
     el1, st1 = run(P, lambda: P.set_sources(fu=fu_np), sync_reads)
     P.close()
-    out["sync_reads"] = {"value": st1["dof_cg_iters"] / el1, "ms_per_step": 1e3 * el1 / k,
+    out["sync_reads"] = {"value": k / el1, "unit": "steps/s", "ms_per_step": 1e3 * el1 / k,
                          "inner_iters_per_solve": ips(st1),
                          "note": "the same loop, reading the results synchronously after every step"}
     P = fresh()
@@ -462,7 +479,7 @@ def run_e2e(torch, T, w, args, stream, dof_iters_device):
     u_np, v_np = u_h.numpy(), v_h.numpy()
     el2, st2 = run(P, lambda: P.set_state(u_np, v_np), sync_reads)
     P.close()
-    out["state_roundtrip"] = {"value": st2["dof_cg_iters"] / el2, "ms_per_step": 1e3 * el2 / k,
+    out["state_roundtrip"] = {"value": k / el2, "unit": "steps/s", "ms_per_step": 1e3 * el2 / k,
                               "inner_iters_per_solve": ips(st2),
                               "h2d_bytes_per_step": 8 * (w.nM + w.nM * w.nm), "d2h_bytes_per_step": 8 * 2 * w.nM}
     return out
@@ -470,8 +487,8 @@ def run_e2e(torch, T, w, args, stream, dof_iters_device):
 
 def run_cpu_baseline(T, w, args, stream):
     """The FP64 oracle on the host cores for a bounded sample of the same
-    workload: full-size steps from the initial state until the time budget is
-    spent; the GPU path is advanced by the same steps and compared."""
+    workload: full-size steps from the initial state, at the benchmark
+    tolerances, until the time budget is spent."""
     import oracle
     R = oracle.Problem(w.Nm, w.NM, w.bc, w.family, w.params, D=w.D, kappa=w.kappa, Du=w.Du)
     R.set_state(w.u0, None)
@@ -484,25 +501,41 @@ def run_cpu_baseline(T, w, args, stream):
             break
     el = time.perf_counter() - t0
     rs = R.stats()
-    cpu = {"value": rs["inner_iters"] * w.nm / el, "unit": "DOF-iter/s", "cores": oracle.num_threads(),
-           "kind": "oracle", "sample": f"{n} full-size steps of the workload from u0=1, v0=0 (FP64, CSR Jacobi-PCG, "
-                                       f"OpenMP over micro problems), {el:.1f} s",
-           "steps_per_s": n / el}
-    P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling])
-    P.step(w.dt, n)
-    P.synchronize()
-    u, v = P.u(), P.v()
-    P.close()
-    err = {"steps": n, "rel_l2_u": float(np.linalg.norm(u - R.u) / np.linalg.norm(R.u)),
-           "rel_l2_v": float(np.linalg.norm(v - R.v) / np.linalg.norm(R.v)),
-           "note": "both sides at the benchmark tolerances (relative residual 1e-8, coupling 1e-10)"}
-    return cpu, err
+    return {"value": n / el, "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} full-size steps of the workload from u0=1, v0=0 (FP64, CSR Jacobi-PCG, partitioned "
+                      f"coupling iteration, OpenMP over micro problems), {el:.1f} s",
+            "dof_cg_iters_per_s": rs["inner_iters"] * w.nm / el}
+
+
+def run_tight_errors(T, w, args, stream, nsteps=10):
+    """Error of the GPU paths as benchmarked (mixed and FP64, the benchmark's
+    tolerances and coupling) against the oracle solved tightly (relative
+    residual 1e-13, coupling 1e-13), after nsteps full-size steps."""
+    import oracle
+    R = oracle.Problem(w.Nm, w.NM, w.bc, w.family, w.params, D=w.D, kappa=w.kappa, Du=w.Du)
+    R.set_state(w.u0, None)
+    t0 = time.perf_counter()
+    R.step(w.dt, nsteps, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13)
+    el = time.perf_counter() - t0
+    ru, rv = R.u, R.v
+    out = {"steps": nsteps, "oracle": "FP64, relative residual 1e-13, coupling 1e-13", "oracle_s": el}
+    for prec in ("mixed", "fp64"):
+        P = make_problem(T, w, prec, stream, coupling=COUPLING[args.coupling])
+        P.step(w.dt, nsteps)
+        P.synchronize()
+        u, v = P.u(), P.v()
+        P.close()
+        out[prec] = {"rel_l2_u": float(np.linalg.norm(u - ru) / np.linalg.norm(ru)),
+                     "rel_l2_v": float(np.linalg.norm(v - rv) / np.linalg.norm(rv)),
+                     "tol": w.tol, "coupling": args.coupling}
+    return out
 
 
 def run_reference(args):
-    """The oracle, as it stands, on the host cores: each step one full-size
-    implicit Euler step of a 16x16-macro sample of the workload (same micro
-    problems, fewer of them)."""
+    """The oracle, as it stands, on the host cores, on the same workload as the
+    GPU arm (full size): the paper's partitioned coupling iteration (Sec. 3.3)
+    with FP64 CSR micro problems and Jacobi-PCG, OpenMP over the micro
+    problems, at the benchmark's tolerances; the same metric (steps/s)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -512,9 +545,7 @@ def run_reference(args):
                           "is timed on the 64x64/32x32 and 128x128/64x64 workloads"}))
         return
     import oracle
-    import workloads as W
-    full = workload(args.workload)
-    w = W.c2(NM=16, Nm=full.Nm) if args.workload == "c2" else W.c3(NM=16, Nm=full.Nm)
+    w = workload(args.workload)
     R = oracle.Problem(w.Nm, w.NM, w.bc, w.family, w.params, D=w.D, kappa=w.kappa, Du=w.Du)
     R.set_state(w.u0, None)
     R.step(w.dt, args.warmup, cg_tol=w.tol, coupling_tol=w.coupling_tol, macro_tol=1e-12)
@@ -523,18 +554,19 @@ def run_reference(args):
     R.step(w.dt, args.steps, cg_tol=w.tol, coupling_tol=w.coupling_tol, macro_tol=1e-12)
     el = time.perf_counter() - t0
     rs = R.stats()
-    value = rs["inner_iters"] * w.nm / el
-    sample = (f"{args.steps} steps of a {w.NM}x{w.NM}-macro sample ({w.nM} micro problems of {w.nm} DoFs) "
-              f"of the {args.workload} workload")
-    line = {"metric": "micro DOF-CG-iters/s", "value": value, "unit": "DOF-iter/s", "n_gpus": world,
+    value = args.steps / el
+    sample = f"{args.steps} full-size steps after {args.warmup} warm-up steps"
+    line = {"metric": "two-scale steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": f"{args.workload} (sample: macro {w.NM}x{w.NM}, micro {w.Nm}x{w.Nm})",
+            "impl": "reference", "same_config": True,
+            "config": {"workload": f"{args.workload}: macro {w.NM}x{w.NM}, micro {w.Nm}x{w.Nm}, dt={w.dt}, "
+                                   f"tol={w.tol}, FP64, partitioned coupling (coupling tol {w.coupling_tol})",
                        "precision": "fp64"},
-            "cpu_baseline": {"value": value, "unit": "DOF-iter/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "dof_cg_iters_per_s": rs["inner_iters"] * w.nm / el,
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
-            "e2e": {"value": value, "unit": "DOF-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 

@@ -65,18 +65,22 @@ typedef enum tsf_status {
     TSF_E_NAN = 5,           /* a non-finite value appeared in a solve */
     TSF_E_CUDA = 6,          /* a CUDA runtime call failed */
     TSF_E_OOM = 7,           /* device memory allocation failed or workspace too small */
-    TSF_E_BREAKDOWN = 8      /* p^T A p <= 0 in a CG solve (operator not SPD) */
+    TSF_E_BREAKDOWN = 8,     /* p^T A p <= 0 in a CG solve (operator not SPD) */
+    TSF_E_TIMEOUT = 9        /* a device-side wait (an asynchronous copy into shared memory) did not
+                                complete within its bound; the results of that step are not valid */
 } tsf_status;
 
 /* arithmetic of the micro solves */
 enum {
     TSF_FP64 = 0,  /* Jacobi-PCG in FP64 */
-    TSF_MIXED = 1  /* FP32 Jacobi-PCG inner solves, FP64 residual and iterative refinement.
-                      The column-strip variants test convergence with FP32 norms: where
-                      cg_tol^2 ||b||^2 is not a normal FP32 number or ||b||^2 > 1e37 (b the
-                      right-hand side of one micro problem) they report TSF_E_NOT_CONVERGED
-                      rather than return an unsolved iterate; rescale such data or use
-                      TSF_FP64 */
+    TSF_MIXED = 1  /* FP32 Jacobi-PCG inner solves inside iterative refinement with an
+                      FP64-accurate residual.  The column-strip variants keep that residual
+                      in float-float arithmetic (pairs of FP32 numbers, about 2^-44) and
+                      scale their FP32 norms per micro problem by a power of two, so the
+                      relative tolerance has no FP32 range limit; under the pipelined
+                      elimination their state is held in FP32 pairs, which represent values
+                      down to about 1e-37 (a micro problem whose right-hand side is smaller
+                      is solved to that absolute level). */
 };
 
 /* deformation families chi(x_i, .) : Z -> Y_{x_i} (Sec. 2, Eqs. (2)-(3)) and their

@@ -18,13 +18,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtsfem.so")
 
 TSF_OK, TSF_E_ARG, TSF_E_STATE, TSF_E_BAD_JACOBIAN, TSF_E_NOT_CONVERGED = 0, 1, 2, 3, 4
-TSF_E_NAN, TSF_E_CUDA, TSF_E_OOM, TSF_E_BREAKDOWN = 5, 6, 7, 8
+TSF_E_NAN, TSF_E_CUDA, TSF_E_OOM, TSF_E_BREAKDOWN, TSF_E_TIMEOUT = 5, 6, 7, 8, 9
 TSF_FP64, TSF_MIXED = 0, 1
 TSF_FAMILY_IDENTITY, TSF_FAMILY_BUMP, TSF_FAMILY_SHEAR_BUMP, TSF_FAMILY_AFFINE, TSF_FAMILY_AFFINE_BUMP = 0, 1, 2, 3, 4
 TSF_BC_NEUMANN, TSF_BC_DIRICHLET = 0, 1
 TSF_COUPLING_PARTITIONED, TSF_COUPLING_ELIMINATION = 0, 1
 STATUS_NAMES = {0: "TSF_OK", 1: "TSF_E_ARG", 2: "TSF_E_STATE", 3: "TSF_E_BAD_JACOBIAN", 4: "TSF_E_NOT_CONVERGED",
-                5: "TSF_E_NAN", 6: "TSF_E_CUDA", 7: "TSF_E_OOM", 8: "TSF_E_BREAKDOWN"}
+                5: "TSF_E_NAN", 6: "TSF_E_CUDA", 7: "TSF_E_OOM", 8: "TSF_E_BREAKDOWN", 9: "TSF_E_TIMEOUT"}
 
 # every symbol include/tsfem.h declares
 EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micro_mesh", "tsf_set_macro_mesh",

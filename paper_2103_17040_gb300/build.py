@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtsfem.so")
-SOURCES = ["tsf_api.cu", "tsf_geometry.cu", "tsf_micro.cu", "tsf_macro.cu", "tsf_noalloc.cu", "tsf_adjoint.cu",
+SOURCES = ["tsf_api.cu", "tsf_geometry.cu", "tsf_micro.cu", "tsf_strip.cu", "tsf_macro.cu", "tsf_noalloc.cu", "tsf_adjoint.cu",
            "tsf_elim.cu", "tsf3.cu", "tsf_band.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

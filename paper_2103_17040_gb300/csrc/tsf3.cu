@@ -65,14 +65,12 @@ struct Geom3Args {
     DevCtl* ctl;
 };
 
-// AFFINE: reference-table path (separate instantiation, as in k_geometry)
-template <bool AFFINE>
+// One thread per (micro node, instance); nodes whose map has b = 0 take the
+// reference-table path (as in k_geometry), the others the quadrature points.
 __global__ void __launch_bounds__(128) k3_geometry(Geom3Args a) {
-    __shared__ double ref[AFFINE ? 64 : 1];
-    if constexpr (AFFINE) {
-        fill_reference_tables(ref);
-        __syncthreads();
-    }
+    __shared__ double ref[64];
+    fill_reference_tables(ref);  // by the first 16 threads, before any thread leaves
+    __syncthreads();
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     const int i = blockIdx.x;
     if (j >= a.nmp) return;
@@ -80,13 +78,13 @@ __global__ void __launch_bounds__(128) k3_geometry(Geom3Args a) {
     double* M64 = a.M64 + (size_t)i * kPlanes * pl;
     double* S64 = a.S64 + (size_t)i * kPlanes * pl;
     float* S32 = a.S32 + (size_t)i * kPlanes * pl;
-    float* S32lo = a.S32lo + (size_t)i * kPlanes * pl;
+    float* S32lo = a.S32lo ? a.S32lo + (size_t)i * kPlanes * pl : nullptr;
     if (j >= a.nm) {
         for (int k = 0; k < kPlanes; ++k) {
             M64[k * pl + j] = 0.0;
             S64[k * pl + j] = 0.0;
             S32[k * pl + j] = 0.0f;
-            S32lo[k * pl + j] = 0.0f;
+            if (S32lo) S32lo[k * pl + j] = 0.0f;
         }
         a.lm[(size_t)i * pl + j] = 0.0;
         return;
@@ -96,7 +94,7 @@ __global__ void __launch_bounds__(128) k3_geometry(Geom3Args a) {
     const Deform d = load_deform(a.prm5, i);
     double m[kPlanes], k[kPlanes], lump;
     bool bad;
-    if constexpr (AFFINE) node_couplings_affine(d, a.D11, a.D12, a.D22, p, q, N, ref, m, k, lump, bad);
+    if (d.bpi == 0.0) node_couplings_affine(d, a.D11, a.D12, a.D22, p, q, N, ref, m, k, lump, bad);
     else node_couplings(d, a.D11, a.D12, a.D22, p, q, N, m, k, lump, bad);
     // edge masses; the Robin edges add to S (their couplings run along q: plane 2)
     const bool on_edge[4] = {p == 0, p == N, q == 0, q == N};
@@ -122,7 +120,7 @@ __global__ void __launch_bounds__(128) k3_geometry(Geom3Args a) {
         S64[c * pl + j] = k[c];
         const float hi = (float)k[c];
         S32[c * pl + j] = hi;
-        S32lo[c * pl + j] = (float)(k[c] - (double)hi);
+        if (S32lo) S32lo[c * pl + j] = (float)(k[c] - (double)hi);
     }
     a.lm[(size_t)i * pl + j] = lump;
     if (bad) atomicOr(&a.ctl->geom_error, 1);
@@ -540,7 +538,9 @@ struct tsf3_ctx {
     double *params = nullptr, *prm5 = nullptr;
     float* map32 = nullptr;
     double *M64 = nullptr, *S64 = nullptr, *lm = nullptr;
-    float *S32 = nullptr, *S32lo = nullptr;
+    float* S32 = nullptr;
+    // column-strip micro solves: the scaled operator and the diagonal scalings as FP32 pairs
+    float4 *chat = nullptr, *chatlo = nullptr, *dsc = nullptr;
     double *eRd = nullptr, *eRu = nullptr, *er = nullptr;
     double *fu = nullptr, *fw = nullptr, *ud = nullptr, *gu = nullptr, *gw = nullptr;
     double *fv = nullptr, *gI = nullptr, *gO = nullptr, *gN = nullptr;
@@ -705,7 +705,9 @@ tsf_status tsf3_set_meshes(tsf3_ctx* ctx, int Nm, int NM, double x0, double L, i
     AL(dalloc(ctx, &ctx->M64, F * kPlanes));
     AL(dalloc(ctx, &ctx->S64, F * kPlanes));
     AL(dalloc(ctx, &ctx->S32, F * kPlanes));
-    AL(dalloc(ctx, &ctx->S32lo, F * kPlanes));
+    AL(dalloc(ctx, &ctx->chat, F * 2));
+    AL(dalloc(ctx, &ctx->chatlo, F * 2));
+    AL(dalloc(ctx, &ctx->dsc, F));
     AL(dalloc(ctx, &ctx->lm, F));
     AL(dalloc(ctx, &ctx->eRd, E));
     AL(dalloc(ctx, &ctx->eRu, E));
@@ -834,8 +836,10 @@ static MicroArgs micro3_args(tsf3_ctx* ctx, int t) {
     a.W = ctx->n1 + 2;
     a.nM = ctx->nM;
     a.S32 = ctx->S32;
-    a.S32lo = ctx->S32lo;
     a.S64 = ctx->S64;
+    a.chat = ctx->chat;
+    a.chatlo = ctx->chatlo;
+    a.dsc = ctx->dsc;
     a.c = ctx->c[t];
     a.v = ctx->x[t];
     a.u = ctx->zero;                                   // the macro values enter through c, not the edge term
@@ -901,7 +905,7 @@ static tsf_status build_geometry(tsf3_ctx* ctx) {
     g.M64 = ctx->M64;
     g.S64 = ctx->S64;
     g.S32 = ctx->S32;
-    g.S32lo = ctx->S32lo;
+    g.S32lo = nullptr;
     g.lm = ctx->lm;
     g.eRd = ctx->eRd;
     g.eRu = ctx->eRu;
@@ -909,13 +913,25 @@ static tsf_status build_geometry(tsf3_ctx* ctx) {
     g.ctl = ctx->ctl;
     g.affine = ctx->family == TSF_FAMILY_IDENTITY || ctx->family == TSF_FAMILY_AFFINE;
     dim3 grid(ctx->nM, (ctx->nmp + 127) / 128);
-    if (g.affine) k3_geometry<true><<<grid, 128, 0, ctx->stream>>>(g);
-    else k3_geometry<false><<<grid, 128, 0, ctx->stream>>>(g);
+    k3_geometry<<<grid, 128, 0, ctx->stream>>>(g);
     CU3(cudaGetLastError());
     int bad = 0;
     CU3(cudaMemcpyAsync(&bad, &ctx->ctl->geom_error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CU3(cudaStreamSynchronize(ctx->stream));
     if (bad) return fail3(ctx, TSF_E_BAD_JACOBIAN, "det F <= 0 at a quadrature point of some micro cell");
+    // operator data of the column-strip micro solves (the residual array of the
+    // third right-hand side is free here: every solve starts from k3_setup)
+    StripSetupArgs ss{};
+    ss.n1 = ctx->n1;
+    ss.nm = ctx->nm;
+    ss.nmp = ctx->nmp;
+    ss.nM = ctx->nM;
+    ss.S64 = ctx->S64;
+    ss.rs = ctx->res[2];
+    ss.chat = ctx->chat;
+    ss.chatlo = ctx->chatlo;
+    ss.dsc = ctx->dsc;
+    CU3(launch_strip_setup(ss, ctx->stream));
     ctx->geom_valid = true;
     ctx->phi_valid = false;
     return TSF_OK;

@@ -59,7 +59,12 @@ struct tsf_ctx {
     // device arrays
     double *prm5 = nullptr, *M64 = nullptr, *S64 = nullptr, *lm = nullptr, *redge = nullptr, *Rd = nullptr,
            *Ru = nullptr, *gam = nullptr, *vol = nullptr;
-    float *S32 = nullptr, *S32lo = nullptr;
+    float* S32 = nullptr;
+    // column-strip kernels: scaled operator, diagonal scalings, M/dt as FP32 pairs
+    float4 *chat = nullptr, *chatlo = nullptr, *dsc = nullptr;
+    float *Mh = nullptr, *Ml = nullptr;
+    float2* mq2 = nullptr;       // [nM][nmp] M psi / dt as float pairs
+    float2 *u_old2 = nullptr, *uzero2 = nullptr;  // [nM] u_old and zeros as float pairs
     double *v = nullptr, *c = nullptr, *vtmp = nullptr, *fv = nullptr, *g = nullptr, *G = nullptr;
     double *u = nullptr, *uk = nullptr, *cH = nullptr, *fu = nullptr, *ud = nullptr, *rho = nullptr,
            *out = nullptr;
@@ -310,7 +315,14 @@ static void layout(tsf_ctx* ctx, Arena& A, size_t* off) {
     off[k++] = A.take(nM * kPlanes * pl * sizeof(double));       // M64
     off[k++] = A.take(nM * kPlanes * pl * sizeof(double));       // S64
     off[k++] = A.take(nM * kPlanes * pl * sizeof(float));        // S32
-    off[k++] = A.take(nM * kPlanes * pl * sizeof(float));        // S32lo
+    off[k++] = A.take(nM * 2 * pl * sizeof(float4));             // chat
+    off[k++] = A.take(nM * 2 * pl * sizeof(float4));             // chatlo
+    off[k++] = A.take(nM * pl * sizeof(float4));                 // dsc
+    off[k++] = A.take(nM * kPlanes * pl * sizeof(float));        // Mh
+    off[k++] = A.take(nM * kPlanes * pl * sizeof(float));        // Ml
+    off[k++] = A.take(nM * pl * sizeof(float2));                 // mq2
+    off[k++] = A.take(nM * sizeof(float2));                      // u_old2
+    off[k++] = A.take(nM * sizeof(float2));                      // uzero2
     off[k++] = A.take(nM * pl * sizeof(double));                 // lm
     off[k++] = A.take(nM * n1 * sizeof(double));                 // redge
     off[k++] = A.take(nM * n1 * sizeof(double));                 // Rd
@@ -348,7 +360,14 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->M64 = (double*)(b + off[k++]);
     ctx->S64 = (double*)(b + off[k++]);
     ctx->S32 = (float*)(b + off[k++]);
-    ctx->S32lo = (float*)(b + off[k++]);
+    ctx->chat = (float4*)(b + off[k++]);
+    ctx->chatlo = (float4*)(b + off[k++]);
+    ctx->dsc = (float4*)(b + off[k++]);
+    ctx->Mh = (float*)(b + off[k++]);
+    ctx->Ml = (float*)(b + off[k++]);
+    ctx->mq2 = (float2*)(b + off[k++]);
+    ctx->u_old2 = (float2*)(b + off[k++]);
+    ctx->uzero2 = (float2*)(b + off[k++]);
     ctx->lm = (double*)(b + off[k++]);
     ctx->redge = (double*)(b + off[k++]);
     ctx->Rd = (double*)(b + off[k++]);
@@ -390,7 +409,7 @@ static void assign(tsf_ctx* ctx, const size_t* off) {
     ctx->rho_eff = (double*)(b + off[k++]);
 }
 
-static constexpr int kNumBuffers = 17 + 13 + 5 + 2 + 5 + 1 + 5 + 1 + 1 + 3 + 1;
+static constexpr int kNumBuffers = 17 + 13 + 5 + 2 + 5 + 1 + 5 + 1 + 1 + 3 + 1 + 5 + 2;
 
 tsf_status tsf_workspace_bytes(tsf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return TSF_E_ARG;
@@ -413,6 +432,7 @@ static tsf_status init_workspace(tsf_ctx* ctx) {
     CU(cudaMemsetAsync(ctx->G, 0, (size_t)ctx->nM * sizeof(double), ctx->stream));
     CU(launch_fill(ctx->uzero, 0.0, ctx->nM, ctx->stream));
     CU(launch_fill(ctx->uone, 1.0, ctx->nM, ctx->stream));
+    CU(cudaMemsetAsync(ctx->uzero2, 0, (size_t)ctx->nM * sizeof(float2), ctx->stream));
     ctx->phi_valid = false;
     if (!ctx->dir_vals.empty())
         CU(cudaMemcpyAsync(ctx->ud, ctx->dir_vals.data(), ctx->nM * sizeof(double), cudaMemcpyHostToDevice,
@@ -495,7 +515,7 @@ static tsf_status build_operators(tsf_ctx* ctx, double dt) {
     a.M64 = ctx->M64;
     a.S64 = ctx->S64;
     a.S32 = ctx->S32;
-    a.S32lo = ctx->S32lo;
+    a.S32lo = nullptr;
     a.lm = ctx->lm;
     a.redge = ctx->redge;
     a.Rd = ctx->Rd;
@@ -504,6 +524,21 @@ static tsf_status build_operators(tsf_ctx* ctx, double dt) {
     CU(launch_geometry(a, ctx->stream));
     CU(launch_instance_sums(ctx->n1, ctx->nm, ctx->nmp, ctx->nM, ctx->lm, ctx->redge, ctx->gam, ctx->vol,
                             ctx->stream));
+    StripSetupArgs ss{};
+    ss.n1 = ctx->n1;
+    ss.nm = ctx->nm;
+    ss.nmp = ctx->nmp;
+    ss.nM = ctx->nM;
+    ss.S64 = ctx->S64;
+    ss.M64 = ctx->M64;
+    ss.idt = 1.0 / dt;
+    ss.rs = ctx->vtmp;  // scratch
+    ss.chat = ctx->chat;
+    ss.chatlo = ctx->chatlo;
+    ss.dsc = ctx->dsc;
+    ss.Mh = ctx->Mh;
+    ss.Ml = ctx->Ml;
+    CU(launch_strip_setup(ss, ctx->stream));
     ctx->ops_dt = dt;
     ctx->ops_valid = true;
     ctx->phi_valid = false;
@@ -595,8 +630,10 @@ static MicroArgs micro_args(tsf_ctx* ctx, double* v) {
     a.W = ctx->n1 + 2;
     a.nM = ctx->nM;
     a.S32 = ctx->S32;
-    a.S32lo = ctx->S32lo;
     a.S64 = ctx->S64;
+    a.chat = ctx->chat;
+    a.chatlo = ctx->chatlo;
+    a.dsc = ctx->dsc;
     a.c = ctx->c;
     a.v = v;
     a.u = ctx->uk;
@@ -671,6 +708,10 @@ static tsf_status enqueue_macro_prologue(tsf_ctx* ctx, double dt, bool pipelined
         m.rho_w = ctx->rho;
         m.gam_psi = ctx->gam_psi;
         m.rho_eff = ctx->rho_eff;
+        if (tiling_uses_stored_residual(ctx->tiling)) {  // r^T w from the ring of the strip kernels
+            m.ring2 = reinterpret_cast<const float2*>(ctx->hist);
+            m.nmp = ctx->nmp;
+        }
     }
     CU(launch_macro_prologue(m, ctx->stream));
     return TSF_OK;
@@ -746,6 +787,7 @@ static ElimArgs elim_args(tsf_ctx* ctx, double dt) {
     a.mpsi = ctx->mpsi;
     a.u = ctx->u;
     a.u_old = ctx->u_old;
+    a.u_old2 = tiling_uses_stored_residual(ctx->tiling) ? ctx->u_old2 : nullptr;
     a.v = ctx->v;
     a.W = ctx->W;
     a.c = ctx->c;
@@ -755,6 +797,12 @@ static ElimArgs elim_args(tsf_ctx* ctx, double dt) {
     a.bnorm = ctx->bnorm;
     a.hist = ctx->hist;
     a.commit_off = tiling_uses_stored_residual(ctx->tiling) ? 2 : 0;
+    a.f2 = tiling_uses_stored_residual(ctx->tiling) ? 1 : 0;
+    a.w2 = reinterpret_cast<float2*>(ctx->W);
+    a.res2 = reinterpret_cast<float2*>(ctx->res);
+    a.mw2 = reinterpret_cast<float2*>(ctx->cnext);
+    a.hist2 = reinterpret_cast<const float2*>(ctx->hist);
+    a.gtmp = ctx->vtmp;
     a.ctl = ctx->ctl;
     return a;
 }
@@ -767,15 +815,20 @@ static ElimArgs elim_args(tsf_ctx* ctx, double dt) {
 static MicroArgs w_solve_args(tsf_ctx* ctx, double dt, bool head = false) {
     MicroArgs ma = micro_args(ctx, ctx->W);
     ma.u = ctx->uzero;
+    (void)dt;
     if (tiling_uses_stored_residual(ctx->tiling)) {
-        ma.M64 = ctx->M64;
-        ma.mw = ctx->cnext;
-        ma.idt = 1.0 / dt;
+        // the pipeline's arrays as float pairs (same 8 bytes per value as the
+        // FP64 arrays they share memory with; k_elim_head writes them)
         ma.pipe = 1;
-        ma.mq = ctx->mpsi;
-        ma.u_old = head ? ctx->uzero : ctx->u_old;
-        ma.hist = ctx->hist;
-        ma.yhist = ctx->yhist;
+        ma.u_old2 = head ? ctx->uzero2 : ctx->u_old2;
+        ma.w2 = reinterpret_cast<float2*>(ctx->W);
+        ma.res2 = reinterpret_cast<float2*>(ctx->res);
+        ma.mw2 = reinterpret_cast<float2*>(ctx->cnext);
+        ma.mq2 = ctx->mq2;
+        ma.hist2 = reinterpret_cast<float2*>(ctx->hist);
+        ma.yhist2 = reinterpret_cast<float2*>(ctx->yhist);
+        ma.Mh = ctx->Mh;
+        ma.Ml = ctx->Ml;
     }
     return ma;
 }
@@ -815,10 +868,14 @@ static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
         CU(cudaEventRecord(ctx->pre_ev, ctx->side));
     }
     // macro branch: its prologue reads r^T w before the next solve rewrites it
+    // (the strip kernels leave w in a ring slot the next solve does not touch,
+    // and the prologue sums r^T w itself: their solve starts at once)
     tsf_status st = enqueue_macro_prologue(ctx, dt, true);
     if (st) return st;
-    CU(cudaEventRecord(ctx->mp_ev, ctx->stream));
-    CU(cudaStreamWaitEvent(ctx->side, ctx->mp_ev, 0));
+    if (!fused) {
+        CU(cudaEventRecord(ctx->mp_ev, ctx->stream));
+        CU(cudaStreamWaitEvent(ctx->side, ctx->mp_ev, 0));
+    }
     if (ev) CU(cudaEventRecord(ev[0], ctx->side));
     CU(launch_micro_solve(w_solve_args(ctx, dt), ctx->opt.precision, ctx->tiling, ctx->side));
     if (ev) CU(cudaEventRecord(ev[1], ctx->side));
@@ -893,6 +950,7 @@ static tsf_status compute_phi(tsf_ctx* ctx) {
     b.rho = ctx->gam_psi;
     CU(launch_micro_solve(b, ctx->opt.precision, ctx->tiling, ctx->stream));
     CU(launch_mass_dt(ea, ctx->psi, ctx->mpsi, nullptr, ctx->stream));
+    CU(launch_split_pairs(ctx->mpsi, ctx->mq2, (size_t)ctx->nM * ctx->nmp, ctx->stream));
     CU(cudaMemcpyAsync(&status, &ctx->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     CU(cudaMemcpyAsync(ctx->ctl, &saved, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));

@@ -24,46 +24,61 @@
 // Without volume or Robin sources only (those are stepped by the unpipelined
 // elimination).
 //
-// The column-strip micro kernels, which keep their FP64 residual between
-// solves, do k_elim_pre's work themselves, so their step has no k_elim_pre:
-// the solve of w_k ends by computing M w_k / dt, pushing w_k, and leaving the
-// warm start g and the u-independent part M w_k / dt - S g of the next
-// residual; the next solve adds u^k M psi / dt to both its right-hand side
-// and that residual.  S g needs no second stencil product: the solve leaves
-// its residual e = c - S w, so S w = c - e is kept in a second ring and S g
-// is the same combination of it.  The push then happens one step earlier, so
-// the commit finds w_k at ring slot hist_step + 2 instead of hist_step
-// (ElimArgs::commit_off).  k_elim_pre remains for the one-block-per-problem
-// variants, which form their residual from scratch.
+// The column-strip micro kernels, which keep their residual between solves,
+// do k_elim_pre's work themselves, so their step has no k_elim_pre: the solve
+// of w_k ends by computing M w_k / dt, pushing w_k, and leaving the warm start
+// g and the u-independent part M w_k / dt - S g of the next residual; the
+// next solve adds u^k M psi / dt to both its right-hand side and that
+// residual.  S g needs no second stencil product: the solve leaves its
+// residual e = c - S w, so S w = c - e is kept in a second ring and S g is
+// the same combination of it.  For these kernels every array of the pipeline
+// holds float pairs (hi, lo) instead of FP64 values (ElimArgs::f2): on GB300
+// FP64 arithmetic runs at about 1/70 of the FP32 rate, and the pairs keep the
+// values to about 2^-44 with FP32 instructions only.  The push happens one
+// step earlier, so the commit finds w_k at ring slot hist_step + 2 instead of
+// hist_step (ElimArgs::commit_off).  k_elim_pre remains for the
+// one-block-per-problem variants, which form their residual from scratch.
 #include "tsf_internal.cuh"
 
 namespace tsf {
 
 // One block per micro problem: right-hand side c = M v/dt - u mphi of the
 // first w (also into cnext, where the pipelined strip solve reads it with
-// u_old = 0), warm start W = v - u (phi + psi), residual and norms.
+// u_old = 0), warm start W = v - u (phi + psi), residual and norms.  For the
+// column-strip kernels (f2) the warm start, its residual and the right-hand
+// side go to the float-pair arrays instead; the residual is that of the pair
+// itself (its FP64 value goes through gtmp), so the solve starts consistent.
 __global__ void __launch_bounds__(256) k_elim_head(ElimArgs a) {
     __shared__ double buf[3 * 32];
     const int i = blockIdx.x, n1 = a.n1, nm = a.nm;
-    const size_t pl = (size_t)a.nmp;
+    const size_t pl = (size_t)a.nmp, io = (size_t)i * pl;
     const double* M = a.M64 + (size_t)i * kPlanes * pl;
     const double* S = a.S64 + (size_t)i * kPlanes * pl;
-    const double* v = a.v + (size_t)i * pl;
-    const double* ph = a.phi + (size_t)i * pl;
-    const double* ps = a.psi + (size_t)i * pl;
-    const double* mp = a.mphi + (size_t)i * pl;
+    const double* v = a.v + io;
+    const double* ph = a.phi + io;
+    const double* ps = a.psi + io;
+    const double* mp = a.mphi + io;
     const double* re = a.redge + (size_t)i * n1;
-    double* c = a.c + (size_t)i * pl;
-    double* W = a.W + (size_t)i * pl;
-    double* res = a.res + (size_t)i * pl;
+    double* c = a.c + io;
+    double* W = a.f2 ? a.gtmp + io : a.W + io;
+    double* res = a.res + io;
     const double ui = a.u[i], idt = 1.0 / a.dt;
     double cc = 0.0, cr = 0.0, rr = 0.0;
     for (int j = threadIdx.x; j < nm; j += blockDim.x) {
         const int p = j % n1, q = j / n1;
         const double cj = fma(plane_apply(M, pl, v, j, p, q, n1), idt, -ui * mp[j]);
         c[j] = cj;
-        a.cnext[(size_t)i * pl + j] = cj;
-        W[j] = fma(-ui, ph[j] + ps[j], v[j]);
+        const double g = fma(-ui, ph[j] + ps[j], v[j]);
+        if (a.f2) {
+            const float gh = __double2float_rn(g), gl = __double2float_rn(g - (double)gh);
+            a.w2[io + j] = make_float2(gh, gl);
+            W[j] = (double)gh + (double)gl;
+            const float ch = __double2float_rn(cj);
+            a.mw2[io + j] = make_float2(ch, __double2float_rn(cj - (double)ch));
+        } else {
+            a.cnext[io + j] = cj;
+            W[j] = g;
+        }
         cc = fma(cj, cj, cc);
         if (p == n1 - 1) {
             cr = fma(cj, re[q], cr);
@@ -73,7 +88,15 @@ __global__ void __launch_bounds__(256) k_elim_head(ElimArgs a) {
     double t[3] = {cc, cr, rr};
     block_allreduce<double, 3>(t, buf);  // (also: every thread has written W)
     __syncthreads();
-    for (int j = threadIdx.x; j < nm; j += blockDim.x) res[j] = c[j] - plane_apply(S, pl, W, j, j % n1, j / n1, n1);
+    for (int j = threadIdx.x; j < nm; j += blockDim.x) {
+        const double rj = c[j] - plane_apply(S, pl, W, j, j % n1, j / n1, n1);
+        if (a.f2) {
+            const float rh = __double2float_rn(rj);
+            a.res2[io + j] = make_float2(rh, __double2float_rn(rj - (double)rh));
+        } else {
+            res[j] = rj;
+        }
+    }
     if (threadIdx.x == 0) {
         double* bn = a.bnorm + (size_t)i * 3;
         bn[0] = t[0];
@@ -87,7 +110,14 @@ __global__ void __launch_bounds__(256) k_elim_head(ElimArgs a) {
 // the previous step's k_elim_pre becomes history.
 __global__ void __launch_bounds__(256) k_elim_start(ElimArgs a) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < a.nM) a.u_old[k] = a.u[k];
+    if (k < a.nM) {
+        const double u = a.u[k];
+        a.u_old[k] = u;
+        if (a.u_old2) {
+            const float h = __double2float_rn(u);
+            a.u_old2[k] = make_float2(h, __double2float_rn(u - (double)h));
+        }
+    }
     if (k == 0 && a.ctl->pushed) {
         a.ctl->pushed = 0;
         a.ctl->hist_step += 1;
@@ -135,8 +165,9 @@ __global__ void __launch_bounds__(256) k_elim_commit(ElimArgs a) {
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     if (j >= a.nm) return;
     const size_t pl = (size_t)a.nmp, o = (size_t)i * pl + j;
-    const double* w = a.hist + (size_t)((a.ctl->hist_step + a.commit_off) % 3) * a.nM * pl;
-    a.v[o] = fma(a.u[i], a.phi[o], fma(a.u_old[i], a.psi[o], w[o]));
+    const size_t ring = (size_t)((a.ctl->hist_step + a.commit_off) % 3) * a.nM * pl;
+    const double w = a.f2 ? (double)a.hist2[ring + o].x + (double)a.hist2[ring + o].y : a.hist[ring + o];
+    a.v[o] = fma(a.u[i], a.phi[o], fma(a.u_old[i], a.psi[o], w));
 }
 
 // out = M x / dt, and ||out||^2, out^T r, ||r||^2 per instance

@@ -35,9 +35,38 @@ __device__ __forceinline__ void jacobian(const Deform& d, double s1, double c1, 
 constexpr double kGauss0 = 0.5 - 0.28867513459481288225;
 constexpr double kGauss1 = 0.5 + 0.28867513459481288225;
 
+// Bilinear shape function l (0: (0,0), 1: (1,0), 2: (0,1), 3: (1,1) corner of
+// the cell) and its derivatives at local point (s, t), by selects (no arrays:
+// the element loops below keep every per-thread value in registers).
+__device__ __forceinline__ double q1_phi(int l, double s, double t) {
+    return ((l & 1) ? s : 1.0 - s) * ((l & 2) ? t : 1.0 - t);
+}
+__device__ __forceinline__ double q1_ds(int l, double t) {
+    const double b = (l & 2) ? t : 1.0 - t;
+    return (l & 1) ? b : -b;
+}
+__device__ __forceinline__ double q1_dt(int l, double s) {
+    const double a = (l & 1) ? s : 1.0 - s;
+    return (l & 2) ? a : -a;
+}
+
+// Stored plane (0 C, 1 E, 2 N, 3 NE, 4 NW) of the coupling between local
+// node la of a cell and local node lb of the same cell, seen from la; -1 for
+// the couplings stored at the other node.
+__host__ __device__ constexpr int q1_plane(int la, int lb) {
+    return ((lb & 1) - (la & 1) == 0 && (lb >> 1) - (la >> 1) == 0)   ? 0
+           : ((lb & 1) - (la & 1) == 1 && (lb >> 1) - (la >> 1) == 0) ? 1
+           : ((lb & 1) - (la & 1) == 0 && (lb >> 1) - (la >> 1) == 1) ? 2
+           : ((lb & 1) - (la & 1) == 1 && (lb >> 1) - (la >> 1) == 1) ? 3
+           : ((lb & 1) - (la & 1) == -1 && (lb >> 1) - (la >> 1) == 1) ? 4
+                                                                       : -1;
+}
+
 // The five stored couplings of node (p, q) in M = int J eta eta and in
 // A = int C grad eta . grad eta, summed over the (up to four) cells around the
-// node with 2x2 Gauss points; lump = row sum of M; bad = some J <= 0.
+// node with 2x2 Gauss points; lump = row sum of M; bad = some J <= 0.  Every
+// loop is unrolled, so the local node numbers and planes are compile-time
+// constants and nothing is indexed at run time.
 __device__ __forceinline__ void node_couplings(const Deform& d, double D11, double D12, double D22, int p, int q,
                                                int N, double (&m)[kPlanes], double (&k)[kPlanes], double& lump,
                                                bool& bad) {
@@ -46,18 +75,21 @@ __device__ __forceinline__ void node_couplings(const Deform& d, double D11, doub
     for (int c = 0; c < kPlanes; ++c) m[c] = k[c] = 0.0;
     lump = 0.0;
     bad = false;
+#pragma unroll
     for (int cb = 0; cb < 2; ++cb) {
         const int b = q - 1 + cb;
-        if (b < 0 || b >= N) continue;
+#pragma unroll
         for (int ca = 0; ca < 2; ++ca) {
             const int ac = p - 1 + ca;
-            if (ac < 0 || ac >= N) continue;
-            // local index of node j in this cell
-            const int lx = p - ac, ly = q - b, la = lx + 2 * ly;
+            if (b < 0 || b >= N || ac < 0 || ac >= N) continue;
+            // local index of node (p, q) in this cell: (1 - ca) + 2 (1 - cb)
+            const int la = (1 - ca) + 2 * (1 - cb);
+#pragma unroll
             for (int qt = 0; qt < 2; ++qt) {
                 const double t = qt ? kGauss1 : kGauss0;
                 double s2, c2;
                 sincospi((b + t) * h, &s2, &c2);
+#pragma unroll
                 for (int qs = 0; qs < 2; ++qs) {
                     const double s = qs ? kGauss1 : kGauss0;
                     double s1, c1;
@@ -74,26 +106,23 @@ __device__ __forceinline__ void node_couplings(const Deform& d, double D11, doub
                     const double C11 = (GD11 * G11 + GD12 * G12) * iJ;
                     const double C12 = (GD11 * G21 + GD12 * G22) * iJ;
                     const double C22 = (GD21 * G21 + GD22 * G22) * iJ;
-                    // bilinear shape functions of the cell at (s, t)
-                    const double phi[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
-                    const double dsv[4] = {-(1 - t), (1 - t), -t, t};
-                    const double dtv[4] = {-(1 - s), -s, (1 - s), s};
                     const double wm = 0.25 * h * h * J;
-                    const double gs = C11 * dsv[la] + C12 * dtv[la];
-                    const double gt = C12 * dsv[la] + C22 * dtv[la];
+                    const double pa = q1_phi(la, s, t), dsa = q1_ds(la, t), dta = q1_dt(la, s);
+                    const double gs = C11 * dsa + C12 * dta;
+                    const double gt = C12 * dsa + C22 * dta;
+#pragma unroll
                     for (int lb = 0; lb < 4; ++lb) {
-                        const double me = wm * phi[la] * phi[lb];
+                        const double me = wm * pa * q1_phi(lb, s, t);
                         lump += me;
-                        const int dp = (lb & 1) - lx, dq = (lb >> 1) - ly;
-                        int plane = -1;
-                        if (dp == 0 && dq == 0) plane = 0;
-                        else if (dp == 1 && dq == 0) plane = 1;
-                        else if (dp == 0 && dq == 1) plane = 2;
-                        else if (dp == 1 && dq == 1) plane = 3;
-                        else if (dp == -1 && dq == 1) plane = 4;
-                        if (plane < 0) continue;
-                        m[plane] += me;
-                        k[plane] += 0.25 * (gs * dsv[lb] + gt * dtv[lb]);
+                        const double ke = 0.25 * (gs * q1_ds(lb, t) + gt * q1_dt(lb, s));
+#pragma unroll
+                        for (int c = 0; c < kPlanes; ++c) {
+                            // la is fixed by (ca, cb) and lb by the unrolled loop
+                            if (c == q1_plane(la, lb)) {
+                                m[c] += me;
+                                k[c] += ke;
+                            }
+                        }
                     }
                 }
             }
@@ -110,17 +139,16 @@ __device__ __forceinline__ void fill_reference_tables(double* ref) {
     if (e >= 16) return;
     const int la = e >> 2, lb = e & 3;
     double m = 0.0, ss = 0.0, st = 0.0, tt = 0.0;
+#pragma unroll
     for (int qt = 0; qt < 2; ++qt) {
         const double t = qt ? kGauss1 : kGauss0;
+#pragma unroll
         for (int qs = 0; qs < 2; ++qs) {
             const double s = qs ? kGauss1 : kGauss0;
-            const double phi[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
-            const double dsv[4] = {-(1 - t), (1 - t), -t, t};
-            const double dtv[4] = {-(1 - s), -s, (1 - s), s};
-            m += 0.25 * phi[la] * phi[lb];
-            ss += 0.25 * dsv[la] * dsv[lb];
-            st += 0.25 * dsv[la] * dtv[lb];
-            tt += 0.25 * dtv[la] * dtv[lb];
+            m += 0.25 * q1_phi(la, s, t) * q1_phi(lb, s, t);
+            ss += 0.25 * q1_ds(la, t) * q1_ds(lb, t);
+            st += 0.25 * q1_ds(la, t) * q1_dt(lb, s);
+            tt += 0.25 * q1_dt(la, s) * q1_dt(lb, s);
         }
     }
     ref[e] = m;
@@ -150,27 +178,28 @@ __device__ __forceinline__ void node_couplings_affine(const Deform& d, double D1
     const double C12 = (GD11 * G21 + GD12 * G22) * iJ;
     const double C22 = (GD21 * G21 + GD22 * G22) * iJ;
     const double Jh2 = J * h * h;
+#pragma unroll
     for (int cb = 0; cb < 2; ++cb) {
         const int b = q - 1 + cb;
-        if (b < 0 || b >= N) continue;
+#pragma unroll
         for (int ca = 0; ca < 2; ++ca) {
             const int ac = p - 1 + ca;
-            if (ac < 0 || ac >= N) continue;
-            const int lx = p - ac, ly = q - b, la = lx + 2 * ly;
+            if (b < 0 || b >= N || ac < 0 || ac >= N) continue;
+            const int la = (1 - ca) + 2 * (1 - cb);
+#pragma unroll
             for (int lb = 0; lb < 4; ++lb) {
                 const int e = la * 4 + lb;
                 const double me = Jh2 * ref[e];
                 lump += me;
-                const int dp = (lb & 1) - lx, dq = (lb >> 1) - ly;
-                int plane = -1;
-                if (dp == 0 && dq == 0) plane = 0;
-                else if (dp == 1 && dq == 0) plane = 1;
-                else if (dp == 0 && dq == 1) plane = 2;
-                else if (dp == 1 && dq == 1) plane = 3;
-                else if (dp == -1 && dq == 1) plane = 4;
-                if (plane < 0) continue;
-                m[plane] += me;
-                k[plane] += C11 * ref[16 + e] + C12 * (ref[32 + e] + ref[32 + lb * 4 + la]) + C22 * ref[48 + e];
+                const double ke =
+                    C11 * ref[16 + e] + C12 * (ref[32 + e] + ref[32 + lb * 4 + la]) + C22 * ref[48 + e];
+#pragma unroll
+                for (int c = 0; c < kPlanes; ++c) {
+                    if (c == q1_plane(la, lb)) {
+                        m[c] += me;
+                        k[c] += ke;
+                    }
+                }
             }
         }
     }

@@ -95,18 +95,17 @@ cudaError_t launch_pushforward(int Nm, int n1, int nm, int nmp, int NM, int nM, 
 // One thread per (micro node j, instance i): the five stored couplings of
 // node j in M and in S = M/dt + A + kappa R, summed over the (up to four)
 // cells around the node with 2x2 Gauss points; on Robin-edge nodes also the
-// boundary mass R (2-point Gauss per edge segment).  AFFINE (identity and
-// affine families): F is constant, the element matrices come from the
-// reference tables.  The two paths are separate instantiations: with both
-// in one kernel behind a run-time branch on b = 0, the general path gave
-// wrong couplings on the GPU (cause not found; each path alone is correct).
-template <bool AFFINE>
+// boundary mass R (2-point Gauss per edge segment).  Where the node's own map
+// has b = 0 (identity and affine maps, and any member of the other families
+// whose bump amplitude is zero) F is constant and the element matrices come
+// from the reference tables; otherwise from the quadrature points.  The
+// tables are filled by the first 16 threads before any thread leaves, and the
+// branch is taken on each node's own parameters, so both paths can run in one
+// launch.
 __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
-    __shared__ double ref[AFFINE ? 64 : 1];
-    if constexpr (AFFINE) {
-        fill_reference_tables(ref);
-        __syncthreads();
-    }
+    __shared__ double ref[64];
+    fill_reference_tables(ref);
+    __syncthreads();
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     const int i = blockIdx.x;  // instances on grid.x (up to 2^31 - 1); nodes on grid.y
     if (j >= a.nmp) return;
@@ -114,13 +113,13 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
     double* M64 = a.M64 + (size_t)i * kPlanes * pl;
     double* S64 = a.S64 + (size_t)i * kPlanes * pl;
     float* S32 = a.S32 + (size_t)i * kPlanes * pl;
-    float* S32lo = a.S32lo + (size_t)i * kPlanes * pl;
+    float* S32lo = a.S32lo ? a.S32lo + (size_t)i * kPlanes * pl : nullptr;
     if (j >= a.nm) {  // padding of the planes: zero couplings
         for (int k = 0; k < kPlanes; ++k) {
             M64[k * pl + j] = 0.0;
             S64[k * pl + j] = 0.0;
             S32[k * pl + j] = 0.0f;
-            S32lo[k * pl + j] = 0.0f;
+            if (S32lo) S32lo[k * pl + j] = 0.0f;
         }
         a.lm[(size_t)i * pl + j] = 0.0;
         return;
@@ -130,7 +129,7 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
     const Deform d = load_deform(a.prm5, i);
     double m[kPlanes], k[kPlanes], lump;
     bool bad;
-    if constexpr (AFFINE) node_couplings_affine(d, a.D11, a.D12, a.D22, p, q, N, ref, m, k, lump, bad);
+    if (d.bpi == 0.0) node_couplings_affine(d, a.D11, a.D12, a.D22, p, q, N, ref, m, k, lump, bad);
     else node_couplings(d, a.D11, a.D12, a.D22, p, q, N, m, k, lump, bad);
 
     // Robin edge yhat_1 = 1: R = int s eta eta with s = |cof(F) e1| = sqrt(F22^2 + F12^2)
@@ -155,7 +154,7 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
         S64[c * pl + j] = sv[c];
         const float hi = (float)sv[c];
         S32[c * pl + j] = hi;
-        S32lo[c * pl + j] = (float)(sv[c] - (double)hi);  // the difference is exact in FP64
+        if (S32lo) S32lo[c * pl + j] = (float)(sv[c] - (double)hi);  // the difference is exact in FP64
     }
     a.lm[(size_t)i * pl + j] = lump;
     if (bad) atomicOr(&a.ctl->geom_error, 1);
@@ -163,8 +162,7 @@ __global__ void __launch_bounds__(128) k_geometry(GeomArgs a) {
 
 cudaError_t launch_geometry(const GeomArgs& a, cudaStream_t s) {
     dim3 grid(a.nM, (a.nmp + 127) / 128);
-    if (a.affine) k_geometry<true><<<grid, 128, 0, s>>>(a);
-    else k_geometry<false><<<grid, 128, 0, s>>>(a);
+    k_geometry<<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ namespace tsf {
 constexpr int kPlanes = 5;
 
 // Device status codes (same values as tsf_status).
-enum : int { kOk = 0, kNotConverged = 4, kNaN = 5, kBreakdown = 8, kBadJacobian = 3 };
+enum : int { kOk = 0, kNotConverged = 4, kNaN = 5, kBreakdown = 8, kBadJacobian = 3, kTimeout = 9 };
 
 // Control and statistics block living in device memory.
 struct DevCtl {
@@ -150,7 +150,7 @@ struct GeomArgs {
     double* M64;            // [nM][5][nmp] mass planes
     double* S64;            // [nM][5][nmp] M/dt + A + kappa R planes
     float* S32;             // [nM][5][nmp] S64 rounded to FP32
-    float* S32lo;           // [nM][5][nmp] S64 - S32 rounded to FP32
+    float* S32lo;           // [nM][5][nmp] S64 - S32 rounded to FP32, or nullptr
     double* lm;             // [nM][nmp]    row sums of M (lumped mass)
     double* redge;          // [nM][n1]     r = R 1 on the Robin edge nodes
     double* Rd;             // [nM][n1]     diagonal of R on the edge
@@ -161,41 +161,60 @@ struct GeomArgs {
 struct MicroArgs {
     int n1, nm, nmp, W;     // W = n1 + 2: width of the zero-haloed shared-memory grid
     int nM;
-    const float* S32;
-    const float* S32lo;     // [nM][5][nmp] S64 - S32 rounded to FP32: S32 + S32lo carries S64 to
-                            // about 2^-48 (the residual update of the column-strip kernels)
+    const float* S32;       // [nM][5][nmp] S64 rounded to FP32 (one-block-per-problem variants)
     const double* S64;
     const double* c;        // [nM][nmp] right-hand side without the u term
     double* v;              // [nM][nmp] in: initial guess, out: solution
     const double* u;        // [nM] macro iterate
     const double* redge;    // [nM][n1]
     double kappa;
-    double tol;             // ||b - S v|| <= tol ||b|| (FP64 residual)
+    double tol;             // ||b - S v|| <= tol ||b|| (FP64-accurate residual)
     double inner_tol;       // mixed: relative tolerance of the FP32 inner solve
     int maxit;              // cap on inner iterations per solve
     int max_sweeps;         // mixed: cap on refinement sweeps
     double* rho;            // [nM] out: r_i^T v_i
     int* inst_iters;        // [nM] out: inner iterations of this solve
     DevCtl* ctl;
-    // stored-residual protocol of the column-strip kernel:
+    // stored-residual protocol of the column-strip kernels:
     double* res;            // [nM][nmp] FP64 residual b(u_used) - S v of the current iterate
     double* u_used;         // [nM] macro value the stored residual belongs to
     const double* bnorm;    // [nM][3] ||c||^2, c^T r, ||r||^2 (so ||b(u)||^2 is a quadratic in u)
-    // column-strip kernels, optional epilogue: mw = M v / dt of the solution (FP64)
-    const double* M64;
-    double* mw;             // [nM][nmp] or nullptr
-    double idt;
-    // column-strip kernels, pipelined elimination (pipe = 1): the solve of w
-    // takes its right-hand side as c = mw + u_old mq (mw as the previous
-    // solve's epilogue left it) and its residual as res + u_old mq; its
-    // epilogue pushes w and S w = c - e into the rings at slot hist_step,
-    // leaves the extrapolated warm start in v, the u-independent part
-    // M w / dt - S g of the next residual in res and M w / dt in mw.
+    // column-strip kernels: the Jacobi-scaled operator S^ = D^-1/2 S D^-1/2
+    // (unit diagonal) and the diagonal scalings, as FP32 pairs hi + lo
+    const float4* chat;     // [nM][2][nmp] couplings of S^, high parts: (E, W, N, S), (NE, NW, SE, SW)
+    const float4* chatlo;   // [nM][2][nmp] the low parts (S^ to about 2^-48)
+    const float4* dsc;      // [nM][nmp] (1/sqrt(S_jj) hi, lo, sqrt(S_jj) hi, lo)
+    // column-strip kernels, pipelined elimination (pipe = 1).  The solve of w
+    // takes its right-hand side as c = mw + u_old mq and its residual as
+    // res2 + u_old mq, starting from the warm start in w2; its epilogue pushes
+    // w and S w = c - e into the rings at slot hist_step, leaves the
+    // extrapolated warm start in w2, M w / dt in mw2 and the u-independent
+    // part M w / dt - S g of the next residual in res2.  Every array of the
+    // pipeline holds float pairs (hi, lo).
     int pipe;
-    const double* mq;       // [nM][nmp] M psi / dt
-    const double* u_old;    // [nM] macro values of the right-hand side (zeros for the first w)
-    double* hist;           // [3][nM][nmp] ring of w
-    double* yhist;          // [3][nM][nmp] ring of S w
+    const float2* u_old2;   // [nM] macro values of the right-hand side as float pairs (zeros for the first w)
+    float2* w2;             // [nM][nmp]
+    float2* res2;           // [nM][nmp]
+    float2* mw2;            // [nM][nmp]
+    const float2* mq2;      // [nM][nmp] M psi / dt
+    float2* hist2;          // [3][nM][nmp] ring of w
+    float2* yhist2;         // [3][nM][nmp] ring of S w
+    const float* Mh;        // [nM][5][nmp] M / dt split as Mh + Ml (FP32 pairs)
+    const float* Ml;
+};
+
+// Per (geometry, dt) set-up of the column-strip kernels' operator data.
+struct StripSetupArgs {
+    int n1, nm, nmp, nM;
+    const double* S64;      // [nM][5][nmp]
+    const double* M64;      // [nM][5][nmp] (only with Mh)
+    double idt;             // 1 / dt (only with Mh)
+    double* rs;             // [nM][nmp] scratch: 1 / sqrt(S_jj)
+    float4* chat;
+    float4* chatlo;
+    float4* dsc;
+    float* Mh;              // [nM][5][nmp] or nullptr
+    float* Ml;
 };
 
 struct PrologueArgs {
@@ -266,6 +285,10 @@ struct MacroPrologueArgs {
     double* uk;             // out: initial iterate (Dirichlet values applied)
     // pipelined elimination: rho_eff = rho_w + u gam_psi (fluxes of z = w + u psi)
     const double* rho_w;    // [nM] r^T w, or nullptr
+    // column-strip kernels: rho_w is summed here from the ring of w (float
+    // pairs) at slot (hist_step + 2) mod 3, the w the last solve pushed
+    const float2* ring2;    // [3][nM][nmp] or nullptr
+    int nmp;
     const double* gam_psi;  // [nM] r^T psi
     double* rho_eff;        // [nM] out
     DevCtl* ctl;
@@ -297,6 +320,13 @@ constexpr int kNumTilings = 10;
 // the three-field system's direct micro solve (banded Cholesky, tsf_band.cu)
 constexpr int kTilingDirect = 10;
 bool tiling_fits(int tiling, int precision, int n1, int smem_optin);
+// column-strip kernels (tsf_strip.cu): strips of R = 3, 5, 7 (registers) or 9, 11, 13 (shared memory)
+cudaError_t launch_strip_setup(const StripSetupArgs& a, cudaStream_t s);
+cudaError_t launch_strip_solve(const MicroArgs& a, int R, cudaStream_t s);
+bool strip_fits(int n1, int R, int smem_optin);
+cudaError_t configure_strip_kernels(int smem_optin);
+// out[k] = the float pair nearest to in[k]
+cudaError_t launch_split_pairs(const double* in, float2* out, size_t n, cudaStream_t s);
 cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cudaStream_t s);
 bool tiling_uses_stored_residual(int tiling);
 cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s);
@@ -330,6 +360,7 @@ struct ElimArgs {
     const double* mpsi;     // [nM][nmp] M psi / dt
     const double* u;        // [nM] committed macro state
     double* u_old;          // [nM] the macro state the prepared w belongs to
+    float2* u_old2;         // [nM] the same as float pairs (column-strip kernels)
     double* v;              // [nM][nmp] committed micro state
     double* W;              // [nM][nmp] unknown of the micro solve (warm start on entry)
     double* c;              // [nM][nmp] right-hand side of the w solve
@@ -340,6 +371,13 @@ struct ElimArgs {
     double* hist;           // [3][nM][nmp] ring of the last solves' w
     int commit_off;         // ring slot of w_k for the commit: (hist_step + commit_off) mod 3 (0: pushed
                             // by k_elim_pre in this step; 2: pushed by the previous solve's epilogue)
+    // column-strip kernels (f2 = 1): the pipeline's arrays are float pairs
+    int f2;
+    float2* w2;             // [nM][nmp] warm start of the first w (head)
+    float2* res2;           // [nM][nmp] its residual (head)
+    float2* mw2;            // [nM][nmp] the first right-hand side (head)
+    const float2* hist2;    // [3][nM][nmp] ring of w (commit)
+    double* gtmp;           // [nM][nmp] scratch: the FP64 value of the warm-start pair (head)
     DevCtl* ctl;
 };
 cudaError_t launch_elim_head(const ElimArgs& a, cudaStream_t s);

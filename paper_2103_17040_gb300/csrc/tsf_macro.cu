@@ -432,7 +432,30 @@ __global__ void k_macro_prologue(MacroPrologueArgs a) {
     double uk = a.u[k];
     if (is_dir_node(a.bc, N, p, q) && a.ud) uk = a.ud[k];
     a.uk[k] = uk;
-    if (a.rho_eff) a.rho_eff[k] = fma(a.u[k], a.gam_psi[k], a.rho_w[k]);  // r^T (w + u psi)
+    if (a.rho_eff) {
+        double rw;
+        if (a.ring2) {
+            // r^T w of the w the last column-strip solve pushed (ring slot
+            // hist_step + 2 after k_elim_start), compensated FP64 over the
+            // Robin-edge nodes of micro problem k
+            const size_t slot = (size_t)((a.ctl->hist_step + 2) % 3) * a.nM * a.nmp + (size_t)k * a.nmp;
+            const double* r = a.redge + (size_t)k * a.n1m;
+            double c = 0.0;
+            rw = 0.0;
+            for (int q = 0; q < a.n1m; ++q) {
+                const float2 wq = a.ring2[slot + (a.n1m - 1) + (size_t)a.n1m * q];
+                const double x = (double)wq.x + (double)wq.y;
+                double sum, err;
+                two_sum(rw, r[q] * x, sum, err);
+                rw = sum;
+                c += err + fma(r[q], x, -(r[q] * x));
+            }
+            rw += c;
+        } else {
+            rw = a.rho_w[k];
+        }
+        a.rho_eff[k] = fma(a.u[k], a.gam_psi[k], rw);  // r^T (w + u psi)
+    }
 }
 
 cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s) {

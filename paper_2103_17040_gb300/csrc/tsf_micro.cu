@@ -377,649 +377,6 @@ static cudaError_t launch_smem(const MicroArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// ===========================================================================
-// Column-strip variant (mixed precision).
-//
-// Thread t owns R consecutive nodes of one column of the micro grid:
-// p = t mod n1, rows q0 .. q0+R-1 with q0 = R (t div n1).  The inner FP32 CG
-// runs on the symmetrically Jacobi-scaled operator  S^ = D^-1/2 S D^-1/2
-// (unit diagonal, so the Jacobi preconditioner becomes the identity): the
-// eight off-diagonal couplings of every node, scaled once with the diagonals
-// of both end nodes, sit in registers for the whole solve, and the vector the
-// operator is applied to reaches the neighbours through one zero-haloed
-// shared-memory plane: per iteration a thread stores R values and loads its
-// two neighbour columns (2R + 4 values) plus two halo values of its own
-// column.  The plane's row stride is padded so that the rows of consecutive
-// strips start in the same bank, which keeps warps that straddle two strips
-// free of bank conflicts.  The CG is the Chronopoulos-Gear form: one operator
-// application and ONE fused reduction (r.r, r.Ar) per iteration.
-//
-// FP64 refinement without recomputing b - S v from scratch: the residual of
-// the current iterate is kept in global memory (written by the step prologue
-// and by every solve), so a solve starts from
-//     r = res + kappa (u_i - u_used_i) r_i          (only Robin-edge nodes change)
-// and after each FP32 correction d updates it as r -= S d, v += d.  The
-// products S d are formed in compensated FP32 from S = S32 + S32lo (S64 to
-// about 2^-48; d is exact in FP32) and subtracted from the FP64 residual:
-// the stored residual stays within about 1e-12 ||b|| of b - S64 v, while
-// FP64 instructions (a small fraction of GB300's FP32 rate) are 7 per node
-// instead of about 20.
-// A micro problem whose residual already meets the tolerance returns before
-// staging anything.  ||b(u)||^2 = ||c||^2 + 2 kappa u c^T r + kappa^2 u^2 ||r||^2
-// comes from three per-instance scalars of the prologue.  Convergence tests
-// use norms accumulated in FP32 from the FP64 residual values (a norm only
-// decides when to stop; the residual itself stays FP64).
-// ===========================================================================
-// Launch bounds per strip height: R = 3 asks for two resident blocks of up to
-// 384 threads (register cap 85), R = 5 and 7 for one block of 512 / 384; the
-// tall strips (R = 9, 11, 13, couplings in shared memory) take up to 384
-// threads at kTallStripRegs registers.
-template <int R>
-struct StripMaxThreads {
-    static constexpr int value = R == 3 ? 384 : (R == 5 ? 512 : 384);
-};
-template <int R>
-struct StripMinBlocks {
-    static constexpr int value = R == 3 ? 2 : 1;
-};
-
-__host__ __device__ inline int strip_rows(int n1, int R) { return (n1 + R - 1) / R; }
-
-// Row stride of the shared plane: the smallest W >= n1 + 2 with
-// R W = n1 (mod 32).  Thread t = s n1 + p reads plane word (s R + m) W + p,
-// which is then t + const (mod 32) for every row offset m, so the 32 lanes of
-// a warp hit 32 distinct banks even when the warp straddles two strips.
-// Needs R odd when n1 is odd (R is then invertible mod 32).
-__host__ __device__ inline int strip_stride(int n1, int R) {
-    for (int W = n1 + 2; W < n1 + 2 + 32; ++W)
-        if ((R * W - n1) % 32 == 0) return W;
-    return n1 + 2;  // not reachable for odd R
-}
-
-static int strip_threads(int n1, int R) {
-    const int t = n1 * strip_rows(n1, R);
-    return (t + 31) / 32 * 32;
-}
-
-// Shared memory of a strip block: the plane, 4 x 64 reduction floats and,
-// with couplings in shared memory (sc), two float4 per node of the padded
-// strip grid (n1 columns x strip_rows * R rows).
-static size_t strip_smem_bytes(int n1, int R, bool sc) {
-    const size_t W = (size_t)strip_stride(n1, R), H = (size_t)strip_rows(n1, R) * R + 2;
-    size_t off = (W * H * sizeof(float) + 15) & ~(size_t)15;
-    off += 4 * 64 * sizeof(float);
-    if (sc) off += 2 * (size_t)n1 * strip_rows(n1, R) * R * sizeof(float4);
-    return off;
-}
-
-// The eight scaled off-diagonal couplings of one node.
-struct Couple8 {
-    float E, W, N, S, NE, NW, SE, SW;
-};
-
-// Where a strip's couplings live: in registers (short strips) ...
-template <int R>
-struct RegCouplings {
-    Couple8 c[R];
-    __device__ __forceinline__ Couple8 get(int k) const { return c[k]; }
-};
-// ... or in shared memory as two float4 per node, (E, W, N, S) and
-// (NE, NW, SE, SW), node (p, q) at index p + n1 q of the padded strip grid
-// (tall strips).
-// (The loads are volatile so that the compiler re-reads the couplings at
-// every operator application instead of hoisting them into registers.)
-__device__ __forceinline__ float4 lds_f4(const float4* p) {
-    float4 v;
-    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(addr)
-                 : "memory");
-    return v;
-}
-struct SmemCouplings {
-    const float4* A;
-    const float4* B;
-    int j0, n1;
-    __device__ __forceinline__ Couple8 get(int k) const {
-        const float4 a = lds_f4(A + j0 + k * n1), b = lds_f4(B + j0 + k * n1);
-        return Couple8{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    }
-};
-
-// Neighbour values of a strip from the shared plane: L/Rt = columns p-1 / p+1
-// at rows q0-1 .. q0+R, xm / xp = own column at rows q0-1 and q0+R.
-template <int R>
-struct StripHalo {
-    float L[R + 2], Rt[R + 2], xm, xp;
-    __device__ __forceinline__ void load(const float* P, int Wd, int p, int q0) {
-#pragma unroll
-        for (int m = 0; m < R + 2; ++m) {
-            const float* row = P + (q0 + m) * Wd + p;  // plane row of grid row q0-1+m, column p-1
-            L[m] = row[0];
-            Rt[m] = row[2];
-        }
-        xm = P[q0 * Wd + p + 1];
-        xp = P[(q0 + R + 1) * Wd + p + 1];
-    }
-};
-
-// y = S^ x = x + off-diagonal part for the R nodes of a strip.
-// y = S^ x reading the neighbour columns from the plane with a sliding
-// window of three rows (fewer live registers than a loaded halo for tall
-// strips).  The plane must hold x.  Entries of nodes outside the mesh (and
-// of threads without a strip, whose coupling reads point at node (0, k)) are
-// set to zero, so that they stay out of the dot products.
-template <int R, class CS>
-__device__ __forceinline__ void strip_apply_plane(const CS& cs, const float (&x)[R], const float* P, int Wd, int p,
-                                                  int q0, const bool (&valid)[R], float (&y)[R]) {
-    const float* cl = P + q0 * Wd + p;  // plane column of grid column p-1, from grid row q0-1
-    float l0 = cl[0], l1 = cl[Wd], r0 = cl[2], r1 = cl[Wd + 2];
-    const float xm = cl[1], xp = cl[(R + 1) * Wd + 1];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const float l2 = cl[(k + 2) * Wd], r2 = cl[(k + 2) * Wd + 2];
-        const Couple8 c = cs.get(k);
-        const float up = (k + 1 < R) ? x[k + 1] : xp;
-        const float dn = (k > 0) ? x[k - 1] : xm;
-        float t = fmaf(c.E, r1, x[k]);
-        t = fmaf(c.W, l1, t);
-        t = fmaf(c.N, up, t);
-        t = fmaf(c.S, dn, t);
-        t = fmaf(c.NE, r2, t);
-        t = fmaf(c.NW, l2, t);
-        t = fmaf(c.SE, r0, t);
-        t = fmaf(c.SW, l0, t);
-        y[k] = valid[k] ? t : 0.f;
-        l0 = l1;
-        l1 = l2;
-        r0 = r1;
-        r1 = r2;
-    }
-}
-
-template <int R, class CS>
-__device__ __forceinline__ void strip_apply(const CS& cs, const float (&x)[R], const StripHalo<R>& h,
-                                            float (&y)[R]) {
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const Couple8 c = cs.get(k);
-        const float up = (k + 1 < R) ? x[k + 1] : h.xp;
-        const float dn = (k > 0) ? x[k - 1] : h.xm;
-        float t = fmaf(c.E, h.Rt[k + 1], x[k]);
-        t = fmaf(c.W, h.L[k + 1], t);
-        t = fmaf(c.N, up, t);
-        t = fmaf(c.S, dn, t);
-        t = fmaf(c.NE, h.Rt[k + 2], t);
-        t = fmaf(c.NW, h.L[k + 2], t);
-        t = fmaf(c.SE, h.Rt[k], t);
-        t = fmaf(c.SW, h.L[k], t);
-        y[k] = t;
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void strip_store(float* P, int Wd, int p, int q0, const bool (&valid)[R],
-                                            const float (&v)[R]) {
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-        if (valid[k]) P[(q0 + k + 1) * Wd + p + 1] = v[k];
-}
-
-// Chronopoulos-Gear CG on the scaled operator (Jacobi-PCG on S); x = 0 on
-// entry, r = rhs.  Stops when ||r||^2 <= rel2 ||r_0||^2 or after maxit
-// iterations; returns the count.  redA/redB: 64-float reduction buffers.
-template <int R, class CS>
-__device__ int strip_cg(const CS& c, const bool (&valid)[R], float (&x)[R], float (&r)[R], float* P,
-                        int Wd, int p, int q0, float rel2, int maxit, float* redA, float* redB, int* flag) {
-    float pv[R], s[R], w[R];
-    StripHalo<R> h;
-    strip_store<R>(P, Wd, p, q0, valid, r);
-    __syncthreads();
-    if constexpr (R >= 9) {
-        strip_apply_plane<R>(c, r, P, Wd, p, q0, valid, w);
-    } else {
-        h.load(P, Wd, p, q0);
-        strip_apply<R>(c, r, h, w);
-    }
-    float g = 0.f, dl = 0.f;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        g = fmaf(r[k], r[k], g);
-        dl = fmaf(r[k], w[k], dl);
-        pv[k] = r[k];
-        s[k] = w[k];
-    }
-    {
-        float t[2] = {g, dl};
-        block_allreduce<float, 2>(t, redA);
-        g = t[0];
-        dl = t[1];
-    }
-    const float stop = rel2 * g;
-    if (!(dl > 0.f)) {
-        *flag = (dl == dl) ? kBreakdown : kNaN;
-        return 0;
-    }
-    // CG scalars with the fast division (a few ulp): they steer the FP32 inner
-    // solve only, whose result is checked by the FP64 residual
-    float alpha = __fdividef(g, dl);
-    int it = 0;
-    while (it < maxit) {
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            x[k] = fmaf(alpha, pv[k], x[k]);
-            r[k] = fmaf(-alpha, s[k], r[k]);
-        }
-        ++it;
-        strip_store<R>(P, Wd, p, q0, valid, r);
-        __syncthreads();
-        if constexpr (R >= 9) {
-            strip_apply_plane<R>(c, r, P, Wd, p, q0, valid, w);
-        } else {
-            h.load(P, Wd, p, q0);
-            strip_apply<R>(c, r, h, w);
-        }
-        float gn = 0.f, dn = 0.f;
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            gn = fmaf(r[k], r[k], gn);
-            dn = fmaf(r[k], w[k], dn);
-        }
-        {
-            float t[2] = {gn, dn};
-            block_allreduce<float, 2>(t, (it & 1) ? redB : redA);
-            gn = t[0];
-            dn = t[1];
-        }
-        if (!(gn == gn) || !(dn == dn)) {
-            *flag = kNaN;
-            break;
-        }
-        if (gn <= stop) break;
-        const float beta = __fdividef(gn, g);
-        const float den = dn - __fdividef(beta * gn, alpha);
-        if (!(den > 0.f)) {
-            *flag = kBreakdown;
-            break;
-        }
-        alpha = __fdividef(gn, den);
-        g = gn;
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            pv[k] = fmaf(beta, pv[k], r[k]);
-            s[k] = fmaf(beta, s[k], w[k]);
-        }
-    }
-    return it;
-}
-
-// Accumulate (hi + lo) x into the unevaluated float pair (s, c) for an FP32
-// x: hi x = p + e exactly (TwoProduct with an FMA), s + p = t + err exactly
-// (Knuth's TwoSum), and the small parts go to c.  For the nine terms of a
-// stencil row the pair carries the FP64 product sum to about 2^-44 of the
-// largest partial sum, without the FP64 pipe (a warp-wide FP64 instruction
-// costs as much issue as 64 FP32 ones on this part).  The round-to-nearest
-// intrinsics keep the compiler from contracting the error-free steps.
-__device__ __forceinline__ void df_add_prod(float& s, float& c, float hi, float lo, float x) {
-    const float p = __fmul_rn(hi, x);
-    const float e = fmaf(hi, x, -p);
-    const float t = __fadd_rn(s, p);
-    const float bp = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(err, fmaf(lo, x, e)));
-}
-
-template <int R, bool SC, bool PIPE>
-__device__ __forceinline__ void micro_strip_body(const MicroArgs& a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int n1 = a.n1, Wd = strip_stride(n1, R);
-    const int Hd = strip_rows(n1, R) * R + 2;
-    float* P = reinterpret_cast<float*>(smem);
-    size_t off = ((size_t)Wd * Hd * sizeof(float) + 15) & ~(size_t)15;
-    float* red = reinterpret_cast<float*>(smem + off);  // 4 x 64 floats
-    // SC: scaled couplings of the padded strip grid (n1 x strip_rows * R nodes)
-    const int ncg = n1 * strip_rows(n1, R) * R;
-    float4* cA = reinterpret_cast<float4*>(smem + off + 4 * 64 * sizeof(float));
-    float4* cB = cA + ncg;
-
-    const int i = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
-    const bool active = tid < n1 * strip_rows(n1, R);
-    const int p = active ? tid % n1 : 0;
-    const int q0 = active ? (tid / n1) * R : 0;
-    const size_t pl = (size_t)a.nmp;
-    double* res = a.res + (size_t)i * pl;
-    double* v = a.v + (size_t)i * pl;
-    const double* re = a.redge + (size_t)i * n1;
-
-    bool valid[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) valid[k] = active && (q0 + k) < n1;
-
-    // residual of the current iterate for the new macro value u_i
-    const double ui = a.u[i];
-    const double kdu = a.kappa * (ui - a.u_used[i]);
-    const bool edge = p == n1 - 1;
-    // pipelined elimination: right-hand side c = mw + u_old mq, residual
-    // res + u_old mq (u_old and the pointers are derived again in the
-    // epilogue, so that nothing of this stays live through the CG loop)
-    constexpr bool pipe = PIPE;
-    double r64[R];
-    float rr = 0.f, cc = 0.f;
-    {
-        const double uo = pipe ? a.u_old[i] : 0.0;
-        const double* mqi = a.mq + (size_t)i * pl;
-        const double* mwi = a.mw + (size_t)i * pl;
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            double r = 0.0;
-            if (valid[k]) {
-                const int q = q0 + k, j = p + n1 * q;
-                r = res[j];
-                if (edge) r = fma(kdu, re[q], r);
-                if (pipe) {
-                    const double m = mqi[j];
-                    r = fma(uo, m, r);
-                    const float cf = (float)fma(uo, m, mwi[j]);
-                    cc = fmaf(cf, cf, cc);
-                }
-            }
-            r64[k] = r;
-            rr = fmaf((float)r, (float)r, rr);
-        }
-    }
-    double bn2;
-    if (pipe) {
-        // ||c||^2 only sets the stopping-test reference: FP32, with an FP64
-        // recomputation when the FP32 sum leaves [1e-30, 1e30]
-        float t[2] = {rr, cc};
-        block_allreduce<float, 2>(t, red + 128);
-        rr = t[0];
-        bn2 = (double)t[1];
-        if (!(bn2 >= 1e-30 && bn2 <= 1e30)) {  // uniform across the block
-            const double uo = a.u_old[i];
-            const double* mqi = a.mq + (size_t)i * pl;
-            const double* mwi = a.mw + (size_t)i * pl;
-            double c2[1] = {0.0};
-#pragma unroll
-            for (int k = 0; k < R; ++k)
-                if (valid[k]) {
-                    const int j = p + n1 * (q0 + k);
-                    const double c = fma(uo, mqi[j], mwi[j]);
-                    c2[0] = fma(c, c, c2[0]);
-                }
-            block_allreduce<double, 1>(c2, reinterpret_cast<double*>(red));
-            bn2 = c2[0];
-        }
-    } else {
-        const double* bn = a.bnorm + (size_t)i * 3;
-        const double ku = a.kappa * ui;
-        bn2 = fma(ku * ku, bn[2], fma(2.0 * ku, bn[1], bn[0]));
-        float t[1] = {rr};
-        block_allreduce<float, 1>(t, red + 128);
-        rr = t[0];
-    }
-    const float stop2 = (float)(a.tol * a.tol * bn2);
-    int inner = 0, sweeps = 0, flag = 0;
-    bool solved = false;
-    if (!(rr == rr)) flag = kNaN;
-    if (bn2 == 0.0) {  // zero right-hand side: the solution is zero
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            r64[k] = 0.0;
-            if (valid[k]) v[p + n1 * (q0 + k)] = 0.0;
-        }
-        solved = true;
-    } else if (!flag && !(stop2 >= 1.17549435e-38f && bn2 <= 1e37)) {
-        // the stopping test and the residual norms are FP32: outside the
-        // range where tol^2 ||b||^2 is a normal FP32 number (and ||r||^2 cannot
-        // overflow) an underflowed ||r||^2 would read as converged, so the
-        // solve reports non-convergence instead (FP64 precision has no limit)
-        flag = kNotConverged;
-    } else if (!flag && rr > stop2) {
-        solved = true;
-        // zero the plane (halo and padding stay zero); scaled couplings into
-        // registers: c^_jl = c_jl / sqrt(C_j C_l), sc_j = 1 / sqrt(C_j)
-        for (int e = tid; e < Wd * Hd; e += T) P[e] = 0.f;
-        const float* S = a.S32 + (size_t)i * kPlanes * pl;
-        RegCouplings<R> c;
-        float sc[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            Couple8 s{0, 0, 0, 0, 0, 0, 0, 0};
-            float d0 = 1.f;
-            if (valid[k]) {
-                const int q = q0 + k, j = p + n1 * q;
-                const bool w = p > 0, e = p + 1 < n1, sd = q > 0, nd = q + 1 < n1;
-                d0 = rsqrtf(S[j]);
-                auto dg = [&](int l) { return rsqrtf(S[l]); };
-                if (e) s.E = S[pl + j] * dg(j + 1);
-                if (w) s.W = S[pl + j - 1] * dg(j - 1);
-                if (nd) s.N = S[2 * pl + j] * dg(j + n1);
-                if (sd) s.S = S[2 * pl + j - n1] * dg(j - n1);
-                if (e && nd) s.NE = S[3 * pl + j] * dg(j + n1 + 1);
-                if (w && nd) s.NW = S[4 * pl + j] * dg(j + n1 - 1);
-                if (e && sd) s.SE = S[4 * pl + j - n1 + 1] * dg(j - n1 + 1);
-                if (w && sd) s.SW = S[3 * pl + j - n1 - 1] * dg(j - n1 - 1);
-                s.E *= d0; s.W *= d0; s.N *= d0; s.S *= d0;
-                s.NE *= d0; s.NW *= d0; s.SE *= d0; s.SW *= d0;
-            }
-            c.c[k] = s;
-            sc[k] = valid[k] ? d0 : 0.f;
-            if (SC && active) {  // padding rows of the last strip get zero couplings
-                const int j = p + n1 * (q0 + k);
-                cA[j] = make_float4(s.E, s.W, s.N, s.S);
-                cB[j] = make_float4(s.NE, s.NW, s.SE, s.SW);
-            }
-        }
-        __syncthreads();
-        const SmemCouplings cs{cA, cB, p + n1 * q0, n1};
-        const float* Sh = S;                                   // S64 = Sh + Sl to about 2^-48
-        const float* Sl = a.S32lo + (size_t)i * kPlanes * pl;
-        for (;;) {
-            if (sweeps >= a.max_sweeps || inner >= a.maxit) {
-                flag = kNotConverged;
-                break;
-            }
-            // FP32 correction on the scaled system S^ y = D^-1/2 r, d = D^-1/2 y,
-            // to inner_tol relative, but no further than half the outer
-            // tolerance requires.  The FP64 residual waits in global memory.
-            float y[R], r[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                y[k] = 0.f;
-                r[k] = sc[k] * (float)r64[k];
-                if (valid[k]) res[p + n1 * (q0 + k)] = r64[k];
-            }
-            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, 0.25f * stop2 / rr);
-            if (SC)
-                inner += strip_cg<R>(cs, valid, y, r, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 64, &flag);
-            else
-                inner += strip_cg<R>(c, valid, y, r, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 64, &flag);
-            if (flag == kNaN) break;
-            flag = 0;
-            // v += d and r -= S d with S = S32 + S32lo (S64 to about 2^-48)
-            // and the FP32 correction d: the products and their sum in
-            // compensated FP32, one FP64 subtraction from the stored residual
-            float d[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) d[k] = sc[k] * y[k];
-            strip_store<R>(P, Wd, p, q0, valid, d);
-            __syncthreads();
-            StripHalo<R> h;
-            h.load(P, Wd, p, q0);
-            rr = 0.f;
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                if (!valid[k]) continue;
-                const int q = q0 + k, j = p + n1 * q;
-                const bool w = p > 0, e = p + 1 < n1, sd = q > 0;
-                const float up = (k + 1 < R) ? d[k + 1] : h.xp;
-                const float dn = (k > 0) ? d[k - 1] : h.xm;
-                float ys = 0.f, yc = 0.f;
-                df_add_prod(ys, yc, Sh[j], Sl[j], d[k]);
-                df_add_prod(ys, yc, Sh[pl + j], Sl[pl + j], h.Rt[k + 1]);
-                if (w) df_add_prod(ys, yc, Sh[pl + j - 1], Sl[pl + j - 1], h.L[k + 1]);
-                df_add_prod(ys, yc, Sh[2 * pl + j], Sl[2 * pl + j], up);
-                if (sd) df_add_prod(ys, yc, Sh[2 * pl + j - n1], Sl[2 * pl + j - n1], dn);
-                df_add_prod(ys, yc, Sh[3 * pl + j], Sl[3 * pl + j], h.Rt[k + 2]);
-                df_add_prod(ys, yc, Sh[4 * pl + j], Sl[4 * pl + j], h.L[k + 2]);
-                if (e && sd) df_add_prod(ys, yc, Sh[4 * pl + j - n1 + 1], Sl[4 * pl + j - n1 + 1], h.Rt[k]);
-                if (w && sd) df_add_prod(ys, yc, Sh[3 * pl + j - n1 - 1], Sl[3 * pl + j - n1 - 1], h.L[k]);
-                r64[k] = res[j] - ((double)ys + (double)yc);
-                const float rf = (float)r64[k];
-                rr = fmaf(rf, rf, rr);
-                v[j] += (double)d[k];
-            }
-            {
-                float t[1] = {rr};
-                block_allreduce<float, 1>(t, red + 128 + 64 * (sweeps & 1));
-                rr = t[0];
-            }
-            ++sweeps;
-            if (!(rr == rr)) {
-                flag = kNaN;
-                break;
-            }
-            if (rr <= stop2) break;
-        }
-    }
-    // store the residual of the new iterate (only Robin-edge values change
-    // when no correction was needed); the pipelined epilogue stores its own
-    if (!pipe) {
-#pragma unroll
-        for (int k = 0; k < R; ++k)
-            if (valid[k] && (solved || (edge && kdu != 0.0))) res[p + n1 * (q0 + k)] = r64[k];
-    }
-    __syncthreads();
-    // pipelined elimination, first half of the epilogue (w = v is final):
-    // M w / dt, S w = c - e, push w and S w into the rings at slot hist_step,
-    // the extrapolated warm start g with S g from the same combination
-    // (quadratic with two older solves, linear with one), and the next
-    // residual's u-independent part M w / dt - S g.  Only v is read at
-    // neighbours, so everything but g is stored at once.
-    double gv[R];
-    if (pipe) {
-        const int st = a.ctl->hist_step, level = a.ctl->hist_level;
-        const double uo = a.u_old[i];
-        const double* mqi = a.mq + (size_t)i * pl;
-        double* mwi = a.mw + (size_t)i * pl;
-        const size_t slot = (size_t)a.nM * pl, io = (size_t)i * pl;
-        const double* Mi = a.M64 + (size_t)i * kPlanes * pl;
-        double* hc = a.hist + (size_t)(st % 3) * slot + io;
-        const double* h1 = a.hist + (size_t)((st + 2) % 3) * slot + io;
-        const double* h2 = a.hist + (size_t)((st + 1) % 3) * slot + io;
-        double* yc = a.yhist + (size_t)(st % 3) * slot + io;
-        const double* y1 = a.yhist + (size_t)((st + 2) % 3) * slot + io;
-        const double* y2 = a.yhist + (size_t)((st + 1) % 3) * slot + io;
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            gv[k] = 0.0;
-            if (!valid[k]) continue;
-            const int q = q0 + k, j = p + n1 * q;
-            const double w = v[j];
-            const double mwn = plane_apply(Mi, pl, v, j, p, q, n1) * a.idt;
-            const double sw = fma(uo, mqi[j], mwi[j]) - r64[k];
-            double g = w, sg = sw;
-            if (level >= 2) {
-                g = fma(3.0, w - h1[j], h2[j]);
-                sg = fma(3.0, sw - y1[j], y2[j]);
-            } else if (level == 1) {
-                g = fma(2.0, w, -h1[j]);
-                sg = fma(2.0, sw, -y1[j]);
-            }
-            hc[j] = w;
-            yc[j] = sw;
-            mwi[j] = mwn;
-            res[j] = mwn - sg;
-            gv[k] = g;
-        }
-    }
-    // optional epilogue: M v / dt of the solution in FP64 (the next step's
-    // right-hand side of the pipelined elimination; the FP64 work overlaps
-    // the FP32 iterations of the other blocks on the SM)
-    if (a.mw && !pipe) {
-        const double* Mi = a.M64 + (size_t)i * kPlanes * pl;
-        double* mw = a.mw + (size_t)i * pl;
-#pragma unroll
-        for (int k = 0; k < R; ++k)
-            if (valid[k]) {
-                const int q = q0 + k, j = p + n1 * q;
-                mw[j] = plane_apply(Mi, pl, v, j, p, q, n1) * a.idt;
-            }
-    }
-    // flux integral rho_i = r_i^T v_i over the Robin-edge nodes, one warp,
-    // compensated (TwoSum) FP64
-    if (tid < 32) {
-        double s = 0.0, cpen = 0.0;
-        for (int q = tid; q < n1; q += 32) {
-            const double t = re[q] * v[(n1 - 1) + n1 * q];
-            double su, er;
-            two_sum(s, t, su, er);
-            s = su;
-            cpen += er;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double so = __shfl_xor_sync(0xffffffffu, s, o);
-            const double co = __shfl_xor_sync(0xffffffffu, cpen, o);
-            double su, er;
-            two_sum(s, so, su, er);
-            s = su;
-            cpen += co + er;
-        }
-        if (tid == 0) {
-            a.u_used[i] = ui;
-            a.rho[i] = s + cpen;
-            a.inst_iters[i] = inner;
-            atomicAdd(&a.ctl->inner_iters, (unsigned long long)inner);
-            atomicAdd(&a.ctl->sweeps, (unsigned long long)sweeps);
-            atomicAdd(&a.ctl->micro_solves, 1ull);
-            atomicMax(&a.ctl->max_inner, inner);
-            if (flag) set_status(a.ctl, flag);
-        }
-    }
-    // pipelined elimination, second half: once every read of w (neighbours,
-    // flux) is done, v becomes the warm start of the next solve
-    if (pipe) {
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < R; ++k)
-            if (valid[k]) v[p + n1 * (q0 + k)] = gv[k];
-        if (i == 0 && tid == 0) a.ctl->pushed = 1;
-    }
-}
-
-// Short strips (couplings in registers) and tall strips (couplings in shared
-// memory, register budget capped so that several blocks share an SM).  PIPE:
-// the pipelined-elimination instantiation (MicroArgs::pipe), separate so that
-// its prologue and epilogue cost the other solves no registers.
-template <int R, bool PIPE>
-__global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::value) k_micro_strip(MicroArgs a) {
-    micro_strip_body<R, false, PIPE>(a);
-}
-constexpr int kTallStripRegs = 160;
-template <int R, bool PIPE>
-__global__ void __maxnreg__(kTallStripRegs) k_micro_strip_tall(MicroArgs a) {
-    micro_strip_body<R, true, PIPE>(a);
-}
-
-template <int R, bool SC>
-static cudaError_t launch_strip(const MicroArgs& a, cudaStream_t s) {
-    const int T = strip_threads(a.n1, R);
-    if (T > StripMaxThreads<R>::value) return cudaErrorInvalidConfiguration;
-    const size_t sm = strip_smem_bytes(a.n1, R, SC);
-    if constexpr (SC) {
-        if (a.pipe) k_micro_strip_tall<R, true><<<a.nM, T, sm, s>>>(a);
-        else k_micro_strip_tall<R, false><<<a.nM, T, sm, s>>>(a);
-    } else {
-        if (a.pipe) k_micro_strip<R, true><<<a.nM, T, sm, s>>>(a);
-        else k_micro_strip<R, false><<<a.nM, T, sm, s>>>(a);
-    }
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------
 // variant table
 // ---------------------------------------------------------------------------
@@ -1035,13 +392,7 @@ bool tiling_fits(int tiling, int precision, int n1, int smem_optin) {
         const int maxT = K <= 2 ? 1024 : (K == 4 ? 512 : 544);
         return smem_threads(nm, K) <= maxT && smem_kernel_bytes(n1, precision) <= (size_t)smem_optin;
     }
-    if (tiling >= 4 && tiling < kNumTilings) {
-        if (precision == 0) return false;
-        const int R = kStripR[tiling - 4];
-        const bool sc = R >= 9;
-        const int maxT = R == 3 ? 384 : (R == 5 ? 512 : 384);
-        return strip_threads(n1, R) <= maxT && strip_smem_bytes(n1, R, sc) <= (size_t)smem_optin;
-    }
+    if (tiling >= 4 && tiling < kNumTilings) return precision != 0 && strip_fits(n1, kStripR[tiling - 4], smem_optin);
     return false;
 }
 
@@ -1059,13 +410,8 @@ cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cu
             case 1: return launch_smem<float, true, 2>(a, s);
             case 2: return launch_smem<float, true, 4>(a, s);
             case 3: return launch_smem<float, true, 8>(a, s);
-            case 4: return launch_strip<3, false>(a, s);
-            case 5: return launch_strip<5, false>(a, s);
-            case 6: return launch_strip<7, false>(a, s);
-            case 7: return launch_strip<9, true>(a, s);
-            case 8: return launch_strip<11, true>(a, s);
-            case 9: return launch_strip<13, true>(a, s);
         }
+        if (tiling >= 4 && tiling < kNumTilings) return launch_strip_solve(a, kStripR[tiling - 4], s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1075,17 +421,12 @@ cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cu
 cudaError_t configure_micro_kernels(int smem_optin) {
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaSuccess;
-    const void* fns[20] = {(const void*)k_micro_solve<double, false, 1>, (const void*)k_micro_solve<double, false, 2>,
-                           (const void*)k_micro_solve<double, false, 4>, (const void*)k_micro_solve<double, false, 8>,
-                           (const void*)k_micro_solve<float, true, 1>,   (const void*)k_micro_solve<float, true, 2>,
-                           (const void*)k_micro_solve<float, true, 4>,   (const void*)k_micro_solve<float, true, 8>,
-                           (const void*)k_micro_strip<3, false>,         (const void*)k_micro_strip<5, false>,
-                           (const void*)k_micro_strip<7, false>,         (const void*)k_micro_strip_tall<9, false>,
-                           (const void*)k_micro_strip_tall<11, false>,   (const void*)k_micro_strip_tall<13, false>,
-                           (const void*)k_micro_strip<3, true>,          (const void*)k_micro_strip<5, true>,
-                           (const void*)k_micro_strip<7, true>,          (const void*)k_micro_strip_tall<9, true>,
-                           (const void*)k_micro_strip_tall<11, true>,    (const void*)k_micro_strip_tall<13, true>};
-    for (int k = 0; k < 20 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
+    const void* fns[8] = {(const void*)k_micro_solve<double, false, 1>, (const void*)k_micro_solve<double, false, 2>,
+                          (const void*)k_micro_solve<double, false, 4>, (const void*)k_micro_solve<double, false, 8>,
+                          (const void*)k_micro_solve<float, true, 1>,   (const void*)k_micro_solve<float, true, 2>,
+                          (const void*)k_micro_solve<float, true, 4>,   (const void*)k_micro_solve<float, true, 8>};
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaFuncSetAttribute(fns[k], at, smem_optin);
+    if (e == cudaSuccess) e = configure_strip_kernels(smem_optin);
     return e;
 }
 

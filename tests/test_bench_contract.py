@@ -21,8 +21,8 @@ def _run(*args):
 
 def test_reference_arm_prints_one_line():
     d = _run("--impl", "reference", "--steps", "1", "--warmup", "1")
-    assert d["impl"] == "reference"
-    assert d["metric"] == "micro DOF-CG-iters/s" and d["unit"] == "DOF-iter/s"
+    assert d["impl"] == "reference" and d["same_config"] is True
+    assert d["metric"] == "two-scale steps/s" and d["unit"] == "steps/s"
     assert d["value"] > 0 and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
     cb = d["cpu_baseline"]
@@ -44,7 +44,20 @@ def test_profiling_case_keeps_the_micro_problems():
     assert (full.NM, small.NM) == (128, 8)
     assert small.Nm == full.Nm and small.family == full.family and small.D == full.D
     assert small.dt == full.dt and small.tol == full.tol
-    # measured DRAM bytes per launch exist for the full-size timed workloads only
-    for (wl, prec, short_strip, coupling), traffic in bench.MICRO_TRAFFIC.items():
+    # measured counters exist for the full-size timed workloads only, and only
+    # counters of the current kernel revision are ever used
+    for (wl, prec, tiling, coupling, rev), ctr in bench.MICRO_COUNTERS.items():
         assert wl in ("c2", "c3") and prec == "mixed" and coupling in ("elimination", "partitioned")
-        assert traffic > 1e8
+        assert 0 <= tiling < len(bench.KERNEL_NAMES) and ctr["dram_bytes"] > 1e8 and ctr["warp_insts"] > 1e6
+
+
+def test_roofline_entry_without_counters_reports_null_traffic():
+    """A kernel revision without an ncu capture gets traffic, dram_frac and the
+    on-chip entry as null, never a stale number."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sp = {"micro_kernel_ms": 6.0, "micro_launches": 10, "dof_cg_iters": 10 * 4225 * 1089 * 25,
+          "refine_sweeps": 10 * 4225, "tiling": 4, "macro_kernel_ms": 1.0}
+    r = bench.micro_roofline(None, "mixed", "elimination", sp, 1089, {"sm_mhz": 2070.0})
+    assert r["traffic"] is None and r["dram_frac"] is None and "onchip" not in r
+    assert r["frac"] == r["achieved"] / r["peak"] and r["frac_kind"].startswith("algorithmic")
