@@ -43,11 +43,14 @@ BYTES_PER_DOF_SWEEP = 64
 
 KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_micro_solve<8>",
                 "k_micro_strip<3>", "k_micro_strip<5>", "k_micro_strip<7>",
-                "k_micro_strip_tall<9>", "k_micro_strip_tall<11>", "k_micro_strip_tall<13>"]
+                "k_micro_strip_tall<9>", "k_micro_strip_tall<11>", "k_micro_strip_tall<13>",
+                "direct band solve (three-field only)",
+                "k_micro_cluster<5> x2", "k_micro_cluster<5> x4", "k_micro_cluster_tall<9> x4",
+                "k_micro_cluster_tall<9> x8", "k_micro_warp<3>", "k_micro_warp<5>"]
 # Source revision of the column-strip kernels that the ncu counters below were
 # taken on.  A kernel change gets a new revision, so counters of an older
 # kernel no longer match and read as null.
-KERNEL_REV = "ff1"
+KERNEL_REV = "ff2"
 # Per-launch ncu counters of the micro-solve kernel (the same bench command,
 # captured after a plain run): DRAM bytes (read + write) and executed warp
 # instructions, keyed by (workload, precision, tiling, coupling, revision).
@@ -61,8 +64,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "t1"],
-                    help="t1: the stationary three-field system (manufactured solution, 128x128 / 64x64)")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "t1", "p43a", "p43b"],
+                    help="t1: the stationary three-field system (manufactured solution, 128x128 / 64x64); "
+                         "p43a / p43b: the two shapes of the paper's parallel benchmark (Sec. 4.3), 64x64 macro "
+                         "with 8x8 micro cells and 8x8 macro with 64x64 micro cells, with the 64x64/32x32 "
+                         "workload's data")
+    ap.add_argument("--tiling-sweep", action="store_true",
+                    help="also time every micro-solve variant that fits (steps/s per variant)")
     ap.add_argument("--fd-dirs", type=int, default=20, help="c5: finite-difference directions per family")
     ap.add_argument("--tiling", type=int, default=-1,
                     help="micro-kernel variant of the main timed problem (-1: the library's autotuner; a fixed "
@@ -80,6 +88,10 @@ def workload(name, seed=0, macro_cells=None):
     import workloads as W
     if name == "c2":
         return W.c2(seed=seed)
+    if name == "p43a":   # fine macro mesh, coarse micro meshes: 4225 micro problems of 81 DoFs
+        return W.c2(NM=64, Nm=8, seed=seed)
+    if name == "p43b":   # coarse macro mesh, fine micro meshes: 81 micro problems of 4225 DoFs
+        return W.c2(NM=8, Nm=64, seed=seed)
     return W.c3(seed=seed) if macro_cells is None else W.c3(NM=macro_cells, seed=seed)
 
 
@@ -298,6 +310,23 @@ def run_gb300(args):
         "clocks": clocks,
     }
 
+    # ---- every micro-solve variant that fits, timed on the same steps ----
+    if args.tiling_sweep or args.workload in ("p43a", "p43b"):
+        sweep = {}
+        for t in [t for t in range(len(KERNEL_NAMES)) if t != 10]:
+            try:
+                Q = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling], tiling=t)
+                Q.step(w.dt, Wm)
+                Q.synchronize()
+            except T.TsfError:
+                continue   # does not fit this micro mesh / precision
+            msq = timed_steps(torch, Q, w, K, lambda: None)
+            sweep[KERNEL_NAMES[t]] = {"tiling": t, "ms_per_step": msq / K}
+            Q.close()
+        line["tiling_sweep"] = sweep
+        line["tiling_sweep_note"] = "steps/s of the same workload with each variant fixed; the line's own value " \
+                                    "uses the variant the library's autotuner picked (key tiling)"
+
     # ---- the same steps with the other way of reaching the coupled solution:
     # exact elimination (one micro solve per step) or the partitioned
     # iteration of the paper (micro and macro solves until u settles) ----
@@ -334,6 +363,7 @@ def run_gb300(args):
     torch.cuda.synchronize()
     pf_ms = pe0.elapsed_time(pe1) / 5
     pf_gbs = 20.0 * nM * nm / (pf_ms / 1e3) / 1e9   # write (X1, X2, v) FP32, read v FP64: 20 B per micro DoF
+    peak = line["roofline"]["peak"]
     line["pushforward"] = {"ms": pf_ms, "achieved_GBs": pf_gbs, "frac": pf_gbs / peak,
                            "note": "includes the getter's stream synchronisation"}
     del xyv
@@ -540,9 +570,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.workload not in ("c2", "c3"):
+    if args.workload not in ("c2", "c3", "p43a", "p43b"):
         print(json.dumps({"impl": "reference", "unavailable": "the reference arm (the oracle on the host cores) "
-                          "is timed on the 64x64/32x32 and 128x128/64x64 workloads"}))
+                          "is timed on the two-field time-stepping workloads"}))
         return
     import oracle
     w = workload(args.workload)
@@ -707,9 +737,12 @@ def run_c4(args):
     dt = ws[0].dt
     K, Wm = args.steps, args.warmup
 
-    def build():
+    persistent = args.coupling == "elimination"
+
+    def build(persistent=persistent):
         B = T.TwoScaleBatch([(w.Nm, w.NM, w.bc) for w in ws], precision=T.TSF_MIXED, stream=stream,
-                            cg_tol=ws[0].tol, coupling_tol=ws[0].coupling_tol, coupling=COUPLING[args.coupling])
+                            cg_tol=ws[0].tol, coupling_tol=ws[0].coupling_tol, coupling=COUPLING[args.coupling],
+                            persistent=persistent)
         for k, w in enumerate(ws):
             B[k].set_physics(w.D, w.kappa, w.Du)
             B[k].set_deformation(w.family, w.params)
@@ -745,11 +778,28 @@ def run_c4(args):
     else:
         ms_max, dof_iters = ms, float(st["dof_cg_iters"])
 
+    # the graph with one branch per problem (each problem's own kernels and
+    # autotuned variant) over the same steps
+    branches = None
+    if persistent:
+        B3 = build(persistent=False)
+        B3.step(dt, Wm)
+        B3.synchronize()
+        B3.reset_stats()
+        e0.record(stream)
+        B3.step(dt, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        br_ms = e0.elapsed_time(e1)
+        branches = {"ms_per_step": br_ms / K, "dof_cg_iters_per_step": B3.stats()["dof_cg_iters"] / K,
+                    "tilings": [B3[k].stats()["tiling"] for k in range(len(ws))]}
+        B3.close()
+
     # the same problems one after another, each its own graph per step: a
     # second, identical batch advanced through the same steps one problem at
     # a time (the solves get cheaper as the march settles, so both are timed
     # over the same step range)
-    B2 = build()
+    B2 = build(persistent=False)
     for _ in range(Wm):
         for k in range(len(ws)):
             B2[k].step(dt, 1)
@@ -795,15 +845,20 @@ def run_c4(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"c4: {len(ws)} independent two-scale problems, macro 16..96 / micro 16..48 cells "
                                f"per side, {ndof} micro DoFs, dt={dt}, tol={ws[0].tol}, mixed, coupling by "
-                               f"{args.coupling}, one graph per batch step", "problems": len(ws), "micro_dofs": ndof,
+                               f"{args.coupling}, one graph per batch step"
+                               + (", micro solves of all problems in one persistent work-queue launch"
+                                  if persistent else ""),
+                   "problems": len(ws), "micro_dofs": ndof, "persistent": persistent,
                    "l2": "working set > L2, no flush"},
+        "branches": branches,
         "batch_steps_per_s": world * K / (ms_max / 1e3),
         "sequential_ms_per_step": seq_ms / ks, "batch_speedup_vs_sequential": (seq_ms / ks) / (ms / K),
         "sequential_dof_cg_iters_per_step": seq_iters / ks, "batch_dof_cg_iters_per_step": st["dof_cg_iters"] / K,
         "coupling_iters_per_problem_step": st["coupling_iters_total"] / (K * len(ws)),
         "tilings": tilings, "coupling": args.coupling,
-        "gpu_launches": (5 * K * len(ws) if args.coupling == "elimination"
-                         else 2 * K * len(ws) + 2 * st["coupling_iters_total"]),
+        "gpu_launches": ((4 * len(ws) + 1) * K if persistent else
+                         (5 * K * len(ws) if args.coupling == "elimination"
+                          else 2 * K * len(ws) + 2 * st["coupling_iters_total"])),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "micro solve (per-problem variant)", "launches_timed": launches,
                      "avg_launch_ms": micro_ms / max(launches, 1),

@@ -143,7 +143,13 @@ typedef struct tsf_stats {
                                    1, 2, 4, 8 nodes per thread (FP64 or mixed); 4..6 column strips
                                    of 3, 5, 7 nodes with the stencil in registers (mixed); 7..9
                                    column strips of 9, 11, 13 nodes with the stencil in shared
-                                   memory (mixed) */
+                                   memory (mixed); 10 is the three-field direct solve
+                                   (tsfem3.h); 11..14 one micro problem per thread-block cluster
+                                   of G CTAs with column strips of R nodes, (R, G) = (5, 2),
+                                   (5, 4) stencil in registers, (9, 4), (9, 8) stencil in shared
+                                   memory (mixed); 15, 16 one warp per micro problem with
+                                   strips of 3, 5 nodes, for micro meshes whose strips fit 32
+                                   threads (mixed) */
     double coupling_change;     /* final ||du|| / ||u|| of the last step */
     int64_t micro_launches;     /* profiled micro-solve kernel launches */
     int64_t macro_launches;     /* profiled macro-solve kernel launches */
@@ -165,8 +171,11 @@ tsf_status tsf_set_options(tsf_ctx *ctx, const tsf_options *opt);
 
 /* Reference micro mesh on Z = [0,1]^2 (Sec. 3.1: one mesh of the reference
  * domain, shared by all micro problems).  nx = ny = Nm cells per side,
- * 1 <= Nm <= 89 (each micro problem must fit one thread block).  robin_edge
- * must be 0 (the edge yhat_1 = 1).  Errors: TSF_E_ARG. */
+ * 1 <= Nm <= 128.  Up to 64 cells a micro problem is solved by one thread
+ * block; the mixed-precision cluster variants (tiling 11..14) spread one
+ * micro problem over a thread-block cluster and are the only variants beyond
+ * 64 cells (TSF_FP64 takes at most 64).  robin_edge must be 0 (the edge
+ * yhat_1 = 1).  Errors: TSF_E_ARG. */
 tsf_status tsf_set_micro_mesh(tsf_ctx *ctx, int nx, int ny, int robin_edge);
 
 /* Macro mesh on Omega = [0,1]^2 with nx = ny = NM cells per side
@@ -320,6 +329,19 @@ tsf_status tsf_batch_instance(tsf_batch *b, int inst, tsf_ctx **out);
  * tsf_batch_synchronize).  TSF_E_STATE if an instance lacks meshes,
  * deformation or state; instance errors name the instance. */
 tsf_status tsf_batch_step(tsf_batch *b, double dt, int nsteps);
+
+/* Persistent batch steps (on = 1; default 0).  Each batch step is then ONE
+ * CUDA graph launch whose micro solves, for every micro problem of every
+ * instance, run in ONE persistent kernel launch (one block per SM) that takes
+ * work items from a global atomic queue ordered largest micro mesh first; a
+ * block runs several small micro problems side by side, each on its own
+ * group of warps.  Beside it, every instance's macro solve runs on its own
+ * branch of the graph.  Requires mixed precision and coupling by elimination
+ * without volume or Robin sources for every instance (tsf_batch_step then
+ * returns TSF_E_ARG otherwise), micro meshes of at most 49 cells per side,
+ * and switches every instance to the column-strip variant of the batch kernel
+ * (tiling 5).  Errors: TSF_E_ARG. */
+tsf_status tsf_batch_set_persistent(tsf_batch *b, int on);
 tsf_status tsf_batch_synchronize(tsf_batch *b);
 
 /* Statistics summed over the instances (coupling_iters_last, max_inner_iters

@@ -64,7 +64,7 @@ typedef struct {
     int64_t micro_solves;    /* micro problems solved (3 per node with a new geometry, else 1) */
     int64_t macro_iters;     /* CG iterations of the coupled macro solve */
     int status;              /* device status of the last solve (tsf_status) */
-    int tiling;              /* micro-solve variant in use (0..9 as tsf_stats.tiling, or TSF3_TILING_DIRECT) */
+    int tiling;              /* micro-solve variant in use (0..9 and 11..14 as tsf_stats.tiling, or TSF3_TILING_DIRECT) */
     double micro_ms;         /* device time of the micro solves of the last tsf3_solve */
     double macro_ms;         /* device time of the macro solve */
     double total_ms;         /* device time of the whole last tsf3_solve */
@@ -76,8 +76,8 @@ typedef struct {
 
 /* Uses from tsf_options: precision, cg_tol (micro relative residual),
  * inner_tol, cg_maxit, max_sweeps, macro_tol, macro_maxit, tiling,
- * cuda_stream (NULL = own stream).  tiling: 0..9 the iterative micro-solve
- * variants of tsf_stats.tiling; TSF3_TILING_DIRECT (mixed precision only): a
+ * cuda_stream (NULL = own stream).  tiling: 0..9 and 11..14 the iterative
+ * micro-solve variants of tsf_stats.tiling; TSF3_TILING_DIRECT (mixed precision only): a
  * banded Cholesky factor of every micro operator in FP32, kept while the
  * geometry and physics stay the same, with FP64 iterative refinement to
  * cg_tol (at most max(max_sweeps, 30) sweeps); -1: the direct solve in

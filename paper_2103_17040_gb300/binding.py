@@ -32,7 +32,7 @@ EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micr
            "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_macro_async",
            "tsf_get_micro_averages_async", "tsf_get_micro_field", "tsf_get_flux", "tsf_get_rho", "tsf_get_geometry", "tsf_get_pushforward", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
            "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u",
-           "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_synchronize",
+           "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_set_persistent", "tsf_batch_synchronize",
            "tsf_batch_get_stats", "tsf_batch_reset_stats", "tsf_batch_last_error", "tsf_batch_destroy"]
 # every symbol include/tsfem3.h declares (the stationary three-field system)
 EXPORTS3 = ["tsf3_create", "tsf3_set_meshes", "tsf3_set_physics", "tsf3_set_deformation", "tsf3_set_sources",
@@ -127,6 +127,7 @@ def load_library(path: str = LIB_PATH):
     L.tsf_batch_create.argtypes = [pp, i, ctypes.POINTER(tsf_options)]
     L.tsf_batch_instance.argtypes = [vp, i, pp]
     L.tsf_batch_step.argtypes = [vp, d, i]
+    L.tsf_batch_set_persistent.argtypes = [vp, i]
     L.tsf_batch_synchronize.argtypes = [vp]
     L.tsf_batch_get_stats.argtypes = [vp, ctypes.POINTER(tsf_stats)]
     L.tsf_batch_reset_stats.argtypes = [vp]
@@ -365,6 +366,10 @@ def tsf_batch_instance(b, inst) -> int:
 
 def tsf_batch_step(b, dt, nsteps=1):
     _bcheck(b, _lib.tsf_batch_step(b, float(dt), int(nsteps)))
+
+
+def tsf_batch_set_persistent(b, on):
+    _bcheck(b, _lib.tsf_batch_set_persistent(b, int(on)))
 
 
 def tsf_batch_synchronize(b):
@@ -677,10 +682,12 @@ class TwoScaleBatch:
 
     ``specs``: sequence of ``(Nm, NM)`` or ``(Nm, NM, bc)``.  ``batch[i]`` is a
     :class:`TwoScale` view of instance i (configure and read it as usual; it
-    is valid while the batch lives).
+    is valid while the batch lives).  ``persistent=True``: the micro solves of
+    all instances run in one persistent launch per step, fed by a work queue
+    (tsf_batch_set_persistent).
     """
 
-    def __init__(self, specs, precision=TSF_MIXED, stream=None, workspace="torch", **opts):
+    def __init__(self, specs, precision=TSF_MIXED, stream=None, workspace="torch", persistent=False, **opts):
         self.b = tsf_batch_create(len(specs), _make_options(precision, stream, opts))
         self.instances = []
         for i, sp in enumerate(specs):
@@ -688,6 +695,8 @@ class TwoScaleBatch:
             bc = int(sp[2]) if len(sp) > 2 else TSF_BC_NEUMANN
             self.instances.append(TwoScale(Nm, NM, bc, workspace=workspace,
                                            _instance=tsf_batch_instance(self.b, i)))
+        if persistent:
+            tsf_batch_set_persistent(self.b, 1)
 
     def __len__(self):
         return len(self.instances)

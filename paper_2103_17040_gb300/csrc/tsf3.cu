@@ -618,7 +618,7 @@ tsf_status tsf3_create(tsf3_ctx** out, const tsf_options* opt) {
     tsf_default_options(&o);
     if (opt) o = *opt;
     if ((o.precision != TSF_FP64 && o.precision != TSF_MIXED) || !(o.cg_tol > 0.0) || !(o.macro_tol > 0.0) ||
-        o.cg_maxit < 1 || o.macro_maxit < 1 || o.tiling < -1 || o.tiling > kTilingDirect)
+        o.cg_maxit < 1 || o.macro_maxit < 1 || o.tiling < -1 || o.tiling >= kNumTilings)
         return TSF_E_ARG;
     tsf3_ctx* ctx = new (std::nothrow) tsf3_ctx();
     if (!ctx) return TSF_E_OOM;

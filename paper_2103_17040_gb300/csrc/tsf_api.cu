@@ -23,7 +23,9 @@ using namespace tsf;
 
 namespace {
 
-constexpr int kMaxNm = 64;     // micro cells per side (one thread block per micro problem)
+constexpr int kPersistentTiling = 5;  // the short strips of R = kBatchR rows, as in k_micro_batch
+constexpr int kMaxNm = 128;    // micro cells per side (up to 64: one thread block per micro problem;
+                               // beyond: one thread-block cluster per micro problem)
 constexpr int kMaxNM = 1023;   // macro cells per side
 constexpr size_t kAlign = 256;
 
@@ -686,7 +688,8 @@ static MacroArgs macro_args(tsf_ctx* ctx, double dt, bool set_cond, cudaGraphCon
 
 static bool eliminating(const tsf_ctx* ctx) { return ctx->opt.coupling == TSF_COUPLING_ELIMINATION; }
 
-static tsf_status enqueue_macro_prologue(tsf_ctx* ctx, double dt, bool pipelined = false) {
+static tsf_status enqueue_macro_prologue(tsf_ctx* ctx, double dt, bool pipelined = false,
+                                         cudaStream_t stream = nullptr) {
     MacroPrologueArgs m{};
     m.NM = ctx->NM;
     m.N1 = ctx->N1;
@@ -713,7 +716,7 @@ static tsf_status enqueue_macro_prologue(tsf_ctx* ctx, double dt, bool pipelined
             m.nmp = ctx->nmp;
         }
     }
-    CU(launch_macro_prologue(m, ctx->stream));
+    CU(launch_macro_prologue(m, stream ? stream : ctx->stream));
     return TSF_OK;
 }
 
@@ -1127,7 +1130,10 @@ static tsf_status prepare_step(tsf_ctx* ctx, double dt) {
     ctx->use_dct = macro_smem_bytes(ctx->N1, ctx->bc, 1) <= (size_t)ctx->smem_optin;
     bool any = false;
     for (int t = 0; t < kNumTilings; ++t) any = any || tiling_fits(t, ctx->opt.precision, ctx->n1, ctx->smem_optin);
-    if (!any) return fail(ctx, TSF_E_ARG, "micro mesh too large for one thread block in this precision");
+    if (!any)
+        return fail(ctx, TSF_E_ARG, "no micro-solve variant fits %d micro cells per side in this precision%s", ctx->Nm,
+                    ctx->opt.precision == TSF_FP64 && ctx->Nm > 64 ? " (above 64 cells only the mixed-precision "
+                                                                      "cluster variants fit)" : "");
     if (ctx->tiling < 0 || ctx->tiling_prec != ctx->opt.precision) {
         tsf_status st = autotune(ctx, dt);
         if (st) return st;
@@ -1525,6 +1531,15 @@ struct tsf_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int use_graph = 1;
+    // persistent mode: one launch of k_micro_batch per step for the micro
+    // solves of all instances (device tables of their arguments and of the
+    // work items, the queue head)
+    int persistent = 0;
+    MicroArgs* d_args = nullptr;
+    int4* d_items = nullptr;
+    int* d_counter = nullptr;
+    size_t cap_args = 0, cap_items = 0;
+    int nitems = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_valid = false;
@@ -1588,7 +1603,149 @@ static tsf_status batch_capture(tsf_batch* b, double dt) {
     return TSF_OK;
 }
 
+// The persistent batch step (pipelined elimination of every instance):
+//   k_elim_start of every instance (the macro state the next w belongs to),
+//   then side by side: ONE persistent launch of k_micro_batch, which solves the
+//   next w of every micro problem of every instance from a work queue ordered
+//   largest micro problem first, and per instance its macro branch (macro
+//   prologue, macro solve, commit) on that instance's side stream.
+static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
+    batch_drop_graph(b, true);
+    const int n = (int)b->inst.size();
+    std::vector<MicroArgs> args(n);
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) {
+        tsf_ctx* c = b->inst[k];
+        args[k] = w_solve_args(c, dt);
+        order[k] = k;
+    }
+    // largest micro problems first (work per item grows with n1^2), then the
+    // instances with more micro problems
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const tsf_ctx *cx = b->inst[x], *cy = b->inst[y];
+        return cx->nm != cy->nm ? cx->nm > cy->nm : cx->nM > cy->nM;
+    });
+    std::vector<int4> items;
+    size_t smem = 0;
+    for (int k : order) {
+        tsf_ctx* c = b->inst[k];
+        const int tw = batch_team_warps(c->n1);
+        if (tw > kBatchWarps)
+            return bfail(b, TSF_E_ARG, "instance %d: %d micro cells per side are too many for the persistent batch",
+                         k, c->Nm);
+        const int cnt = std::min(kBatchWarps / tw, 15);
+        smem = std::max(smem, (size_t)cnt * batch_team_smem(c->n1));
+        for (int i = 0; i < c->nM; i += cnt) items.push_back(make_int4(k, i, std::min(cnt, c->nM - i), tw));
+    }
+    tsf_ctx* c0 = b->inst[0];
+    if (smem > (size_t)c0->smem_optin) return bfail(b, TSF_E_ARG, "persistent batch: shared memory %zu > %d", smem,
+                                                    c0->smem_optin);
+    cudaError_t e = cudaSuccess;
+    if (b->cap_args < (size_t)n) {
+        if (b->d_args) cudaFree(b->d_args);
+        e = cudaMalloc((void**)&b->d_args, (size_t)n * sizeof(MicroArgs));
+        b->cap_args = e == cudaSuccess ? (size_t)n : 0;
+    }
+    if (e == cudaSuccess && b->cap_items < items.size()) {
+        if (b->d_items) cudaFree(b->d_items);
+        e = cudaMalloc((void**)&b->d_items, items.size() * sizeof(int4));
+        b->cap_items = e == cudaSuccess ? items.size() : 0;
+    }
+    if (e == cudaSuccess && !b->d_counter) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_args, args.data(), (size_t)n * sizeof(MicroArgs), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_micro_batch_entry(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, e == cudaErrorMemoryAllocation ? TSF_E_OOM : TSF_E_CUDA, "persistent batch set-up: %s",
+                     cudaGetErrorString(e));
+    }
+    b->nitems = (int)items.size();
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c0->device);
+
+    e = cudaGraphCreate(&b->graph, 0);
+    if (e != cudaSuccess) return bfail(b, TSF_E_CUDA, "cudaGraphCreate: %s", cudaGetErrorString(e));
+    cudaStream_t s = b->stream;
+    tsf_status st = TSF_OK;
+    auto body = [&]() -> cudaError_t {
+        cudaError_t er = cudaStreamBeginCaptureToGraph(s, b->graph, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal);
+        if (er != cudaSuccess) return er;
+        for (int k = 0; k < n && er == cudaSuccess; ++k) er = launch_elim_start(elim_args(b->inst[k], dt), s);
+        if (er == cudaSuccess) er = cudaEventRecord(c0->fork_ev, s);
+        for (int k = 0; k < n && er == cudaSuccess; ++k) {
+            tsf_ctx* c = b->inst[k];
+            er = cudaStreamWaitEvent(c->side, c0->fork_ev, 0);
+            if (er != cudaSuccess) break;
+            if ((st = enqueue_macro_prologue(c, dt, true, c->side))) {
+                er = cudaErrorUnknown;  // (the capture is still ended below)
+                break;
+            }
+            cudaGraphConditionalHandle none{};
+            MacroArgs mg = macro_args(c, dt, false, none);
+            mg.gam = c->gam_eff;
+            mg.rho = c->rho_eff;
+            mg.coupling_tol = HUGE_VAL;
+            mg.coupling_maxit = 1;
+            er = launch_macro_solve(mg, c->side, c->prio_hi);
+            if (er == cudaSuccess) er = launch_elim_commit(elim_args(c, dt), c->side);
+            if (er == cudaSuccess) er = cudaEventRecord(c->join_ev, c->side);
+        }
+        if (er == cudaSuccess) er = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+        if (er == cudaSuccess) {
+            BatchSolveArgs ba{b->d_args, b->d_items, b->nitems, b->d_counter};
+            er = launch_batch_solve(ba, smem, nsm, s);
+        }
+        for (int k = 0; k < n && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->inst[k]->join_ev, 0);
+        cudaGraph_t endg = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(s, &endg);
+        return er != cudaSuccess ? er : e2;
+    };
+    e = body();
+    if (e != cudaSuccess || st) {
+        batch_drop_graph(b, false);
+        cudaGetLastError();
+        return st ? st : bfail(b, TSF_E_CUDA, "persistent batch capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&b->gexec, b->graph, cudaGraphInstantiateFlagUseNodePriority);
+    if (e != cudaSuccess) {
+        batch_drop_graph(b, false);
+        cudaGetLastError();
+        return bfail(b, TSF_E_CUDA, "persistent batch instantiate: %s", cudaGetErrorString(e));
+    }
+    b->gen.resize(n);
+    for (int k = 0; k < n; ++k) b->gen[k] = b->inst[k]->graph_gen;
+    b->graph_valid = true;
+    b->graph_dt = dt;
+    return TSF_OK;
+}
+
 extern "C" {
+
+tsf_status tsf_batch_set_persistent(tsf_batch* b, int on) {
+    if (!b) return TSF_E_ARG;
+    if (on != 0 && on != 1) return bfail(b, TSF_E_ARG, "on must be 0 or 1");
+    if (b->persistent != on) batch_drop_graph(b, true);
+    b->persistent = on;
+    if (on) {
+        // every instance solves its micro problems with the column strips of
+        // the batch kernel (the head solves and the set-up solves included)
+        for (tsf_ctx* c : b->inst) {
+            if (c->opt.tiling != kPersistentTiling) {
+                c->opt.tiling = kPersistentTiling;
+                c->tiling = -1;
+                c->phi_valid = false;
+                invalidate_graph(c);
+            }
+        }
+    }
+    return TSF_OK;
+}
 
 tsf_status tsf_batch_create(tsf_batch** out, int ninst, const tsf_options* opt) {
     if (!out) return TSF_E_ARG;
@@ -1653,7 +1810,15 @@ tsf_status tsf_batch_step(tsf_batch* b, double dt, int nsteps) {
             c->w_valid = true;
         }
     }
-    if (!b->use_graph) {
+    if (b->persistent) {
+        for (int i = 0; i < n; ++i) {
+            tsf_ctx* c = b->inst[i];
+            if (c->opt.precision != TSF_MIXED || !pipelined(c) || c->tiling != kPersistentTiling)
+                return bfail(b, TSF_E_ARG, "instance %d: the persistent batch needs mixed precision and the pipelined "
+                                           "elimination (coupling = elimination, no volume or Robin sources)", i);
+        }
+    }
+    if (!b->use_graph && !b->persistent) {
         for (int s = 0; s < nsteps; ++s) {
             for (int i = 0; i < n; ++i) {
                 tsf_status st = run_plain_steps(b->inst[i], dt, 1);
@@ -1666,7 +1831,7 @@ tsf_status tsf_batch_step(tsf_batch* b, double dt, int nsteps) {
     bool stale = !b->graph_valid || b->graph_dt != dt || b->gen.size() != (size_t)n;
     for (int i = 0; i < n && !stale; ++i) stale = b->gen[i] != b->inst[i]->graph_gen;
     if (stale) {
-        tsf_status st = batch_capture(b, dt);
+        tsf_status st = b->persistent ? batch_capture_persistent(b, dt) : batch_capture(b, dt);
         if (st) return st;
     }
     for (int s = 0; s < nsteps; ++s) {
@@ -1731,6 +1896,9 @@ void tsf_batch_destroy(tsf_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graph(b, true);
+    if (b->d_args) cudaFree(b->d_args);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_counter) cudaFree(b->d_counter);
     for (tsf_ctx* c : b->inst) tsf_destroy(c);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;

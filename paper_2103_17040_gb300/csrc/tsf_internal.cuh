@@ -313,17 +313,48 @@ cudaError_t launch_commit(int nm, int nmp, int nM, const double* u, const double
 // out = a - b elementwise
 cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);
 // Micro-solve variants ("tilings"):
-//   0..3  shared-memory stencil, K = 1, 2, 4, 8 nodes per thread (strided), FP64 or mixed
-//   4..6  column strips of R = 3, 5, 7 nodes with register stencils, mixed only
-//   7..9  column strips of R = 9, 11, 13 nodes with the stencil in shared memory, mixed only
-constexpr int kNumTilings = 10;
-// the three-field system's direct micro solve (banded Cholesky, tsf_band.cu)
+//   0..3   shared-memory stencil, K = 1, 2, 4, 8 nodes per thread (strided), FP64 or mixed
+//   4..6   column strips of R = 3, 5, 7 nodes with register stencils, mixed only
+//   7..9   column strips of R = 9, 11, 13 nodes with the stencil in shared memory, mixed only
+//   10     the three-field system's direct micro solve (banded Cholesky, tsf_band.cu)
+//   11..14 one micro problem per thread-block cluster of G CTAs, column strips of R rows,
+//          (R, G) = (5, 2), (5, 4) with register stencils, (9, 4), (9, 8) with the stencil in
+//          shared memory; mixed only
+//   15, 16 one warp per micro problem (several per block), column strips of R = 3, 5 rows,
+//          register stencils, for micro meshes whose strips fit 32 threads; mixed only
+constexpr int kNumTilings = 17;
 constexpr int kTilingDirect = 10;
+constexpr int kFirstClusterTiling = 11;
+constexpr int kNumClusterTilings = 4;
+constexpr int kFirstWarpTiling = 15;
 bool tiling_fits(int tiling, int precision, int n1, int smem_optin);
 // column-strip kernels (tsf_strip.cu): strips of R = 3, 5, 7 (registers) or 9, 11, 13 (shared memory)
 cudaError_t launch_strip_setup(const StripSetupArgs& a, cudaStream_t s);
 cudaError_t launch_strip_solve(const MicroArgs& a, int R, cudaStream_t s);
 bool strip_fits(int n1, int R, int smem_optin);
+// cluster variants c = tiling - kFirstClusterTiling
+cudaError_t launch_cluster_solve(const MicroArgs& a, int c, cudaStream_t s);
+bool cluster_fits(int c, int n1, int smem_optin);
+// Persistent micro solve of a batch of two-scale problems (pipelined
+// elimination, column strips of kBatchR rows): one launch of one block per
+// SM; every block takes work items from an atomic queue, largest micro
+// problems first.  An item is `count` consecutive micro problems of one
+// problem instance, solved side by side by teams of `warps` warps.
+constexpr int kBatchR = 5;
+constexpr int kBatchWarps = 16;            // warps per block
+struct BatchSolveArgs {
+    const MicroArgs* args;                 // [ninst] per-instance arguments (pipe = 1)
+    const int4* items;                     // [nitems] (instance, first problem, count, warps per team)
+    int nitems;
+    int* counter;                          // queue head, zero before the launch
+};
+int batch_team_warps(int n1);              // warps of the team that solves one micro problem of n1^2 nodes
+size_t batch_team_smem(int n1);            // shared memory of one team
+cudaError_t launch_batch_solve(const BatchSolveArgs& b, size_t smem_bytes, int blocks, cudaStream_t s);
+const void* k_micro_batch_entry();         // the kernel, for its shared-memory attribute
+// one-warp variants (R = 3, 5)
+cudaError_t launch_warp_solve(const MicroArgs& a, int R, cudaStream_t s);
+bool warp_fits(int n1, int R, int smem_optin);
 cudaError_t configure_strip_kernels(int smem_optin);
 // out[k] = the float pair nearest to in[k]
 cudaError_t launch_split_pairs(const double* in, float2* out, size_t n, cudaStream_t s);

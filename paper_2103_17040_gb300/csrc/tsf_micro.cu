@@ -383,7 +383,7 @@ static cudaError_t launch_smem(const MicroArgs& a, cudaStream_t s) {
 static const int kSmemK[4] = {1, 2, 4, 8};
 static const int kStripR[6] = {3, 5, 7, 9, 11, 13};  // 3..7 couplings in registers, 9..13 in shared memory
 
-bool tiling_uses_stored_residual(int tiling) { return tiling >= 4; }
+bool tiling_uses_stored_residual(int tiling) { return tiling >= 4 && tiling != kTilingDirect; }
 
 bool tiling_fits(int tiling, int precision, int n1, int smem_optin) {
     const int nm = n1 * n1;
@@ -392,7 +392,11 @@ bool tiling_fits(int tiling, int precision, int n1, int smem_optin) {
         const int maxT = K <= 2 ? 1024 : (K == 4 ? 512 : 544);
         return smem_threads(nm, K) <= maxT && smem_kernel_bytes(n1, precision) <= (size_t)smem_optin;
     }
-    if (tiling >= 4 && tiling < kNumTilings) return precision != 0 && strip_fits(n1, kStripR[tiling - 4], smem_optin);
+    if (tiling >= 4 && tiling < kTilingDirect) return precision != 0 && strip_fits(n1, kStripR[tiling - 4], smem_optin);
+    if (tiling >= kFirstClusterTiling && tiling < kFirstWarpTiling)
+        return precision != 0 && cluster_fits(tiling - kFirstClusterTiling, n1, smem_optin);
+    if (tiling >= kFirstWarpTiling && tiling < kNumTilings)
+        return precision != 0 && warp_fits(n1, tiling == kFirstWarpTiling ? 3 : 5, smem_optin);
     return false;
 }
 
@@ -411,7 +415,11 @@ cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cu
             case 2: return launch_smem<float, true, 4>(a, s);
             case 3: return launch_smem<float, true, 8>(a, s);
         }
-        if (tiling >= 4 && tiling < kNumTilings) return launch_strip_solve(a, kStripR[tiling - 4], s);
+        if (tiling >= 4 && tiling < kTilingDirect) return launch_strip_solve(a, kStripR[tiling - 4], s);
+        if (tiling >= kFirstClusterTiling && tiling < kFirstWarpTiling)
+            return launch_cluster_solve(a, tiling - kFirstClusterTiling, s);
+        if (tiling >= kFirstWarpTiling && tiling < kNumTilings)
+            return launch_warp_solve(a, tiling == kFirstWarpTiling ? 3 : 5, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -45,7 +45,11 @@
 // has no FP32 range limit.
 #include "tsf_internal.cuh"
 
+#include <cooperative_groups.h>
+
 namespace tsf {
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // float-float arithmetic.  The round-to-nearest intrinsics keep the compiler
@@ -237,7 +241,7 @@ __host__ __device__ inline int padded_nodes(int n1) { return (n1 * n1 + 31) / 32
 // staging (pref) an mbarrier and copies of the low parts of the couplings and
 // the diagonal scalings (48 bytes per padded node), and under the pipelined
 // epilogue of M/dt (40 more).
-static size_t strip_smem_bytes(int n1, int R, bool sc, bool pipe, bool pref) {
+__host__ __device__ inline size_t strip_smem_bytes(int n1, int R, bool sc, bool pipe, bool pref) {
     const size_t W = (size_t)strip_stride(n1, R), H = (size_t)strip_rows(n1, R) * R + 2;
     size_t off = ((pipe ? 2 : 1) * W * H * sizeof(float) + 15) & ~(size_t)15;
     off += 4 * 32 * sizeof(float2);
@@ -362,11 +366,12 @@ __device__ __forceinline__ void strip_store(float* P, int Wd, int p, int q0, con
         if (valid[k]) P[(q0 + k + 1) * Wd + p + 1] = v[k];
 }
 
-// Block-wide sums of two FP32 values: a butterfly inside each warp, then
-// every thread adds the per-warp partials in warp order (the same order in
-// every thread, so all threads get the same, reproducible value).  buf (32
-// float2) must not be written again by the block before every thread has
-// passed one more __syncthreads.
+// Block-wide sums of two FP32 values: a butterfly inside each warp, the
+// per-warp partials through shared memory, and a second butterfly over them
+// in every warp (lanes past the last warp add zeros).  The summation order is
+// fixed and the same in every warp, so all threads get the same, reproducible
+// value.  buf (32 float2) must not be written again by the block before every
+// thread has passed one more __syncthreads.
 __device__ __forceinline__ void block_sum2(float& x, float& y, float2* buf) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -376,21 +381,14 @@ __device__ __forceinline__ void block_sum2(float& x, float& y, float2* buf) {
     }
     if (lane == 0) buf[warp] = make_float2(x, y);
     __syncthreads();
-    float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;
-    int k = 0;
-    for (; k + 1 < nw; k += 2) {  // two chains, combined in a fixed order
-        const float4 t = *reinterpret_cast<const float4*>(buf + k);
-        sx += t.x;
-        sy += t.y;
-        tx += t.z;
-        ty += t.w;
+    const float2 t = lane < nw ? buf[lane] : make_float2(0.f, 0.f);
+    x = t.x;
+    y = t.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
     }
-    if (k < nw) {
-        sx += buf[k].x;
-        sy += buf[k].y;
-    }
-    x = sx + tx;
-    y = sy + ty;
 }
 
 // Block-wide maximum of a non-negative FP32 value (the bit patterns of
@@ -429,16 +427,102 @@ __device__ __forceinline__ void block_sum2_max(float& x, float& y, float& m, flo
     m = mx;
 }
 
+// Who solves one micro problem: a whole thread block (BlockTeam), or one
+// warp, several micro problems per block (WarpTeam, for micro meshes whose
+// strips fit 32 threads).  A warp synchronises with __syncwarp and reduces
+// with shuffles alone, so its CG iterations need no block barrier and no
+// shared-memory partials.
+struct BlockTeam {
+    static constexpr bool kWarp = false;
+    __device__ int thread() const { return threadIdx.x; }
+    __device__ int size() const { return blockDim.x; }
+    __device__ int slot() const { return 0; }  // team index within the block
+    __device__ int problem() const { return blockIdx.x; }
+    __device__ void sync() const { __syncthreads(); }
+    __device__ void sum2(float& x, float& y, float2* buf) const { block_sum2(x, y, buf); }
+    __device__ void sum2_max(float& x, float& y, float& m, float4* buf) const { block_sum2_max(x, y, m, buf); }
+};
+struct WarpTeam {
+    static constexpr bool kWarp = true;
+    __device__ int thread() const { return threadIdx.x & 31; }
+    __device__ int size() const { return 32; }
+    __device__ int slot() const { return threadIdx.x >> 5; }
+    __device__ int problem() const { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+    __device__ void sync() const { __syncwarp(); }
+    __device__ void sum2(float& x, float& y, float2*) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+    }
+    __device__ void sum2_max(float& x, float& y, float& m, float4*) const {
+        sum2(x, y, nullptr);
+        m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+    }
+};
+// A group of nw consecutive warps of a block (the persistent batch kernel runs
+// several micro problems side by side in one block): named barrier bar (1..15)
+// over its nw * 32 threads, reductions through its own partial buffers.
+struct GroupTeam {
+    static constexpr bool kWarp = false;
+    int tid0, nw, bar, slot_, prob;
+    __device__ int thread() const { return (int)threadIdx.x - tid0; }
+    __device__ int size() const { return nw * 32; }
+    __device__ int slot() const { return slot_; }
+    __device__ int problem() const { return prob; }
+    __device__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nw * 32) : "memory"); }
+    __device__ void sum2(float& x, float& y, float2* buf) const {
+        const int lane = threadIdx.x & 31, warp = thread() >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) buf[warp] = make_float2(x, y);
+        sync();
+        const float2 t = lane < nw ? buf[lane] : make_float2(0.f, 0.f);
+        x = t.x;
+        y = t.y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+    }
+    __device__ void sum2_max(float& x, float& y, float& m, float4* buf) const {
+        const int lane = threadIdx.x & 31, warp = thread() >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        const float mb = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+        if (lane == 0) buf[warp] = make_float4(x, y, mb, 0.f);
+        sync();
+        float sx = 0.f, sy = 0.f, mx = 0.f;
+        for (int k = 0; k < nw; ++k) {
+            const float4 t = buf[k];
+            sx += t.x;
+            sy += t.y;
+            mx = fmaxf(mx, t.z);
+        }
+        x = sx;
+        y = sy;
+        m = mx;
+    }
+};
+
 // Chronopoulos-Gear CG on the scaled operator (Jacobi-PCG on S); x = 0 on
 // entry, r = rhs.  Stops when ||r||^2 <= rel2 ||r_0||^2 or after maxit
 // iterations; returns the count.  redA/redB: 32-float2 reduction buffers.
-template <int R, class CS>
+template <int R, class CS, class TEAM = BlockTeam>
 __device__ int strip_cg(const CS& c, const bool (&valid)[R], float (&x)[R], float (&r)[R], float* P, int Wd, int p,
-                        int q0, float rel2, int maxit, float2* redA, float2* redB, int* flag) {
+                        int q0, float rel2, int maxit, float2* redA, float2* redB, int* flag, const TEAM& tm = TEAM()) {
     float pv[R], s[R], w[R];
     StripHalo<R> h;
     strip_store<R>(P, Wd, p, q0, valid, r);
-    __syncthreads();
+    tm.sync();
     if constexpr (R >= 9) {
         strip_apply_plane<R>(c, r, P, Wd, p, q0, valid, w);
     } else {
@@ -453,7 +537,7 @@ __device__ int strip_cg(const CS& c, const bool (&valid)[R], float (&x)[R], floa
         pv[k] = r[k];
         s[k] = w[k];
     }
-    block_sum2(g, dl, redA);
+    tm.sum2(g, dl, redA);
     const float stop = rel2 * g;
     if (!(dl > 0.f)) {
         *flag = (dl == dl) ? kBreakdown : kNaN;
@@ -471,7 +555,7 @@ __device__ int strip_cg(const CS& c, const bool (&valid)[R], float (&x)[R], floa
         }
         ++it;
         strip_store<R>(P, Wd, p, q0, valid, r);
-        __syncthreads();
+        tm.sync();
         if constexpr (R >= 9) {
             strip_apply_plane<R>(c, r, P, Wd, p, q0, valid, w);
         } else {
@@ -484,11 +568,8 @@ __device__ int strip_cg(const CS& c, const bool (&valid)[R], float (&x)[R], floa
             gn = fmaf(r[k], r[k], gn);
             dn = fmaf(r[k], w[k], dn);
         }
-        block_sum2(gn, dn, (it & 1) ? redB : redA);
-        if (!(gn == gn) || !(dn == dn)) {
-            *flag = kNaN;
-            break;
-        }
+        tm.sum2(gn, dn, (it & 1) ? redB : redA);
+        // (a NaN fails the test on den below; the refinement's residual norm reports it)
         if (gn <= stop) break;
         const float beta = __fdividef(gn, g);
         const float den = dn - __fdividef(beta * gn, alpha);
@@ -559,10 +640,13 @@ __device__ __forceinline__ double pow2_scale_of_norm2(double x) {
     return ldexp(1.0, 1 - e);
 }
 
-template <int R, bool SC, bool PIPE, bool PREF>
-__device__ __forceinline__ void strip_body(const MicroArgs& a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+template <int R, bool SC, bool PIPE, bool PREF, class TEAM = BlockTeam>
+__device__ __forceinline__ void strip_body(const MicroArgs& a, const TEAM& tm = TEAM()) {
+    static_assert(!(TEAM::kWarp && (PREF || SC)), "one-warp teams keep their couplings in registers, unstaged");
+    extern __shared__ __align__(16) unsigned char smem_all[];
     const int n1 = a.n1, Wd = strip_stride(n1, R);
+    // this team's part of the block's shared memory
+    unsigned char* smem = smem_all + (size_t)tm.slot() * strip_smem_bytes(n1, R, SC, PIPE, PREF);
     const int Hd = strip_rows(n1, R) * R + 2, pw = Wd * Hd;
     const size_t pl = (size_t)a.nmp;
     float* P = reinterpret_cast<float*>(smem);
@@ -583,7 +667,8 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
     float4* cA = reinterpret_cast<float4*>(smem + off);
     float4* cB = cA + ncg;
 
-    const int i = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+    const int i = tm.problem(), tid = tm.thread(), T = tm.size();
+    if (i >= a.nM) return;  // (one-warp teams: the warps past the last micro problem)
     const bool active = tid < n1 * strip_rows(n1, R);
     const int p = active ? tid % n1 : 0;
     const int q0 = active ? (tid / n1) * R : 0;
@@ -591,7 +676,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
     bool staged = false, timed_out = false;
     if constexpr (PREF) {
         if (tid == 0) mbar_init(bar, 1);
-        __syncthreads();
+        __syncthreads();  // (block teams only)
         if (tid == 0) {
             const unsigned lo = (unsigned)(2 * pl * sizeof(float4)), ds = (unsigned)(pl * sizeof(float4));
             const unsigned mp = PIPE ? (unsigned)(kPlanes * pl * sizeof(float)) : 0u;
@@ -650,7 +735,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
         // one reduction for ||r||^2, ||c||^2 and max |c|, |r|; values far
         // from 1 (whose squares could leave the FP32 range) are summed again
         // scaled by a power of two
-        block_sum2_max(rs, cs, m, reinterpret_cast<float4*>(red));
+        tm.sum2_max(rs, cs, m, reinterpret_cast<float4*>(red));
         if (!(m >= 0x1p-16f && m <= 0x1p+40f) && m > 0.f && m <= 3.0e38f) {
             const int e = ilogbf(m);
             s = pow2f(-e);
@@ -663,7 +748,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
                 rs = fmaf(x, x, rs);
                 cs = fmaf(c, c, cs);
             }
-            block_sum2(rs, cs, red + 96);
+            tm.sum2(rs, cs, red + 96);
         }
         rr = rs;
         zero_rhs = cs == 0.f;
@@ -703,7 +788,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
             }
         }
         float dummy = 0.f;
-        block_sum2(rr, dummy, red);
+        tm.sum2(rr, dummy, red);
         stop2 = (float)(a.tol * a.tol * bn2 * s64 * s64);
         if (!zero_rhs && rr > stop2) {  // low parts only where a solve follows
 #pragma unroll
@@ -746,7 +831,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
                 creg.c[k] = c8;
             }
         }
-        __syncthreads();
+        tm.sync();
         const SmemCouplings cs{cA, cB, p + n1 * q0, n1};
         const float4* clo = a.chatlo + (size_t)i * 2 * pl;
         for (;;) {
@@ -769,14 +854,14 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
             }
             const float rel2 = fmaxf(a.inner_tol * a.inner_tol, 0.25f * stop2 / rr);
             if constexpr (SC)
-                inner += strip_cg<R>(cs, valid, y, rhs, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 32, &flag);
+                inner += strip_cg<R, SmemCouplings, TEAM>(cs, valid, y, rhs, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 32, &flag, tm);
             else
-                inner += strip_cg<R>(creg, valid, y, rhs, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 32, &flag);
+                inner += strip_cg<R, RegCouplings<R>, TEAM>(creg, valid, y, rhs, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 32, &flag, tm);
             if (flag == kNaN) break;
             flag = 0;  // an FP32 breakdown only ends this inner solve; the residual decides
             // S d = D^1/2 (S^ y) and d = D^-1/2 y in float-float
             strip_store<R>(P, Wd, p, q0, valid, y);
-            __syncthreads();
+            tm.sync();
             wait_staged();
             StripHalo<R> h;
             h.load(P, Wd, p, q0);
@@ -818,7 +903,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
                 rs = fmaf(x, x, rs);
             }
             float dummy = 0.f;
-            block_sum2(rs, dummy, red + 64 + 32 * (sweeps & 1));
+            tm.sum2(rs, dummy, red + 64 + 32 * (sweeps & 1));
             rr = rs;
             ++sweeps;
             if (!(rr == rr)) {
@@ -849,7 +934,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
                 res[j] = fma(kdu, re[q], res[j]);
             }
         }
-        __syncthreads();
+        tm.sync();
         // flux integral rho_i = r_i^T v_i over the Robin-edge nodes, one warp,
         // compensated (TwoSum) FP64
         if (tid < 32) {
@@ -899,13 +984,13 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a) {
             wh[k] = w[k].x;
             wl[k] = w[k].y;
         }
-        __syncthreads();  // every read of the plane is done
+        tm.sync();  // every read of the plane is done
         if (!planes_zero)
             for (int e = tid; e < 2 * pw; e += T) P[e] = 0.f;
-        __syncthreads();
+        tm.sync();
         strip_store<R>(P, Wd, p, q0, valid, wh);
         strip_store<R>(P2, Wd, p, q0, valid, wl);
-        __syncthreads();
+        tm.sync();
         StripHalo<R> hh, hl;
         hh.load(P, Wd, p, q0);
         hl.load(P2, Wd, p, q0);
@@ -978,6 +1063,81 @@ __global__ void __maxnreg__(kTallStripRegs) k_micro_strip_tall(MicroArgs a) {
     strip_body<R, true, PIPE, false>(a);
 }
 
+// One warp per micro problem, kWarpsPerBlock problems per block (micro meshes
+// whose strips fit 32 threads).
+constexpr int kWarpsPerBlock = 8;
+template <int R>
+struct WarpMinBlocks {
+    static constexpr int value = R == 3 ? 3 : 2;
+};
+template <int R, bool PIPE>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, WarpMinBlocks<R>::value) k_micro_warp(MicroArgs a) {
+    strip_body<R, false, PIPE, false, WarpTeam>(a);
+}
+
+bool warp_fits(int n1, int R, int smem_optin) {
+    return n1 * strip_rows(n1, R) <= 32 &&
+           kWarpsPerBlock * strip_smem_bytes(n1, R, false, true, false) <= (size_t)smem_optin;
+}
+
+cudaError_t launch_warp_solve(const MicroArgs& a, int R, cudaStream_t s) {
+    const bool pipe = a.pipe != 0;
+    const size_t sm = kWarpsPerBlock * strip_smem_bytes(a.n1, R, false, pipe, false);
+    const unsigned nb = (unsigned)((a.nM + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    const int T = 32 * kWarpsPerBlock;
+    if (a.n1 * strip_rows(a.n1, R) > 32) return cudaErrorInvalidConfiguration;
+    if (R == 3) {
+        if (pipe) k_micro_warp<3, true><<<nb, T, sm, s>>>(a);
+        else k_micro_warp<3, false><<<nb, T, sm, s>>>(a);
+    } else if (R == 5) {
+        if (pipe) k_micro_warp<5, true><<<nb, T, sm, s>>>(a);
+        else k_micro_warp<5, false><<<nb, T, sm, s>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batch kernel.  Each block loops: take the next item from the
+// queue, copy that problem instance's arguments into shared memory, let
+// team t of its warps solve micro problem first + t with the column-strip
+// body (named barrier 1 + t), and wait for every team before the next item.
+// ---------------------------------------------------------------------------
+int batch_team_warps(int n1) { return (n1 * strip_rows(n1, kBatchR) + 31) / 32; }
+size_t batch_team_smem(int n1) { return strip_smem_bytes(n1, kBatchR, false, true, false); }
+
+__global__ void __launch_bounds__(32 * kBatchWarps, 1) k_micro_batch(BatchSolveArgs b) {
+    __shared__ MicroArgs s_args;
+    __shared__ int4 s_item;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(b.counter, 1);
+            s_item = it < b.nitems ? b.items[it] : make_int4(-1, 0, 0, 0);
+        }
+        __syncthreads();
+        const int4 item = s_item;
+        if (item.x < 0) break;  // queue drained (the same in every thread)
+        const int* src = reinterpret_cast<const int*>(b.args + item.x);
+        for (int k = threadIdx.x; k < (int)(sizeof(MicroArgs) / sizeof(int)); k += blockDim.x)
+            reinterpret_cast<int*>(&s_args)[k] = src[k];
+        __syncthreads();
+        const int t = (threadIdx.x >> 5) / item.w;
+        if (t < item.z) {
+            GroupTeam tm{t * item.w * 32, item.w, 1 + t, t, item.y + t};
+            strip_body<kBatchR, false, true, false, GroupTeam>(s_args, tm);
+        }
+        __syncthreads();  // every team is done with the arguments and the item
+    }
+}
+
+const void* k_micro_batch_entry() { return (const void*)k_micro_batch; }
+
+cudaError_t launch_batch_solve(const BatchSolveArgs& b, size_t smem_bytes, int blocks, cudaStream_t s) {
+    k_micro_batch<<<blocks, 32 * kBatchWarps, smem_bytes, s>>>(b);
+    return cudaGetLastError();
+}
+
 template <int R, bool SC>
 static cudaError_t launch_strip(const MicroArgs& a, cudaStream_t s) {
     const int T = strip_threads(a.n1, R);
@@ -1013,6 +1173,623 @@ cudaError_t launch_strip_solve(const MicroArgs& a, int R, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// ===========================================================================
+// One micro problem per thread-block cluster (multi-CTA per problem).
+//
+// For micro meshes too large for one block, and for batches with fewer micro
+// problems than the GPU has SMs, the strips of one problem are divided among
+// the G CTAs of a cluster: CTA g owns strips [g ns / G, (g+1) ns / G).  Each
+// CTA keeps its rows in its own shared-memory plane; the rows next to a CTA
+// boundary reach the neighbouring CTA by stores into its plane through
+// distributed shared memory, and the dot products of the CG go to every CTA
+// of the cluster the same way, so that the vectors never leave the chip.
+// Barriers are cluster barriers.  The arithmetic per node is that of the
+// single-block strip kernels above.
+// ===========================================================================
+__host__ __device__ inline int cl_strip_begin(int ns, int G, int g) { return (int)(((long long)ns * g) / G); }
+
+// Where the CTA's boundary rows go: the plane of rank g-1 receives this CTA's
+// first grid row as its top halo row (rowDn), the plane of rank g+1 this
+// CTA's last grid row as its bottom halo row (row 0).
+struct ClusterLink {
+    int g, G;
+    float* Pdn;     // plane of rank g - 1 (nullptr for g = 0)
+    float* Pup;     // plane of rank g + 1 (nullptr for the last rank)
+    float* P2dn;    // second planes (pipelined epilogue)
+    float* P2up;
+    int rowDn;      // local row of this CTA's first grid row in rank g - 1's plane
+    bool first, last;  // this thread owns the CTA's first / last strip
+};
+
+// Store the strip's R values into the local plane (local rows lq0 + 1 ..) and
+// the boundary rows into the neighbours' planes.
+template <int R>
+__device__ __forceinline__ void cl_store(float* P, float* Pdn, float* Pup, const ClusterLink& L, int Wd, int p,
+                                         int lq0, const bool (&valid)[R], const float (&v)[R]) {
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if (valid[k]) P[(lq0 + k + 1) * Wd + p + 1] = v[k];
+    if (L.first && Pdn && valid[0]) Pdn[L.rowDn * Wd + p + 1] = v[0];
+    if (L.last && Pup && valid[R - 1]) Pup[p + 1] = v[R - 1];
+}
+
+// Sums of two FP32 values over every thread of the cluster: a butterfly in
+// each warp, then lane l < G of each warp stores the warp's partial into the
+// buffer of CTA l at slot g * 32 + warp; after the cluster barrier every thread
+// adds all G x nw partials in the same fixed order.  buf: G x 32 float2, not
+// written again before every thread of the cluster has passed one more
+// cluster barrier.
+__device__ __forceinline__ void cluster_sum2(float& x, float& y, float2* buf, const ClusterLink& L) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (lane < L.G) cl.map_shared_rank(buf, lane)[L.g * 32 + warp] = make_float2(x, y);
+    cl.sync();
+    float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;
+    for (int r = 0; r < L.G; ++r) {
+        const float2* b = buf + r * 32;
+        int k = 0;
+        for (; k + 1 < nw; k += 2) {
+            const float4 t = *reinterpret_cast<const float4*>(b + k);
+            sx += t.x;
+            sy += t.y;
+            tx += t.z;
+            ty += t.w;
+        }
+        if (k < nw) {
+            sx += b[k].x;
+            sy += b[k].y;
+        }
+    }
+    x = sx + tx;
+    y = sy + ty;
+}
+
+// The same for two sums and a maximum of a non-negative value.  buf: G x 32 float4.
+__device__ __forceinline__ void cluster_sum2_max(float& x, float& y, float& m, float4* buf, const ClusterLink& L) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    const float mb = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+    if (lane < L.G) cl.map_shared_rank(buf, lane)[L.g * 32 + warp] = make_float4(x, y, mb, 0.f);
+    cl.sync();
+    float sx = 0.f, sy = 0.f, mx = 0.f;
+    for (int r = 0; r < L.G; ++r)
+        for (int k = 0; k < nw; ++k) {
+            const float4 t = buf[r * 32 + k];
+            sx += t.x;
+            sy += t.y;
+            mx = fmaxf(mx, t.z);
+        }
+    x = sx;
+    y = sy;
+    m = mx;
+}
+
+// Chronopoulos-Gear CG of the cluster (strip_cg with the plane stores and
+// reductions of the cluster).
+template <int R, class CS>
+__device__ int cluster_cg(const CS& c, const bool (&valid)[R], float (&x)[R], float (&r)[R], float* P,
+                          const ClusterLink& L, int Wd, int p, int lq0, float rel2, int maxit, float2* redA,
+                          float2* redB, int* flag) {
+    cg::cluster_group cl = cg::this_cluster();
+    float pv[R], s[R], w[R];
+    StripHalo<R> h;
+    cl_store<R>(P, L.Pdn, L.Pup, L, Wd, p, lq0, valid, r);
+    cl.sync();
+    if constexpr (R >= 9) {
+        strip_apply_plane<R>(c, r, P, Wd, p, lq0, valid, w);
+    } else {
+        h.load(P, Wd, p, lq0);
+        strip_apply<R>(c, r, h, w);
+    }
+    float g = 0.f, dl = 0.f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        g = fmaf(r[k], r[k], g);
+        dl = fmaf(r[k], w[k], dl);
+        pv[k] = r[k];
+        s[k] = w[k];
+    }
+    cluster_sum2(g, dl, redA, L);
+    const float stop = rel2 * g;
+    if (!(dl > 0.f)) {
+        *flag = (dl == dl) ? kBreakdown : kNaN;
+        return 0;
+    }
+    float alpha = __fdividef(g, dl);
+    int it = 0;
+    while (it < maxit) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            x[k] = fmaf(alpha, pv[k], x[k]);
+            r[k] = fmaf(-alpha, s[k], r[k]);
+        }
+        ++it;
+        cl_store<R>(P, L.Pdn, L.Pup, L, Wd, p, lq0, valid, r);
+        cl.sync();
+        if constexpr (R >= 9) {
+            strip_apply_plane<R>(c, r, P, Wd, p, lq0, valid, w);
+        } else {
+            h.load(P, Wd, p, lq0);
+            strip_apply<R>(c, r, h, w);
+        }
+        float gn = 0.f, dn = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            gn = fmaf(r[k], r[k], gn);
+            dn = fmaf(r[k], w[k], dn);
+        }
+        cluster_sum2(gn, dn, (it & 1) ? redB : redA, L);
+        if (!(gn == gn) || !(dn == dn)) {
+            *flag = kNaN;
+            break;
+        }
+        if (gn <= stop) break;
+        const float beta = __fdividef(gn, g);
+        const float den = dn - __fdividef(beta * gn, alpha);
+        if (!(den > 0.f)) {
+            *flag = kBreakdown;
+            break;
+        }
+        alpha = __fdividef(gn, den);
+        g = gn;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            pv[k] = fmaf(beta, pv[k], r[k]);
+            s[k] = fmaf(beta, s[k], w[k]);
+        }
+    }
+    return it;
+}
+
+// Shared memory of one CTA of a cluster: the plane(s) for the largest share
+// of strips, four reduction buffers of G x 32 float4, and (sc) the couplings
+// of the CTA's rows.
+static size_t cluster_smem_bytes(int n1, int R, int G, bool sc, bool pipe) {
+    const int ns = strip_rows(n1, R), smax = (ns + G - 1) / G;
+    const size_t W = (size_t)strip_stride(n1, R), H = (size_t)smax * R + 2;
+    size_t off = ((pipe ? 2 : 1) * W * H * sizeof(float) + 15) & ~(size_t)15;
+    off += 4 * (size_t)G * 32 * sizeof(float4);
+    if (sc) off += 2 * (size_t)n1 * smax * R * sizeof(float4);
+    return off;
+}
+static int cluster_threads(int n1, int R, int G) {
+    const int ns = strip_rows(n1, R), smax = (ns + G - 1) / G;
+    return (n1 * smax + 31) / 32 * 32;
+}
+
+template <int R, bool SC, bool PIPE>
+__device__ __forceinline__ void cluster_body(const MicroArgs& a) {
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int G = (int)cl.num_blocks(), g = (int)cl.block_rank();
+    const int n1 = a.n1, Wd = strip_stride(n1, R), ns = strip_rows(n1, R);
+    const int s0 = cl_strip_begin(ns, G, g), s1 = cl_strip_begin(ns, G, g + 1);
+    const int smax = (ns + G - 1) / G, Hd = smax * R + 2, pw = Wd * Hd;
+    float* P = reinterpret_cast<float*>(smem);
+    float* P2 = P + pw;
+    size_t off = ((size_t)(PIPE ? 2 : 1) * pw * sizeof(float) + 15) & ~(size_t)15;
+    float4* red4 = reinterpret_cast<float4*>(smem + off);  // 4 buffers of G x 32 float4
+    float2* redA = reinterpret_cast<float2*>(red4);
+    float2* redB = reinterpret_cast<float2*>(red4 + G * 32);
+    float2* redC = reinterpret_cast<float2*>(red4 + 2 * G * 32);
+    float4* redD = red4 + 3 * G * 32;
+    off += 4 * (size_t)G * 32 * sizeof(float4);
+    float4* cA = reinterpret_cast<float4*>(smem + off);
+    float4* cB = cA + n1 * smax * R;
+
+    const int i = blockIdx.x / G, tid = threadIdx.x;
+    const int nst = s1 - s0;
+    const bool active = tid < n1 * nst;
+    const int p = active ? tid % n1 : 0;
+    const int sl = active ? tid / n1 : 0;  // local strip
+    const int lq0 = sl * R;                // local row of the strip's first node (plane row lq0 + 1)
+    const int q0 = (s0 + sl) * R;          // its grid row
+    const size_t pl = (size_t)a.nmp, io = (size_t)i * pl;
+    const double* re = a.redge + (size_t)i * n1;
+    const bool edge = p == n1 - 1;
+    bool valid[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) valid[k] = active && (q0 + k) < n1;
+    ClusterLink L;
+    L.g = g;
+    L.G = G;
+    L.Pdn = g > 0 ? cl.map_shared_rank(P, g - 1) : nullptr;
+    L.Pup = g + 1 < G ? cl.map_shared_rank(P, g + 1) : nullptr;
+    L.P2dn = g > 0 ? cl.map_shared_rank(P2, g - 1) : nullptr;
+    L.P2up = g + 1 < G ? cl.map_shared_rank(P2, g + 1) : nullptr;
+    L.rowDn = g > 0 ? (s0 - cl_strip_begin(ns, G, g - 1)) * R + 1 : 0;
+    L.first = active && sl == 0;
+    L.last = active && sl == nst - 1;
+    // zero planes (the halo rows of the mesh boundary stay zero), then make
+    // sure no CTA stores into a neighbour's plane before it is zeroed
+    for (int e = tid; e < (PIPE ? 2 : 1) * pw; e += blockDim.x) P[e] = 0.f;
+    cl.sync();
+
+    float2 r[R];
+    float s = 1.f, si = 1.f;
+    double s64 = 1.0;
+    float rr = 0.f, stop2 = 0.f;
+    bool zero_rhs = false;
+    double ui = 0.0, kdu = 0.0;
+    float2 uo2 = make_float2(0.f, 0.f);
+    if constexpr (PIPE) {
+        uo2 = a.u_old2[i];
+        float cv[R];
+        float m = 0.f, rs = 0.f, cs = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            r[k] = make_float2(0.f, 0.f);
+            cv[k] = 0.f;
+            if (valid[k]) {
+                const size_t j = io + p + n1 * (q0 + k);
+                const float2 t = ff_mul(a.mq2[j], uo2);
+                r[k] = ff_add(a.res2[j], t);
+                cv[k] = a.mw2[j].x + t.x;
+                m = fmaxf(m, fmaxf(fabsf(cv[k]), fabsf(r[k].x)));
+                rs = fmaf(r[k].x, r[k].x, rs);
+                cs = fmaf(cv[k], cv[k], cs);
+            }
+        }
+        cluster_sum2_max(rs, cs, m, redD, L);
+        if (!(m >= 0x1p-16f && m <= 0x1p+40f) && m > 0.f && m <= 3.0e38f) {
+            const int e = ilogbf(m);
+            s = pow2f(-e);
+            si = pow2f(e);
+            rs = 0.f;
+            cs = 0.f;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const float x = r[k].x * s, c = cv[k] * s;
+                rs = fmaf(x, x, rs);
+                cs = fmaf(c, c, cs);
+            }
+            cluster_sum2(rs, cs, redC, L);
+        }
+        rr = rs;
+        zero_rhs = cs == 0.f;
+        stop2 = (float)(a.tol * a.tol) * cs;
+        if (s > 0x1p+100f) {
+            const float f = 0x1p-149f * s;
+            stop2 = fmaxf(stop2, 16.f * (float)a.nm * f * f);
+        }
+        if (zero_rhs) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) r[k] = make_float2(0.f, 0.f);
+        }
+    } else {
+        ui = a.u[i];
+        kdu = a.kappa * (ui - a.u_used[i]);
+        const double* bn = a.bnorm + (size_t)i * 3;
+        const double ku = a.kappa * ui;
+        const double bn2 = fma(ku * ku, bn[2], fma(2.0 * ku, bn[1], bn[0]));
+        zero_rhs = !(bn2 > 0.0);
+        s64 = pow2_scale_of_norm2(bn2);
+        const double* res = a.res + io;
+        double r64[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            r64[k] = 0.0;
+            r[k] = make_float2(0.f, 0.f);
+            if (valid[k]) {
+                const int q = q0 + k;
+                double x = res[p + n1 * q];
+                if (edge) x = fma(kdu, re[q], x);
+                r64[k] = x * s64;
+                r[k].x = __double2float_rn(r64[k]);
+                rr = fmaf(r[k].x, r[k].x, rr);
+            }
+        }
+        float dummy = 0.f;
+        cluster_sum2(rr, dummy, redC, L);
+        stop2 = (float)(a.tol * a.tol * bn2 * s64 * s64);
+        if (!zero_rhs && rr > stop2) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) r[k].y = __double2float_rn(r64[k] - (double)r[k].x);
+        }
+    }
+
+    int inner = 0, sweeps = 0, flag = 0;
+    bool solved = false;
+    float2 dv[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) dv[k] = make_float2(0.f, 0.f);
+    if (!(rr == rr)) {
+        flag = kNaN;
+    } else if (zero_rhs) {
+        solved = true;
+    } else if (rr > stop2) {
+        solved = true;
+        const float4* ch = a.chat + (size_t)i * 2 * pl;
+        RegCouplings<R> creg;
+        float sch[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int j = p + n1 * (q0 + k);
+            Couple8 c8{0, 0, 0, 0, 0, 0, 0, 0};
+            sch[k] = 0.f;
+            if (valid[k]) {
+                c8 = couple8(ch[j], ch[pl + j]);
+                sch[k] = a.dsc[io + j].x;
+            }
+            if constexpr (SC) {
+                if (active) {
+                    const int jl = p + n1 * (lq0 + k);  // node of the CTA's rows
+                    cA[jl] = make_float4(c8.E, c8.W, c8.N, c8.S);
+                    cB[jl] = make_float4(c8.NE, c8.NW, c8.SE, c8.SW);
+                }
+            } else {
+                creg.c[k] = c8;
+            }
+        }
+        __syncthreads();
+        const SmemCouplings cs{cA, cB, p + n1 * lq0, n1};
+        const float4* clo = a.chatlo + (size_t)i * 2 * pl;
+        for (;;) {
+            if (sweeps >= a.max_sweeps || inner >= a.maxit) {
+                flag = kNotConverged;
+                break;
+            }
+            const int et = ilogbf(sqrtf(rr));
+            const float t = pow2f(-et), ti = pow2f(et);
+            float y[R], rhs[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                y[k] = 0.f;
+                rhs[k] = sch[k] * ((PIPE ? r[k].x * s : r[k].x) * t);
+            }
+            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, 0.25f * stop2 / rr);
+            if constexpr (SC)
+                inner += cluster_cg<R>(cs, valid, y, rhs, P, L, Wd, p, lq0, rel2, a.maxit - inner, redA, redB, &flag);
+            else
+                inner += cluster_cg<R>(creg, valid, y, rhs, P, L, Wd, p, lq0, rel2, a.maxit - inner, redA, redB,
+                                       &flag);
+            if (flag == kNaN) break;
+            flag = 0;
+            cl_store<R>(P, L.Pdn, L.Pup, L, Wd, p, lq0, valid, y);
+            cl.sync();
+            StripHalo<R> h;
+            h.load(P, Wd, p, lq0);
+            float rs = 0.f;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if (!valid[k]) continue;
+                const int j = p + n1 * (q0 + k);
+                Couple8 c;
+                if constexpr (SC)
+                    c = cs.get(k);
+                else
+                    c = creg.get(k);
+                const float4 la = clo[j], lb = clo[pl + j];
+                const float4 ds = a.dsc[io + j];
+                const float up = (k + 1 < R) ? y[k + 1] : h.xp;
+                const float dn = (k > 0) ? y[k - 1] : h.xm;
+                float ts = y[k], tc = 0.f;
+                ff_acc(ts, tc, c.E, la.x, h.Rt[k + 1]);
+                ff_acc(ts, tc, c.W, la.y, h.L[k + 1]);
+                ff_acc(ts, tc, c.N, la.z, up);
+                ff_acc(ts, tc, c.S, la.w, dn);
+                ff_acc(ts, tc, c.NE, lb.x, h.Rt[k + 2]);
+                ff_acc(ts, tc, c.NW, lb.y, h.L[k + 2]);
+                ff_acc(ts, tc, c.SE, lb.z, h.Rt[k]);
+                ff_acc(ts, tc, c.SW, lb.w, h.L[k]);
+                float2 sd = ff_mul(make_float2(ds.z, ds.w), fast_two_sum_f(ts, tc));
+                float2 d = ff_mul(make_float2(ds.x, ds.y), make_float2(y[k], 0.f));
+                sd = make_float2(sd.x * ti, sd.y * ti);
+                d = make_float2(d.x * ti, d.y * ti);
+                if constexpr (PIPE) {
+                    sd = make_float2(sd.x * si, sd.y * si);
+                    d = make_float2(d.x * si, d.y * si);
+                }
+                r[k] = ff_sub(r[k], sd);
+                dv[k] = ff_add(dv[k], d);
+                const float x = PIPE ? r[k].x * s : r[k].x;
+                rs = fmaf(x, x, rs);
+            }
+            float dummy = 0.f;
+            cluster_sum2(rs, dummy, (sweeps & 1) ? redB : redA, L);
+            rr = rs;
+            ++sweeps;
+            if (!(rr == rr)) {
+                flag = kNaN;
+                break;
+            }
+            if (rr <= stop2) break;
+        }
+    }
+
+    if constexpr (!PIPE) {
+        double* v = a.v + io;
+        double* res = a.res + io;
+        const double sinv = 1.0 / s64;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (!valid[k]) continue;
+            const int q = q0 + k, j = p + n1 * q;
+            if (zero_rhs) {
+                v[j] = 0.0;
+                res[j] = 0.0;
+            } else if (solved) {
+                v[j] += ff_to_double(dv[k]) * sinv;
+                res[j] = ff_to_double(r[k]) * sinv;
+            } else if (edge && kdu != 0.0) {
+                res[j] = fma(kdu, re[q], res[j]);
+            }
+        }
+        __syncthreads();
+        // rho_i = r_i^T v_i: each CTA sums its rows' Robin-edge nodes (one warp,
+        // compensated FP64), rank 0 adds the G partial pairs in rank order
+        double2* part = reinterpret_cast<double2*>(redD);  // G entries in rank 0's buffer
+        if (tid < 32) {
+            double sm = 0.0, cp = 0.0;
+            const int qa = s0 * R, qb = min(s1 * R, n1);
+            for (int q = qa + tid; q < qb; q += 32) {
+                double su, er;
+                two_sum(sm, re[q] * v[(n1 - 1) + n1 * q], su, er);
+                sm = su;
+                cp += er;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                double su, er;
+                two_sum(sm, __shfl_xor_sync(0xffffffffu, sm, o), su, er);
+                sm = su;
+                cp += __shfl_xor_sync(0xffffffffu, cp, o) + er;
+            }
+            if (tid == 0) cl.map_shared_rank(part, 0)[g] = make_double2(sm, cp);
+        }
+        cl.sync();
+        if (g == 0 && tid == 0) {
+            double sm = 0.0, cp = 0.0;
+            for (int k = 0; k < G; ++k) {
+                double su, er;
+                two_sum(sm, part[k].x, su, er);
+                sm = su;
+                cp += er + part[k].y;
+            }
+            a.u_used[i] = ui;
+            a.rho[i] = sm + cp;
+        }
+    } else {
+        const int st = a.ctl->hist_step, level = a.ctl->hist_level;
+        const size_t slot = (size_t)a.nM * pl;
+        float2* hc = a.hist2 + (size_t)(st % 3) * slot + io;
+        const float2* h1 = a.hist2 + (size_t)((st + 2) % 3) * slot + io;
+        const float2* h2 = a.hist2 + (size_t)((st + 1) % 3) * slot + io;
+        float2* yc = a.yhist2 + (size_t)(st % 3) * slot + io;
+        const float2* y1 = a.yhist2 + (size_t)((st + 2) % 3) * slot + io;
+        const float2* y2 = a.yhist2 + (size_t)((st + 1) % 3) * slot + io;
+        float2 w[R];
+        float wh[R], wl[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            w[k] = make_float2(0.f, 0.f);
+            if (valid[k] && !zero_rhs) {
+                const float2 gg = a.w2[io + p + n1 * (q0 + k)];
+                w[k] = solved ? ff_add(gg, dv[k]) : gg;
+            }
+            wh[k] = w[k].x;
+            wl[k] = w[k].y;
+        }
+        // (every CTA has finished reading its planes: the last reduction
+        // ended with a cluster barrier, and the stores below only replace
+        // values at owned or halo positions of the same planes)
+        cl.sync();
+        cl_store<R>(P, L.Pdn, L.Pup, L, Wd, p, lq0, valid, wh);
+        cl_store<R>(P2, L.P2dn, L.P2up, L, Wd, p, lq0, valid, wl);
+        cl.sync();
+        StripHalo<R> hh, hl;
+        hh.load(P, Wd, p, lq0);
+        hl.load(P2, Wd, p, lq0);
+        const float* Mh = a.Mh + (size_t)i * kPlanes * pl;
+        const float* Ml = a.Ml + (size_t)i * kPlanes * pl;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (!valid[k]) continue;
+            const int q = q0 + k, j = p + n1 * q;
+            const bool ww = p > 0, ee = p + 1 < n1, sd = q > 0;
+            const float uph = (k + 1 < R) ? wh[k + 1] : hh.xp, upl = (k + 1 < R) ? wl[k + 1] : hl.xp;
+            const float dnh = (k > 0) ? wh[k - 1] : hh.xm, dnl = (k > 0) ? wl[k - 1] : hl.xm;
+            float ms = 0.f, mc = 0.f;
+            ff_acc2(ms, mc, Mh[j], Ml[j], wh[k], wl[k]);
+            ff_acc2(ms, mc, Mh[pl + j], Ml[pl + j], hh.Rt[k + 1], hl.Rt[k + 1]);
+            ff_acc2(ms, mc, Mh[2 * pl + j], Ml[2 * pl + j], uph, upl);
+            ff_acc2(ms, mc, Mh[3 * pl + j], Ml[3 * pl + j], hh.Rt[k + 2], hl.Rt[k + 2]);
+            ff_acc2(ms, mc, Mh[4 * pl + j], Ml[4 * pl + j], hh.L[k + 2], hl.L[k + 2]);
+            if (ww) ff_acc2(ms, mc, Mh[pl + j - 1], Ml[pl + j - 1], hh.L[k + 1], hl.L[k + 1]);
+            if (sd) {
+                ff_acc2(ms, mc, Mh[2 * pl + j - n1], Ml[2 * pl + j - n1], dnh, dnl);
+                if (ww) ff_acc2(ms, mc, Mh[3 * pl + j - n1 - 1], Ml[3 * pl + j - n1 - 1], hh.L[k], hl.L[k]);
+                if (ee) ff_acc2(ms, mc, Mh[4 * pl + j - n1 + 1], Ml[4 * pl + j - n1 + 1], hh.Rt[k], hl.Rt[k]);
+            }
+            const float2 mwn = fast_two_sum_f(ms, mc);
+            const float2 c = ff_add(a.mw2[io + j], ff_mul(a.mq2[io + j], uo2));
+            const float2 sw = ff_sub(c, r[k]);
+            float2 gn = w[k], sg = sw;
+            if (level >= 2) {
+                gn = ff_add(ff_scale(ff_sub(w[k], h1[j]), 3.f), h2[j]);
+                sg = ff_add(ff_scale(ff_sub(sw, y1[j]), 3.f), y2[j]);
+            } else if (level == 1) {
+                gn = ff_sub(ff_scale(w[k], 2.f), h1[j]);
+                sg = ff_sub(ff_scale(sw, 2.f), y1[j]);
+            }
+            hc[j] = w[k];
+            yc[j] = sw;
+            a.mw2[io + j] = mwn;
+            a.res2[io + j] = ff_sub(mwn, sg);
+            a.w2[io + j] = gn;
+        }
+        if (i == 0 && g == 0 && tid == 0) a.ctl->pushed = 1;
+        cl.sync();  // no CTA leaves while a neighbour may still read its planes
+    }
+    if (g == 0 && tid == 0) {
+        a.inst_iters[i] = inner;
+        atomicAdd(&a.ctl->inner_iters, (unsigned long long)inner);
+        atomicAdd(&a.ctl->sweeps, (unsigned long long)sweeps);
+        atomicAdd(&a.ctl->micro_solves, 1ull);
+        atomicMax(&a.ctl->max_inner, inner);
+        if (flag) set_status(a.ctl, flag);
+    }
+}
+
+// Cluster variants: R = 5 (couplings in registers) and R = 9 (couplings in
+// shared memory), G CTAs per micro problem set at launch.
+template <int R, bool PIPE>
+__global__ void __launch_bounds__(512, 1) k_micro_cluster(MicroArgs a) {
+    cluster_body<R, false, PIPE>(a);
+}
+template <int R, bool PIPE>
+__global__ void __maxnreg__(kTallStripRegs) k_micro_cluster_tall(MicroArgs a) {
+    cluster_body<R, true, PIPE>(a);
+}
+
+// (R, G) of the cluster tilings, in tiling order
+static const int kClusterR[kNumClusterTilings] = {5, 5, 9, 9};
+static const int kClusterG[kNumClusterTilings] = {2, 4, 4, 8};
+
+bool cluster_fits(int c, int n1, int smem_optin) {
+    if (c < 0 || c >= kNumClusterTilings) return false;
+    const int R = kClusterR[c], G = kClusterG[c];
+    if (strip_rows(n1, R) < G) return false;  // every CTA needs a strip
+    const int maxT = R >= 9 ? 384 : 512;
+    return cluster_threads(n1, R, G) <= maxT &&
+           cluster_smem_bytes(n1, R, G, R >= 9, true) <= (size_t)smem_optin;
+}
+
+template <int R, bool SC, bool PIPE>
+static cudaError_t launch_cluster_kernel(const MicroArgs& a, int G, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)a.nM * G);
+    cfg.blockDim = dim3(cluster_threads(a.n1, R, G));
+    cfg.dynamicSmemBytes = cluster_smem_bytes(a.n1, R, G, SC, PIPE);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = G;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if constexpr (SC) return cudaLaunchKernelEx(&cfg, k_micro_cluster_tall<R, PIPE>, a);
+    else return cudaLaunchKernelEx(&cfg, k_micro_cluster<R, PIPE>, a);
+}
+
+cudaError_t launch_cluster_solve(const MicroArgs& a, int c, cudaStream_t s) {
+    if (c < 0 || c >= kNumClusterTilings) return cudaErrorInvalidValue;
+    const int R = kClusterR[c], G = kClusterG[c];
+    if (R == 5) return a.pipe ? launch_cluster_kernel<5, false, true>(a, G, s) : launch_cluster_kernel<5, false, false>(a, G, s);
+    return a.pipe ? launch_cluster_kernel<9, true, true>(a, G, s) : launch_cluster_kernel<9, true, false>(a, G, s);
+}
+
 bool strip_fits(int n1, int R, int smem_optin) {
     const bool sc = R >= 9;
     const int maxT = R == 3 ? 384 : (R == 5 ? 512 : 384);
@@ -1024,6 +1801,15 @@ bool strip_fits(int n1, int R, int smem_optin) {
 // outside any stream capture).
 cudaError_t configure_strip_kernels(int smem_optin) {
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const void* cfns[9] = {(const void*)k_micro_cluster<5, false>,      (const void*)k_micro_cluster<5, true>,
+                           (const void*)k_micro_cluster_tall<9, false>, (const void*)k_micro_cluster_tall<9, true>,
+                           (const void*)k_micro_warp<3, false>,         (const void*)k_micro_warp<3, true>,
+                           (const void*)k_micro_warp<5, false>,         (const void*)k_micro_warp<5, true>,
+                           (const void*)k_micro_batch};
+    for (int k = 0; k < 9; ++k) {
+        const cudaError_t e = cudaFuncSetAttribute(cfns[k], at, smem_optin);
+        if (e != cudaSuccess) return e;
+    }
     const void* fns[18] = {
         (const void*)k_micro_strip<3, false, false>, (const void*)k_micro_strip<5, false, false>,
         (const void*)k_micro_strip<7, false, false>, (const void*)k_micro_strip<3, true, false>,

@@ -121,13 +121,19 @@ def test_batch_errors():
     B.close()
 
 
-def test_uneven_32_instance_workload_sampled():
-    """The 32-instance uneven workload at full size, one graph per step,
-    autotuned: the two smallest instances against the oracle at the same
-    tolerances, and discrete mass balance on every instance."""
+@pytest.mark.parametrize("persistent", [False, True])
+def test_uneven_32_instance_workload_every_instance(persistent):
+    """The 32-instance uneven workload at full size (200M micro DoFs), mixed
+    precision by pipelined elimination, one graph per batch step -- one
+    branch per instance, or (persistent) one work-queue launch for all micro
+    solves: every instance against the oracle after 3 steps (the extrapolated
+    warm start runs), GPU at tolerance 1e-11, oracle at 1e-12; discrete mass
+    balance on every instance."""
     T = _T()
     ws = W.c4()
-    B = T.TwoScaleBatch([(w.Nm, w.NM, w.bc) for w in ws], precision=1, cg_tol=1e-8, coupling_tol=1e-10)
+    nsteps = 3
+    B = T.TwoScaleBatch([(w.Nm, w.NM, w.bc) for w in ws], precision=1, cg_tol=1e-11, macro_tol=1e-13,
+                        coupling=T.TSF_COUPLING_ELIMINATION, persistent=persistent)
     m0 = []
     for k, w in enumerate(ws):
         B[k].set_physics(w.D, w.kappa, w.Du)
@@ -135,21 +141,73 @@ def test_uneven_32_instance_workload_sampled():
         B[k].set_state(w.u0, None)
     for k, w in enumerate(ws):
         m0.append(_mass(B[k], w))
-    B.step(ws[0].dt, ws[0].nsteps)
+    B.step(ws[0].dt, nsteps)
     B.synchronize()
     st = B.stats()
-    assert st["status"] == 0 and st["steps"] == ws[0].nsteps
+    assert st["status"] == 0 and st["steps"] == nsteps
     for k, w in enumerate(ws):
-        assert abs(_mass(B[k], w) - m0[k]) <= 1e-6 * abs(m0[k]), k  # solver tolerance 1e-8 per solve
-    order = sorted(range(len(ws)), key=lambda k: ws[k].nM * ws[k].nm)[:2]
-    for k in order:
-        w = ws[k]
+        assert abs(_mass(B[k], w) - m0[k]) <= 1e-9 * abs(m0[k]), k
+        if persistent:
+            assert B[k].stats()["tiling"] == 5
         R = oracle.Problem(w.Nm, w.NM, w.bc, w.family, w.params, D=w.D, kappa=w.kappa, Du=w.Du)
         R.set_state(w.u0, None)
-        R.step(w.dt, w.nsteps, cg_tol=1e-12, coupling_tol=1e-12, macro_tol=1e-13)
+        R.step(w.dt, nsteps, cg_tol=1e-12, coupling_tol=1e-12, macro_tol=1e-13)
         u, v = B[k].u(), B[k].v()
         assert np.linalg.norm(u - R.u) <= 1e-8 * np.linalg.norm(R.u), k
-        assert np.linalg.norm(v.ravel() - R.v.ravel()) <= 1e-6 * np.linalg.norm(R.v), k
+        assert np.linalg.norm(v.ravel() - R.v.ravel()) <= 1e-8 * np.linalg.norm(R.v), k
+    B.close()
+
+
+def test_persistent_batch_equals_single_contexts_bitwise():
+    """One persistent launch with a work queue solves the micro problems of all
+    instances, small ones several to a block on their own groups of warps: the
+    results equal those of single contexts stepping with the same column-strip
+    variant (tiling 5) bit for bit."""
+    T = _T()
+    specs = SPECS + [(16, 6, 2, 0.9, (1.0, 0.0, 0.1)), (33, 2, 1, 1.1, (1.0, 0.0, 1.0))]
+    opts = dict(TIGHT, coupling=T.TSF_COUPLING_ELIMINATION)
+    B = T.TwoScaleBatch([(s[0], s[1]) for s in specs], precision=1, persistent=True, **opts)
+    for k, s in enumerate(specs):
+        _configure(B[k], k, s)
+    B.step(0.01, 4)
+    B.synchronize()
+    assert B.stats()["status"] == 0
+    for k, s in enumerate(specs):
+        P = T.TwoScale(s[0], s[1], precision=1, tiling=5, **opts)
+        _configure(P, k, s)
+        P.step(0.01, 4)
+        assert np.array_equal(P.u(), B[k].u()), k
+        assert np.array_equal(P.v(), B[k].v()), k
+        P.close()
+    B.close()
+
+
+def test_persistent_batch_matches_oracle():
+    T = _T()
+    B = T.TwoScaleBatch([(s[0], s[1]) for s in SPECS], precision=1, coupling=T.TSF_COUPLING_ELIMINATION,
+                        persistent=True, cg_tol=1e-11, macro_tol=1e-13)
+    inputs = [_configure(B[k], k, s) for k, s in enumerate(SPECS)]
+    dt, n = 0.01, 4
+    B.step(dt, n)
+    B.synchronize()
+    for k, (s, (prm, u0, v0)) in enumerate(zip(SPECS, inputs)):
+        Nm, NM, fam, kappa, D = s
+        R = oracle.Problem(Nm, NM, 0, fam, prm, D=D, kappa=kappa)
+        R.set_state(u0, v0)
+        R.step(dt, n, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13)
+        assert np.linalg.norm(B[k].u() - R.u) <= 1e-8 * np.linalg.norm(R.u), k
+        assert np.linalg.norm(B[k].v().ravel() - R.v.ravel()) <= 1e-8 * np.linalg.norm(R.v), k
+    B.close()
+
+
+def test_persistent_batch_rejects_the_partitioned_coupling():
+    T = _T()
+    B = T.TwoScaleBatch([(3, 2), (4, 2)], precision=1, coupling=T.TSF_COUPLING_PARTITIONED, persistent=True)
+    for k in range(2):
+        _configure(B[k], k, SPECS[k])
+    with pytest.raises(T.TsfError) as ei:
+        B.step(0.01, 1)
+    assert ei.value.status == T.TSF_E_ARG
     B.close()
 
 
