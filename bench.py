@@ -51,10 +51,16 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # taken on.  A kernel change gets a new revision, so counters of an older
 # kernel no longer match and read as null.
 KERNEL_REV = "ff2"
-# Per-launch ncu counters of the micro-solve kernel (the same bench command,
-# captured after a plain run): DRAM bytes (read + write) and executed warp
-# instructions, keyed by (workload, precision, tiling, coupling, revision).
-MICRO_COUNTERS = {}
+# Per-launch ncu counters of the micro-solve kernel (`bench.py --steps 3
+# --warmup 1 --no-extras --tiling 4` under ncu after a plain run of it): DRAM
+# bytes (read + write) of a steady pipelined launch, and the executed warp
+# instructions as a fixed part plus a part per micro-problem CG iteration
+# (exactly linear over the captured launches), keyed by (workload, precision,
+# tiling, coupling, revision).
+MICRO_COUNTERS = {
+    ("c2", "mixed", 4, "elimination", "ff2"): {"dram_bytes": 1.0496e9, "warp_insts_fixed": 167.2e6,
+                                               "warp_insts_per_problem_iter": 2318.0},
+}
 # warp instructions one SM can issue per clock (four schedulers)
 ISSUE_PER_SM_CLK = 4
 def parse():
@@ -396,7 +402,7 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def micro_roofline(workload_key, precision, coupling, sp, nm, clocks):
+def micro_roofline(workload_key, precision, coupling, sp, nm, clocks, nsm=None):
     """Roofline entry of the micro-solve kernel from its CUDA-event launch time
     (plain launches, profiled by the library) and, where an ncu capture of the
     same kernel revision exists, its measured DRAM bytes and instructions.
@@ -427,15 +433,19 @@ def micro_roofline(workload_key, precision, coupling, sp, nm, clocks):
            "macro_kernel_share": sp["macro_kernel_ms"] / max(sp["macro_kernel_ms"] + sp["micro_kernel_ms"], 1e-30),
            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s"}
     if ctr:
-        import torch
-        nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        if nsm is None:
+            import torch
+            nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         mhz = clocks.get("sm_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
         ipeak = ISSUE_PER_SM_CLK * nsm * mhz * 1e6
-        ach = ctr["warp_insts"] / (micro_ms / 1e3)
+        insts = ctr["warp_insts_fixed"] + ctr["warp_insts_per_problem_iter"] * sp["inner_iters"] / max(
+            sp["micro_launches"], 1)
+        ach = insts / (micro_ms / 1e3)
         out["onchip"] = {"bound": "issue", "achieved": ach, "peak": ipeak, "unit": "warp-inst/s",
-                         "frac": ach / ipeak, "warp_insts_per_launch": ctr["warp_insts"],
+                         "frac": ach / ipeak, "warp_insts_per_launch": insts,
                          "note": f"{ISSUE_PER_SM_CLK} warp instructions per clock per SM at {mhz:.0f} MHz, "
-                                 f"{nsm} SMs; instructions from ncu (smsp__inst_executed.sum)"}
+                                 f"{nsm} SMs; instructions per launch from ncu (smsp__inst_executed.sum: fixed "
+                                 f"part + part per micro-problem CG iteration) at this run's iteration count"}
     return out
 
 

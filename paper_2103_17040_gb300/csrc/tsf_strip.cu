@@ -1801,12 +1801,13 @@ bool strip_fits(int n1, int R, int smem_optin) {
 // outside any stream capture).
 cudaError_t configure_strip_kernels(int smem_optin) {
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    const void* cfns[9] = {(const void*)k_micro_cluster<5, false>,      (const void*)k_micro_cluster<5, true>,
+    // (k_micro_batch, which also has static shared memory, gets its limit when
+    // a persistent batch step is captured)
+    const void* cfns[8] = {(const void*)k_micro_cluster<5, false>,      (const void*)k_micro_cluster<5, true>,
                            (const void*)k_micro_cluster_tall<9, false>, (const void*)k_micro_cluster_tall<9, true>,
                            (const void*)k_micro_warp<3, false>,         (const void*)k_micro_warp<3, true>,
-                           (const void*)k_micro_warp<5, false>,         (const void*)k_micro_warp<5, true>,
-                           (const void*)k_micro_batch};
-    for (int k = 0; k < 9; ++k) {
+                           (const void*)k_micro_warp<5, false>,         (const void*)k_micro_warp<5, true>};
+    for (int k = 0; k < 8; ++k) {
         const cudaError_t e = cudaFuncSetAttribute(cfns[k], at, smem_optin);
         if (e != cudaSuccess) return e;
     }

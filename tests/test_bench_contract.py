@@ -48,7 +48,8 @@ def test_profiling_case_keeps_the_micro_problems():
     # counters of the current kernel revision are ever used
     for (wl, prec, tiling, coupling, rev), ctr in bench.MICRO_COUNTERS.items():
         assert wl in ("c2", "c3") and prec == "mixed" and coupling in ("elimination", "partitioned")
-        assert 0 <= tiling < len(bench.KERNEL_NAMES) and ctr["dram_bytes"] > 1e8 and ctr["warp_insts"] > 1e6
+        assert 0 <= tiling < len(bench.KERNEL_NAMES) and ctr["dram_bytes"] > 1e8
+        assert ctr["warp_insts_fixed"] > 1e6 and ctr["warp_insts_per_problem_iter"] > 100
 
 
 def test_roofline_entry_without_counters_reports_null_traffic():
@@ -57,7 +58,14 @@ def test_roofline_entry_without_counters_reports_null_traffic():
     sys.path.insert(0, ROOT)
     import bench
     sp = {"micro_kernel_ms": 6.0, "micro_launches": 10, "dof_cg_iters": 10 * 4225 * 1089 * 25,
-          "refine_sweeps": 10 * 4225, "tiling": 4, "macro_kernel_ms": 1.0}
+          "refine_sweeps": 10 * 4225, "tiling": 4, "macro_kernel_ms": 1.0, "inner_iters": 10 * 4225 * 25}
     r = bench.micro_roofline(None, "mixed", "elimination", sp, 1089, {"sm_mhz": 2070.0})
     assert r["traffic"] is None and r["dram_frac"] is None and "onchip" not in r
+    old_rev = dict(sp)
+    r2 = bench.micro_roofline("c2", "mixed", "elimination", old_rev, 1089, {"sm_mhz": 2070.0}, nsm=152)
+    has = ("c2", "mixed", 4, "elimination", bench.KERNEL_REV) in bench.MICRO_COUNTERS
+    assert (r2["traffic"] is not None) == has and ("onchip" in r2) == has
+    if has:
+        on = r2["onchip"]
+        assert on["peak"] == 4 * 152 * 2070e6 and abs(on["frac"] - on["achieved"] / on["peak"]) < 1e-12
     assert r["frac"] == r["achieved"] / r["peak"] and r["frac_kind"].startswith("algorithmic")
