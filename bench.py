@@ -727,8 +727,11 @@ def run_c4(args):
     """32 independent two-scale problems of uneven sizes (macro 16..96 cells,
     micro 16..48 cells per side, 200M micro DoFs in all), mixed precision,
     each with its autotuned micro-solve variant; one batch step is one CUDA
-    graph launch with one branch per problem.  Beside the batch: the same
-    problems stepped one after another (one graph per problem and step)."""
+    graph launch with one branch per problem (the library's default batch
+    mode).  Beside it, over the same steps: the persistent batch mode (the
+    micro solves of all problems in one work-queue launch, eliminated
+    coupling only) and the same problems stepped one after another (one graph
+    per problem and step)."""
     import torch
     import paper_2103_17040_gb300 as T
     import workloads as W
@@ -747,9 +750,7 @@ def run_c4(args):
     dt = ws[0].dt
     K, Wm = args.steps, args.warmup
 
-    persistent = args.coupling == "elimination"
-
-    def build(persistent=persistent):
+    def build(persistent=False):
         B = T.TwoScaleBatch([(w.Nm, w.NM, w.bc) for w in ws], precision=T.TSF_MIXED, stream=stream,
                             cg_tol=ws[0].tol, coupling_tol=ws[0].coupling_tol, coupling=COUPLING[args.coupling],
                             persistent=persistent)
@@ -759,6 +760,16 @@ def run_c4(args):
             B[k].set_state(w.u0, None)
         return B
 
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
     B = build()
     B.step(dt, Wm)
     B.synchronize()
@@ -766,17 +777,11 @@ def run_c4(args):
     barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
     clk = Clocks(local)
     clk.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    B.step(dt, K)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms = timed(lambda: B.step(dt, K))
     barrier()
     clocks = clk.stop()
     B.synchronize()
-    ms = e0.elapsed_time(e1)
     st = B.stats()
     tilings = [B[k].stats()["tiling"] for k in range(len(ws))]
     if world > 1:
@@ -788,43 +793,40 @@ def run_c4(args):
     else:
         ms_max, dof_iters = ms, float(st["dof_cg_iters"])
 
-    # the graph with one branch per problem (each problem's own kernels and
-    # autotuned variant) over the same steps
-    branches = None
-    if persistent:
-        B3 = build(persistent=False)
+    # the persistent mode over the same steps (micro solves of every problem
+    # in one work-queue launch beside one macro branch per problem)
+    persistent = None
+    if args.coupling == "elimination":
+        B3 = build(persistent=True)
         B3.step(dt, Wm)
         B3.synchronize()
         B3.reset_stats()
-        e0.record(stream)
-        B3.step(dt, K)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        br_ms = e0.elapsed_time(e1)
-        branches = {"ms_per_step": br_ms / K, "dof_cg_iters_per_step": B3.stats()["dof_cg_iters"] / K,
-                    "tilings": [B3[k].stats()["tiling"] for k in range(len(ws))]}
+        pm = timed(lambda: B3.step(dt, K))
+        persistent = {"ms_per_step": pm / K, "dof_cg_iters_per_step": B3.stats()["dof_cg_iters"] / K,
+                      "tiling": 5, "gpu_launches": (4 * len(ws) + 1) * K}
         B3.close()
 
     # the same problems one after another, each its own graph per step: a
     # second, identical batch advanced through the same steps one problem at
     # a time (the solves get cheaper as the march settles, so both are timed
     # over the same step range)
-    B2 = build(persistent=False)
+    B2 = build()
     for _ in range(Wm):
         for k in range(len(ws)):
             B2[k].step(dt, 1)
     torch.cuda.synchronize()
     for k in range(len(ws)):
         B2[k].reset_stats()
-    e0.record(stream)
-    for _ in range(K):
-        for k in range(len(ws)):
-            B2[k].step(dt, 1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = e0.elapsed_time(e1)
+
+    def seq():
+        for _ in range(K):
+            for k in range(len(ws)):
+                B2[k].step(dt, 1)
+    seq_ms = timed(seq)
     seq_iters = sum(B2[k].stats()["dof_cg_iters"] for k in range(len(ws)))
     B2.close()
+    if persistent is not None:
+        persistent["speedup_vs_sequential"] = (seq_ms / K) / persistent["ms_per_step"]
     ks = K
 
     # per-kernel timing of the micro solves (plain launches, one problem at a time)
@@ -855,20 +857,17 @@ def run_c4(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"c4: {len(ws)} independent two-scale problems, macro 16..96 / micro 16..48 cells "
                                f"per side, {ndof} micro DoFs, dt={dt}, tol={ws[0].tol}, mixed, coupling by "
-                               f"{args.coupling}, one graph per batch step"
-                               + (", micro solves of all problems in one persistent work-queue launch"
-                                  if persistent else ""),
-                   "problems": len(ws), "micro_dofs": ndof, "persistent": persistent,
+                               f"{args.coupling}, one graph per batch step with one branch per problem",
+                   "problems": len(ws), "micro_dofs": ndof, "batch_mode": "branches",
                    "l2": "working set > L2, no flush"},
-        "branches": branches,
+        "persistent": persistent,
         "batch_steps_per_s": world * K / (ms_max / 1e3),
         "sequential_ms_per_step": seq_ms / ks, "batch_speedup_vs_sequential": (seq_ms / ks) / (ms / K),
         "sequential_dof_cg_iters_per_step": seq_iters / ks, "batch_dof_cg_iters_per_step": st["dof_cg_iters"] / K,
         "coupling_iters_per_problem_step": st["coupling_iters_total"] / (K * len(ws)),
         "tilings": tilings, "coupling": args.coupling,
-        "gpu_launches": ((4 * len(ws) + 1) * K if persistent else
-                         (5 * K * len(ws) if args.coupling == "elimination"
-                          else 2 * K * len(ws) + 2 * st["coupling_iters_total"])),
+        "gpu_launches": (5 * K * len(ws) if args.coupling == "elimination"
+                         else 2 * K * len(ws) + 2 * st["coupling_iters_total"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "micro solve (per-problem variant)", "launches_timed": launches,
                      "avg_launch_ms": micro_ms / max(launches, 1),

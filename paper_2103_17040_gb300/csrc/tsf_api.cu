@@ -1017,12 +1017,18 @@ static tsf_status autotune(tsf_ctx* ctx, double dt) {
     CU(cudaStreamSynchronize(ctx->stream));
     if (best_t < 0) return fail(ctx, TSF_E_ARG, "no micro-solve variant fits this mesh");
     // The variants are timed without the pipelined elimination's epilogue,
-    // whose serial per-thread work grows with the strip height: on 32x32
-    // micro cells the short strips R = 3 and R = 5 solve within 1 % of each
-    // other, but with the epilogue R = 3 takes 0.62 ms and R = 5 0.76 ms a
-    // launch.  Eliminating, the lowest short strip is taken when it fits.
-    if (eliminating(ctx) && (best_t == 5 || best_t == 6) && tiling_fits(4, prec, ctx->n1, ctx->smem_optin))
-        best_t = 4;
+    // whose per-thread work grows with the strip height.  Eliminating, the
+    // lowest short strip that fits is taken when a short strip won: with the
+    // epilogue, R = 5 solves 48x48 micro cells 10 % faster than R = 7, and
+    // R = 3 16x16 cells faster than R = 5 (on 32x32 cells R = 3 and R = 5
+    // are within a few per cent of each other).
+    if (eliminating(ctx) && best_t >= 4 && best_t <= 6) {
+        for (int t = 4; t < best_t; ++t)
+            if (tiling_fits(t, prec, ctx->n1, ctx->smem_optin)) {
+                best_t = t;
+                break;
+            }
+    }
     ctx->tiling = best_t;
     ctx->tiling_prec = prec;
     return TSF_OK;

@@ -372,8 +372,51 @@ __device__ __forceinline__ void strip_store(float* P, int Wd, int p, int q0, con
 // fixed and the same in every warp, so all threads get the same, reproducible
 // value.  buf (32 float2) must not be written again by the block before every
 // thread has passed one more __syncthreads.
+// Warp sums of two values with the values split across the half-warps: the
+// first exchange leaves x in the lower and y in the upper sixteen lanes, so
+// every further step moves one value instead of two.  Returns the total of x
+// in lanes 0-15 and of y in lanes 16-31 (the same bits in every lane of a
+// half: each butterfly step adds the same two operands on both sides).
+__device__ __forceinline__ float warp_sum2_split(float x, float y) {
+    const bool hi = (threadIdx.x & 16) != 0;
+    float v = hi ? y : x;
+    v += __shfl_xor_sync(0xffffffffu, hi ? x : y, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// (x, y) = the totals of a split sum, in every lane
+__device__ __forceinline__ void split_join(float v, float& x, float& y) {
+    const float o = __shfl_xor_sync(0xffffffffu, v, 16);
+    const bool hi = (threadIdx.x & 16) != 0;
+    x = hi ? o : v;
+    y = hi ? v : o;
+}
+// Sums of two values over nw <= 16 warps of 32 consecutive threads starting
+// at a warp boundary: split warp sums, the partials through buf (lane 0 of
+// each warp writes x, lane 16 y), the barrier `sync`, and a split sum of the
+// nw partials in every warp -- a fixed order, so every thread gets the same
+// bits.
+template <class SYNC>
+__device__ __forceinline__ void group_sum2_split(float& x, float& y, float2* buf, int warp, int nw, SYNC sync) {
+    const int lane = threadIdx.x & 31;
+    float v = warp_sum2_split(x, y);
+    float* b = reinterpret_cast<float*>(buf);
+    if ((lane & 15) == 0) b[2 * warp + (lane >> 4)] = v;
+    sync();
+    const int k = lane & 15;
+    v = k < nw ? b[2 * k + (lane >> 4)] : 0.f;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    split_join(v, x, y);
+}
+
 __device__ __forceinline__ void block_sum2(float& x, float& y, float2* buf) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (nw <= 16) {
+        group_sum2_split(x, y, buf, warp, nw, [] { __syncthreads(); });
+        return;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -449,13 +492,7 @@ struct WarpTeam {
     __device__ int slot() const { return threadIdx.x >> 5; }
     __device__ int problem() const { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
     __device__ void sync() const { __syncwarp(); }
-    __device__ void sum2(float& x, float& y, float2*) const {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_xor_sync(0xffffffffu, x, o);
-            y += __shfl_xor_sync(0xffffffffu, y, o);
-        }
-    }
+    __device__ void sum2(float& x, float& y, float2*) const { split_join(warp_sum2_split(x, y), x, y); }
     __device__ void sum2_max(float& x, float& y, float& m, float4*) const {
         sum2(x, y, nullptr);
         m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
@@ -472,23 +509,8 @@ struct GroupTeam {
     __device__ int slot() const { return slot_; }
     __device__ int problem() const { return prob; }
     __device__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nw * 32) : "memory"); }
-    __device__ void sum2(float& x, float& y, float2* buf) const {
-        const int lane = threadIdx.x & 31, warp = thread() >> 5;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_xor_sync(0xffffffffu, x, o);
-            y += __shfl_xor_sync(0xffffffffu, y, o);
-        }
-        if (lane == 0) buf[warp] = make_float2(x, y);
-        sync();
-        const float2 t = lane < nw ? buf[lane] : make_float2(0.f, 0.f);
-        x = t.x;
-        y = t.y;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_xor_sync(0xffffffffu, x, o);
-            y += __shfl_xor_sync(0xffffffffu, y, o);
-        }
+    __device__ void sum2(float& x, float& y, float2* buf) const {  // (nw <= 16)
+        group_sum2_split(x, y, buf, thread() >> 5, nw, [this] { sync(); });
     }
     __device__ void sum2_max(float& x, float& y, float& m, float4* buf) const {
         const int lane = threadIdx.x & 31, warp = thread() >> 5;

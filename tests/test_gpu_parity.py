@@ -60,6 +60,32 @@ def test_geometry_matches_oracle(family, Nm):
     assert np.max(np.abs(vol - vr)) < 1e-13
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_geometry_paths_mixed_in_one_launch(precision):
+    """The geometry kernel takes the reference-table path where a node's map
+    has zero bump amplitude (F constant) and the quadrature path elsewhere,
+    node by node in one launch.  Half of the nodes take each path here; the
+    operators are checked through a whole step against the oracle (any wrong
+    coupling shows in u, v and rho) and the geometry sums directly."""
+    NM, Nm = 5, 9
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_AFFINE_BUMP, nM, seed=41)
+    prm[::2, 4] = 0.0
+    P, R = _pair(Nm, NM, W.FAMILY_AFFINE_BUMP, prm, D=(0.9, 0.1, 0.6), kappa=1.3, precision=precision)
+    gam, vol = P.geometry()
+    gr, vr, _ = R.geometry()
+    assert np.max(np.abs(gam - gr)) < 1e-13 and np.max(np.abs(vol - vr)) < 1e-13
+    u0, v0 = W.random_state(nM, nm, seed=6)
+    P.set_state(u0, v0)
+    R.set_state(u0, v0)
+    P.step(0.01, 2)
+    P.synchronize()
+    R.step(0.01, 2, cg_tol=1e-13, coupling_tol=1e-13, macro_tol=1e-13)
+    tol = FP64_TOL if precision == 0 else MIXED_TOL
+    assert rel(P.u(), R.u) < tol and rel(P.v(), R.v) < tol
+    assert rel(P.rho(), oracle_rho(R)) < tol
+
+
 STEP_CASES = [
     # family, Nm, NM, bc, D, kappa, Du, nsteps
     (W.FAMILY_BUMP, 8, 4, 0, (1.0, 0.0, 1.0), 1.0, 1.0, 2),
