@@ -50,7 +50,7 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # Source revision of the column-strip kernels that the ncu counters below were
 # taken on.  A kernel change gets a new revision, so counters of an older
 # kernel no longer match and read as null.
-KERNEL_REV = "ff2"
+KERNEL_REV = "ff3"
 # Per-launch ncu counters of the micro-solve kernel (`bench.py --steps 3
 # --warmup 1 --no-extras --tiling 4` under ncu after a plain run of it): DRAM
 # bytes (read + write) of a steady pipelined launch, and the executed warp
@@ -280,9 +280,10 @@ def run_gb300(args):
     dof_rate, ms_max, dof_iters = whole_job_rate(float(st["dof_cg_iters"]), ms, world, "cuda")
     steps_per_s = world * K / (ms_max / 1e3)
     # partitioned: 2 prologues + (micro, macro) per coupling iteration; pipelined elimination: start,
-    # macro prologue, micro solve, macro solve, commit (+ k_elim_pre with the one-block-per-problem variants)
+    # macro prologue, micro solve, macro solve (+ k_elim_pre with the one-block-per-problem variants),
+    # and the commit of v in the last step of the call
     if args.coupling == "elimination":
-        launches = (5 if st["tiling"] >= 4 else 6) * K
+        launches = (4 if st["tiling"] >= 4 else 5) * K + 1
     else:
         launches = 2 * K + 2 * st["coupling_iters_total"]
 
@@ -615,10 +616,11 @@ def run_c5(args):
     with respect to the per-node deformation parameters, after the 50-step FP64
     march of the 64x64 macro / 32x32 micro bump workload with checkpoints every
     10 steps (discrete adjoint on the GPU).  Timed at the workload's
-    tolerances; then checked against central differences (h = 1e-6) of the GPU
-    forward march along seeded unit directions, both sides at tolerance 1e-14
-    with a fixed micro-solve variant, on the bump family and on the
-    shear+bump family (64x64 / 32x32, D = diag(1, 0.1))."""
+    tolerances; then checked against Richardson-extrapolated central
+    differences (h = 1e-2 and 5e-3) of the GPU forward march along seeded unit
+    directions, both sides at tolerance 1e-14 with a fixed micro-solve
+    variant, on the bump family and on the shear+bump family (64x64 / 32x32,
+    D = diag(1, 0.1))."""
     import torch
     import paper_2103_17040_gb300 as T
     import workloads as W
@@ -686,13 +688,17 @@ def run_c5(args):
         L.step(w.dt, w.nsteps)
         epsJ = abs(float(np.dot(mH, L.u())) - J0)
         L.close()
-        h = 1e-6
+        # Richardson-extrapolated central difference: D(h) and D(h/2) have
+        # the same h^2 truncation term, (4 D(h/2) - D(h)) / 3 cancels it
+        h = 1e-2
         rows = []
         t0 = time.perf_counter()
         for k in range(ndirs):
             e = W.rng(1000 + seed + k).standard_normal(prm.shape)
             e /= np.linalg.norm(e)
-            fd = (J_at(prm + h * e) - J_at(prm - h * e)) / (2 * h)
+            d1 = (J_at(prm + h * e) - J_at(prm - h * e)) / (2 * h)
+            d2 = (J_at(prm + 0.5 * h * e) - J_at(prm - 0.5 * h * e)) / h
+            fd = (4.0 * d2 - d1) / 3.0
             ad = float(np.sum(g0 * e))
             rows.append((ad, fd))
         t_fd = time.perf_counter() - t0
@@ -700,7 +706,9 @@ def run_c5(args):
         ad = np.array([r[0] for r in rows])
         fd = np.array([r[1] for r in rows])
         rel = np.abs(fd - ad) / np.abs(ad)
-        return {"family": fam, "directions": ndirs, "h": h, "J": J0, "grad_norm": float(np.linalg.norm(g0)),
+        return {"family": fam, "directions": ndirs, "h": h,
+                "method": "Richardson-extrapolated central difference (4 D(h/2) - D(h)) / 3, truncation O(h^4)",
+                "J": J0, "grad_norm": float(np.linalg.norm(g0)),
                 "median_abs_directional": float(np.median(np.abs(ad))),
                 "rel_err_max": float(rel.max()), "rel_err_median": float(np.median(rel)),
                 "abs_err_max": float(np.abs(fd - ad).max()),
@@ -730,8 +738,8 @@ def run_c4(args):
     graph launch with one branch per problem (the library's default batch
     mode).  Beside it, over the same steps: the persistent batch mode (the
     micro solves of all problems in one work-queue launch, eliminated
-    coupling only) and the same problems stepped one after another (one graph
-    per problem and step)."""
+    coupling only) and the same problems stepped one after another (each
+    problem through all the steps, its own step graph)."""
     import torch
     import paper_2103_17040_gb300 as T
     import workloads as W
@@ -803,25 +811,23 @@ def run_c4(args):
         B3.reset_stats()
         pm = timed(lambda: B3.step(dt, K))
         persistent = {"ms_per_step": pm / K, "dof_cg_iters_per_step": B3.stats()["dof_cg_iters"] / K,
-                      "tiling": 5, "gpu_launches": (4 * len(ws) + 1) * K}
+                      "tiling": 5, "gpu_launches": (3 * len(ws) + 1) * K + len(ws)}
         B3.close()
 
-    # the same problems one after another, each its own graph per step: a
-    # second, identical batch advanced through the same steps one problem at
-    # a time (the solves get cheaper as the march settles, so both are timed
-    # over the same step range)
+    # the same problems one after another: a second, identical batch whose
+    # problems are stepped through the same step range one problem at a time,
+    # each with its own step graph (the solves get cheaper as the march
+    # settles, so both are timed over the same steps)
     B2 = build()
-    for _ in range(Wm):
-        for k in range(len(ws)):
-            B2[k].step(dt, 1)
+    for k in range(len(ws)):
+        B2[k].step(dt, Wm)
     torch.cuda.synchronize()
     for k in range(len(ws)):
         B2[k].reset_stats()
 
     def seq():
-        for _ in range(K):
-            for k in range(len(ws)):
-                B2[k].step(dt, 1)
+        for k in range(len(ws)):
+            B2[k].step(dt, K)
     seq_ms = timed(seq)
     seq_iters = sum(B2[k].stats()["dof_cg_iters"] for k in range(len(ws)))
     B2.close()
@@ -866,10 +872,13 @@ def run_c4(args):
         "sequential_dof_cg_iters_per_step": seq_iters / ks, "batch_dof_cg_iters_per_step": st["dof_cg_iters"] / K,
         "coupling_iters_per_problem_step": st["coupling_iters_total"] / (K * len(ws)),
         "tilings": tilings, "coupling": args.coupling,
-        "gpu_launches": (5 * K * len(ws) if args.coupling == "elimination"
+        "gpu_launches": ((4 * K + 1) * len(ws) if args.coupling == "elimination"
                          else 2 * K * len(ws) + 2 * st["coupling_iters_total"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "micro solve (per-problem variant)", "launches_timed": launches,
+                     "frac_kind": "algorithmic-equivalent (streaming accounting; the CG state stays on chip)",
+                     "traffic": None, "dram_frac": None,
+                     "kernel": "micro solves (each problem's autotuned variant, plain launches one problem at a time)",
+                     "launches_timed": launches,
                      "avg_launch_ms": micro_ms / max(launches, 1),
                      "bytes_per_launch": bytes_total / max(launches, 1),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s"},

@@ -102,9 +102,12 @@ struct tsf_ctx {
     int tiling_prec = -1;        // precision it was chosen for
     float tune_ms[kNumTilings] = {0};
     bool use_dct = false;
-    // graph
+    // graph of one step; under the pipelined elimination a second one without
+    // the commit of v (steps whose v nobody reads: all but the last of a call)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph_nc = nullptr;
+    cudaGraphExec_t gexec_nc = nullptr;
     bool graph_valid = false;
     double graph_dt = -1.0;
     uint64_t graph_gen = 0;      // bumped whenever a captured step would go stale
@@ -148,8 +151,12 @@ static void invalidate_graph(tsf_ctx* ctx) {
     ctx->graph_gen++;
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->gexec_nc) cudaGraphExecDestroy(ctx->gexec_nc);
+    if (ctx->graph_nc) cudaGraphDestroy(ctx->graph_nc);
     ctx->gexec = nullptr;
     ctx->graph = nullptr;
+    ctx->gexec_nc = nullptr;
+    ctx->graph_nc = nullptr;
     ctx->graph_valid = false;
 }
 
@@ -859,7 +866,10 @@ static tsf_status enqueue_head(tsf_ctx* ctx, double dt) {
 //   -> join.
 // ev: optional events around the micro solve (ev[0], ev[1], side stream) and
 // the macro solve (ev[2], ev[3], this stream).
-static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
+// commit = false leaves v as it was: within a run of pipelined steps nothing
+// reads v (the micro solves work on w, the macro branch on the ring of w), so
+// only the last step of a call has to write it.
+static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev, bool commit = true) {
     const ElimArgs ea = elim_args(ctx, dt);
     CU(launch_elim_start(ea, ctx->stream));
     CU(cudaEventRecord(ctx->fork_ev, ctx->stream));
@@ -894,14 +904,14 @@ static tsf_status enqueue_steady(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
     CU(launch_macro_solve(mg, ctx->stream, ctx->prio_hi));
     if (ev) CU(cudaEventRecord(ev[3], ctx->stream));
     if (!fused) CU(cudaStreamWaitEvent(ctx->stream, ctx->pre_ev, 0));
-    CU(launch_elim_commit(ea, ctx->stream));
+    if (commit) CU(launch_elim_commit(ea, ctx->stream));
     CU(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
     return TSF_OK;
 }
 
 // the step of the elimination mode in use
-static tsf_status enqueue_elim(tsf_ctx* ctx, double dt, cudaEvent_t* ev) {
-    return pipelined(ctx) ? enqueue_steady(ctx, dt, ev) : enqueue_elimination_step(ctx, dt, ev);
+static tsf_status enqueue_elim(tsf_ctx* ctx, double dt, cudaEvent_t* ev, bool commit = true) {
+    return pipelined(ctx) ? enqueue_steady(ctx, dt, ev, commit) : enqueue_elimination_step(ctx, dt, ev);
 }
 
 static double phi_tol(double cg_tol) { return std::max(1e-3 * cg_tol, 1e-13); }
@@ -1040,30 +1050,43 @@ static tsf_status autotune(tsf_ctx* ctx, double dt) {
 static tsf_status capture_failed(tsf_ctx* ctx, tsf_status st, cudaError_t e, const char* what) {
     ctx->graph = nullptr;
     ctx->gexec = nullptr;
+    ctx->graph_nc = nullptr;
+    ctx->gexec_nc = nullptr;
     ctx->graph_valid = false;
     cudaGetLastError();
     if (st) return st;
     return fail(ctx, TSF_E_CUDA, "graph capture failed at %s: %s", what, cudaGetErrorString(e));
 }
 
-// Appends one step of ctx to graph G as an independent branch: the macro and
-// micro prologues, then a WHILE conditional node whose body is one coupling
-// iteration (micro solve, macro solve; the macro kernel clears the condition
-// when the coupling test passes).  On failure *what names the stage; the
-// caller abandons G.
-static cudaError_t capture_step_into(tsf_ctx* ctx, cudaGraph_t G, double dt, tsf_status* st, const char** what) {
+// Appends one step of ctx to graph G as a branch that starts after the nodes
+// dep[0..ndep) (none: a root branch): the macro and micro prologues, then a
+// WHILE conditional node whose body is one coupling iteration (micro solve,
+// macro solve; the macro kernel clears the condition when the coupling test
+// passes), or the eliminated step (without the commit of v when commit is
+// false and the steps are pipelined).  The branch's last nodes are appended to
+// *tails when given.  On failure *what names the stage; the caller abandons G.
+static cudaError_t capture_step_into(tsf_ctx* ctx, cudaGraph_t G, double dt, tsf_status* st, const char** what,
+                                     const cudaGraphNode_t* dep = nullptr, size_t ndep = 0,
+                                     std::vector<cudaGraphNode_t>* tails = nullptr, bool commit = true) {
     *st = TSF_OK;
     cudaError_t e;
     if (eliminating(ctx)) {  // the eliminated step: no coupling loop
         *what = "begin capture";
-        e = cudaStreamBeginCaptureToGraph(ctx->stream, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        e = cudaStreamBeginCaptureToGraph(ctx->stream, G, dep, nullptr, ndep, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        *st = enqueue_elim(ctx, dt, nullptr);
+        *st = enqueue_elim(ctx, dt, nullptr, commit);
+        if (!*st && tails) {
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t* last = nullptr;
+            size_t nlast = 0;
+            e = cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, nullptr, &last, nullptr, &nlast);
+            if (e == cudaSuccess) tails->insert(tails->end(), last, last + nlast);
+        }
         cudaGraph_t endg = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &endg);
         *what = "elimination step";
         if (*st) return cudaErrorUnknown;
-        return e2;
+        return e != cudaSuccess ? e : e2;
     }
     // (a conditional handle must belong to a conditional node of G)
     cudaGraphConditionalHandle cond;
@@ -1071,7 +1094,7 @@ static cudaError_t capture_step_into(tsf_ctx* ctx, cudaGraph_t G, double dt, tsf
     e = cudaGraphConditionalHandleCreate(&cond, G, 1, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) return e;
     *what = "begin capture";
-    e = cudaStreamBeginCaptureToGraph(ctx->stream, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    e = cudaStreamBeginCaptureToGraph(ctx->stream, G, dep, nullptr, ndep, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     *st = enqueue_prologue(ctx, dt, false);
     cudaStreamCaptureStatus cs;
@@ -1093,6 +1116,7 @@ static cudaError_t capture_step_into(tsf_ctx* ctx, cudaGraph_t G, double dt, tsf
         if (e == cudaSuccess) {
             body = cp.conditional.phGraph_out[0];
             e = cudaStreamUpdateCaptureDependencies(ctx->stream, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+            if (tails) tails->push_back(cnode);
         }
     }
     cudaGraph_t endg = nullptr;
@@ -1120,6 +1144,13 @@ static tsf_status capture_graph(tsf_ctx* ctx, double dt) {
     if (e != cudaSuccess) return capture_failed(ctx, st, e, what);
     e = cudaGraphInstantiate(&ctx->gexec, ctx->graph, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "instantiate");
+    if (pipelined(ctx)) {
+        CU(cudaGraphCreate(&ctx->graph_nc, 0));
+        e = capture_step_into(ctx, ctx->graph_nc, dt, &st, &what, nullptr, 0, nullptr, false);
+        if (e != cudaSuccess) return capture_failed(ctx, st, e, what);
+        e = cudaGraphInstantiate(&ctx->gexec_nc, ctx->graph_nc, cudaGraphInstantiateFlagUseNodePriority);
+        if (e != cudaSuccess) return capture_failed(ctx, TSF_OK, e, "instantiate");
+    }
     ctx->graph_valid = true;
     ctx->graph_dt = dt;
     return TSF_OK;
@@ -1221,7 +1252,8 @@ tsf_status tsf_step(tsf_ctx* ctx, double dt, int nsteps) {
             st = capture_graph(ctx, dt);
             if (st) return st;
         }
-        for (int s = 0; s < nsteps; ++s) CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
+        for (int s = 0; s < nsteps; ++s)
+            CU(cudaGraphLaunch(ctx->gexec_nc && s + 1 < nsteps ? ctx->gexec_nc : ctx->gexec, ctx->stream));
         return TSF_OK;
     }
     return run_plain_steps(ctx, dt, nsteps);
@@ -1546,8 +1578,10 @@ struct tsf_batch {
     int* d_counter = nullptr;
     size_t cap_args = 0, cap_items = 0;
     int nitems = 0;
-    cudaGraph_t graph = nullptr;
+    cudaGraph_t graph = nullptr;       // one batch step
     cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph_nc = nullptr;    // the same without the commits of v (all but a call's last step)
+    cudaGraphExec_t gexec_nc = nullptr;
     bool graph_valid = false;
     double graph_dt = -1.0;
     std::vector<uint64_t> gen;   // instance graph generations the graph was captured at
@@ -1569,9 +1603,13 @@ static void batch_drop_graph(tsf_batch* b, bool destroy) {
     if (destroy) {
         if (b->gexec) cudaGraphExecDestroy(b->gexec);
         if (b->graph) cudaGraphDestroy(b->graph);
+        if (b->gexec_nc) cudaGraphExecDestroy(b->gexec_nc);
+        if (b->graph_nc) cudaGraphDestroy(b->graph_nc);
     }
     b->gexec = nullptr;
     b->graph = nullptr;
+    b->gexec_nc = nullptr;
+    b->graph_nc = nullptr;
     b->graph_valid = false;
 }
 
@@ -1580,28 +1618,68 @@ static tsf_status inst_fail(tsf_batch* b, int i, tsf_status st) {
     return bfail(b, st, "instance %d: %s", i, b->inst[i]->err.c_str());
 }
 
-static tsf_status batch_capture(tsf_batch* b, double dt) {
-    batch_drop_graph(b, true);
-    cudaError_t e = cudaGraphCreate(&b->graph, 0);
+// One batch step as one graph.  Problems with the same micro mesh and
+// variant run as concurrent branches; these groups run one after another,
+// largest micro mesh first.  Blocks of different variants (registers, shared
+// memory, threads) pack an SM badly when they run together: on the 32-problem
+// uneven workload one phase per micro mesh was 5 % faster than all branches at
+// once.
+static tsf_status batch_capture_one(tsf_batch* b, double dt, bool commit, cudaGraph_t& G, cudaGraphExec_t& X) {
+    cudaError_t e = cudaGraphCreate(&G, 0);
     if (e != cudaSuccess) return bfail(b, TSF_E_CUDA, "cudaGraphCreate: %s", cudaGetErrorString(e));
-    for (size_t i = 0; i < b->inst.size(); ++i) {
-        tsf_status st;
-        const char* what;
-        e = capture_step_into(b->inst[i], b->graph, dt, &st, &what);
-        if (e != cudaSuccess) {
-            batch_drop_graph(b, false);  // abandoned, as for a single context
-            cudaGetLastError();
-            if (st) return inst_fail(b, (int)i, st);
-            return bfail(b, TSF_E_CUDA, "instance %d: graph capture failed at %s: %s", (int)i, what,
-                         cudaGetErrorString(e));
+    const int n = (int)b->inst.size();
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const tsf_ctx *cx = b->inst[x], *cy = b->inst[y];
+        return cx->n1 != cy->n1 ? cx->n1 > cy->n1 : cx->tiling < cy->tiling;
+    });
+    cudaGraphNode_t join = nullptr;  // end of the previous group
+    std::vector<cudaGraphNode_t> tails;
+    for (int a = 0; a < n;) {
+        int z = a;
+        while (z < n && b->inst[order[z]]->n1 == b->inst[order[a]]->n1 &&
+               b->inst[order[z]]->tiling == b->inst[order[a]]->tiling)
+            ++z;
+        tails.clear();
+        for (int m = a; m < z; ++m) {
+            const int i = order[m];
+            tsf_status st;
+            const char* what;
+            e = capture_step_into(b->inst[i], G, dt, &st, &what, join ? &join : nullptr, join ? 1 : 0, &tails,
+                                  commit);
+            if (e != cudaSuccess) {
+                batch_drop_graph(b, false);  // abandoned, as for a single context
+                cudaGetLastError();
+                if (st) return inst_fail(b, i, st);
+                return bfail(b, TSF_E_CUDA, "instance %d: graph capture failed at %s: %s", i, what,
+                             cudaGetErrorString(e));
+            }
         }
+        if (z < n) {
+            e = cudaGraphAddEmptyNode(&join, G, tails.data(), tails.size());
+            if (e != cudaSuccess) {
+                batch_drop_graph(b, false);
+                cudaGetLastError();
+                return bfail(b, TSF_E_CUDA, "batch graph: %s", cudaGetErrorString(e));
+            }
+        }
+        a = z;
     }
-    e = cudaGraphInstantiate(&b->gexec, b->graph, cudaGraphInstantiateFlagUseNodePriority);
+    e = cudaGraphInstantiate(&X, G, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) {
         batch_drop_graph(b, false);
         cudaGetLastError();
         return bfail(b, TSF_E_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
     }
+    return TSF_OK;
+}
+
+static tsf_status batch_capture(tsf_batch* b, double dt) {
+    batch_drop_graph(b, true);
+    tsf_status st = batch_capture_one(b, dt, true, b->graph, b->gexec);
+    if (!st) st = batch_capture_one(b, dt, false, b->graph_nc, b->gexec_nc);
+    if (st) return st;
     b->gen.resize(b->inst.size());
     for (size_t i = 0; i < b->inst.size(); ++i) b->gen[i] = b->inst[i]->graph_gen;
     b->graph_valid = true;
@@ -1674,56 +1752,60 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c0->device);
 
-    e = cudaGraphCreate(&b->graph, 0);
-    if (e != cudaSuccess) return bfail(b, TSF_E_CUDA, "cudaGraphCreate: %s", cudaGetErrorString(e));
     cudaStream_t s = b->stream;
-    tsf_status st = TSF_OK;
-    auto body = [&]() -> cudaError_t {
-        cudaError_t er = cudaStreamBeginCaptureToGraph(s, b->graph, nullptr, nullptr, 0,
-                                                       cudaStreamCaptureModeThreadLocal);
-        if (er != cudaSuccess) return er;
-        for (int k = 0; k < n && er == cudaSuccess; ++k) er = launch_elim_start(elim_args(b->inst[k], dt), s);
-        if (er == cudaSuccess) er = cudaEventRecord(c0->fork_ev, s);
-        for (int k = 0; k < n && er == cudaSuccess; ++k) {
-            tsf_ctx* c = b->inst[k];
-            er = cudaStreamWaitEvent(c->side, c0->fork_ev, 0);
-            if (er != cudaSuccess) break;
-            if ((st = enqueue_macro_prologue(c, dt, true, c->side))) {
-                er = cudaErrorUnknown;  // (the capture is still ended below)
-                break;
-            }
-            cudaGraphConditionalHandle none{};
-            MacroArgs mg = macro_args(c, dt, false, none);
-            mg.gam = c->gam_eff;
-            mg.rho = c->rho_eff;
-            mg.coupling_tol = HUGE_VAL;
-            mg.coupling_maxit = 1;
-            er = launch_macro_solve(mg, c->side, c->prio_hi);
-            if (er == cudaSuccess) er = launch_elim_commit(elim_args(c, dt), c->side);
-            if (er == cudaSuccess) er = cudaEventRecord(c->join_ev, c->side);
-        }
-        if (er == cudaSuccess) er = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+    // capture one batch step into G (with or without the commits of v)
+    auto capture = [&](bool commit, cudaGraph_t& G, cudaGraphExec_t& X) -> tsf_status {
+        cudaError_t er = cudaGraphCreate(&G, 0);
+        if (er != cudaSuccess) return bfail(b, TSF_E_CUDA, "cudaGraphCreate: %s", cudaGetErrorString(er));
+        tsf_status st = TSF_OK;
+        er = cudaStreamBeginCaptureToGraph(s, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (er == cudaSuccess) {
-            BatchSolveArgs ba{b->d_args, b->d_items, b->nitems, b->d_counter};
-            er = launch_batch_solve(ba, smem, nsm, s);
+            for (int k = 0; k < n && er == cudaSuccess; ++k) er = launch_elim_start(elim_args(b->inst[k], dt), s);
+            if (er == cudaSuccess) er = cudaEventRecord(c0->fork_ev, s);
+            for (int k = 0; k < n && er == cudaSuccess; ++k) {
+                tsf_ctx* c = b->inst[k];
+                er = cudaStreamWaitEvent(c->side, c0->fork_ev, 0);
+                if (er != cudaSuccess) break;
+                if ((st = enqueue_macro_prologue(c, dt, true, c->side))) {
+                    er = cudaErrorUnknown;  // (the capture is still ended below)
+                    break;
+                }
+                cudaGraphConditionalHandle none{};
+                MacroArgs mg = macro_args(c, dt, false, none);
+                mg.gam = c->gam_eff;
+                mg.rho = c->rho_eff;
+                mg.coupling_tol = HUGE_VAL;
+                mg.coupling_maxit = 1;
+                er = launch_macro_solve(mg, c->side, c->prio_hi);
+                if (er == cudaSuccess && commit) er = launch_elim_commit(elim_args(c, dt), c->side);
+                if (er == cudaSuccess) er = cudaEventRecord(c->join_ev, c->side);
+            }
+            if (er == cudaSuccess) er = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+            if (er == cudaSuccess) {
+                BatchSolveArgs ba{b->d_args, b->d_items, b->nitems, b->d_counter};
+                er = launch_batch_solve(ba, smem, nsm, s);
+            }
+            for (int k = 0; k < n && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->inst[k]->join_ev, 0);
+            cudaGraph_t endg = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(s, &endg);
+            if (er == cudaSuccess) er = e2;
         }
-        for (int k = 0; k < n && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->inst[k]->join_ev, 0);
-        cudaGraph_t endg = nullptr;
-        const cudaError_t e2 = cudaStreamEndCapture(s, &endg);
-        return er != cudaSuccess ? er : e2;
+        if (er != cudaSuccess || st) {
+            batch_drop_graph(b, false);
+            cudaGetLastError();
+            return st ? st : bfail(b, TSF_E_CUDA, "persistent batch capture: %s", cudaGetErrorString(er));
+        }
+        er = cudaGraphInstantiate(&X, G, cudaGraphInstantiateFlagUseNodePriority);
+        if (er != cudaSuccess) {
+            batch_drop_graph(b, false);
+            cudaGetLastError();
+            return bfail(b, TSF_E_CUDA, "persistent batch instantiate: %s", cudaGetErrorString(er));
+        }
+        return TSF_OK;
     };
-    e = body();
-    if (e != cudaSuccess || st) {
-        batch_drop_graph(b, false);
-        cudaGetLastError();
-        return st ? st : bfail(b, TSF_E_CUDA, "persistent batch capture: %s", cudaGetErrorString(e));
-    }
-    e = cudaGraphInstantiate(&b->gexec, b->graph, cudaGraphInstantiateFlagUseNodePriority);
-    if (e != cudaSuccess) {
-        batch_drop_graph(b, false);
-        cudaGetLastError();
-        return bfail(b, TSF_E_CUDA, "persistent batch instantiate: %s", cudaGetErrorString(e));
-    }
+    tsf_status st = capture(true, b->graph, b->gexec);
+    if (!st) st = capture(false, b->graph_nc, b->gexec_nc);
+    if (st) return st;
     b->gen.resize(n);
     for (int k = 0; k < n; ++k) b->gen[k] = b->inst[k]->graph_gen;
     b->graph_valid = true;
@@ -1841,7 +1923,7 @@ tsf_status tsf_batch_step(tsf_batch* b, double dt, int nsteps) {
         if (st) return st;
     }
     for (int s = 0; s < nsteps; ++s) {
-        cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+        cudaError_t e = cudaGraphLaunch(b->gexec_nc && s + 1 < nsteps ? b->gexec_nc : b->gexec, b->stream);
         if (e != cudaSuccess) return bfail(b, TSF_E_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
         b->steps++;
     }

@@ -252,6 +252,12 @@ __host__ __device__ inline size_t strip_smem_bytes(int n1, int R, bool sc, bool 
 // Staging is used where it still lets two blocks share an SM (228 KB of
 // shared memory per SM, 1 KB of it reserved per block).
 constexpr size_t kStageSmemLimit = 113 * 1024;
+// An FP32 inner solve stops at kInnerMargin2 (squared norms) of the residual
+// the outer tolerance asks for.  The rest of the gap covers the drift of the
+// CG's recursively updated residual from the true one (a few FP32 ulps of
+// the sweep's starting residual times the iteration count) and the rounding
+// of the float-float update, both far smaller on the workloads' tolerances.
+constexpr float kInnerMargin2 = 0.81f;
 static bool strip_stages(int n1, int R, bool pipe) {
     return R < 9 && strip_smem_bytes(n1, R, false, pipe, true) <= kStageSmemLimit;
 }
@@ -861,8 +867,9 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a, const TEAM& tm = 
                 flag = kNotConverged;
                 break;
             }
-            // FP32 correction to inner_tol relative, but no further than half
-            // of what the outer tolerance still needs.  The inner right-hand
+            // FP32 correction to inner_tol relative, but no further than 0.9
+            // of what the outer tolerance still needs (kInnerMargin2 = 0.9^2).
+            // The inner right-hand
             // side is the residual normalised by a power of two t (exact), so
             // the FP32 CG works on values of order one however far the
             // refinement has come; t and s are undone on the correction.
@@ -874,7 +881,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a, const TEAM& tm = 
                 y[k] = 0.f;
                 rhs[k] = sch[k] * ((PIPE ? r[k].x * s : r[k].x) * t);
             }
-            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, 0.25f * stop2 / rr);
+            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, kInnerMargin2 * stop2 / rr);
             if constexpr (SC)
                 inner += strip_cg<R, SmemCouplings, TEAM>(cs, valid, y, rhs, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 32, &flag, tm);
             else
@@ -1569,7 +1576,7 @@ __device__ __forceinline__ void cluster_body(const MicroArgs& a) {
                 y[k] = 0.f;
                 rhs[k] = sch[k] * ((PIPE ? r[k].x * s : r[k].x) * t);
             }
-            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, 0.25f * stop2 / rr);
+            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, kInnerMargin2 * stop2 / rr);
             if constexpr (SC)
                 inner += cluster_cg<R>(cs, valid, y, rhs, P, L, Wd, p, lq0, rel2, a.maxit - inner, redA, redB, &flag);
             else

@@ -14,7 +14,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests are skipped, not failed, on machines without a GPU when they
-    # are selected explicitly; the driver's CPU run deselects them with -m.
+    # are selected explicitly; a CPU-only run deselects them with -m "not gpu".
     try:
         import torch
         has_gpu = torch.cuda.is_available()

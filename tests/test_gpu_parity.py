@@ -203,6 +203,32 @@ def test_graph_and_plain_launches_agree_bitwise(coupling):
     assert out[0][2]["coupling_iters_total"] == out[1][2]["coupling_iters_total"]
 
 
+@pytest.mark.parametrize("tiling", [4, 1])
+def test_multi_step_calls_commit_the_state_once(tiling):
+    """Under the pipelined elimination a call of n graph steps commits v only
+    in its last step (nothing reads v in between).  n steps in one call, n
+    calls of one step and plain launches give the same bits for u, v and the
+    micro averages."""
+    NM, Nm = 4, 12
+    nM, nm = (NM + 1) ** 2, (Nm + 1) ** 2
+    prm = W.random_params(W.FAMILY_SHEAR_BUMP, nM, seed=13)
+    u0 = W.random_state(nM, nm, seed=14)[0]
+    T = _T()
+    out = []
+    for graph, calls in ((1, (6,)), (1, (1,) * 6), (1, (2, 1, 3)), (0, (6,))):
+        P = T.TwoScale(Nm, NM, precision=1, use_graph=graph, tiling=tiling, coupling=1)
+        P.set_deformation(W.FAMILY_SHEAR_BUMP, prm)
+        P.set_state(u0, None)
+        for n in calls:
+            P.step(0.005, n)
+        P.synchronize()
+        out.append((P.u(), P.v(), P.vbar()))
+        P.close()
+    for o in out[1:]:
+        for a, b in zip(o, out[0]):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_all_tilings_agree(precision):
     Nm, NM = 20, 3
