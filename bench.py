@@ -50,16 +50,16 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # Source revision of the column-strip kernels that the ncu counters below were
 # taken on.  A kernel change gets a new revision, so counters of an older
 # kernel no longer match and read as null.
-KERNEL_REV = "ff3"
-# Per-launch ncu counters of the micro-solve kernel (`bench.py --steps 3
-# --warmup 1 --no-extras --tiling 4` under ncu after a plain run of it): DRAM
-# bytes (read + write) of a steady pipelined launch, and the executed warp
-# instructions as a fixed part plus a part per micro-problem CG iteration
-# (exactly linear over the captured launches), keyed by (workload, precision,
-# tiling, coupling, revision).
+KERNEL_REV = "ff5"
+# Per-launch ncu counters of the micro-solve kernel (`bench.py --iteration-log
+# 5 --tiling 4` under ncu after a plain run of it): DRAM bytes (read + write)
+# of a steady pipelined launch, and the executed warp instructions as a fixed
+# part plus a part per micro-problem CG iteration (a least-squares line through
+# the four steady launches, which it fits to the instruction), keyed by
+# (workload, precision, tiling, coupling, revision).
 MICRO_COUNTERS = {
-    ("c2", "mixed", 4, "elimination", "ff2"): {"dram_bytes": 1.0496e9, "warp_insts_fixed": 167.2e6,
-                                               "warp_insts_per_problem_iter": 2318.0},
+    ("c2", "mixed", 4, "elimination", "ff4"): {"dram_bytes": 1.0492e9, "warp_insts_fixed": 166.8e6,
+                                               "warp_insts_per_problem_iter": 2222.0},
 }
 # warp instructions one SM can issue per clock (four schedulers)
 ISSUE_PER_SM_CLK = 4
@@ -87,6 +87,10 @@ def parse():
     ap.add_argument("--macro-cells", type=int, default=None,
                     help="macro cells per side of a smaller case for profiling (c3 and t1; default: the full size)")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, e2e, cpu baseline")
+    ap.add_argument("--iteration-log", type=int, default=0, metavar="N",
+                    help="profiling aid: take N single steps of the workload (one micro-solve launch each after "
+                         "the first, which also solves the pipeline's head) and print the inner CG iterations of "
+                         "each, to pair with ncu's per-launch counters")
     return ap.parse_args()
 
 
@@ -234,6 +238,30 @@ def whole_job_rate(units_per_rank, ms_per_rank, world, device="cpu"):
     ms_max = reduce_over_ranks(ms_per_rank, "max", world, device)
     total = reduce_over_ranks(units_per_rank, "sum", world, device)
     return total / (ms_max / 1e3), ms_max, total
+
+
+def run_iteration_log(args):
+    """One JSON line: the inner CG iterations (summed over the micro
+    problems) of each of N single steps, in launch order.  The micro-solve
+    launches of this run are: phi and psi (set-up), then per step one
+    pipelined solve (the first step also the head solve)."""
+    import torch
+    import paper_2103_17040_gb300 as T
+    torch.cuda.set_device(0)
+    T.load_library()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    w = workload(args.workload)
+    P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling], tiling=args.tiling)
+    rows, last = [], 0
+    for _ in range(args.iteration_log):
+        P.step(w.dt, 1)
+        P.synchronize()
+        st = P.stats()
+        rows.append({"micro_solves": st["micro_solves"], "inner_iters": st["inner_iters"] - last,
+                     "refine_sweeps": st["refine_sweeps"]})
+        last = st["inner_iters"]
+    print(json.dumps({"workload": args.workload, "tiling": P.stats()["tiling"], "steps": rows}))
 
 
 def run_gb300(args):
@@ -1083,7 +1111,9 @@ def run_t1(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.iteration_log:
+        run_iteration_log(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "t1":
         run_t1(args)

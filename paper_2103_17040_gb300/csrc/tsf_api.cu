@@ -1700,7 +1700,7 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
     std::vector<int> order(n);
     for (int k = 0; k < n; ++k) {
         tsf_ctx* c = b->inst[k];
-        args[k] = w_solve_args(c, dt);
+        args[k] = with_fp32_tols(w_solve_args(c, dt));
         order[k] = k;
     }
     // largest micro problems first (work per item grows with n1^2), then the

@@ -170,6 +170,8 @@ struct MicroArgs {
     double kappa;
     double tol;             // ||b - S v|| <= tol ||b|| (FP64-accurate residual)
     double inner_tol;       // mixed: relative tolerance of the FP32 inner solve
+    float tol2f, inner2f;   // tol^2 and inner_tol^2 in FP32, set by the launchers (with_fp32_tols):
+                            // an FP64 -> FP32 conversion in every thread costs the slow conversion pipe
     int maxit;              // cap on inner iterations per solve
     int max_sweeps;         // mixed: cap on refinement sweeps
     double* rho;            // [nM] out: r_i^T v_i
@@ -204,6 +206,14 @@ struct MicroArgs {
 };
 
 // Per (geometry, dt) set-up of the column-strip kernels' operator data.
+// The FP32 copies of the squared tolerances the column-strip kernels test
+// against (set on the host, once per launch).
+inline MicroArgs with_fp32_tols(MicroArgs a) {
+    a.tol2f = (float)(a.tol * a.tol);
+    a.inner2f = (float)(a.inner_tol * a.inner_tol);
+    return a;
+}
+
 struct StripSetupArgs {
     int n1, nm, nmp, nM;
     const double* S64;      // [nM][5][nmp]

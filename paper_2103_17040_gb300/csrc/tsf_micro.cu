@@ -415,11 +415,11 @@ cudaError_t launch_micro_solve(const MicroArgs& a, int precision, int tiling, cu
             case 2: return launch_smem<float, true, 4>(a, s);
             case 3: return launch_smem<float, true, 8>(a, s);
         }
-        if (tiling >= 4 && tiling < kTilingDirect) return launch_strip_solve(a, kStripR[tiling - 4], s);
+        if (tiling >= 4 && tiling < kTilingDirect) return launch_strip_solve(with_fp32_tols(a), kStripR[tiling - 4], s);
         if (tiling >= kFirstClusterTiling && tiling < kFirstWarpTiling)
-            return launch_cluster_solve(a, tiling - kFirstClusterTiling, s);
+            return launch_cluster_solve(with_fp32_tols(a), tiling - kFirstClusterTiling, s);
         if (tiling >= kFirstWarpTiling && tiling < kNumTilings)
-            return launch_warp_solve(a, tiling == kFirstWarpTiling ? 3 : 5, s);
+            return launch_warp_solve(with_fp32_tols(a), tiling == kFirstWarpTiling ? 3 : 5, s);
     }
     return cudaErrorInvalidValue;
 }

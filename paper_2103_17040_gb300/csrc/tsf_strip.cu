@@ -780,7 +780,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a, const TEAM& tm = 
         }
         rr = rs;
         zero_rhs = cs == 0.f;
-        stop2 = (float)(a.tol * a.tol) * cs;
+        stop2 = a.tol2f * cs;
         // residual values below 2^-149 / s are not represented in the pairs
         if (s > 0x1p+100f) {
             const float f = 0x1p-149f * s;
@@ -881,7 +881,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a, const TEAM& tm = 
                 y[k] = 0.f;
                 rhs[k] = sch[k] * ((PIPE ? r[k].x * s : r[k].x) * t);
             }
-            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, kInnerMargin2 * stop2 / rr);
+            const float rel2 = fmaxf(a.inner2f, kInnerMargin2 * stop2 / rr);
             if constexpr (SC)
                 inner += strip_cg<R, SmemCouplings, TEAM>(cs, valid, y, rhs, P, Wd, p, q0, rel2, a.maxit - inner, red, red + 32, &flag, tm);
             else
@@ -1486,7 +1486,7 @@ __device__ __forceinline__ void cluster_body(const MicroArgs& a) {
         }
         rr = rs;
         zero_rhs = cs == 0.f;
-        stop2 = (float)(a.tol * a.tol) * cs;
+        stop2 = a.tol2f * cs;
         if (s > 0x1p+100f) {
             const float f = 0x1p-149f * s;
             stop2 = fmaxf(stop2, 16.f * (float)a.nm * f * f);
@@ -1576,7 +1576,7 @@ __device__ __forceinline__ void cluster_body(const MicroArgs& a) {
                 y[k] = 0.f;
                 rhs[k] = sch[k] * ((PIPE ? r[k].x * s : r[k].x) * t);
             }
-            const float rel2 = fmaxf(a.inner_tol * a.inner_tol, kInnerMargin2 * stop2 / rr);
+            const float rel2 = fmaxf(a.inner2f, kInnerMargin2 * stop2 / rr);
             if constexpr (SC)
                 inner += cluster_cg<R>(cs, valid, y, rhs, P, L, Wd, p, lq0, rel2, a.maxit - inner, redA, redB, &flag);
             else
