@@ -51,15 +51,26 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # taken on.  A kernel change gets a new revision, so counters of an older
 # kernel no longer match and read as null.
 KERNEL_REV = "ff5"
-# Per-launch ncu counters of the micro-solve kernel (`bench.py --iteration-log
-# 5 --tiling 4` under ncu after a plain run of it): DRAM bytes (read + write)
-# of a steady pipelined launch, and the executed warp instructions as a fixed
-# part plus a part per micro-problem CG iteration (a least-squares line through
-# the four steady launches, which it fits to the instruction), keyed by
-# (workload, precision, tiling, coupling, revision).
+# Per-launch ncu counters of the micro-solve kernel, taken with `bench.py
+# --iteration-log 5 --tiling T` under ncu after a plain run of it: DRAM bytes
+# (read + write) of a steady pipelined launch, and the executed warp
+# instructions as a fixed part plus a part per micro-problem CG iteration (a
+# least-squares line through the four steady launches, which it fits to the
+# instruction), keyed by (workload, precision, tiling, coupling, revision).
+# The 128x128/64x64 workload holds 19 GB on the device, beyond what a capture
+# should hold, so its counters come from the same micro problems on 32x32
+# macro cells (`--workload c3 --macro-cells 32`, 1089 problems, 1.1 GB of
+# DRAM traffic a launch): every problem is solved by its own block from its
+# own data, so the DRAM bytes and the fixed instructions scale with the
+# number of problems (x 16641 / 1089) and the part per problem-iteration
+# does not change.
+C3_SCALE = 16641 / 1089
 MICRO_COUNTERS = {
-    ("c2", "mixed", 4, "elimination", "ff4"): {"dram_bytes": 1.0492e9, "warp_insts_fixed": 166.8e6,
+    ("c2", "mixed", 4, "elimination", "ff5"): {"dram_bytes": 1.0490e9, "warp_insts_fixed": 166.3e6,
                                                "warp_insts_per_problem_iter": 2222.0},
+    ("c3", "mixed", 9, "elimination", "ff5"): {"dram_bytes": 1.135e9 * C3_SCALE, "warp_insts_fixed": 152.7e6 * C3_SCALE,
+                                               "warp_insts_per_problem_iter": 7260.0,
+                                               "captured_on": "32x32 macro cells (1089 problems), scaled x 16641/1089"},
 }
 # warp instructions one SM can issue per clock (four schedulers)
 ISSUE_PER_SM_CLK = 4
@@ -251,7 +262,7 @@ def run_iteration_log(args):
     T.load_library()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    w = workload(args.workload)
+    w = workload(args.workload, macro_cells=args.macro_cells)
     P = make_problem(T, w, args.precision, stream, coupling=COUPLING[args.coupling], tiling=args.tiling)
     rows, last = [], 0
     for _ in range(args.iteration_log):
