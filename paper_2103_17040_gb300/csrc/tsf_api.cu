@@ -71,6 +71,7 @@ struct tsf_ctx {
     double *u = nullptr, *uk = nullptr, *cH = nullptr, *fu = nullptr, *ud = nullptr, *rho = nullptr,
            *out = nullptr;
     double *mx = nullptr, *mr = nullptr, *mz = nullptr, *mzo = nullptr, *mp = nullptr, *mq = nullptr;
+    int macro_ncta = 1;          // CTAs of the macro solve (1 or kMacroCluster)
     double *res = nullptr, *res2 = nullptr, *u_used = nullptr, *uu2 = nullptr, *bnorm = nullptr;
     // exact elimination: phi_i = S_i^-1 kappa r_i, beta_i = r_i^T phi_i,
     // gam_eff = |Gam| - beta, constant macro vectors 0 and 1
@@ -690,6 +691,7 @@ static MacroArgs macro_args(tsf_ctx* ctx, double dt, bool set_cond, cudaGraphCon
     a.set_cond = set_cond ? 1 : 0;
     a.cond = cond;
     a.ctl = ctx->ctl;
+    a.ncta = ctx->macro_ncta;
     return a;
 }
 
@@ -1165,6 +1167,20 @@ static tsf_status prepare_step(tsf_ctx* ctx, double dt) {
         invalidate_graph(ctx);
     }
     ctx->use_dct = macro_smem_bytes(ctx->N1, ctx->bc, 1) <= (size_t)ctx->smem_optin;
+    // The macro solve runs on one SM unless a cluster of kMacroCluster CTAs
+    // pays: when it is on the step's critical path (the partitioned loop, the
+    // unpipelined elimination, and pipelined steps whose micro solve is too
+    // short to hide it).  Beside a long pipelined micro solve one block is
+    // better: it takes one SM as soon as one frees, where a cluster would
+    // wait for kMacroCluster of them.
+    {
+        const bool hidden = pipelined(ctx) && (double)ctx->nM * ctx->nm > 2e6;
+        const int ncta = !hidden && macro_cluster_ok(ctx->N1, ctx->bc, ctx->use_dct) ? kMacroCluster : 1;
+        if (ncta != ctx->macro_ncta) {
+            ctx->macro_ncta = ncta;
+            invalidate_graph(ctx);
+        }
+    }
     bool any = false;
     for (int t = 0; t < kNumTilings; ++t) any = any || tiling_fits(t, ctx->opt.precision, ctx->n1, ctx->smem_optin);
     if (!any)

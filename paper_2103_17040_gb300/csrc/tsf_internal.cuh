@@ -280,7 +280,10 @@ struct MacroArgs {
     int set_cond;           // call cudaGraphSetConditional
     cudaGraphConditionalHandle cond;
     DevCtl* ctl;
+    int ncta;               // 1 (or 0): one thread block; kMacroCluster: one thread-block cluster
 };
+// CTAs of the cluster variant of the macro solve
+constexpr int kMacroCluster = 8;
 
 struct MacroPrologueArgs {
     int NM, N1, nM, bc, n1m;  // n1m: micro nodes per side (Robin edge length in nodes)
@@ -377,6 +380,7 @@ cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s);
 // the macro solve's SM while it runs concurrently with them.
 cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s, int priority = 0, size_t reserve_smem = 0);
 size_t macro_smem_bytes(int N1, int bc, int use_dct);
+bool macro_cluster_ok(int N1, int bc, int use_dct);
 cudaError_t launch_vbar(int nm, int nmp, int nM, const double* lm, const double* vol, const double* v,
                         double* vbar, cudaStream_t s);
 // flux_i = kappa (|Gam_i| u_i - rho_i) + r_i^T g_i and rho_i = r_i^T v_i (compensated); either output may be null

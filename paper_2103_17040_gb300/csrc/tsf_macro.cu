@@ -21,13 +21,22 @@
 // needs two or three iterations.  Meshes too large for the shared-memory
 // transforms fall back to Jacobi.
 //
-// The macro problem is tiny (4225 unknowns for a 64x64 mesh), so it runs in a
-// single thread block; its cost is latency, not bandwidth.
+// The macro problem is small (4225 unknowns for a 64x64 mesh), so it runs in
+// one thread block, or in one thread-block cluster of kMacroCluster CTAs
+// (k_macro_solve_cl).  Its cost is FP64 arithmetic at GB300's FP64 rate (about
+// 30 FP64 operations per node and CG iteration; one SM does 1.65 a clock) and
+// latency, not bandwidth.  The cluster variant spreads the node loops and the
+// dense transforms over its CTAs, with cluster barriers in place of block
+// barriers and the dot products gathered through distributed shared memory.
 #include "tsf_internal.cuh"
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 
 namespace tsf {
+
+namespace cg = cooperative_groups;
 
 __device__ __forceinline__ bool is_dir_node(int bc, int N, int p, int q) {
     return bc == 1 && (p == 0 || q == 0 || p == N || q == N);
@@ -67,39 +76,46 @@ __device__ __forceinline__ double macro_diag(const MacroArgs& a, const MacroCoef
     return cx * cy * fma(m.km, a.gam[k], m.A0);
 }
 
-// out = in * V (right) or V * in (left); np x np row-major, np even, 2x2
-// register blocks, V symmetric.
+// One 2x2 block (rows r0, r0 + 1; columns c0, c0 + 1) of in * V (right) or
+// V * in (left); np x np row-major, np even, V symmetric.
+__device__ __forceinline__ float4 mm_block(const float* __restrict__ in, const float* __restrict__ V, int np,
+                                          bool left, int r0, int c0) {
+    float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+    if (!left) {
+        const float* x0 = in + r0 * np;
+        const float* x1 = x0 + np;
+        for (int m = 0; m < np; ++m) {
+            const float2 v = *reinterpret_cast<const float2*>(V + m * np + c0);
+            const float u0 = x0[m], u1 = x1[m];
+            a00 = fmaf(u0, v.x, a00);
+            a01 = fmaf(u0, v.y, a01);
+            a10 = fmaf(u1, v.x, a10);
+            a11 = fmaf(u1, v.y, a11);
+        }
+    } else {
+        const float* v0 = V + r0 * np;
+        const float* v1 = v0 + np;
+        for (int m = 0; m < np; ++m) {
+            const float2 x = *reinterpret_cast<const float2*>(in + m * np + c0);
+            const float w0 = v0[m], w1 = v1[m];
+            a00 = fmaf(w0, x.x, a00);
+            a01 = fmaf(w0, x.y, a01);
+            a10 = fmaf(w1, x.x, a10);
+            a11 = fmaf(w1, x.y, a11);
+        }
+    }
+    return make_float4(a00, a01, a10, a11);
+}
+
+// out = in * V (right) or V * in (left), all 2x2 blocks, by the threads of one block
 __device__ void mm_pass(const float* __restrict__ in, float* __restrict__ out, const float* __restrict__ V, int np,
                         bool left) {
     const int nb = np >> 1, nblk = nb * nb;
     for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
         const int r0 = (blk / nb) * 2, c0 = (blk % nb) * 2;
-        float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
-        if (!left) {
-            const float* x0 = in + r0 * np;
-            const float* x1 = x0 + np;
-            for (int m = 0; m < np; ++m) {
-                const float2 v = *reinterpret_cast<const float2*>(V + m * np + c0);
-                const float u0 = x0[m], u1 = x1[m];
-                a00 = fmaf(u0, v.x, a00);
-                a01 = fmaf(u0, v.y, a01);
-                a10 = fmaf(u1, v.x, a10);
-                a11 = fmaf(u1, v.y, a11);
-            }
-        } else {
-            const float* v0 = V + r0 * np;
-            const float* v1 = v0 + np;
-            for (int m = 0; m < np; ++m) {
-                const float2 x = *reinterpret_cast<const float2*>(in + m * np + c0);
-                const float w0 = v0[m], w1 = v1[m];
-                a00 = fmaf(w0, x.x, a00);
-                a01 = fmaf(w0, x.y, a01);
-                a10 = fmaf(w1, x.x, a10);
-                a11 = fmaf(w1, x.y, a11);
-            }
-        }
-        *reinterpret_cast<float2*>(out + r0 * np + c0) = make_float2(a00, a01);
-        *reinterpret_cast<float2*>(out + (r0 + 1) * np + c0) = make_float2(a10, a11);
+        const float4 t = mm_block(in, V, np, left, r0, c0);
+        *reinterpret_cast<float2*>(out + r0 * np + c0) = make_float2(t.x, t.y);
+        *reinterpret_cast<float2*>(out + (r0 + 1) * np + c0) = make_float2(t.z, t.w);
     }
 }
 
@@ -109,8 +125,62 @@ struct DctView {
     float gterm;        // kappa * gamma_bar * H^2
 };
 
-// z = P^{-1} r (fast diagonalisation, FP32 transforms).  All threads.
-__device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* r, double* z) {
+// Who runs the macro solve: one thread block ...
+struct MacroBlock {
+    __device__ int gtid() const { return threadIdx.x; }
+    __device__ int gsize() const { return blockDim.x; }
+    __device__ bool leader() const { return threadIdx.x == 0; }
+    __device__ void sync() const { __syncthreads(); }
+    template <class T, int NV>
+    __device__ void allreduce(T (&v)[NV], T* buf) const { block_allreduce<T, NV>(v, buf); }
+};
+// ... or the CTAs of one cluster: thread t = rank T + threadIdx.x takes the
+// nodes t, t + G T, ... of every loop (the same nodes in every loop); the
+// barrier is the cluster's (release / acquire at cluster scope, so global
+// writes before it are seen by every CTA after it).  A sum: the block sum in
+// each CTA, its total in slot 64 + i of the CTA's buffer, then every thread
+// adds the G totals in rank order (the same bits everywhere).
+struct MacroCluster {
+    int rank, G;
+    __device__ int gtid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+    __device__ int gsize() const { return G * (int)blockDim.x; }
+    __device__ bool leader() const { return rank == 0 && threadIdx.x == 0; }
+    __device__ void sync() const { cg::this_cluster().sync(); }
+    template <class T, int NV>
+    __device__ void allreduce(T (&v)[NV], T* buf) const {
+        static_assert(NV <= 2, "slots 64.. of the 96-entry buffer hold the CTA totals");
+        block_allreduce<T, NV>(v, buf);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) buf[64 + i] = v[i];
+        }
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            T s = T(0);
+            for (int r = 0; r < G; ++r) s += *cl.map_shared_rank(buf + 64 + i, r);
+            v[i] = s;
+        }
+    }
+};
+
+// The diagonal scaling of the transformed residual, X <- X / (Dn Dn lambda),
+// elements e0, e0 + es, ...
+__device__ __forceinline__ void dct_scale(const MacroArgs& a, const DctView& d, float* X, int e0, int es) {
+    const int n = d.n, np = d.np;
+    const float idt = (float)(1.0 / a.dt), Du = (float)a.Du;
+    for (int e = e0; e < n * n; e += es) {
+        const int l = e / n, k = e % n;
+        const float lam = d.lamM[k] * d.lamM[l] * idt + Du * (d.lamK[k] * d.lamM[l] + d.lamM[k] * d.lamK[l]) +
+                          d.gterm;
+        X[l * np + k] *= 1.0f / (d.Dn[l] * d.Dn[k] * lam);
+    }
+}
+
+// z = P^{-1} r (fast diagonalisation, FP32 transforms): V (V r V) V with the
+// scaling in between.  All threads of one block.
+__device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* r, double* z, const MacroBlock&) {
     const int n = d.n, np = d.np, n1 = a.N1;
     for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
         const int rr = e / np, cc = e % np;
@@ -123,13 +193,7 @@ __device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* 
     __syncthreads();
     mm_pass(d.X1, d.X0, d.V, np, true);
     __syncthreads();
-    const float idt = (float)(1.0 / a.dt), Du = (float)a.Du;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int l = e / n, k = e % n;
-        const float lam = d.lamM[k] * d.lamM[l] * idt + Du * (d.lamK[k] * d.lamM[l] + d.lamM[k] * d.lamK[l]) +
-                          d.gterm;
-        d.X0[l * np + k] *= 1.0f / (d.Dn[l] * d.Dn[k] * lam);
-    }
+    dct_scale(a, d, d.X0, threadIdx.x, blockDim.x);
     __syncthreads();
     mm_pass(d.X0, d.X1, d.V, np, false);
     __syncthreads();
@@ -143,9 +207,76 @@ __device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* 
     __syncthreads();
 }
 
+// The same by the CTAs of a cluster.  Every CTA keeps whole copies of the two
+// transform buffers in its shared memory; CTA g computes the 2x2 blocks of
+// block rows [g nb / G, (g + 1) nb / G) of each product from its own copies
+// and stores them into every CTA's copy through distributed shared memory
+// (the last product into its own copy only: each CTA then writes z for the
+// rows it computed).  One cluster barrier after each broadcast product.
+__device__ void mm_pass_cl(const float* __restrict__ in, float* __restrict__ out, const float* __restrict__ V, int np,
+                           bool left, const MacroCluster& tm, bool broadcast) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int nb = np >> 1;
+    const int b0 = tm.rank * nb / tm.G, b1 = (tm.rank + 1) * nb / tm.G;
+    const int nblk = (b1 - b0) * nb;
+    for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
+        const int r0 = (b0 + blk / nb) * 2, c0 = (blk % nb) * 2;
+        const float4 t = mm_block(in, V, np, left, r0, c0);
+        const float2 lo = make_float2(t.x, t.y), hi = make_float2(t.z, t.w);
+        if (broadcast) {
+            for (int g = 0; g < tm.G; ++g) {
+                float* o = cl.map_shared_rank(out, g);
+                *reinterpret_cast<float2*>(o + r0 * np + c0) = lo;
+                *reinterpret_cast<float2*>(o + (r0 + 1) * np + c0) = hi;
+            }
+        } else {
+            *reinterpret_cast<float2*>(out + r0 * np + c0) = lo;
+            *reinterpret_cast<float2*>(out + (r0 + 1) * np + c0) = hi;
+        }
+    }
+}
+
+__device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* r, double* z,
+                            const MacroCluster& tm) {
+    const int n = d.n, np = d.np, n1 = a.N1;
+    // every CTA reads the whole residual (global, complete after the last barrier)
+    for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+        const int rr = e / np, cc = e % np;
+        float val = 0.f;
+        if (rr < n && cc < n) val = (float)r[(cc + d.off) + n1 * (rr + d.off)];
+        d.X0[e] = val;
+    }
+    __syncthreads();
+    mm_pass_cl(d.X0, d.X1, d.V, np, false, tm, true);
+    tm.sync();
+    mm_pass_cl(d.X1, d.X0, d.V, np, true, tm, true);
+    tm.sync();
+    dct_scale(a, d, d.X0, threadIdx.x, blockDim.x);  // (every CTA its whole copy)
+    __syncthreads();
+    mm_pass_cl(d.X0, d.X1, d.V, np, false, tm, true);
+    tm.sync();
+    mm_pass_cl(d.X1, d.X0, d.V, np, true, tm, false);
+    __syncthreads();
+    const int nb = np >> 1;
+    const int rlo = 2 * (tm.rank * nb / tm.G), rhi = 2 * ((tm.rank + 1) * nb / tm.G);
+    for (int e = threadIdx.x; e < (rhi - rlo) * np; e += blockDim.x) {
+        const int rr = rlo + e / np, cc = e % np;
+        if (rr < n && cc < n) z[(cc + d.off) + n1 * (rr + d.off)] = (double)d.X0[rr * np + cc];
+    }
+    if (d.off) {  // Dirichlet: the boundary nodes outside the transform get z = 0
+        for (int k = tm.gtid(); k < a.nM; k += tm.gsize()) {
+            const int p = k % n1, q = k / n1;
+            if (p < d.off || q < d.off || p >= n + d.off || q >= n + d.off) z[k] = 0.0;
+        }
+    }
+    tm.sync();
+}
+
 // one block of this many threads runs the macro solve (launch and launch bounds)
 constexpr int kMacroThreads = 512;
 
+// reductions, basis V, eigenvalues and scaling, then the two transform
+// buffers (every CTA of the cluster variant holds all of them)
 size_t macro_smem_bytes(int N1, int bc, int use_dct) {
     size_t b = 4 * 96 * sizeof(double);
     if (use_dct) {
@@ -155,11 +286,14 @@ size_t macro_smem_bytes(int N1, int bc, int use_dct) {
     }
     return b;
 }
+static size_t macro_cl_smem_bytes(int N1, int bc, int use_dct) { return macro_smem_bytes(N1, bc, use_dct); }
 
-__global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// The solve, by one block or one cluster (TEAM).  X0, X1: the transform
+// buffers (shared memory of the block, or global scratch the cluster shares).
+template <class TEAM>
+__device__ void macro_solve_body(const MacroArgs& a, const TEAM& tm, unsigned char* smem, float* X0, float* X1) {
     double* red = reinterpret_cast<double*>(smem);  // 4 x 96
-    const int tid = threadIdx.x, T = blockDim.x;
+    const int tid = tm.gtid(), T = tm.gsize();
     const int nM = a.nM, n1 = a.N1, N = a.NM;
     int rb = 0;
     auto nextbuf = [&]() { double* b = red + 96 * rb; rb = (rb + 1) & 3; return b; };
@@ -172,14 +306,15 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
         d.off = a.bc ? 1 : 0;
         d.np = (d.n + 1) & ~1;
         float* f = reinterpret_cast<float*>(red + 4 * 96);
-        d.X0 = f;
-        d.X1 = f + d.np * d.np;
-        d.V = f + 2 * d.np * d.np;
-        d.lamM = f + 3 * d.np * d.np;
+        d.X0 = X0;
+        d.X1 = X1;
+        d.V = f;
+        d.lamM = f + d.np * d.np;
         d.lamK = d.lamM + d.np;
         d.Dn = d.lamK + d.np;
-        // basis: cos (Neumann) or sin (Dirichlet interior) of pi (a+off)(b+off)/N
-        for (int e = tid; e < d.np * d.np; e += T) {
+        // basis: cos (Neumann) or sin (Dirichlet interior) of pi (a+off)(b+off)/N,
+        // in every CTA's own shared memory
+        for (int e = threadIdx.x; e < d.np * d.np; e += blockDim.x) {
             const int r = e / d.np, c = e % d.np;
             float v = 0.f;
             if (r < d.n && c < d.n) {
@@ -189,7 +324,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
             d.V[e] = v;
         }
         const float H = (float)a.H;
-        for (int k = tid; k < d.n; k += T) {
+        for (int k = threadIdx.x; k < d.n; k += blockDim.x) {
             const float ck = cospif((float)(k + d.off) / (float)N);
             d.lamM[k] = (H / 6.f) * (4.f + 2.f * ck);
             d.lamK[k] = (2.f / H) * (1.f - ck);
@@ -208,7 +343,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
             }
         }
         float t[2] = {sg, cnt};
-        block_allreduce<float, 2>(t, reinterpret_cast<float*>(nextbuf()));
+        tm.allreduce(t, reinterpret_cast<float*>(nextbuf()));
         d.gterm = (float)a.kappa * (t[1] > 0.f ? t[0] / t[1] : 1.f) * (float)(a.H * a.H);
     }
     // right-hand side and initial guess; b kept in q until the residual is formed
@@ -220,7 +355,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
         a.q[k] = b;
         a.x[k] = a.uk[k];
     }
-    __syncthreads();
+    tm.sync();
     // stopping norms in FP64 like everything else here: FP32 sums of squares
     // would underflow for data scaled below about 1e-19 and stop the solve
     // before it starts
@@ -235,7 +370,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
     }
     {
         double t[2] = {bn2, rr};
-        block_allreduce<double, 2>(t, nextbuf());
+        tm.allreduce(t, nextbuf());
         bn2 = t[0];
         rr = t[1];
     }
@@ -245,10 +380,10 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
     if (rr > stop2 && bn2 > 0.0) {
         // z = P r, p = z
         if (a.use_dct) {
-            dct_precond(a, d, a.r, a.z);
+            dct_precond(a, d, a.r, a.z, tm);
         } else {
             for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, mc, k, k % n1, k / n1);
-            __syncthreads();
+            tm.sync();
         }
         double rz = 0.0;
         for (int k = tid; k < nM; k += T) {
@@ -257,7 +392,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
         }
         {
             double t[1] = {rz};
-            block_allreduce<double, 1>(t, nextbuf());
+            tm.allreduce(t, nextbuf());
             rz = t[0];
         }
         while (it < a.maxit) {
@@ -270,7 +405,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
             }
             {
                 double t[1] = {pq};
-                block_allreduce<double, 1>(t, nextbuf());
+                tm.allreduce(t, nextbuf());
                 pq = t[0];
             }
             ++it;
@@ -289,7 +424,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
             }
             {
                 double t[1] = {rr};
-                block_allreduce<double, 1>(t, nextbuf());
+                tm.allreduce(t, nextbuf());
                 rr = t[0];
             }
             if (!(rr == rr)) {
@@ -298,10 +433,10 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
             }
             if (rr <= stop2) break;
             if (a.use_dct) {
-                dct_precond(a, d, a.r, a.z);
+                dct_precond(a, d, a.r, a.z, tm);
             } else {
                 for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, mc, k, k % n1, k / n1);
-                __syncthreads();
+                tm.sync();
             }
             // flexible (Polak-Ribiere) beta: robust to the FP32 preconditioner
             double rzn = 0.0, rzo = 0.0;
@@ -311,14 +446,14 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
             }
             {
                 double t[2] = {rzn, rzo};
-                block_allreduce<double, 2>(t, nextbuf());
+                tm.allreduce(t, nextbuf());
                 rzn = t[0];
                 rzo = t[1];
             }
             const double beta = (rzn - rzo) / rz;
             rz = rzn;
             for (int k = tid; k < nM; k += T) a.p[k] = fma(beta, a.p[k], a.z[k]);
-            __syncthreads();
+            tm.sync();
         }
         if (!fail && rr > stop2) fail = true;
     }
@@ -334,7 +469,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
     }
     {
         double t[2] = {dn2, un2};
-        block_allreduce<double, 2>(t, nextbuf());
+        tm.allreduce(t, nextbuf());
         dn2 = t[0];
         un2 = t[1];
     }
@@ -347,7 +482,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
         a.uk[k] = xn;
         if (last) a.u[k] = xn;
     }
-    if (tid == 0) {
+    if (tm.leader()) {
         DevCtl* c = a.ctl;
         c->macro_iters += (unsigned long long)it;
         c->coupling_iter = iter;
@@ -367,7 +502,74 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    // the transform buffers after the reduction buffers, the basis and the eigenvalues
+    float* f = reinterpret_cast<float*>(smem + 4 * 96 * sizeof(double));
+    const int np = a.use_dct ? ((a.bc ? a.NM - 1 : a.NM + 1) + 1) & ~1 : 0;
+    float* X0 = f + np * np + 3 * np;
+    macro_solve_body(a, MacroBlock{}, smem, X0, X0 + np * np);
+}
+
+__global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve_cl(MacroArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    const MacroCluster tm{(int)cl.block_rank(), (int)cl.num_blocks()};
+    float* f = reinterpret_cast<float*>(smem + 4 * 96 * sizeof(double));
+    const int np = a.use_dct ? ((a.bc ? a.NM - 1 : a.NM + 1) + 1) & ~1 : 0;
+    float* X0 = f + np * np + 3 * np;
+    macro_solve_body(a, tm, smem, X0, X0 + np * np);
+    cl.sync();  // no CTA leaves while another may still read or write its shared memory
+}
+
+// Whether a cluster of kMacroCluster CTAs of the macro solve fits the device
+// (queried once per shared-memory size).
+bool macro_cluster_ok(int N1, int bc, int use_dct) {
+    static int cached_dev = -1;
+    static size_t cached_sm = 0;
+    static bool cached_ok = false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const size_t sm = macro_cl_smem_bytes(N1, bc, use_dct);
+    if (dev == cached_dev && sm == cached_sm) return cached_ok;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(kMacroCluster);
+    cfg.blockDim = dim3(kMacroThreads);
+    cfg.dynamicSmemBytes = sm;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kMacroCluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&n, k_macro_solve_cl, &cfg) == cudaSuccess && n > 0;
+    cudaGetLastError();
+    cached_dev = dev;
+    cached_sm = sm;
+    cached_ok = ok;
+    return ok;
+}
+
 cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s, int priority, size_t reserve_smem) {
+    if (a.ncta > 1) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(a.ncta);
+        cfg.blockDim = dim3(kMacroThreads);
+        cfg.dynamicSmemBytes = macro_cl_smem_bytes(a.N1, a.bc, a.use_dct);
+        cfg.stream = s;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = a.ncta;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributePriority;
+        at[1].val.priority = priority;
+        cfg.attrs = at;
+        cfg.numAttrs = priority ? 2 : 1;
+        return cudaLaunchKernelEx(&cfg, k_macro_solve_cl, a);
+    }
     const size_t sm = std::max(macro_smem_bytes(a.N1, a.bc, a.use_dct), reserve_smem);
     if (priority == 0) {
         k_macro_solve<<<1, kMacroThreads, sm, s>>>(a);
@@ -388,7 +590,10 @@ cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s, int priority,
 }
 
 cudaError_t configure_macro_kernels(int smem_optin) {
-    return cudaFuncSetAttribute(k_macro_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    cudaError_t e = cudaFuncSetAttribute(k_macro_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_macro_solve_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    return e;
 }
 
 // cH = M_H (u^n/dt + fu) - L G ; initial macro iterate with the Dirichlet values;
