@@ -126,20 +126,61 @@ struct DctView {
 };
 
 // Who runs the macro solve: one thread block ...
+// Sums for the macro solve.  Every thread holds NV partial sums (NV <= 2);
+// the warp butterflies them, lane 0 of each warp puts the warp sums into buf
+// (slots i 32 + warp), and after a block barrier warp 0 alone sums the warp
+// sums: the FP64 adds of a sum no longer grow with the warps times the warps.
+// The block total goes to slot 64 + i; the cluster variant gathers the G
+// block totals there through distributed shared memory (warp 0 again) and
+// leaves the cluster total in slot 80 + i.  Fixed order throughout, so every
+// thread of every CTA gets the same bits.  buf: one of the 96-entry buffers,
+// reused only after three more sums.
+template <class T, int NV>
+__device__ __forceinline__ void warp_sums_to_buf(T (&v)[NV], T* buf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) buf[i * 32 + warp] = v[i];
+    }
+}
+template <class T, int NV>
+__device__ __forceinline__ void warp0_block_total(T* buf) {  // (warp 0 only)
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T s = lane < nw ? buf[i * 32 + lane] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) buf[64 + i] = s;
+    }
+}
+
+// Who runs the macro solve: one thread block ...
 struct MacroBlock {
     __device__ int gtid() const { return threadIdx.x; }
     __device__ int gsize() const { return blockDim.x; }
     __device__ bool leader() const { return threadIdx.x == 0; }
     __device__ void sync() const { __syncthreads(); }
     template <class T, int NV>
-    __device__ void allreduce(T (&v)[NV], T* buf) const { block_allreduce<T, NV>(v, buf); }
+    __device__ void allreduce(T (&v)[NV], T* buf) const {
+        static_assert(NV <= 2, "slots 64.. of the 96-entry buffer hold the totals");
+        warp_sums_to_buf<T, NV>(v, buf);
+        __syncthreads();
+        if (threadIdx.x < 32) warp0_block_total<T, NV>(buf);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = buf[64 + i];
+    }
 };
 // ... or the CTAs of one cluster: thread t = rank T + threadIdx.x takes the
 // nodes t, t + G T, ... of every loop (the same nodes in every loop); the
 // barrier is the cluster's (release / acquire at cluster scope, so global
-// writes before it are seen by every CTA after it).  A sum: the block sum in
-// each CTA, its total in slot 64 + i of the CTA's buffer, then every thread
-// adds the G totals in rank order (the same bits everywhere).
+// writes before it are seen by every CTA after it).
 struct MacroCluster {
     int rank, G;
     __device__ int gtid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
@@ -148,20 +189,25 @@ struct MacroCluster {
     __device__ void sync() const { cg::this_cluster().sync(); }
     template <class T, int NV>
     __device__ void allreduce(T (&v)[NV], T* buf) const {
-        static_assert(NV <= 2, "slots 64.. of the 96-entry buffer hold the CTA totals");
-        block_allreduce<T, NV>(v, buf);
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int i = 0; i < NV; ++i) buf[64 + i] = v[i];
-        }
+        static_assert(NV <= 2, "slots 64.. and 80.. of the 96-entry buffer hold the totals");
+        warp_sums_to_buf<T, NV>(v, buf);
+        __syncthreads();
+        if (threadIdx.x < 32) warp0_block_total<T, NV>(buf);
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
 #pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            T s = T(0);
-            for (int r = 0; r < G; ++r) s += *cl.map_shared_rank(buf + 64 + i, r);
-            v[i] = s;
+            for (int i = 0; i < NV; ++i) {
+                T s = lane < G ? *cl.map_shared_rank(buf + 64 + i, lane) : T(0);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) buf[80 + i] = s;
+            }
         }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = buf[80 + i];
     }
 };
 
@@ -272,8 +318,11 @@ __device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* 
     tm.sync();
 }
 
-// one block of this many threads runs the macro solve (launch and launch bounds)
+// one block of this many threads runs the macro solve (launch and launch
+// bounds); each CTA of the cluster variant has kMacroClThreads (fewer threads
+// a CTA: fewer FP64 adds in every sum, and the node loops still fill them)
 constexpr int kMacroThreads = 512;
+constexpr int kMacroClThreads = 256;
 
 // reductions, basis V, eigenvalues and scaling, then the two transform
 // buffers (every CTA of the cluster variant holds all of them)
@@ -511,7 +560,7 @@ __global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve(MacroArgs a) {
     macro_solve_body(a, MacroBlock{}, smem, X0, X0 + np * np);
 }
 
-__global__ void __launch_bounds__(kMacroThreads, 1) k_macro_solve_cl(MacroArgs a) {
+__global__ void __launch_bounds__(kMacroClThreads, 1) k_macro_solve_cl(MacroArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cl = cg::this_cluster();
     const MacroCluster tm{(int)cl.block_rank(), (int)cl.num_blocks()};
@@ -534,7 +583,7 @@ bool macro_cluster_ok(int N1, int bc, int use_dct) {
     if (dev == cached_dev && sm == cached_sm) return cached_ok;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(kMacroCluster);
-    cfg.blockDim = dim3(kMacroThreads);
+    cfg.blockDim = dim3(kMacroClThreads);
     cfg.dynamicSmemBytes = sm;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -556,7 +605,7 @@ cudaError_t launch_macro_solve(const MacroArgs& a, cudaStream_t s, int priority,
     if (a.ncta > 1) {
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(a.ncta);
-        cfg.blockDim = dim3(kMacroThreads);
+        cfg.blockDim = dim3(kMacroClThreads);
         cfg.dynamicSmemBytes = macro_cl_smem_bytes(a.N1, a.bc, a.use_dct);
         cfg.stream = s;
         cudaLaunchAttribute at[2];
