@@ -225,8 +225,11 @@ __device__ __forceinline__ void dct_scale(const MacroArgs& a, const DctView& d, 
 }
 
 // z = P^{-1} r (fast diagonalisation, FP32 transforms): V (V r V) V with the
-// scaling in between.  All threads of one block.
-__device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* r, double* z, const MacroBlock&) {
+// scaling in between, and the sums dots = (r^T z, r^T zo) (the second only
+// with use_zo), whose reduction is the step's last barrier.  All threads of
+// one block.
+__device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* r, double* z, const MacroBlock& tm,
+                            bool use_zo, double (&dots)[2], double* buf) {
     const int n = d.n, np = d.np, n1 = a.N1;
     for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
         const int rr = e / np, cc = e % np;
@@ -245,12 +248,18 @@ __device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* 
     __syncthreads();
     mm_pass(d.X1, d.X0, d.V, np, true);
     __syncthreads();
+    double rz = 0.0, rzo = 0.0;
     for (int k = threadIdx.x; k < a.nM; k += blockDim.x) {
         const int p = k % n1, q = k / n1;
         const int cc = p - d.off, rr = q - d.off;
-        z[k] = (cc >= 0 && rr >= 0 && cc < n && rr < n) ? (double)d.X0[rr * np + cc] : 0.0;
+        const double zk = (cc >= 0 && rr >= 0 && cc < n && rr < n) ? (double)d.X0[rr * np + cc] : 0.0;
+        z[k] = zk;
+        rz = fma(r[k], zk, rz);
+        if (use_zo) rzo = fma(r[k], a.zo[k], rzo);
     }
-    __syncthreads();
+    dots[0] = rz;
+    dots[1] = rzo;
+    tm.allreduce(dots, buf);
 }
 
 // The same by the CTAs of a cluster.  Every CTA keeps whole copies of the two
@@ -283,7 +292,7 @@ __device__ void mm_pass_cl(const float* __restrict__ in, float* __restrict__ out
 }
 
 __device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* r, double* z,
-                            const MacroCluster& tm) {
+                            const MacroCluster& tm, bool use_zo, double (&dots)[2], double* buf) {
     const int n = d.n, np = d.np, n1 = a.N1;
     // every CTA reads the whole residual (global, complete after the last barrier)
     for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
@@ -305,9 +314,16 @@ __device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* 
     __syncthreads();
     const int nb = np >> 1;
     const int rlo = 2 * (tm.rank * nb / tm.G), rhi = 2 * ((tm.rank + 1) * nb / tm.G);
+    double rz = 0.0, rzo = 0.0;
     for (int e = threadIdx.x; e < (rhi - rlo) * np; e += blockDim.x) {
         const int rr = rlo + e / np, cc = e % np;
-        if (rr < n && cc < n) z[(cc + d.off) + n1 * (rr + d.off)] = (double)d.X0[rr * np + cc];
+        if (rr < n && cc < n) {
+            const int k = (cc + d.off) + n1 * (rr + d.off);
+            const double zk = (double)d.X0[rr * np + cc];
+            z[k] = zk;
+            rz = fma(r[k], zk, rz);
+            if (use_zo) rzo = fma(r[k], a.zo[k], rzo);
+        }
     }
     if (d.off) {  // Dirichlet: the boundary nodes outside the transform get z = 0
         for (int k = tm.gtid(); k < a.nM; k += tm.gsize()) {
@@ -315,7 +331,9 @@ __device__ void dct_precond(const MacroArgs& a, const DctView& d, const double* 
             if (p < d.off || q < d.off || p >= n + d.off || q >= n + d.off) z[k] = 0.0;
         }
     }
-    tm.sync();
+    dots[0] = rz;
+    dots[1] = rzo;
+    tm.allreduce(dots, buf);  // (its cluster barrier publishes z)
 }
 
 // one block of this many threads runs the macro solve (launch and launch
@@ -427,30 +445,41 @@ __device__ void macro_solve_body(const MacroArgs& a, const TEAM& tm, unsigned ch
     int it = 0;
     bool fail = false;
     if (rr > stop2 && bn2 > 0.0) {
-        // z = P r, p = z
-        if (a.use_dct) {
-            dct_precond(a, d, a.r, a.z, tm);
-        } else {
-            for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, mc, k, k % n1, k / n1);
-            tm.sync();
-        }
-        double rz = 0.0;
-        for (int k = tid; k < nM; k += T) {
-            a.p[k] = a.z[k];
-            rz = fma(a.r[k], a.z[k], rz);
-        }
-        {
-            double t[1] = {rz};
-            tm.allreduce(t, nextbuf());
-            rz = t[0];
-        }
+        // z = P r and the sums r^T z, r^T zo (zo: the z of the previous
+        // iteration) in one phase that ends with the sums' barrier
+        auto precond = [&](bool use_zo, double (&dots)[2]) {
+            if (a.use_dct) {
+                dct_precond(a, d, a.r, a.z, tm, use_zo, dots, nextbuf());
+            } else {
+                double rz = 0.0, rzo = 0.0;
+                for (int k = tid; k < nM; k += T) {
+                    const double zk = a.r[k] / macro_diag(a, mc, k, k % n1, k / n1);
+                    a.z[k] = zk;
+                    rz = fma(a.r[k], zk, rz);
+                    if (use_zo) rzo = fma(a.r[k], a.zo[k], rzo);
+                }
+                dots[0] = rz;
+                dots[1] = rzo;
+                tm.allreduce(dots, nextbuf());
+            }
+        };
+        double dots[2];
+        precond(false, dots);
+        double rz = dots[0], beta = 0.0;
         while (it < a.maxit) {
+            // p = z + beta p and q = A p = A z + beta q in one pass: A z needs
+            // only z, complete after the last sums' barrier, so no barrier
+            // separates the direction update from the operator
             double pq = 0.0;
             for (int k = tid; k < nM; k += T) {
                 const int p = k % n1, q = k / n1;
-                const double y = is_dir_node(a.bc, N, p, q) ? 0.0 : macro_apply(a, mc, a.p, k, p, q);
-                a.q[k] = y;
-                pq = fma(a.p[k], y, pq);
+                const double az = is_dir_node(a.bc, N, p, q) ? 0.0 : macro_apply(a, mc, a.z, k, p, q);
+                // (the first pass reads no p, q: they hold whatever the last solve left)
+                const double pk = it ? fma(beta, a.p[k], a.z[k]) : a.z[k];
+                const double qk = it ? fma(beta, a.q[k], az) : az;
+                a.p[k] = pk;
+                a.q[k] = qk;
+                pq = fma(pk, qk, pq);
             }
             {
                 double t[1] = {pq};
@@ -481,28 +510,10 @@ __device__ void macro_solve_body(const MacroArgs& a, const TEAM& tm, unsigned ch
                 break;
             }
             if (rr <= stop2) break;
-            if (a.use_dct) {
-                dct_precond(a, d, a.r, a.z, tm);
-            } else {
-                for (int k = tid; k < nM; k += T) a.z[k] = a.r[k] / macro_diag(a, mc, k, k % n1, k / n1);
-                tm.sync();
-            }
+            precond(true, dots);
             // flexible (Polak-Ribiere) beta: robust to the FP32 preconditioner
-            double rzn = 0.0, rzo = 0.0;
-            for (int k = tid; k < nM; k += T) {
-                rzn = fma(a.r[k], a.z[k], rzn);
-                rzo = fma(a.r[k], a.zo[k], rzo);
-            }
-            {
-                double t[2] = {rzn, rzo};
-                tm.allreduce(t, nextbuf());
-                rzn = t[0];
-                rzo = t[1];
-            }
-            const double beta = (rzn - rzo) / rz;
-            rz = rzn;
-            for (int k = tid; k < nM; k += T) a.p[k] = fma(beta, a.p[k], a.z[k]);
-            tm.sync();
+            beta = (dots[0] - dots[1]) / rz;
+            rz = dots[0];
         }
         if (!fail && rr > stop2) fail = true;
     }
