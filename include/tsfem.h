@@ -338,9 +338,9 @@ tsf_status tsf_batch_step(tsf_batch *b, double dt, int nsteps);
  * group of warps.  Beside it, every instance's macro solve runs on its own
  * branch of the graph.  Requires mixed precision and coupling by elimination
  * without volume or Robin sources for every instance (tsf_batch_step then
- * returns TSF_E_ARG otherwise), micro meshes of at most 49 cells per side,
- * and switches every instance to the column-strip variant of the batch kernel
- * (tiling 5).  Errors: TSF_E_ARG. */
+ * returns TSF_E_ARG otherwise), micro meshes of at most 49 cells per side and
+ * at most 64 instances, and switches every instance to the column-strip
+ * variant of the batch kernel (tiling 5).  Errors: TSF_E_ARG. */
 tsf_status tsf_batch_set_persistent(tsf_batch *b, int on);
 tsf_status tsf_batch_synchronize(tsf_batch *b);
 

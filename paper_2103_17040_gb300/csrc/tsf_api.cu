@@ -1589,10 +1589,9 @@ struct tsf_batch {
     // solves of all instances (device tables of their arguments and of the
     // work items, the queue head)
     int persistent = 0;
-    MicroArgs* d_args = nullptr;
     int4* d_items = nullptr;
     int* d_counter = nullptr;
-    size_t cap_args = 0, cap_items = 0;
+    size_t cap_items = 0;
     int nitems = 0;
     cudaGraph_t graph = nullptr;       // one batch step
     cudaGraphExec_t gexec = nullptr;
@@ -1712,6 +1711,8 @@ static tsf_status batch_capture(tsf_batch* b, double dt) {
 static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
     batch_drop_graph(b, true);
     const int n = (int)b->inst.size();
+    if (n > kBatchMaxProblems)
+        return bfail(b, TSF_E_ARG, "the persistent batch takes at most %d problems (%d given)", kBatchMaxProblems, n);
     std::vector<MicroArgs> args(n);
     std::vector<int> order(n);
     for (int k = 0; k < n; ++k) {
@@ -1733,27 +1734,27 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
         if (tw > kBatchWarps)
             return bfail(b, TSF_E_ARG, "instance %d: %d micro cells per side are too many for the persistent batch",
                          k, c->Nm);
-        const int cnt = std::min(kBatchWarps / tw, 15);
-        smem = std::max(smem, (size_t)cnt * batch_team_smem(c->n1));
-        for (int i = 0; i < c->nM; i += cnt) items.push_back(make_int4(k, i, std::min(cnt, c->nM - i), tw));
+        // an item: kBatchChunk problems per team of the block, which the
+        // teams take one at a time (the block waits for its slowest team
+        // once per item, not once per problem)
+        const int teams = std::min(kBatchWarps / tw, 15);
+        const int cnt = teams * kBatchChunk;
+        // the bulk-copy staging where the teams' shared memory still fits a block
+        const bool pref = teams * batch_team_smem_pref(c->n1, true) + kBatchStaticSmem <= (size_t)c->smem_optin;
+        smem = std::max(smem, (size_t)teams * batch_team_smem_pref(c->n1, pref));
+        for (int i = 0; i < c->nM; i += cnt)
+            items.push_back(make_int4(k, i, std::min(cnt, c->nM - i), tw | (pref ? 1 << 8 : 0)));
     }
     tsf_ctx* c0 = b->inst[0];
-    if (smem > (size_t)c0->smem_optin) return bfail(b, TSF_E_ARG, "persistent batch: shared memory %zu > %d", smem,
-                                                    c0->smem_optin);
+    if (smem + kBatchStaticSmem > (size_t)c0->smem_optin)
+        return bfail(b, TSF_E_ARG, "persistent batch: shared memory %zu > %d", smem, c0->smem_optin);
     cudaError_t e = cudaSuccess;
-    if (b->cap_args < (size_t)n) {
-        if (b->d_args) cudaFree(b->d_args);
-        e = cudaMalloc((void**)&b->d_args, (size_t)n * sizeof(MicroArgs));
-        b->cap_args = e == cudaSuccess ? (size_t)n : 0;
-    }
-    if (e == cudaSuccess && b->cap_items < items.size()) {
+    if (b->cap_items < items.size()) {
         if (b->d_items) cudaFree(b->d_items);
         e = cudaMalloc((void**)&b->d_items, items.size() * sizeof(int4));
         b->cap_items = e == cudaSuccess ? items.size() : 0;
     }
     if (e == cudaSuccess && !b->d_counter) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_args, args.data(), (size_t)n * sizeof(MicroArgs), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1798,7 +1799,11 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
             }
             if (er == cudaSuccess) er = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
             if (er == cudaSuccess) {
-                BatchSolveArgs ba{b->d_args, b->d_items, b->nitems, b->d_counter};
+                BatchSolveArgs ba{};
+                for (int k = 0; k < n; ++k) ba.args[k] = args[k];
+                ba.items = b->d_items;
+                ba.nitems = b->nitems;
+                ba.counter = b->d_counter;
                 er = launch_batch_solve(ba, smem, nsm, s);
             }
             for (int k = 0; k < n && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->inst[k]->join_ev, 0);
@@ -2000,7 +2005,6 @@ void tsf_batch_destroy(tsf_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graph(b, true);
-    if (b->d_args) cudaFree(b->d_args);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_counter) cudaFree(b->d_counter);
     for (tsf_ctx* c : b->inst) tsf_destroy(c);

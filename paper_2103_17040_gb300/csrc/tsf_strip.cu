@@ -488,6 +488,21 @@ struct BlockTeam {
     __device__ int slot() const { return 0; }  // team index within the block
     __device__ int problem() const { return blockIdx.x; }
     __device__ void sync() const { __syncthreads(); }
+    __device__ bool all(bool ok) const { return __syncthreads_and(ok) != 0; }  // (also a barrier)
+    __device__ void sum2(float& x, float& y, float2* buf) const { block_sum2(x, y, buf); }
+    __device__ void sum2_max(float& x, float& y, float& m, float4* buf) const { block_sum2_max(x, y, m, buf); }
+};
+// A whole block on a given micro problem (the persistent batch kernel, when
+// one team fills the block): BlockTeam's barriers and sums.
+struct BlockTeamAt {
+    static constexpr bool kWarp = false;
+    int prob;
+    __device__ int thread() const { return threadIdx.x; }
+    __device__ int size() const { return blockDim.x; }
+    __device__ int slot() const { return 0; }
+    __device__ int problem() const { return prob; }
+    __device__ void sync() const { __syncthreads(); }
+    __device__ bool all(bool ok) const { return __syncthreads_and(ok) != 0; }
     __device__ void sum2(float& x, float& y, float2* buf) const { block_sum2(x, y, buf); }
     __device__ void sum2_max(float& x, float& y, float& m, float4* buf) const { block_sum2_max(x, y, m, buf); }
 };
@@ -498,6 +513,7 @@ struct WarpTeam {
     __device__ int slot() const { return threadIdx.x >> 5; }
     __device__ int problem() const { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
     __device__ void sync() const { __syncwarp(); }
+    __device__ bool all(bool ok) const { return __all_sync(0xffffffffu, ok) != 0; }
     __device__ void sum2(float& x, float& y, float2*) const { split_join(warp_sum2_split(x, y), x, y); }
     __device__ void sum2_max(float& x, float& y, float& m, float4*) const {
         sum2(x, y, nullptr);
@@ -515,6 +531,14 @@ struct GroupTeam {
     __device__ int slot() const { return slot_; }
     __device__ int problem() const { return prob; }
     __device__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nw * 32) : "memory"); }
+    __device__ bool all(bool ok) const {  // (also a barrier of the group)
+        unsigned r;
+        asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(r)
+                     : "r"((unsigned)ok), "r"(bar), "r"(nw * 32)
+                     : "memory");
+        return r != 0;
+    }
     __device__ void sum2(float& x, float& y, float2* buf) const {  // (nw <= 16)
         group_sum2_split(x, y, buf, thread() >> 5, nw, [this] { sync(); });
     }
@@ -648,10 +672,16 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // Bounded wait for phase 0 of the barrier, by every thread of the block; the
 // result is the same in every thread.  Each try suspends the thread for a
 // short while, so the bound is of the order of a second.
-__device__ __forceinline__ bool mbar_wait_block(unsigned long long* bar) {
+template <class TEAM>
+__device__ __forceinline__ bool mbar_wait_team(unsigned long long* bar, const TEAM& tm) {
     bool ok = false;
     for (int k = 0; k < (1 << 22) && !ok; ++k) ok = mbar_try_wait(bar, 0);
-    return __syncthreads_and(ok) != 0;
+    return tm.all(ok);
+}
+// the barrier object's memory can be initialised again (a persistent team
+// stages the next problem through the same barrier)
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // 2^e as an FP32 number, e clamped to the normal range
@@ -704,7 +734,7 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a, const TEAM& tm = 
     bool staged = false, timed_out = false;
     if constexpr (PREF) {
         if (tid == 0) mbar_init(bar, 1);
-        __syncthreads();  // (block teams only)
+        tm.sync();
         if (tid == 0) {
             const unsigned lo = (unsigned)(2 * pl * sizeof(float4)), ds = (unsigned)(pl * sizeof(float4));
             const unsigned mp = PIPE ? (unsigned)(kPlanes * pl * sizeof(float)) : 0u;
@@ -721,9 +751,11 @@ __device__ __forceinline__ void strip_body(const MicroArgs& a, const TEAM& tm = 
     auto wait_staged = [&]() {
         if (PREF && !staged) {
             staged = true;
-            if (!mbar_wait_block(bar)) {
+            if (!mbar_wait_team(bar, tm)) {
                 timed_out = true;
-                mbar_wait_block(bar);
+                mbar_wait_team(bar, tm);
+            } else if (tid == 0) {
+                mbar_inval(bar);  // (every thread is past its wait: the vote is a barrier)
             }
         }
     };
@@ -1134,29 +1166,53 @@ cudaError_t launch_warp_solve(const MicroArgs& a, int R, cudaStream_t s) {
 // body (named barrier 1 + t), and wait for every team before the next item.
 // ---------------------------------------------------------------------------
 int batch_team_warps(int n1) { return (n1 * strip_rows(n1, kBatchR) + 31) / 32; }
-size_t batch_team_smem(int n1) { return strip_smem_bytes(n1, kBatchR, false, true, false); }
+// shared memory of one team, with (pref) or without the bulk-copy staging
+size_t batch_team_smem_pref(int n1, bool pref) { return strip_smem_bytes(n1, kBatchR, false, true, pref); }
+// teams of w warps in a block of kBatchWarps (named barriers 1..15)
+__host__ __device__ inline int batch_teams(int w) { return kBatchWarps / w < 15 ? kBatchWarps / w : 15; }
 
-__global__ void __launch_bounds__(32 * kBatchWarps, 1) k_micro_batch(BatchSolveArgs b) {
-    __shared__ MicroArgs s_args;
+__global__ void __launch_bounds__(32 * kBatchWarps, 1) k_micro_batch(const __grid_constant__ BatchSolveArgs b) {
     __shared__ int4 s_item;
+    __shared__ int s_next;        // next micro problem of the item (index within it)
+    __shared__ int s_take[16];    // the problem each team takes next
     for (;;) {
         if (threadIdx.x == 0) {
             const int it = atomicAdd(b.counter, 1);
             s_item = it < b.nitems ? b.items[it] : make_int4(-1, 0, 0, 0);
+            s_next = 0;
         }
         __syncthreads();
         const int4 item = s_item;
         if (item.x < 0) break;  // queue drained (the same in every thread)
-        const int* src = reinterpret_cast<const int*>(b.args + item.x);
-        for (int k = threadIdx.x; k < (int)(sizeof(MicroArgs) / sizeof(int)); k += blockDim.x)
-            reinterpret_cast<int*>(&s_args)[k] = src[k];
-        __syncthreads();
-        const int t = (threadIdx.x >> 5) / item.w;
-        if (t < item.z) {
-            GroupTeam tm{t * item.w * 32, item.w, 1 + t, t, item.y + t};
-            strip_body<kBatchR, false, true, false, GroupTeam>(s_args, tm);
+        const MicroArgs& a = b.args[item.x];
+        // teams of w warps; each takes the item's problems one at a time
+        // until none is left, so a team that finishes early does not wait.
+        // item.w: the warps per team, and bit 8 for the bulk-copy staging
+        const int w = item.w & 0xff;
+        const bool pref = (item.w >> 8) & 1;
+        const int t = (threadIdx.x >> 5) / w;
+        if (t < batch_teams(w)) {
+            const int lead = t * w * 32, nthr = w * 32;
+            for (;;) {
+                if ((int)threadIdx.x == lead) s_take[t] = atomicAdd(&s_next, 1);
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + t), "r"(nthr) : "memory");
+                const int j = s_take[t];
+                // (every thread of the team has read s_take[t] before the
+                // leader writes it again: the barrier below comes first)
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + t), "r"(nthr) : "memory");
+                if (j >= item.z) break;
+                if (w == kBatchWarps) {  // one team fills the block: block barriers, fewer registers
+                    strip_body<kBatchR, false, true, false, BlockTeamAt>(a, BlockTeamAt{item.y + j});
+                } else {
+                    GroupTeam tm{lead, w, 1 + t, t, item.y + j};
+                    if (pref)
+                        strip_body<kBatchR, false, true, true, GroupTeam>(a, tm);
+                    else
+                        strip_body<kBatchR, false, true, false, GroupTeam>(a, tm);
+                }
+            }
         }
-        __syncthreads();  // every team is done with the arguments and the item
+        __syncthreads();  // every team is done with the item
     }
 }
 
