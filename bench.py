@@ -50,7 +50,7 @@ KERNEL_NAMES = ["k_micro_solve<1>", "k_micro_solve<2>", "k_micro_solve<4>", "k_m
 # Source revision of the column-strip kernels that the ncu counters below were
 # taken on.  A kernel change gets a new revision, so counters of an older
 # kernel no longer match and read as null.
-KERNEL_REV = "ff5"
+KERNEL_REV = "ff6"
 # Per-launch ncu counters of the micro-solve kernel, taken with `bench.py
 # --iteration-log 5 --tiling T` under ncu after a plain run of it: DRAM bytes
 # (read + write) of a steady pipelined launch, and the executed warp
