@@ -66,9 +66,9 @@ KERNEL_REV = "ff6"
 # does not change.
 C3_SCALE = 16641 / 1089
 MICRO_COUNTERS = {
-    ("c2", "mixed", 4, "elimination", "ff5"): {"dram_bytes": 1.0490e9, "warp_insts_fixed": 166.3e6,
+    ("c2", "mixed", 4, "elimination", "ff6"): {"dram_bytes": 1.0491e9, "warp_insts_fixed": 166.45e6,
                                                "warp_insts_per_problem_iter": 2222.0},
-    ("c3", "mixed", 9, "elimination", "ff5"): {"dram_bytes": 1.135e9 * C3_SCALE, "warp_insts_fixed": 152.7e6 * C3_SCALE,
+    ("c3", "mixed", 9, "elimination", "ff6"): {"dram_bytes": 1.135e9 * C3_SCALE, "warp_insts_fixed": 152.7e6 * C3_SCALE,
                                                "warp_insts_per_problem_iter": 7260.0,
                                                "captured_on": "32x32 macro cells (1089 problems), scaled x 16641/1089"},
 }
