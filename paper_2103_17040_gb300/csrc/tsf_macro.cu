@@ -656,90 +656,75 @@ cudaError_t configure_macro_kernels(int smem_optin) {
     return e;
 }
 
-// Compensated sum of the products r_q x_q, q = lane, lane + 32, ... < n, over
-// one warp: each lane's terms with TwoSum and the exact product errors, then
-// a butterfly of (sum, error) pairs.  TwoSum gives the same (exact) error in
-// either operand order, so every lane ends with the same bits.
-template <class X>
-__device__ __forceinline__ double warp_dot_compensated(const double* r, X x, int n) {
-    const int lane = threadIdx.x & 31;
-    double s = 0.0, c = 0.0;
-    for (int q = lane; q < n; q += 32) {
-        const double xq = x(q), p = r[q] * xq;
-        double t, e;
-        two_sum(s, p, t, e);
-        s = t;
-        c += e + fma(r[q], xq, -p);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
-        double t, e;
-        two_sum(s, so, t, e);
-        s = t;
-        c = c + co + e;
-    }
-    return s + c;
-}
-
 // cH = M_H (u^n/dt + fu) - L G ; initial macro iterate with the Dirichlet values;
-// resets the per-step coupling counter.  One warp per macro node: the sums
-// over the node's Robin-edge nodes (G = r^T g, and r^T w of the pipelined
-// elimination) run across the warp's lanes.
-constexpr int kPrologueWarps = 8;
-__global__ void __launch_bounds__(32 * kPrologueWarps) k_macro_prologue(MacroPrologueArgs a) {
-    const int k = blockIdx.x * kPrologueWarps + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (k == 0 && lane == 0) {
+// resets the per-step coupling counter.  One thread per macro node.
+__global__ void k_macro_prologue(MacroPrologueArgs a) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) {
         a.ctl->coupling_iter = 0;
         a.ctl->cont = 1;
     }
-    if (k >= a.nM) return;  // (whole warps)
-    // G_k = int_Gamma g = r_k^T g_k
-    double G = 0.0;
-    if (a.g) {
-        const double* g = a.g + (size_t)k * a.n1m;
-        G = warp_dot_compensated(a.redge + (size_t)k * a.n1m, [&](int q) { return g[q]; }, a.n1m);
-    }
-    double rw = 0.0;
-    if (a.rho_eff && a.ring2) {
-        // r^T w of the w the last column-strip solve pushed (ring slot
-        // hist_step + 2 after k_elim_start): the Robin edge is the last
-        // column of micro problem k
-        const size_t slot = (size_t)((a.ctl->hist_step + 2) % 3) * a.nM * a.nmp + (size_t)k * a.nmp;
-        const float2* w = a.ring2 + slot + (a.n1m - 1);
-        const int n1m = a.n1m;
-        rw = warp_dot_compensated(a.redge + (size_t)k * a.n1m,
-                                  [&](int q) { const float2 wq = w[(size_t)n1m * q]; return (double)wq.x + (double)wq.y; },
-                                  a.n1m);
-    }
-    if (lane != 0) return;
+    if (k >= a.nM) return;
     const int N = a.NM, n1 = a.N1;
     const int p = k % n1, q = k / n1;
     const double idt = 1.0 / a.dt;
-    auto wv = [&](int l) { return a.fu ? fma(a.u[l], idt, a.fu[l]) : a.u[l] * idt; };
+    auto w = [&](int l) { return a.fu ? fma(a.u[l], idt, a.fu[l]) : a.u[l] * idt; };
     const double cx = (p == 0 || p == N) ? 1.0 : 2.0, cy = (q == 0 || q == N) ? 1.0 : 2.0;
     const bool e = p < N, wst = p > 0, nn = q < N, s = q > 0;
-    const double ew = (e ? wv(k + 1) : 0.0) + (wst ? wv(k - 1) : 0.0);
-    const double ns = (nn ? wv(k + n1) : 0.0) + (s ? wv(k - n1) : 0.0);
-    const double dg = ((e && nn) ? wv(k + n1 + 1) : 0.0) + ((wst && nn) ? wv(k + n1 - 1) : 0.0) +
-                      ((e && s) ? wv(k - n1 + 1) : 0.0) + ((wst && s) ? wv(k - n1 - 1) : 0.0);
+    const double ew = (e ? w(k + 1) : 0.0) + (wst ? w(k - 1) : 0.0);
+    const double ns = (nn ? w(k + n1) : 0.0) + (s ? w(k - n1) : 0.0);
+    const double dg = ((e && nn) ? w(k + n1 + 1) : 0.0) + ((wst && nn) ? w(k + n1 - 1) : 0.0) +
+                      ((e && s) ? w(k - n1 + 1) : 0.0) + ((wst && s) ? w(k - n1 - 1) : 0.0);
     const double H2 = a.H * a.H;
-    const double Mw = (H2 / 36.0) * (4.0 * cx * cy * wv(k) + 2.0 * cy * ew + 2.0 * cx * ns + dg);
+    const double Mw = (H2 / 36.0) * (4.0 * cx * cy * w(k) + 2.0 * cy * ew + 2.0 * cx * ns + dg);
     const double m = cx * cy * 0.25 * H2;
+    // G_k = int_Gamma g = r_k^T g_k (compensated sum over the Robin-edge nodes)
+    double G = 0.0;
+    if (a.g) {
+        const double* r = a.redge + (size_t)k * a.n1m;
+        const double* g = a.g + (size_t)k * a.n1m;
+        double c = 0.0;
+        for (int j = 0; j < a.n1m; ++j) {
+            double sum, err;
+            two_sum(G, r[j] * g[j], sum, err);
+            G = sum;
+            c += err + fma(r[j], g[j], -(r[j] * g[j]));
+        }
+        G += c;
+    }
     a.G[k] = G;
     a.cH[k] = Mw - m * G;
     double uk = a.u[k];
     if (is_dir_node(a.bc, N, p, q) && a.ud) uk = a.ud[k];
     a.uk[k] = uk;
     if (a.rho_eff) {
-        if (!a.ring2) rw = a.rho_w[k];
+        double rw;
+        if (a.ring2) {
+            // r^T w of the w the last column-strip solve pushed (ring slot
+            // hist_step + 2 after k_elim_start), compensated FP64 over the
+            // Robin-edge nodes of micro problem k
+            const size_t slot = (size_t)((a.ctl->hist_step + 2) % 3) * a.nM * a.nmp + (size_t)k * a.nmp;
+            const double* r = a.redge + (size_t)k * a.n1m;
+            double c = 0.0;
+            rw = 0.0;
+            for (int q = 0; q < a.n1m; ++q) {
+                const float2 wq = a.ring2[slot + (a.n1m - 1) + (size_t)a.n1m * q];
+                const double x = (double)wq.x + (double)wq.y;
+                double sum, err;
+                two_sum(rw, r[q] * x, sum, err);
+                rw = sum;
+                c += err + fma(r[q], x, -(r[q] * x));
+            }
+            rw += c;
+        } else {
+            rw = a.rho_w[k];
+        }
         a.rho_eff[k] = fma(a.u[k], a.gam_psi[k], rw);  // r^T (w + u psi)
     }
 }
 
 cudaError_t launch_macro_prologue(const MacroPrologueArgs& a, cudaStream_t s) {
-    k_macro_prologue<<<(a.nM + kPrologueWarps - 1) / kPrologueWarps, 32 * kPrologueWarps, 0, s>>>(a);
+    k_macro_prologue<<<(a.nM + 255) / 256, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
