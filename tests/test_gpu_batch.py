@@ -219,3 +219,25 @@ def _mass(P, w):
     u = P.u()
     # consistent macro mass: 1^T M_H u = m^T u
     return float(np.dot(m, u) + np.dot(m, vol * P.vbar()))
+
+
+def test_persistent_batch_limits():
+    """The persistent batch takes at most 64 problems (their arguments sit in
+    the kernel's parameter space) and micro meshes whose strips of 5 rows fit
+    one block (at most 49 cells per side); beyond either a step reports
+    TSF_E_ARG.  The branch mode steps the 65 problems."""
+    T = _T()
+    for specs in ([(2, 1)] * 65, [(50, 1)]):
+        B = T.TwoScaleBatch(specs, precision=1, coupling=T.TSF_COUPLING_ELIMINATION, persistent=True)
+        for k in range(len(specs)):
+            B[k].set_deformation(W.FAMILY_BUMP, np.full((4, 1), 0.05))
+            B[k].set_state(np.ones(4), None)
+        with pytest.raises(T.TsfError) as ei:
+            B.step(0.01, 1)
+        assert ei.value.status == T.TSF_E_ARG
+        if len(specs) == 65:
+            T.tsf_batch_set_persistent(B.b, 0)
+            B.step(0.01, 1)
+            B.synchronize()
+            assert all(np.all(np.isfinite(B[k].u())) for k in range(len(specs)))
+        B.close()
