@@ -776,7 +776,7 @@ def run_c4(args):
     each with its autotuned micro-solve variant; one batch step is one CUDA
     graph launch with one branch per problem (the library's default batch
     mode).  Beside it, over the same steps: the persistent batch mode (the
-    micro solves of all problems in one work-queue launch, eliminated
+    micro solves of all problems in work-queue launches, one per solve path, eliminated
     coupling only) and the same problems stepped one after another (each
     problem through all the steps, its own step graph)."""
     import torch
@@ -841,7 +841,7 @@ def run_c4(args):
         ms_max, dof_iters = ms, float(st["dof_cg_iters"])
 
     # the persistent mode over the same steps (micro solves of every problem
-    # in one work-queue launch beside one macro branch per problem)
+    # in work-queue launches beside one macro branch per problem)
     persistent = None
     if args.coupling == "elimination":
         B3 = build(persistent=True)
@@ -849,8 +849,10 @@ def run_c4(args):
         B3.synchronize()
         B3.reset_stats()
         pm = timed(lambda: B3.step(dt, K))
+        nq = B3.persistent_launches()  # micro-solve launches a step, one per solve path
         persistent = {"ms_per_step": pm / K, "dof_cg_iters_per_step": B3.stats()["dof_cg_iters"] / K,
-                      "tiling": 5, "gpu_launches": (3 * len(ws) + 1) * K + len(ws)}
+                      "tiling": 5, "micro_launches_per_step": nq,
+                      "gpu_launches": (3 * len(ws) + nq) * K + len(ws)}
         B3.close()
 
     # the same problems one after another: a second, identical batch whose

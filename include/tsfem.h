@@ -332,16 +332,23 @@ tsf_status tsf_batch_step(tsf_batch *b, double dt, int nsteps);
 
 /* Persistent batch steps (on = 1; default 0).  Each batch step is then ONE
  * CUDA graph launch whose micro solves, for every micro problem of every
- * instance, run in ONE persistent kernel launch (one block per SM) that takes
- * work items from a global atomic queue ordered largest micro mesh first; a
- * block runs several small micro problems side by side, each on its own
- * group of warps.  Beside it, every instance's macro solve runs on its own
- * branch of the graph.  Requires mixed precision and coupling by elimination
+ * instance, run in persistent kernel launches (at most one block per SM), one
+ * launch per solve path, side by side: micro meshes whose column strips fill
+ * a block of 16 warps, and smaller ones, several a block on their own groups
+ * of warps, with or without bulk-copy staging.  Each launch takes work items
+ * from its own global atomic queue ordered largest micro mesh first.  Beside
+ * them, every instance's macro solve runs on its own branch of the graph.  Requires mixed precision and coupling by elimination
  * without volume or Robin sources for every instance (tsf_batch_step then
  * returns TSF_E_ARG otherwise), micro meshes of at most 49 cells per side and
  * at most 64 instances, and switches every instance to the column-strip
  * variant of the batch kernel (tiling 5).  Errors: TSF_E_ARG. */
 tsf_status tsf_batch_set_persistent(tsf_batch *b, int on);
+
+/* *out = the persistent micro-solve launches of one batch step (1..3, one per
+ * solve path the instances need), as captured by the last persistent batch
+ * step; 0 if no persistent batch step has been captured.
+ * Errors: TSF_E_ARG (NULL pointer). */
+tsf_status tsf_batch_persistent_launches(const tsf_batch *b, int *out);
 tsf_status tsf_batch_synchronize(tsf_batch *b);
 
 /* Statistics summed over the instances (coupling_iters_last, max_inner_iters

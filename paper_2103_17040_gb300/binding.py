@@ -32,7 +32,8 @@ EXPORTS = ["tsf_default_options", "tsf_create", "tsf_set_options", "tsf_set_micr
            "tsf_synchronize", "tsf_get_macro", "tsf_get_micro_averages", "tsf_get_macro_async",
            "tsf_get_micro_averages_async", "tsf_get_micro_field", "tsf_get_flux", "tsf_get_rho", "tsf_get_geometry", "tsf_get_pushforward", "tsf_get_stats", "tsf_reset_stats", "tsf_workspace_bytes", "tsf_bind_workspace",
            "tsf_last_error", "tsf_destroy", "tsf_version", "tsf_macro_solve_noalloc", "tsf_adjoint_mean_u",
-           "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_set_persistent", "tsf_batch_synchronize",
+           "tsf_batch_create", "tsf_batch_instance", "tsf_batch_step", "tsf_batch_set_persistent",
+           "tsf_batch_persistent_launches", "tsf_batch_synchronize",
            "tsf_batch_get_stats", "tsf_batch_reset_stats", "tsf_batch_last_error", "tsf_batch_destroy"]
 # every symbol include/tsfem3.h declares (the stationary three-field system)
 EXPORTS3 = ["tsf3_create", "tsf3_set_meshes", "tsf3_set_physics", "tsf3_set_deformation", "tsf3_set_sources",
@@ -128,6 +129,7 @@ def load_library(path: str = LIB_PATH):
     L.tsf_batch_instance.argtypes = [vp, i, pp]
     L.tsf_batch_step.argtypes = [vp, d, i]
     L.tsf_batch_set_persistent.argtypes = [vp, i]
+    L.tsf_batch_persistent_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.tsf_batch_synchronize.argtypes = [vp]
     L.tsf_batch_get_stats.argtypes = [vp, ctypes.POINTER(tsf_stats)]
     L.tsf_batch_reset_stats.argtypes = [vp]
@@ -370,6 +372,12 @@ def tsf_batch_step(b, dt, nsteps=1):
 
 def tsf_batch_set_persistent(b, on):
     _bcheck(b, _lib.tsf_batch_set_persistent(b, int(on)))
+
+
+def tsf_batch_persistent_launches(b) -> int:
+    n = ctypes.c_int()
+    _bcheck(b, _lib.tsf_batch_persistent_launches(b, ctypes.byref(n)))
+    return n.value
 
 
 def tsf_batch_synchronize(b):
@@ -683,8 +691,8 @@ class TwoScaleBatch:
     ``specs``: sequence of ``(Nm, NM)`` or ``(Nm, NM, bc)``.  ``batch[i]`` is a
     :class:`TwoScale` view of instance i (configure and read it as usual; it
     is valid while the batch lives).  ``persistent=True``: the micro solves of
-    all instances run in one persistent launch per step, fed by a work queue
-    (tsf_batch_set_persistent).
+    all instances run in persistent launches (one per solve path) fed by work
+    queues (tsf_batch_set_persistent).
     """
 
     def __init__(self, specs, precision=TSF_MIXED, stream=None, workspace="torch", persistent=False, **opts):
@@ -712,6 +720,9 @@ class TwoScaleBatch:
 
     def stats(self):
         return tsf_batch_get_stats(self.b)
+
+    def persistent_launches(self):
+        return tsf_batch_persistent_launches(self.b)
 
     def reset_stats(self):
         tsf_batch_reset_stats(self.b)

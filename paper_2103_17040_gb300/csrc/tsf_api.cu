@@ -1585,14 +1585,20 @@ struct tsf_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int use_graph = 1;
-    // persistent mode: one launch of k_micro_batch per step for the micro
-    // solves of all instances (device tables of their arguments and of the
-    // work items, the queue head)
+    // persistent mode: per step one launch of k_micro_batch for each solve
+    // path the instances need, for the micro solves of all instances (the
+    // device table of the work items, the queue heads)
     int persistent = 0;
     int4* d_items = nullptr;
-    int* d_counter = nullptr;
+    int* d_counter = nullptr;          // [kBatchKinds] queue heads
     size_t cap_items = 0;
     int nitems = 0;
+    // the solve paths' launches run side by side: streams and events of the
+    // fork and the join (the first path runs on the batch's stream)
+    cudaStream_t kside[kBatchKinds - 1] = {};
+    cudaEvent_t kfork = nullptr;
+    cudaEvent_t kjoin[kBatchKinds - 1] = {};
+    int nlaunch = 0;                   // persistent micro-solve launches of the captured step
     cudaGraph_t graph = nullptr;       // one batch step
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph_nc = nullptr;    // the same without the commits of v (all but a call's last step)
@@ -1704,10 +1710,11 @@ static tsf_status batch_capture(tsf_batch* b, double dt) {
 
 // The persistent batch step (pipelined elimination of every instance):
 //   k_elim_start of every instance (the macro state the next w belongs to),
-//   then side by side: ONE persistent launch of k_micro_batch, which solves the
-//   next w of every micro problem of every instance from a work queue ordered
-//   largest micro problem first, and per instance its macro branch (macro
-//   prologue, macro solve, commit) on that instance's side stream.
+//   then side by side: the persistent launches of k_micro_batch, one per solve
+//   path, which solve the next w of every micro problem of every instance
+//   from work queues ordered largest micro problem first, and per instance
+//   its macro branch (macro prologue, macro solve, commit) on that
+//   instance's side stream.
 static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
     batch_drop_graph(b, true);
     const int n = (int)b->inst.size();
@@ -1726,48 +1733,78 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
         const tsf_ctx *cx = b->inst[x], *cy = b->inst[y];
         return cx->nm != cy->nm ? cx->nm > cy->nm : cx->nM > cy->nM;
     });
-    std::vector<int4> items;
-    size_t smem = 0;
-    for (int k : order) {
+    // the items of each solve path, in queue order
+    std::vector<int4> kitems[kBatchKinds];
+    size_t smem[kBatchKinds] = {0, 0, 0};
+    std::vector<int> kind(n), teams(n);
+    long left[kBatchKinds] = {0, 0, 0};  // micro problems of each path
+    for (int k = 0; k < n; ++k) {
         tsf_ctx* c = b->inst[k];
         const int tw = batch_team_warps(c->n1);
         if (tw > kBatchWarps)
             return bfail(b, TSF_E_ARG, "instance %d: %d micro cells per side are too many for the persistent batch",
                          k, c->Nm);
-        // an item: kBatchChunk problems per team of the block, which the
-        // teams take one at a time (the block waits for its slowest team
-        // once per item, not once per problem)
-        const int teams = std::min(kBatchWarps / tw, 15);
-        const int cnt = teams * kBatchChunk;
+        teams[k] = std::min(kBatchWarps / tw, 15);
         // the bulk-copy staging where the teams' shared memory still fits a block
-        const bool pref = teams * batch_team_smem_pref(c->n1, true) + kBatchStaticSmem <= (size_t)c->smem_optin;
-        smem = std::max(smem, (size_t)teams * batch_team_smem_pref(c->n1, pref));
-        for (int i = 0; i < c->nM; i += cnt)
-            items.push_back(make_int4(k, i, std::min(cnt, c->nM - i), tw | (pref ? 1 << 8 : 0)));
+        const bool pref = teams[k] * batch_team_smem_pref(c->n1, true) + kBatchStaticSmem <= (size_t)c->smem_optin;
+        kind[k] = tw == kBatchWarps ? kBatchBlock : (pref ? kBatchGroupStaged : kBatchGroup);
+        smem[kind[k]] = std::max(smem[kind[k]], (size_t)teams[k] * batch_team_smem_pref(c->n1, pref));
+        left[kind[k]] += c->nM;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->inst[0]->device);
+    for (int k : order) {
+        tsf_ctx* c = b->inst[k];
+        const int q = kind[k];
+        // a whole-block team takes one problem an item.  Smaller teams take
+        // kBatchChunk problems each an item (the block waits for its slowest
+        // team once per item, not once per problem), one each in the last
+        // wave of the path's queue, where a long item would leave SMs idle.
+        for (int i = 0; i < c->nM;) {
+            const int chunk = q == kBatchBlock || left[q] <= (long)nsm * teams[k] * kBatchChunk ? 1 : kBatchChunk;
+            const int cnt = std::min(teams[k] * chunk, c->nM - i);
+            kitems[q].push_back(make_int4(k, i, cnt, q == kBatchBlock ? kBatchWarps : batch_team_warps(c->n1)));
+            i += cnt;
+            left[q] -= cnt;
+        }
+    }
+    std::vector<int4> items;
+    int koff[kBatchKinds], kcnt[kBatchKinds];
+    for (int q = 0; q < kBatchKinds; ++q) {
+        koff[q] = (int)items.size();
+        kcnt[q] = (int)kitems[q].size();
+        items.insert(items.end(), kitems[q].begin(), kitems[q].end());
+        if (smem[q] + kBatchStaticSmem > (size_t)b->inst[0]->smem_optin)
+            return bfail(b, TSF_E_ARG, "persistent batch: shared memory %zu > %d", smem[q], b->inst[0]->smem_optin);
     }
     tsf_ctx* c0 = b->inst[0];
-    if (smem + kBatchStaticSmem > (size_t)c0->smem_optin)
-        return bfail(b, TSF_E_ARG, "persistent batch: shared memory %zu > %d", smem, c0->smem_optin);
     cudaError_t e = cudaSuccess;
     if (b->cap_items < items.size()) {
         if (b->d_items) cudaFree(b->d_items);
         e = cudaMalloc((void**)&b->d_items, items.size() * sizeof(int4));
         b->cap_items = e == cudaSuccess ? items.size() : 0;
     }
-    if (e == cudaSuccess && !b->d_counter) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
+    if (e == cudaSuccess && !b->d_counter) e = cudaMalloc((void**)&b->d_counter, kBatchKinds * sizeof(int));
+    for (int k = 0; k < kBatchKinds - 1 && e == cudaSuccess; ++k) {
+        if (!b->kside[k]) e = cudaStreamCreateWithFlags(&b->kside[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !b->kjoin[k]) e = cudaEventCreateWithFlags(&b->kjoin[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && !b->kfork) e = cudaEventCreateWithFlags(&b->kfork, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_micro_batch_entry(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
+    for (int q = 0; q < kBatchKinds && e == cudaSuccess; ++q)
+        if (kcnt[q])
+            e = cudaFuncSetAttribute(k_micro_batch_entry(q), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem[q]);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return bfail(b, e == cudaErrorMemoryAllocation ? TSF_E_OOM : TSF_E_CUDA, "persistent batch set-up: %s",
                      cudaGetErrorString(e));
     }
     b->nitems = (int)items.size();
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c0->device);
+    b->nlaunch = 0;
+    for (int q = 0; q < kBatchKinds; ++q) b->nlaunch += kcnt[q] > 0;
 
     cudaStream_t s = b->stream;
     // capture one batch step into G (with or without the commits of v)
@@ -1797,15 +1834,33 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
                 if (er == cudaSuccess && commit) er = launch_elim_commit(elim_args(c, dt), c->side);
                 if (er == cudaSuccess) er = cudaEventRecord(c->join_ev, c->side);
             }
-            if (er == cudaSuccess) er = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
-            if (er == cudaSuccess) {
+            if (er == cudaSuccess) er = cudaMemsetAsync(b->d_counter, 0, kBatchKinds * sizeof(int), s);
+            if (er == cudaSuccess) er = cudaEventRecord(b->kfork, s);
+            // the paths side by side, the whole-block path (the largest micro
+            // problems) first and at a higher priority: the blocks of the
+            // other paths take the SMs that its blocks leave
+            int side = 0;
+            for (int q = 0; q < kBatchKinds && er == cudaSuccess; ++q) {
+                if (!kcnt[q]) continue;
+                cudaStream_t qs = s;
+                if (q != kBatchBlock) {
+                    qs = b->kside[side];
+                    er = cudaStreamWaitEvent(qs, b->kfork, 0);
+                }
                 BatchSolveArgs ba{};
                 for (int k = 0; k < n; ++k) ba.args[k] = args[k];
-                ba.items = b->d_items;
-                ba.nitems = b->nitems;
-                ba.counter = b->d_counter;
-                er = launch_batch_solve(ba, smem, nsm, s);
+                ba.items = b->d_items + koff[q];
+                ba.nitems = kcnt[q];
+                ba.counter = b->d_counter + q;
+                const int prio = q == kBatchBlock ? std::min(c0->prio_lo, c0->prio_hi + 1) : c0->prio_lo;
+                if (er == cudaSuccess)
+                    er = launch_batch_solve(ba, q, smem[q], std::min(nsm, kcnt[q]), prio, qs);
+                if (qs != s) {
+                    if (er == cudaSuccess) er = cudaEventRecord(b->kjoin[side], qs);
+                    ++side;
+                }
             }
+            for (int k = 0; k < side && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->kjoin[k], 0);
             for (int k = 0; k < n && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->inst[k]->join_ev, 0);
             cudaGraph_t endg = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(s, &endg);
@@ -1962,6 +2017,12 @@ tsf_status tsf_batch_synchronize(tsf_batch* b) {
     return TSF_OK;
 }
 
+tsf_status tsf_batch_persistent_launches(const tsf_batch* b, int* out) {
+    if (!b || !out) return TSF_E_ARG;
+    *out = b->graph_valid && b->persistent ? b->nlaunch : 0;
+    return TSF_OK;
+}
+
 tsf_status tsf_batch_get_stats(tsf_batch* b, tsf_stats* out) {
     if (!b || !out) return TSF_E_ARG;
     memset(out, 0, sizeof *out);
@@ -2007,6 +2068,11 @@ void tsf_batch_destroy(tsf_batch* b) {
     batch_drop_graph(b, true);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_counter) cudaFree(b->d_counter);
+    for (int k = 0; k < kBatchKinds - 1; ++k) {
+        if (b->kside[k]) cudaStreamDestroy(b->kside[k]);
+        if (b->kjoin[k]) cudaEventDestroy(b->kjoin[k]);
+    }
+    if (b->kfork) cudaEventDestroy(b->kfork);
     for (tsf_ctx* c : b->inst) tsf_destroy(c);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -125,8 +125,8 @@ def test_batch_errors():
 def test_uneven_32_instance_workload_every_instance(persistent):
     """The 32-instance uneven workload at full size (200M micro DoFs), mixed
     precision by pipelined elimination, one graph per batch step -- one
-    branch per instance, or (persistent) one work-queue launch for all micro
-    solves: every instance against the oracle after 3 steps (the extrapolated
+    branch per instance, or (persistent) work-queue launches, one per solve
+    path, for all micro solves: every instance against the oracle after 3 steps (the extrapolated
     warm start runs), GPU at tolerance 1e-11, oracle at 1e-12; discrete mass
     balance on every instance."""
     T = _T()
@@ -159,19 +159,24 @@ def test_uneven_32_instance_workload_every_instance(persistent):
 
 
 def test_persistent_batch_equals_single_contexts_bitwise():
-    """One persistent launch with a work queue solves the micro problems of all
-    instances, small ones several to a block on their own groups of warps: the
-    results equal those of single contexts stepping with the same column-strip
-    variant (tiling 5) bit for bit."""
+    """Persistent launches with work queues, one per solve path, solve the
+    micro problems of all instances side by side: the 49x49-node micro
+    problems one to a block, the small ones several to a block on their own
+    groups of warps.  The results equal those of single contexts stepping with
+    the same column-strip variant (tiling 5) bit for bit."""
     T = _T()
-    specs = SPECS + [(16, 6, 2, 0.9, (1.0, 0.0, 0.1)), (33, 2, 1, 1.1, (1.0, 0.0, 1.0))]
+    specs = SPECS + [(16, 6, 2, 0.9, (1.0, 0.0, 0.1)), (33, 2, 1, 1.1, (1.0, 0.0, 1.0)),
+                     (48, 1, 1, 1.0, (1.0, 0.0, 1.0))]
     opts = dict(TIGHT, coupling=T.TSF_COUPLING_ELIMINATION)
     B = T.TwoScaleBatch([(s[0], s[1]) for s in specs], precision=1, persistent=True, **opts)
     for k, s in enumerate(specs):
         _configure(B[k], k, s)
+    assert B.persistent_launches() == 0
     B.step(0.01, 4)
     B.synchronize()
     assert B.stats()["status"] == 0
+    # the whole-block path and at least one path of smaller teams
+    assert 2 <= B.persistent_launches() <= 3
     for k, s in enumerate(specs):
         P = T.TwoScale(s[0], s[1], precision=1, tiling=5, **opts)
         _configure(P, k, s)
