@@ -386,8 +386,8 @@ void tsf_batch_destroy(tsf_batch *b);
  * calls on a device share the array (it keeps the last call's contents; the
  * call clears what must start from zero): calls that overlap on the GPU, e.g.
  * on two streams at once, race and must not be issued.  The call blocks: it
- * reads the solve's status back and waits for cuda_stream before returning,
- * so it must not be issued on a stream that is being captured.  Errors: TSF_E_ARG (NM outside 1..TSF_NOALLOC_MAX_NM, bad
+ * reads the solve's status back and waits for cuda_stream before returning.
+ * Errors: TSF_E_ARG (NM outside 1..TSF_NOALLOC_MAX_NM, bad
  * scalar, NULL array), TSF_E_CUDA (runtime failure), TSF_E_NOT_CONVERGED or
  * TSF_E_NAN from the solve; there is no context, so tsf_last_error does not
  * apply.

@@ -10,8 +10,7 @@
 // in a fixed file-scope device array instead of a workspace.  The array is
 // part of the loaded library, so every GPU that loads the library holds it
 // (about 0.8 MB) until the process exits.  The call reads its status back and
-// waits for the stream, so it must not be issued on a stream that is being
-// captured into a CUDA graph.
+// waits for the stream before it returns.
 #include "tsfem.h"
 #include "tsf_internal.cuh"
 
