@@ -776,7 +776,7 @@ def run_c4(args):
     each with its autotuned micro-solve variant; one batch step is one CUDA
     graph launch with one branch per problem (the library's default batch
     mode).  Beside it, over the same steps: the persistent batch mode (the
-    micro solves of all problems in work-queue launches, one per solve path, eliminated
+    micro solves of all problems in work-queue launches, one per class of micro mesh, eliminated
     coupling only) and the same problems stepped one after another (each
     problem through all the steps, its own step graph)."""
     import torch
@@ -849,9 +849,9 @@ def run_c4(args):
         B3.synchronize()
         B3.reset_stats()
         pm = timed(lambda: B3.step(dt, K))
-        nq = B3.persistent_launches()  # micro-solve launches a step, one per solve path
+        nq = B3.persistent_launches()  # micro-solve launches a step, one per class of micro mesh
         persistent = {"ms_per_step": pm / K, "dof_cg_iters_per_step": B3.stats()["dof_cg_iters"] / K,
-                      "tiling": 5, "micro_launches_per_step": nq,
+                      "tilings": [B3[k].stats()["tiling"] for k in range(len(ws))], "micro_launches_per_step": nq,
                       "gpu_launches": (3 * len(ws) + nq) * K + len(ws)}
         B3.close()
 

@@ -331,22 +331,24 @@ tsf_status tsf_batch_instance(tsf_batch *b, int inst, tsf_ctx **out);
 tsf_status tsf_batch_step(tsf_batch *b, double dt, int nsteps);
 
 /* Persistent batch steps (on = 1; default 0).  Each batch step is then ONE
- * CUDA graph launch whose micro solves, for every micro problem of every
- * instance, run in persistent kernel launches (at most one block per SM), one
- * launch per solve path, side by side: micro meshes whose column strips fill
- * a block of 16 warps, and smaller ones, several a block on their own groups
- * of warps, with or without bulk-copy staging.  Each launch takes work items
- * from its own global atomic queue ordered largest micro mesh first.  Beside
- * them, every instance's macro solve runs on its own branch of the graph.  Requires mixed precision and coupling by elimination
- * without volume or Robin sources for every instance (tsf_batch_step then
- * returns TSF_E_ARG otherwise), micro meshes of at most 49 cells per side and
- * at most 64 instances, and switches every instance to the column-strip
- * variant of the batch kernel (tiling 5).  Errors: TSF_E_ARG. */
+ * CUDA graph launch: per instance, on its own branch, the macro prologue and
+ * the macro solve; after the prologues, the micro solves of every micro
+ * problem of every instance in persistent kernel launches, one per class of
+ * micro mesh (strip height, threads a block, bulk-copy staging), side by side,
+ * each of as many blocks as fit the GPU at once.  Every block solves one micro
+ * problem at a time and takes work items from its class's global atomic
+ * queue, ordered largest micro mesh first.  Requires mixed precision and
+ * coupling by elimination without volume or Robin sources for every instance
+ * (tsf_batch_step then returns TSF_E_ARG otherwise), micro meshes of at most
+ * 49 cells per side, at most 64 instances and at most 8 classes, and switches
+ * every instance to the column-strip variant whose arithmetic the batch
+ * kernel runs: strips of 3 rows (tiling 4) up to 32 micro cells per side, of 5
+ * rows (tiling 5) beyond.  Errors: TSF_E_ARG. */
 tsf_status tsf_batch_set_persistent(tsf_batch *b, int on);
 
-/* *out = the persistent micro-solve launches of one batch step (1..3, one per
- * solve path the instances need), as captured by the last persistent batch
- * step; 0 if no persistent batch step has been captured.
+/* *out = the persistent micro-solve launches of one batch step (1..8, one per
+ * class of micro mesh), as captured by the last persistent batch step; 0 if
+ * no persistent batch step has been captured.
  * Errors: TSF_E_ARG (NULL pointer). */
 tsf_status tsf_batch_persistent_launches(const tsf_batch *b, int *out);
 tsf_status tsf_batch_synchronize(tsf_batch *b);

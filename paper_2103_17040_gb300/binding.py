@@ -691,7 +691,7 @@ class TwoScaleBatch:
     ``specs``: sequence of ``(Nm, NM)`` or ``(Nm, NM, bc)``.  ``batch[i]`` is a
     :class:`TwoScale` view of instance i (configure and read it as usual; it
     is valid while the batch lives).  ``persistent=True``: the micro solves of
-    all instances run in persistent launches (one per solve path) fed by work
+    all instances run in persistent launches (one per class of micro mesh) fed by work
     queues (tsf_batch_set_persistent).
     """
 

@@ -23,7 +23,6 @@ using namespace tsf;
 
 namespace {
 
-constexpr int kPersistentTiling = 5;  // the short strips of R = kBatchR rows, as in k_micro_batch
 constexpr int kMaxNm = 128;    // micro cells per side (up to 64: one thread block per micro problem;
                                // beyond: one thread-block cluster per micro problem)
 constexpr int kMaxNM = 1023;   // macro cells per side
@@ -1585,19 +1584,19 @@ struct tsf_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int use_graph = 1;
-    // persistent mode: per step one launch of k_micro_batch for each solve
-    // path the instances need, for the micro solves of all instances (the
-    // device table of the work items, the queue heads)
+    // persistent mode: per step one launch of k_micro_batch for each class
+    // of micro mesh, for the micro solves of all instances (the device table
+    // of the work items, the queue heads)
     int persistent = 0;
     int4* d_items = nullptr;
-    int* d_counter = nullptr;          // [kBatchKinds] queue heads
+    int* d_counter = nullptr;          // [kBatchMaxClasses] queue heads
     size_t cap_items = 0;
     int nitems = 0;
-    // the solve paths' launches run side by side: streams and events of the
+    // the classes' launches run side by side: streams and events of the
     // fork and the join (the first path runs on the batch's stream)
-    cudaStream_t kside[kBatchKinds - 1] = {};
+    cudaStream_t kside[kBatchMaxClasses - 1] = {};
     cudaEvent_t kfork = nullptr;
-    cudaEvent_t kjoin[kBatchKinds - 1] = {};
+    cudaEvent_t kjoin[kBatchMaxClasses - 1] = {};
     int nlaunch = 0;                   // persistent micro-solve launches of the captured step
     cudaGraph_t graph = nullptr;       // one batch step
     cudaGraphExec_t gexec = nullptr;
@@ -1696,6 +1695,23 @@ static tsf_status batch_capture_one(tsf_batch* b, double dt, bool commit, cudaGr
     return TSF_OK;
 }
 
+// The variant whose arithmetic the persistent batch kernel runs for an
+// instance: column strips of 3 rows (tiling 4), or of 5 (tiling 5) where strips
+// of 3 need more than 384 threads.
+static int persistent_tiling(const tsf_ctx* c) { return batch_strip_R(c->n1) == 3 ? 4 : 5; }
+
+// Every micro solve of an instance in a persistent batch (its head solves
+// and set-up solves included) runs that variant.
+static void use_persistent_tiling(tsf_ctx* c) {
+    const int t = persistent_tiling(c);
+    if (c->opt.tiling != t) {
+        c->opt.tiling = t;
+        c->tiling = -1;
+        c->phi_valid = false;
+        invalidate_graph(c);
+    }
+}
+
 static tsf_status batch_capture(tsf_batch* b, double dt) {
     batch_drop_graph(b, true);
     tsf_status st = batch_capture_one(b, dt, true, b->graph, b->gexec);
@@ -1709,12 +1725,16 @@ static tsf_status batch_capture(tsf_batch* b, double dt) {
 }
 
 // The persistent batch step (pipelined elimination of every instance):
-//   k_elim_start of every instance (the macro state the next w belongs to),
-//   then side by side: the persistent launches of k_micro_batch, one per solve
-//   path, which solve the next w of every micro problem of every instance
-//   from work queues ordered largest micro problem first, and per instance
-//   its macro branch (macro prologue, macro solve, commit) on that
-//   instance's side stream.
+//   per instance, on its side stream: k_elim_start (the macro state the next w
+//   belongs to), the macro prologue, then the macro solve (high priority) and,
+//   in a call's last step, the commit;
+//   once every prologue is done: the persistent launches of k_micro_batch,
+//   one per class of micro mesh (strip height, threads, staging), side by
+//   side at the lowest priority, which solve the next w of every micro problem
+//   of every instance from work queues ordered largest micro problem first.
+//   The micro launches wait for the prologues so that the macro solves, ready
+//   at the same time or earlier and of higher priority, take their SMs first:
+//   the persistent blocks leave an SM only when their queue is drained.
 static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
     batch_drop_graph(b, true);
     const int n = (int)b->inst.size();
@@ -1727,65 +1747,91 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
         args[k] = with_fp32_tols(w_solve_args(c, dt));
         order[k] = k;
     }
-    // largest micro problems first (work per item grows with n1^2), then the
-    // instances with more micro problems
+    // largest micro problems first (work per problem grows with n1^2), then
+    // the instances with more micro problems
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         const tsf_ctx *cx = b->inst[x], *cy = b->inst[y];
         return cx->nm != cy->nm ? cx->nm > cy->nm : cx->nM > cy->nM;
     });
-    // the items of each solve path, in queue order
-    std::vector<int4> kitems[kBatchKinds];
-    size_t smem[kBatchKinds] = {0, 0, 0};
-    std::vector<int> kind(n), teams(n);
-    long left[kBatchKinds] = {0, 0, 0};  // micro problems of each path
-    for (int k = 0; k < n; ++k) {
-        tsf_ctx* c = b->inst[k];
-        const int tw = batch_team_warps(c->n1);
-        if (tw > kBatchWarps)
-            return bfail(b, TSF_E_ARG, "instance %d: %d micro cells per side are too many for the persistent batch",
-                         k, c->Nm);
-        teams[k] = std::min(kBatchWarps / tw, 15);
-        // the bulk-copy staging where the teams' shared memory still fits a block
-        const bool pref = teams[k] * batch_team_smem_pref(c->n1, true) + kBatchStaticSmem <= (size_t)c->smem_optin;
-        kind[k] = tw == kBatchWarps ? kBatchBlock : (pref ? kBatchGroupStaged : kBatchGroup);
-        smem[kind[k]] = std::max(smem[kind[k]], (size_t)teams[k] * batch_team_smem_pref(c->n1, pref));
-        left[kind[k]] += c->nM;
-    }
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->inst[0]->device);
+    // the classes, in the order of their largest micro mesh
+    struct Class {
+        int R, threads;
+        bool pref;
+        size_t smem;
+        long problems;
+        int grid;
+        std::vector<int4> items;
+    };
+    std::vector<Class> cls;
+    std::vector<int> cof(n);
+    tsf_ctx* c0 = b->inst[0];
     for (int k : order) {
         tsf_ctx* c = b->inst[k];
-        const int q = kind[k];
-        // a whole-block team takes one problem an item.  Smaller teams take
-        // kBatchChunk problems each an item (the block waits for its slowest
-        // team once per item, not once per problem), one each in the last
-        // wave of the path's queue, where a long item would leave SMs idle.
+        const int R = batch_strip_R(c->n1);
+        if (!R)
+            return bfail(b, TSF_E_ARG, "instance %d: %d micro cells per side are too many for the persistent batch",
+                         k, c->Nm);
+        const int T = batch_threads(c->n1, R);
+        const bool pref = batch_stages(c->n1, R);
+        int q = 0;
+        while (q < (int)cls.size() && !(cls[q].R == R && cls[q].threads == T && cls[q].pref == pref)) ++q;
+        if (q == (int)cls.size()) {
+            if (q == kBatchMaxClasses)
+                return bfail(b, TSF_E_ARG, "the persistent batch takes micro meshes of at most %d classes",
+                             kBatchMaxClasses);
+            cls.push_back(Class{R, T, pref, 0, 0, 0, {}});
+        }
+        cls[q].smem = std::max(cls[q].smem, batch_smem(c->n1, R, pref));
+        cls[q].problems += c->nM;
+        cof[k] = q;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c0->device);
+    cudaError_t e = cudaSuccess;
+    // each kernel's shared-memory limit: the largest of the classes it serves
+    for (const Class& q : cls) {
+        if (q.smem + kBatchStaticSmem > (size_t)c0->smem_optin)
+            return bfail(b, TSF_E_ARG, "persistent batch: shared memory %zu > %d", q.smem, c0->smem_optin);
+        size_t most = 0;
+        for (const Class& o : cls)
+            if (o.R == q.R && o.pref == q.pref) most = std::max(most, o.smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_micro_batch_entry(q.R, q.pref), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)most);
+    }
+    for (Class& q : cls) {
+        int per_sm = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_micro_batch_entry(q.R, q.pref), q.threads,
+                                                              q.smem);
+        q.grid = (int)std::min<long>((long)std::max(per_sm, 1) * nsm, q.problems);
+    }
+    // the items: kBatchChunk micro problems each, one each in the last two
+    // waves of the class's queue, where long items would leave SMs idle
+    for (int k : order) {
+        tsf_ctx* c = b->inst[k];
+        Class& q = cls[cof[k]];
         for (int i = 0; i < c->nM;) {
-            const int chunk = q == kBatchBlock || left[q] <= (long)nsm * teams[k] * kBatchChunk ? 1 : kBatchChunk;
-            const int cnt = std::min(teams[k] * chunk, c->nM - i);
-            kitems[q].push_back(make_int4(k, i, cnt, q == kBatchBlock ? kBatchWarps : batch_team_warps(c->n1)));
+            const int chunk = q.problems > 2L * q.grid * kBatchChunk ? kBatchChunk : 1;
+            const int cnt = std::min(chunk, c->nM - i);
+            q.items.push_back(make_int4(k, i, cnt, 0));
             i += cnt;
-            left[q] -= cnt;
+            q.problems -= cnt;
         }
     }
     std::vector<int4> items;
-    int koff[kBatchKinds], kcnt[kBatchKinds];
-    for (int q = 0; q < kBatchKinds; ++q) {
-        koff[q] = (int)items.size();
-        kcnt[q] = (int)kitems[q].size();
-        items.insert(items.end(), kitems[q].begin(), kitems[q].end());
-        if (smem[q] + kBatchStaticSmem > (size_t)b->inst[0]->smem_optin)
-            return bfail(b, TSF_E_ARG, "persistent batch: shared memory %zu > %d", smem[q], b->inst[0]->smem_optin);
+    std::vector<int> koff;
+    for (const Class& q : cls) {
+        koff.push_back((int)items.size());
+        items.insert(items.end(), q.items.begin(), q.items.end());
     }
-    tsf_ctx* c0 = b->inst[0];
-    cudaError_t e = cudaSuccess;
-    if (b->cap_items < items.size()) {
+    if (e == cudaSuccess && b->cap_items < items.size()) {
         if (b->d_items) cudaFree(b->d_items);
         e = cudaMalloc((void**)&b->d_items, items.size() * sizeof(int4));
         b->cap_items = e == cudaSuccess ? items.size() : 0;
     }
-    if (e == cudaSuccess && !b->d_counter) e = cudaMalloc((void**)&b->d_counter, kBatchKinds * sizeof(int));
-    for (int k = 0; k < kBatchKinds - 1 && e == cudaSuccess; ++k) {
+    if (e == cudaSuccess && !b->d_counter) e = cudaMalloc((void**)&b->d_counter, kBatchMaxClasses * sizeof(int));
+    for (int k = 0; k < kBatchMaxClasses - 1 && e == cudaSuccess; ++k) {
         if (!b->kside[k]) e = cudaStreamCreateWithFlags(&b->kside[k], cudaStreamNonBlocking);
         if (e == cudaSuccess && !b->kjoin[k]) e = cudaEventCreateWithFlags(&b->kjoin[k], cudaEventDisableTiming);
     }
@@ -1793,18 +1839,13 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    for (int q = 0; q < kBatchKinds && e == cudaSuccess; ++q)
-        if (kcnt[q])
-            e = cudaFuncSetAttribute(k_micro_batch_entry(q), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem[q]);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return bfail(b, e == cudaErrorMemoryAllocation ? TSF_E_OOM : TSF_E_CUDA, "persistent batch set-up: %s",
                      cudaGetErrorString(e));
     }
     b->nitems = (int)items.size();
-    b->nlaunch = 0;
-    for (int q = 0; q < kBatchKinds; ++q) b->nlaunch += kcnt[q] > 0;
+    b->nlaunch = (int)cls.size();
 
     cudaStream_t s = b->stream;
     // capture one batch step into G (with or without the commits of v)
@@ -1814,53 +1855,44 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
         tsf_status st = TSF_OK;
         er = cudaStreamBeginCaptureToGraph(s, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (er == cudaSuccess) {
-            for (int k = 0; k < n && er == cudaSuccess; ++k) er = launch_elim_start(elim_args(b->inst[k], dt), s);
-            if (er == cudaSuccess) er = cudaEventRecord(c0->fork_ev, s);
+            er = cudaEventRecord(c0->fork_ev, s);
             for (int k = 0; k < n && er == cudaSuccess; ++k) {
                 tsf_ctx* c = b->inst[k];
                 er = cudaStreamWaitEvent(c->side, c0->fork_ev, 0);
+                if (er == cudaSuccess) er = launch_elim_start(elim_args(c, dt), c->side);
                 if (er != cudaSuccess) break;
                 if ((st = enqueue_macro_prologue(c, dt, true, c->side))) {
                     er = cudaErrorUnknown;  // (the capture is still ended below)
                     break;
                 }
+                er = cudaEventRecord(c->pre_ev, c->side);
                 cudaGraphConditionalHandle none{};
                 MacroArgs mg = macro_args(c, dt, false, none);
                 mg.gam = c->gam_eff;
                 mg.rho = c->rho_eff;
                 mg.coupling_tol = HUGE_VAL;
                 mg.coupling_maxit = 1;
-                er = launch_macro_solve(mg, c->side, c->prio_hi);
+                if (er == cudaSuccess) er = launch_macro_solve(mg, c->side, c->prio_hi);
                 if (er == cudaSuccess && commit) er = launch_elim_commit(elim_args(c, dt), c->side);
                 if (er == cudaSuccess) er = cudaEventRecord(c->join_ev, c->side);
             }
-            if (er == cudaSuccess) er = cudaMemsetAsync(b->d_counter, 0, kBatchKinds * sizeof(int), s);
+            for (int k = 0; k < n && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->inst[k]->pre_ev, 0);
+            if (er == cudaSuccess) er = cudaMemsetAsync(b->d_counter, 0, cls.size() * sizeof(int), s);
             if (er == cudaSuccess) er = cudaEventRecord(b->kfork, s);
-            // the paths side by side, the whole-block path (the largest micro
-            // problems) first and at a higher priority: the blocks of the
-            // other paths take the SMs that its blocks leave
-            int side = 0;
-            for (int q = 0; q < kBatchKinds && er == cudaSuccess; ++q) {
-                if (!kcnt[q]) continue;
-                cudaStream_t qs = s;
-                if (q != kBatchBlock) {
-                    qs = b->kside[side];
-                    er = cudaStreamWaitEvent(qs, b->kfork, 0);
-                }
+            for (int q = 0; q < (int)cls.size() && er == cudaSuccess; ++q) {
+                cudaStream_t qs = q == 0 ? s : b->kside[q - 1];
+                if (q) er = cudaStreamWaitEvent(qs, b->kfork, 0);
                 BatchSolveArgs ba{};
                 for (int k = 0; k < n; ++k) ba.args[k] = args[k];
                 ba.items = b->d_items + koff[q];
-                ba.nitems = kcnt[q];
+                ba.nitems = (int)cls[q].items.size();
                 ba.counter = b->d_counter + q;
-                const int prio = q == kBatchBlock ? std::min(c0->prio_lo, c0->prio_hi + 1) : c0->prio_lo;
                 if (er == cudaSuccess)
-                    er = launch_batch_solve(ba, q, smem[q], std::min(nsm, kcnt[q]), prio, qs);
-                if (qs != s) {
-                    if (er == cudaSuccess) er = cudaEventRecord(b->kjoin[side], qs);
-                    ++side;
-                }
+                    er = launch_batch_solve(ba, cls[q].R, cls[q].pref, cls[q].threads, cls[q].smem, cls[q].grid,
+                                            c0->prio_lo, qs);
+                if (er == cudaSuccess && q) er = cudaEventRecord(b->kjoin[q - 1], qs);
             }
-            for (int k = 0; k < side && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->kjoin[k], 0);
+            for (int q = 1; q < (int)cls.size() && er == cudaSuccess; ++q) er = cudaStreamWaitEvent(s, b->kjoin[q - 1], 0);
             for (int k = 0; k < n && er == cudaSuccess; ++k) er = cudaStreamWaitEvent(s, b->inst[k]->join_ev, 0);
             cudaGraph_t endg = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(s, &endg);
@@ -1896,18 +1928,8 @@ tsf_status tsf_batch_set_persistent(tsf_batch* b, int on) {
     if (on != 0 && on != 1) return bfail(b, TSF_E_ARG, "on must be 0 or 1");
     if (b->persistent != on) batch_drop_graph(b, true);
     b->persistent = on;
-    if (on) {
-        // every instance solves its micro problems with the column strips of
-        // the batch kernel (the head solves and the set-up solves included)
-        for (tsf_ctx* c : b->inst) {
-            if (c->opt.tiling != kPersistentTiling) {
-                c->opt.tiling = kPersistentTiling;
-                c->tiling = -1;
-                c->phi_valid = false;
-                invalidate_graph(c);
-            }
-        }
-    }
+    if (on)
+        for (tsf_ctx* c : b->inst) use_persistent_tiling(c);
     return TSF_OK;
 }
 
@@ -1965,6 +1987,8 @@ tsf_status tsf_batch_step(tsf_batch* b, double dt, int nsteps) {
             return bfail(b, TSF_E_STATE, "instance %d: set meshes, deformation and state first", i);
     }
     if (nsteps == 0) return TSF_OK;
+    if (b->persistent)
+        for (tsf_ctx* c : b->inst) use_persistent_tiling(c);  // (after a change of micro mesh)
     for (int i = 0; i < n; ++i) {
         tsf_ctx* c = b->inst[i];
         tsf_status st = prepare_step(c, dt);
@@ -1977,7 +2001,7 @@ tsf_status tsf_batch_step(tsf_batch* b, double dt, int nsteps) {
     if (b->persistent) {
         for (int i = 0; i < n; ++i) {
             tsf_ctx* c = b->inst[i];
-            if (c->opt.precision != TSF_MIXED || !pipelined(c) || c->tiling != kPersistentTiling)
+            if (c->opt.precision != TSF_MIXED || !pipelined(c) || c->tiling != persistent_tiling(c))
                 return bfail(b, TSF_E_ARG, "instance %d: the persistent batch needs mixed precision and the pipelined "
                                            "elimination (coupling = elimination, no volume or Robin sources)", i);
         }
@@ -2068,7 +2092,7 @@ void tsf_batch_destroy(tsf_batch* b) {
     batch_drop_graph(b, true);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_counter) cudaFree(b->d_counter);
-    for (int k = 0; k < kBatchKinds - 1; ++k) {
+    for (int k = 0; k < kBatchMaxClasses - 1; ++k) {
         if (b->kside[k]) cudaStreamDestroy(b->kside[k]);
         if (b->kjoin[k]) cudaEventDestroy(b->kjoin[k]);
     }

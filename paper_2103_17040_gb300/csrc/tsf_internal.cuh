@@ -349,32 +349,31 @@ bool strip_fits(int n1, int R, int smem_optin);
 cudaError_t launch_cluster_solve(const MicroArgs& a, int c, cudaStream_t s);
 bool cluster_fits(int c, int n1, int smem_optin);
 // Persistent micro solve of a batch of two-scale problems (pipelined
-// elimination, column strips of kBatchR rows): per solve path one launch of
-// at most one block per SM; every block takes work items from that path's
+// elimination, column strips of R = 3 rows, or 5 where strips of 3 need more
+// than 384 threads): per class of micro mesh (strip height, threads, staging)
+// one launch of as many blocks as fit the GPU at once, each block one team of
+// the column-strip solve; every block takes work items from its class's
 // atomic queue, largest micro problems first.  An item is `count`
-// consecutive micro problems of one problem instance, taken one at a time by
-// the block's teams of `warps` warps.  The solve paths: one team of
-// kBatchWarps warps a block, or several smaller teams a block, without or
-// with the bulk-copy staging.
-constexpr int kBatchR = 5;
-constexpr int kBatchWarps = 16;            // warps per block
-constexpr int kBatchChunk = 4;             // micro problems per team and work item (smaller teams)
-constexpr int kBatchBlock = 0, kBatchGroup = 1, kBatchGroupStaged = 2, kBatchKinds = 3;
+// consecutive micro problems of one problem instance.
+constexpr int kBatchChunk = 4;             // micro problems per work item, before the last waves
 constexpr size_t kBatchStaticSmem = 1024;  // bound on k_micro_batch's static shared memory
 constexpr int kBatchMaxProblems = 64;      // problem instances of one persistent batch
+constexpr int kBatchMaxClasses = 8;        // launches (classes of micro mesh) of one persistent step
 struct BatchSolveArgs {
     // per-instance arguments (pipe = 1), in the kernel's parameter space: the
     // solves read them through the constant cache, as read-only data
     MicroArgs args[kBatchMaxProblems];
-    const int4* items;                     // [nitems] (instance, first problem, count, warps per team)
+    const int4* items;                     // [nitems] (instance, first problem, count, 0)
     int nitems;
     int* counter;                          // queue head, zero before the launch
 };
-int batch_team_warps(int n1);              // warps of the team that solves one micro problem of n1^2 nodes
-size_t batch_team_smem_pref(int n1, bool pref);  // shared memory of one team (with the staging: pref)
-cudaError_t launch_batch_solve(const BatchSolveArgs& b, int kind, size_t smem_bytes, int blocks, int priority,
-                               cudaStream_t s);
-const void* k_micro_batch_entry(int kind); // the kernel of a solve path, for its shared-memory attribute
+int batch_strip_R(int n1);                 // strip height for micro meshes of n1^2 nodes (3, 5; 0: too large)
+int batch_threads(int n1, int R);          // threads of the block that solves one micro problem
+bool batch_stages(int n1, int R);          // with the bulk-copy staging (as the single-problem kernel)
+size_t batch_smem(int n1, int R, bool pref);  // dynamic shared memory of that block
+cudaError_t launch_batch_solve(const BatchSolveArgs& b, int R, bool pref, int threads, size_t smem_bytes, int blocks,
+                               int priority, cudaStream_t s);
+const void* k_micro_batch_entry(int R, bool pref);  // the kernel, for its attributes and occupancy
 // one-warp variants (R = 3, 5)
 cudaError_t launch_warp_solve(const MicroArgs& a, int R, cudaStream_t s);
 bool warp_fits(int n1, int R, int smem_optin);

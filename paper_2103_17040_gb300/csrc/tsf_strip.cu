@@ -492,8 +492,8 @@ struct BlockTeam {
     __device__ void sum2(float& x, float& y, float2* buf) const { block_sum2(x, y, buf); }
     __device__ void sum2_max(float& x, float& y, float& m, float4* buf) const { block_sum2_max(x, y, m, buf); }
 };
-// A whole block on a given micro problem (the persistent batch kernel, when
-// one team fills the block): BlockTeam's barriers and sums.
+// A whole block on a given micro problem (the persistent batch kernel):
+// BlockTeam's barriers and sums.
 struct BlockTeamAt {
     static constexpr bool kWarp = false;
     int prob;
@@ -518,50 +518,6 @@ struct WarpTeam {
     __device__ void sum2_max(float& x, float& y, float& m, float4*) const {
         sum2(x, y, nullptr);
         m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
-    }
-};
-// A group of nw consecutive warps of a block (the persistent batch kernel runs
-// several micro problems side by side in one block): named barrier bar (1..15)
-// over its nw * 32 threads, reductions through its own partial buffers.
-struct GroupTeam {
-    static constexpr bool kWarp = false;
-    int tid0, nw, bar, slot_, prob;
-    __device__ int thread() const { return (int)threadIdx.x - tid0; }
-    __device__ int size() const { return nw * 32; }
-    __device__ int slot() const { return slot_; }
-    __device__ int problem() const { return prob; }
-    __device__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nw * 32) : "memory"); }
-    __device__ bool all(bool ok) const {  // (also a barrier of the group)
-        unsigned r;
-        asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
-                     : "=r"(r)
-                     : "r"((unsigned)ok), "r"(bar), "r"(nw * 32)
-                     : "memory");
-        return r != 0;
-    }
-    __device__ void sum2(float& x, float& y, float2* buf) const {  // (nw <= 16)
-        group_sum2_split(x, y, buf, thread() >> 5, nw, [this] { sync(); });
-    }
-    __device__ void sum2_max(float& x, float& y, float& m, float4* buf) const {
-        const int lane = threadIdx.x & 31, warp = thread() >> 5;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_xor_sync(0xffffffffu, x, o);
-            y += __shfl_xor_sync(0xffffffffu, y, o);
-        }
-        const float mb = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
-        if (lane == 0) buf[warp] = make_float4(x, y, mb, 0.f);
-        sync();
-        float sx = 0.f, sy = 0.f, mx = 0.f;
-        for (int k = 0; k < nw; ++k) {
-            const float4 t = buf[k];
-            sx += t.x;
-            sy += t.y;
-            mx = fmaxf(mx, t.z);
-        }
-        x = sx;
-        y = sy;
-        m = mx;
     }
 };
 
@@ -1160,77 +1116,53 @@ cudaError_t launch_warp_solve(const MicroArgs& a, int R, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent batch kernel.  Each block loops: take the next item from the
-// queue, read that problem instance's arguments from the kernel parameters,
-// let its teams of warps solve the item's micro problems with the
-// column-strip body (team t on named barrier 1 + t), and wait for every team
-// before the next item.
+// Persistent batch kernel.  Each block is one team of the column-strip solve
+// (R rows a thread, the block's threads those of one micro problem) and
+// loops: take the next item from its queue, read that problem instance's
+// arguments from the kernel parameters, solve the item's micro problems one
+// after another.  The launch bounds are those of k_micro_strip<R>, so the
+// solve body gets the same register allocation.
 // ---------------------------------------------------------------------------
-int batch_team_warps(int n1) { return (n1 * strip_rows(n1, kBatchR) + 31) / 32; }
-// shared memory of one team, with (pref) or without the bulk-copy staging
-size_t batch_team_smem_pref(int n1, bool pref) { return strip_smem_bytes(n1, kBatchR, false, true, pref); }
-// teams of w warps in a block of kBatchWarps (named barriers 1..15)
-__host__ __device__ inline int batch_teams(int w) { return kBatchWarps / w < 15 ? kBatchWarps / w : 15; }
+int batch_strip_R(int n1) {
+    if (strip_threads(n1, 3) <= StripMaxThreads<3>::value) return 3;
+    if (strip_threads(n1, 5) <= StripMaxThreads<5>::value) return 5;
+    return 0;
+}
+int batch_threads(int n1, int R) { return strip_threads(n1, R); }
+bool batch_stages(int n1, int R) { return strip_stages(n1, R, true); }
+size_t batch_smem(int n1, int R, bool pref) { return strip_smem_bytes(n1, R, false, true, pref); }
 
-// One kernel per solve path (KIND: kBatchBlock, kBatchGroup, kBatchGroupStaged),
-// so that each path gets a register allocation of its own: with the three
-// paths compiled into one kernel, the whole-block path executed 18 % more
-// instructions than the same body as a kernel of its own.
-template <int KIND>
-__global__ void __launch_bounds__(32 * kBatchWarps, 1) k_micro_batch(const __grid_constant__ BatchSolveArgs b) {
+template <int R, bool PREF>
+__global__ void __launch_bounds__(StripMaxThreads<R>::value, StripMinBlocks<R>::value)
+    k_micro_batch(const __grid_constant__ BatchSolveArgs b) {
     __shared__ int4 s_item;
-    __shared__ int s_next;        // next micro problem of the item (index within it)
-    __shared__ int s_take[16];    // the problem each team takes next
     for (;;) {
         if (threadIdx.x == 0) {
             const int it = atomicAdd(b.counter, 1);
             s_item = it < b.nitems ? b.items[it] : make_int4(-1, 0, 0, 0);
-            s_next = 0;
         }
         __syncthreads();
         const int4 item = s_item;
         if (item.x < 0) break;  // queue drained (the same in every thread)
         const MicroArgs& a = b.args[item.x];
-        if (KIND == kBatchBlock) {
-            // one team fills the block: the item's problems one after another
-            for (int j = 0; j < item.z; ++j)
-                strip_body<kBatchR, false, true, false, BlockTeamAt>(a, BlockTeamAt{item.y + j});
-        } else {
-            // teams of w warps (item.w); each takes the item's problems one
-            // at a time until none is left, so a team that finishes early
-            // does not wait
-            const int w = item.w;
-            const int t = (threadIdx.x >> 5) / w;
-            if (t < batch_teams(w)) {
-                const int lead = t * w * 32, nthr = w * 32;
-                for (;;) {
-                    if ((int)threadIdx.x == lead) s_take[t] = atomicAdd(&s_next, 1);
-                    asm volatile("bar.sync %0, %1;" ::"r"(1 + t), "r"(nthr) : "memory");
-                    const int j = s_take[t];
-                    // (every thread of the team has read s_take[t] before the
-                    // leader writes it again: the barrier below comes first)
-                    asm volatile("bar.sync %0, %1;" ::"r"(1 + t), "r"(nthr) : "memory");
-                    if (j >= item.z) break;
-                    const GroupTeam tm{lead, w, 1 + t, t, item.y + j};
-                    strip_body<kBatchR, false, true, KIND == kBatchGroupStaged, GroupTeam>(a, tm);
-                }
-            }
-        }
-        __syncthreads();  // every team is done with the item
+        for (int j = 0; j < item.z; ++j) strip_body<R, false, true, PREF, BlockTeamAt>(a, BlockTeamAt{item.y + j});
+        __syncthreads();  // every thread has read s_item before it is written again
     }
 }
 
-static const void* const batch_kernels[kBatchKinds] = {(const void*)k_micro_batch<kBatchBlock>,
-                                                       (const void*)k_micro_batch<kBatchGroup>,
-                                                       (const void*)k_micro_batch<kBatchGroupStaged>};
+const void* k_micro_batch_entry(int R, bool pref) {
+    if (R == 3) return pref ? (const void*)k_micro_batch<3, true> : (const void*)k_micro_batch<3, false>;
+    if (R == 5) return pref ? (const void*)k_micro_batch<5, true> : (const void*)k_micro_batch<5, false>;
+    return nullptr;
+}
 
-const void* k_micro_batch_entry(int kind) { return batch_kernels[kind]; }
-
-cudaError_t launch_batch_solve(const BatchSolveArgs& b, int kind, size_t smem_bytes, int blocks, int priority,
-                               cudaStream_t s) {
+cudaError_t launch_batch_solve(const BatchSolveArgs& b, int R, bool pref, int threads, size_t smem_bytes, int blocks,
+                               int priority, cudaStream_t s) {
+    const void* fn = k_micro_batch_entry(R, pref);
+    if (!fn) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(32 * kBatchWarps);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -1238,12 +1170,8 @@ cudaError_t launch_batch_solve(const BatchSolveArgs& b, int kind, size_t smem_by
     at[0].val.priority = priority;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    switch (kind) {
-        case kBatchBlock: return cudaLaunchKernelEx(&cfg, k_micro_batch<kBatchBlock>, b);
-        case kBatchGroup: return cudaLaunchKernelEx(&cfg, k_micro_batch<kBatchGroup>, b);
-        case kBatchGroupStaged: return cudaLaunchKernelEx(&cfg, k_micro_batch<kBatchGroupStaged>, b);
-        default: return cudaErrorInvalidValue;
-    }
+    void* params[] = {const_cast<BatchSolveArgs*>(&b)};
+    return cudaLaunchKernelExC(&cfg, fn, params);
 }
 
 template <int R, bool SC>

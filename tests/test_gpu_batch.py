@@ -125,8 +125,8 @@ def test_batch_errors():
 def test_uneven_32_instance_workload_every_instance(persistent):
     """The 32-instance uneven workload at full size (200M micro DoFs), mixed
     precision by pipelined elimination, one graph per batch step -- one
-    branch per instance, or (persistent) work-queue launches, one per solve
-    path, for all micro solves: every instance against the oracle after 3 steps (the extrapolated
+    branch per instance, or (persistent) work-queue launches, one per class
+    of micro mesh, for all micro solves: every instance against the oracle after 3 steps (the extrapolated
     warm start runs), GPU at tolerance 1e-11, oracle at 1e-12; discrete mass
     balance on every instance."""
     T = _T()
@@ -148,7 +148,7 @@ def test_uneven_32_instance_workload_every_instance(persistent):
     for k, w in enumerate(ws):
         assert abs(_mass(B[k], w) - m0[k]) <= 1e-9 * abs(m0[k]), k
         if persistent:
-            assert B[k].stats()["tiling"] == 5
+            assert B[k].stats()["tiling"] == (4 if w.Nm <= 32 else 5)
         R = oracle.Problem(w.Nm, w.NM, w.bc, w.family, w.params, D=w.D, kappa=w.kappa, Du=w.Du)
         R.set_state(w.u0, None)
         R.step(w.dt, nsteps, cg_tol=1e-12, coupling_tol=1e-12, macro_tol=1e-13)
@@ -159,11 +159,12 @@ def test_uneven_32_instance_workload_every_instance(persistent):
 
 
 def test_persistent_batch_equals_single_contexts_bitwise():
-    """Persistent launches with work queues, one per solve path, solve the
-    micro problems of all instances side by side: the 49x49-node micro
-    problems one to a block, the small ones several to a block on their own
-    groups of warps.  The results equal those of single contexts stepping with
-    the same column-strip variant (tiling 5) bit for bit."""
+    """Persistent launches with work queues, one per class of micro mesh
+    (strip height, threads a block, staging), solve the micro problems of all
+    instances side by side, one block per micro problem at a time: strips of
+    3 rows up to 32 micro cells per side (tiling 4), of 5 beyond (tiling 5).
+    The results equal those of single contexts stepping with the same
+    column-strip variant bit for bit."""
     T = _T()
     specs = SPECS + [(16, 6, 2, 0.9, (1.0, 0.0, 0.1)), (33, 2, 1, 1.1, (1.0, 0.0, 1.0)),
                      (48, 1, 1, 1.0, (1.0, 0.0, 1.0))]
@@ -175,10 +176,13 @@ def test_persistent_batch_equals_single_contexts_bitwise():
     B.step(0.01, 4)
     B.synchronize()
     assert B.stats()["status"] == 0
-    # the whole-block path and at least one path of smaller teams
-    assert 2 <= B.persistent_launches() <= 3
+    # classes (R, threads): (3, 32) for 3..6 cells, (3, 128) for 16, (5, 256)
+    # for 33, (5, 512) for 48
+    assert B.persistent_launches() == 4
     for k, s in enumerate(specs):
-        P = T.TwoScale(s[0], s[1], precision=1, tiling=5, **opts)
+        t = B[k].stats()["tiling"]
+        assert t == (4 if s[0] <= 32 else 5), k
+        P = T.TwoScale(s[0], s[1], precision=1, tiling=t, **opts)
         _configure(P, k, s)
         P.step(0.01, 4)
         assert np.array_equal(P.u(), B[k].u()), k
