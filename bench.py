@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--macro-cells", type=int, default=None,
                     help="macro cells per side of a smaller case for profiling (c3 and t1; default: the full size)")
+    ap.add_argument("--problems", type=int, default=32,
+                    help="c4: the first N of the 32 problems (a smaller case for profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, e2e, cpu baseline")
     ap.add_argument("--iteration-log", type=int, default=0, metavar="N",
                     help="profiling aid: take N single steps of the workload (one micro-solve launch each after "
@@ -793,7 +795,7 @@ def run_c4(args):
     T.load_library()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ws = W.c4(seed=rank)
+    ws = W.c4(seed=rank)[:max(1, args.problems)]
     dt = ws[0].dt
     K, Wm = args.steps, args.warmup
 
