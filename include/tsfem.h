@@ -340,13 +340,13 @@ tsf_status tsf_batch_step(tsf_batch *b, double dt, int nsteps);
  * queue, ordered largest micro mesh first.  Requires mixed precision and
  * coupling by elimination without volume or Robin sources for every instance
  * (tsf_batch_step then returns TSF_E_ARG otherwise), micro meshes of at most
- * 49 cells per side, at most 64 instances and at most 8 classes, and switches
+ * 49 cells per side and at most 64 instances, and switches
  * every instance to the column-strip variant whose arithmetic the batch
  * kernel runs: strips of 3 rows (tiling 4) up to 32 micro cells per side, of 5
  * rows (tiling 5) beyond.  Errors: TSF_E_ARG. */
 tsf_status tsf_batch_set_persistent(tsf_batch *b, int on);
 
-/* *out = the persistent micro-solve launches of one batch step (1..8, one per
+/* *out = the persistent micro-solve launches of one batch step (one per
  * class of micro mesh), as captured by the last persistent batch step; 0 if
  * no persistent batch step has been captured.
  * Errors: TSF_E_ARG (NULL pointer). */

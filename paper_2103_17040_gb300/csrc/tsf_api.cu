@@ -1831,7 +1831,7 @@ static tsf_status batch_capture_persistent(tsf_batch* b, double dt) {
         b->cap_items = e == cudaSuccess ? items.size() : 0;
     }
     if (e == cudaSuccess && !b->d_counter) e = cudaMalloc((void**)&b->d_counter, kBatchMaxClasses * sizeof(int));
-    for (int k = 0; k < kBatchMaxClasses - 1 && e == cudaSuccess; ++k) {
+    for (int k = 0; k + 1 < (int)cls.size() && e == cudaSuccess; ++k) {  // (kept for later captures)
         if (!b->kside[k]) e = cudaStreamCreateWithFlags(&b->kside[k], cudaStreamNonBlocking);
         if (e == cudaSuccess && !b->kjoin[k]) e = cudaEventCreateWithFlags(&b->kjoin[k], cudaEventDisableTiming);
     }

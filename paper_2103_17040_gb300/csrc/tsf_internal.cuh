@@ -358,7 +358,7 @@ bool cluster_fits(int c, int n1, int smem_optin);
 constexpr int kBatchChunk = 4;             // micro problems per work item, before the last waves
 constexpr size_t kBatchStaticSmem = 1024;  // bound on k_micro_batch's static shared memory
 constexpr int kBatchMaxProblems = 64;      // problem instances of one persistent batch
-constexpr int kBatchMaxClasses = 8;        // launches (classes of micro mesh) of one persistent step
+constexpr int kBatchMaxClasses = 32;       // launches (classes of micro mesh) of one persistent step
 struct BatchSolveArgs {
     // per-instance arguments (pipe = 1), in the kernel's parameter space: the
     // solves read them through the constant cache, as read-only data

@@ -191,6 +191,31 @@ def test_persistent_batch_equals_single_contexts_bitwise():
     B.close()
 
 
+def test_persistent_batch_many_classes():
+    """Fourteen micro meshes of 2 to 47 cells per side, one macro cell each:
+    a class (one persistent launch) per block size, all side by side; every
+    instance bit for bit as a single context on the same variant."""
+    T = _T()
+    cells = [2, 5, 8, 11, 14, 17, 20, 23, 26, 29, 32, 35, 41, 47]
+    specs = [(Nm, 1, 1, 1.0, (1.0, 0.0, 1.0)) for Nm in cells]
+    opts = dict(TIGHT, coupling=T.TSF_COUPLING_ELIMINATION)
+    B = T.TwoScaleBatch([(s[0], s[1]) for s in specs], precision=1, persistent=True, **opts)
+    for k, s in enumerate(specs):
+        _configure(B[k], k, s)
+    B.step(0.01, 3)
+    B.synchronize()
+    assert B.stats()["status"] == 0
+    assert B.persistent_launches() > 8
+    for k, s in enumerate(specs):
+        P = T.TwoScale(s[0], s[1], precision=1, tiling=B[k].stats()["tiling"], **opts)
+        _configure(P, k, s)
+        P.step(0.01, 3)
+        assert np.array_equal(P.u(), B[k].u()), k
+        assert np.array_equal(P.v(), B[k].v()), k
+        P.close()
+    B.close()
+
+
 def test_persistent_batch_matches_oracle():
     T = _T()
     B = T.TwoScaleBatch([(s[0], s[1]) for s in SPECS], precision=1, coupling=T.TSF_COUPLING_ELIMINATION,
